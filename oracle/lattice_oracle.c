@@ -1,0 +1,673 @@
+/*
+ * lattice_oracle.c -- plain FP64 CPU oracle for the staggered-leapfrog evolution
+ * of two interacting scalar fields (phi, chi) on a periodic 3D lattice in an
+ * expanding FRW universe, after J. Sainio, "CUDAEASY - a GPU Accelerated
+ * Cosmological Lattice Program" (arXiv:0911.5692).
+ *
+ * TEST INFRASTRUCTURE. This is the slow, obviously-correct reference that the
+ * CUDA library is checked against. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load it. The product library neither links nor
+ * calls it, and the two share no source, header, table or helper. Every loop
+ * here is a direct transcription of one equation; nothing is fused or blocked.
+ * OpenMP only splits the outermost z loop; every sum is taken per z-plane and
+ * the planes are added in index order, so results do not depend on the thread
+ * count.
+ *
+ * Equations followed (all in program units, primes are d/dt_pr):
+ *   rescaling          Sec. II.B: f = A a^r phi, x_pr = B x, dt_pr = B a^s dt,
+ *                      s - 2r + 3 = 0; for a dominant term cpl/beta phi^beta the
+ *                      choice A = 1/phi0, B = sqrt(cpl) phi0^(beta/2-1),
+ *                      r = 6/(2+beta), s = 3(2-beta)/(2+beta).
+ *   potential          Sec. II.B: V_pr = (A^2/B^2) a^(2r-2s) V(f/(A a^r)).
+ *   field equation     Sec. II.B, eq. scalar-evo:
+ *                      f'' = a^(-2s-2) Lap f + (r(s-r+2) h^2 + r a''/a) f - dV_pr/df,
+ *                      h = a'/a. The printed coefficient r(s-r-2) does not follow
+ *                      from eq. fe under the rescaling; r(s-r+2) does (it is the
+ *                      one that vanishes in the conformal case r=1, s=-1).
+ *   scale factor       Sec. II.B, eq. scale:
+ *                      a'' = -(s+2) a'^2/a + (8piG/A^2) a^(-2s-2r-1)
+ *                            < sum_i |grad f_i|^2 / 3 + a^(2s+2) V_pr >.
+ *   leapfrog           Sec. II.B, eq. evo: fields and momenta stored half a step
+ *                      apart, kick then drift; a and a' are staggered the same
+ *                      way, and a'' at the field time uses the momentum average
+ *                      a'_{n+1/2} = (a'_n + a'_{n+1})/2, which makes the a' update
+ *                      an exactly solvable quadratic.
+ *   gradient average   Sec. II.B, divergence-theorem identity: on a periodic
+ *                      lattice <|grad f|^2> = -<f Lap f>; here it is evaluated
+ *                      from forward differences, the 7-point stencil's gradient.
+ *   Laplacian          Sec. II.C names the 7-point ("naive", LATTICEEASY) stencil.
+ *   initial conditions Sec. II.B, last paragraph: homogeneous values plus Gaussian
+ *                      vacuum fluctuations (DEFROST style), converted with
+ *                      f = A a^r phi, f' = (A/B) a^(r-s) phidot + r (a'/a) f, then
+ *                      fields advanced by dt/2.
+ *   energy, pressure   Sec. II.B, eq. rho-pres; residual curvature and w of Sec. III.
+ *   spectrum           Sec. IV (named as future work): shell-binned |f_k|^2.
+ *
+ * Counter-based random numbers: Philox-4x32-10 (J. Salmon, M. Moraes, R. Dror,
+ * D. Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11), normals by the
+ * Box-Muller transform.
+ *
+ * parity unpinned: the physical normalisation of the initial fluctuation
+ * spectrum against DEFROST (its source and data are not available); the
+ * statistics of the generated spectrum are pinned instead.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 3
+#define ORC_ENONFINITE 5
+
+typedef struct {
+    int32_t n;          /* lattice is n^3 */
+    int32_t model;      /* 0: V = lambda/4 phi^4 + g2/2 phi^2 chi^2; 1: V = m^2/2 phi^2 + g2/2 phi^2 chi^2 */
+    int32_t expansion;  /* 0: static space, a = 1; 1: FRW */
+    int32_t reserved;
+    double L, dt;       /* box side and time step, program units */
+    double lambda, m, g2;
+    double phi0[2], dphi0[2]; /* homogeneous values and physical-time derivatives */
+    double eight_pi_G;
+    double A, B, r, s;  /* all zero: derive from the dominant term */
+    double kcut;        /* fluctuation cutoff in units of 2 pi / L; 0 = n/4 */
+    double fluct;       /* multiplier on the vacuum fluctuation amplitude */
+    uint64_t seed;
+} orc_params;
+
+typedef struct {
+    orc_params p;
+    int n;
+    size_t nsites;
+    double dx;
+    double A, B, r, s, beta, cpl;
+    double cdom0, pdom, kappa0, pint;   /* V_pr = cdom0 a^pdom f^beta/beta + kappa0 a^pint f^2 chi^2 / 2 */
+    double *f[2], *pi[2];
+    double t;      /* program time of the momenta; fields and a live at t + dt/2 */
+    double a;      /* a at t + dt/2 */
+    double ad;     /* a' at t */
+    double S[4];   /* <|grad f0|^2>, <|grad f1|^2>, <f0^beta/beta>, <f0^2 f1^2/2> at field time */
+    int64_t step;
+} orc_lattice;
+
+static size_t idx(int n, int x, int y, int z) { return ((size_t)z * n + y) * n + x; }
+static int wrap(int i, int n) { return (i % n + n) % n; }
+
+/* ---------------------------------------------------------------- rescaling */
+
+int orc_derive(orc_lattice *L)
+{
+    const orc_params *p = &L->p;
+    if (p->model == 0) { L->cpl = p->lambda; L->beta = 4.0; }
+    else if (p->model == 1) { L->cpl = p->m * p->m; L->beta = 2.0; }
+    else return ORC_EINVAL;
+    if (p->phi0[0] == 0.0 || L->cpl <= 0.0) return ORC_EINVAL;
+    if (p->A == 0.0 && p->B == 0.0 && p->r == 0.0 && p->s == 0.0) {
+        /* Sec. II.B: rescaling for a dominant term cpl/beta phi^beta */
+        L->A = 1.0 / p->phi0[0];
+        L->B = sqrt(L->cpl) * pow(fabs(p->phi0[0]), -1.0 + L->beta / 2.0);
+        L->r = 6.0 / (2.0 + L->beta);
+        L->s = 3.0 * (2.0 - L->beta) / (2.0 + L->beta);
+    } else {
+        L->A = p->A; L->B = p->B; L->r = p->r; L->s = p->s;
+    }
+    /* Sec. II.B: the first-derivative term vanishes only if s - 2r + 3 = 0 */
+    if (fabs(L->s - 2.0 * L->r + 3.0) > 1e-12 || L->A == 0.0 || L->B <= 0.0) return ORC_EINVAL;
+    /* V_pr = (A^2/B^2) a^(2r-2s) V(phi = f / (A a^r)) */
+    L->cdom0 = L->cpl * pow(L->A, 2.0 - L->beta) / (L->B * L->B);
+    L->pdom = 2.0 * L->r - 2.0 * L->s - L->beta * L->r;
+    L->kappa0 = p->g2 / (L->A * L->A * L->B * L->B);
+    L->pint = -2.0 * L->r - 2.0 * L->s;
+    return ORC_OK;
+}
+
+/* physical potential V(phi, chi), Sec. III and the configured lambda model */
+static double V_phys(const orc_lattice *L, double phi, double chi)
+{
+    return L->cpl / L->beta * pow(phi, L->beta) + 0.5 * L->p.g2 * phi * phi * chi * chi;
+}
+
+static double cdom_at(const orc_lattice *L, double a) { return L->cdom0 * pow(a, L->pdom); }
+static double kappa_at(const orc_lattice *L, double a) { return L->kappa0 * pow(a, L->pint); }
+
+/* program-unit potential and its derivatives at one site */
+static double Vpr(const orc_lattice *L, double a, double f0, double f1)
+{
+    return cdom_at(L, a) * pow(f0, L->beta) / L->beta + 0.5 * kappa_at(L, a) * f0 * f0 * f1 * f1;
+}
+static double dVpr0(const orc_lattice *L, double a, double f0, double f1)
+{
+    return cdom_at(L, a) * pow(f0, L->beta - 1.0) + kappa_at(L, a) * f0 * f1 * f1;
+}
+static double dVpr1(const orc_lattice *L, double a, double f0, double f1)
+{
+    return kappa_at(L, a) * f0 * f0 * f1;
+}
+
+/* ---------------------------------------------------------------- creation */
+
+int orc_create(const orc_params *p, orc_lattice **out)
+{
+    *out = NULL;
+    if (p->n < 2 || p->n > 1024 || p->L <= 0.0 || p->dt <= 0.0) return ORC_EINVAL;
+    orc_lattice *L = (orc_lattice *)calloc(1, sizeof(orc_lattice));
+    if (!L) return ORC_ENOMEM;
+    L->p = *p;
+    L->n = p->n;
+    L->nsites = (size_t)p->n * p->n * p->n;
+    L->dx = p->L / p->n;
+    int st = orc_derive(L);
+    if (st != ORC_OK) { free(L); return st; }
+    for (int i = 0; i < 2; i++) {
+        L->f[i] = (double *)calloc(L->nsites, sizeof(double));
+        L->pi[i] = (double *)calloc(L->nsites, sizeof(double));
+        if (!L->f[i] || !L->pi[i]) {
+            for (int j = 0; j < 2; j++) { free(L->f[j]); free(L->pi[j]); }
+            free(L);
+            return ORC_ENOMEM;
+        }
+    }
+    L->a = 1.0;
+    *out = L;
+    return ORC_OK;
+}
+
+void orc_destroy(orc_lattice *L)
+{
+    if (!L) return;
+    for (int i = 0; i < 2; i++) { free(L->f[i]); free(L->pi[i]); }
+    free(L);
+}
+
+/* derived constants: A, B, r, s, beta, cdom0, pdom, kappa0, pint, dx */
+void orc_get_derived(const orc_lattice *L, double out[10])
+{
+    out[0] = L->A; out[1] = L->B; out[2] = L->r; out[3] = L->s; out[4] = L->beta;
+    out[5] = L->cdom0; out[6] = L->pdom; out[7] = L->kappa0; out[8] = L->pint; out[9] = L->dx;
+}
+
+double *orc_array(orc_lattice *L, int field, int what) { return what == 0 ? L->f[field] : L->pi[field]; }
+
+/* scalars: t, a, a', step, S[0..3] */
+void orc_get_scalars(const orc_lattice *L, double out[8])
+{
+    out[0] = L->t; out[1] = L->a; out[2] = L->ad; out[3] = (double)L->step;
+    for (int i = 0; i < 4; i++) out[4 + i] = L->S[i];
+}
+
+/* ---------------------------------------------------------------- operators */
+
+/* 7-point Laplacian with periodic wrap: (sum of the six neighbours - 6 f) / dx^2 */
+void orc_laplacian(int n, double dx, const double *f, double *out)
+{
+    double inv = 1.0 / (dx * dx);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < n; z++)
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                double nb = f[idx(n, wrap(x + 1, n), y, z)] + f[idx(n, wrap(x - 1, n), y, z)]
+                          + f[idx(n, x, wrap(y + 1, n), z)] + f[idx(n, x, wrap(y - 1, n), z)]
+                          + f[idx(n, x, y, wrap(z + 1, n))] + f[idx(n, x, y, wrap(z - 1, n))];
+                out[idx(n, x, y, z)] = (nb - 6.0 * f[idx(n, x, y, z)]) * inv;
+            }
+}
+
+/* volume average of |grad f|^2 with forward differences */
+double orc_grad2_mean(int n, double dx, const double *f)
+{
+    double *plane = (double *)calloc((size_t)n, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < n; z++) {
+        double acc = 0.0;
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                double c = f[idx(n, x, y, z)];
+                double gx = f[idx(n, wrap(x + 1, n), y, z)] - c;
+                double gy = f[idx(n, x, wrap(y + 1, n), z)] - c;
+                double gz = f[idx(n, x, y, wrap(z + 1, n))] - c;
+                acc += gx * gx + gy * gy + gz * gz;
+            }
+        plane[z] = acc;
+    }
+    double tot = 0.0;
+    for (int z = 0; z < n; z++) tot += plane[z];
+    free(plane);
+    return tot / (dx * dx) / ((double)n * n * n);
+}
+
+/* volume averages S = (<|grad f0|^2>, <|grad f1|^2>, <f0^beta/beta>, <f0^2 f1^2/2>) */
+void orc_sums(orc_lattice *L)
+{
+    int n = L->n;
+    L->S[0] = orc_grad2_mean(n, L->dx, L->f[0]);
+    L->S[1] = orc_grad2_mean(n, L->dx, L->f[1]);
+    double *pd = (double *)calloc((size_t)n, sizeof(double));
+    double *pi = (double *)calloc((size_t)n, sizeof(double));
+    const double *f0 = L->f[0], *f1 = L->f[1];
+    size_t plane = (size_t)n * n;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < n; z++) {
+        double ad = 0.0, ai = 0.0;
+        for (size_t k = 0; k < plane; k++) {
+            size_t i = (size_t)z * plane + k;
+            ad += pow(f0[i], L->beta) / L->beta;
+            ai += 0.5 * f0[i] * f0[i] * f1[i] * f1[i];
+        }
+        pd[z] = ad; pi[z] = ai;
+    }
+    double td = 0.0, ti = 0.0;
+    for (int z = 0; z < n; z++) { td += pd[z]; ti += pi[z]; }
+    free(pd); free(pi);
+    L->S[2] = td / (double)L->nsites;
+    L->S[3] = ti / (double)L->nsites;
+}
+
+/* ---------------------------------------------------------------- scale factor */
+
+/* Right-hand side of eq. scale without the a'^2 term:
+ * c = (8piG/A^2) a^(-2s-2r-1) ( (S0+S1)/3 + a^(2s+2) <V_pr> ). */
+static double scale_source(const orc_lattice *L, double a)
+{
+    double vpr = cdom_at(L, a) * L->S[2] + kappa_at(L, a) * L->S[3];
+    return L->p.eight_pi_G / (L->A * L->A) * pow(a, -2.0 * L->s - 2.0 * L->r - 1.0)
+         * ((L->S[0] + L->S[1]) / 3.0 + pow(a, 2.0 * L->s + 2.0) * vpr);
+}
+
+/* Staggered update of a' across one step: with a and the sums at t_{n+1/2}
+ * and a'_n, solve a'_{n+1} = a'_n + dt a''_{n+1/2} where
+ * a''_{n+1/2} = q a'_{n+1/2}^2 + c, q = -(s+2)/a and a'_{n+1/2} = (a'_n + a'_{n+1})/2.
+ * With y = a'_n + a'_{n+1}: (dt q/4) y^2 - y + (2 a'_n + dt c) = 0; the root that
+ * tends to 2a'_n + dt c as dt -> 0 is y = 2 gamma / (1 + sqrt(1 - 4 alpha gamma)). */
+int orc_scale_update(const orc_lattice *L, double *ad_next, double *ad_half, double *add)
+{
+    double a = L->a, dt = L->p.dt;
+    double c = scale_source(L, a);
+    double q = -(L->s + 2.0) / a;
+    double alpha = dt * q / 4.0;
+    double gamma = 2.0 * L->ad + dt * c;
+    double disc = 1.0 - 4.0 * alpha * gamma;
+    if (!(disc >= 0.0)) return ORC_ENONFINITE;
+    double y = 2.0 * gamma / (1.0 + sqrt(disc));
+    *ad_half = 0.5 * y;
+    *ad_next = y - L->ad;
+    *add = q * (*ad_half) * (*ad_half) + c;
+    return ORC_OK;
+}
+
+/* coefficients of the field equation at the field time:
+ * cL = a^(-2s-2), cF = r(s-r+2) h^2 + r a''/a, h = a'/a */
+static void field_coefficients(const orc_lattice *L, double a, double ad_half, double add,
+                               double *cL, double *cF)
+{
+    *cL = pow(a, -2.0 * L->s - 2.0);
+    double h = ad_half / a;
+    *cF = L->r * (L->s - L->r + 2.0) * h * h + L->r * add / a;
+}
+
+/* ---------------------------------------------------------------- leapfrog */
+
+/* acceleration F_i = cL Lap f_i + cF f_i - dV_pr/df_i at the field time */
+static void accelerations(const orc_lattice *L, double cL, double cF, double *F0, double *F1)
+{
+    orc_laplacian(L->n, L->dx, L->f[0], F0);
+    orc_laplacian(L->n, L->dx, L->f[1], F1);
+    const double *f0 = L->f[0], *f1 = L->f[1];
+    double a = L->a;
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < (long long)L->nsites; i++) {
+        double p0 = f0[i], p1 = f1[i];
+        F0[i] = cL * F0[i] + cF * p0 - dVpr0(L, a, p0, p1);
+        F1[i] = cL * F1[i] + cF * p1 - dVpr1(L, a, p0, p1);
+    }
+}
+
+/* one step of eq. evo for both fields and for a:
+ *   pi_{n+1}    = pi_n + dt F(f_{n+1/2})           (kick, both fields from the same f)
+ *   f_{n+3/2}   = f_{n+1/2} + dt pi_{n+1}           (drift)
+ *   a_{n+3/2}   = a_{n+1/2} + dt a'_{n+1}
+ * then the sums are recomputed at the new field time. */
+static int one_step(orc_lattice *L, double *F0, double *F1)
+{
+    double cL = 1.0, cF = 0.0, ad_next = 0.0, ad_half = 0.0, add = 0.0;
+    if (L->p.expansion) {
+        int st = orc_scale_update(L, &ad_next, &ad_half, &add);
+        if (st != ORC_OK) return st;
+        field_coefficients(L, L->a, ad_half, add, &cL, &cF);
+    }
+    double dt = L->p.dt;
+    accelerations(L, cL, cF, F0, F1);
+    double *f0 = L->f[0], *f1 = L->f[1], *p0 = L->pi[0], *p1 = L->pi[1];
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < (long long)L->nsites; i++) {
+        p0[i] += dt * F0[i];
+        p1[i] += dt * F1[i];
+    }
+#pragma omp parallel for schedule(static)
+    for (long long i = 0; i < (long long)L->nsites; i++) {
+        f0[i] += dt * p0[i];
+        f1[i] += dt * p1[i];
+    }
+    if (L->p.expansion) {
+        L->a += dt * ad_next;
+        L->ad = ad_next;
+    }
+    L->t += dt;
+    L->step += 1;
+    orc_sums(L);
+    if (!isfinite(L->S[0]) || !isfinite(L->S[1]) || !isfinite(L->S[2]) || !isfinite(L->S[3])
+        || !isfinite(L->a))
+        return ORC_ENONFINITE;
+    return ORC_OK;
+}
+
+int orc_step(orc_lattice *L, int64_t nsteps)
+{
+    double *F0 = (double *)malloc(L->nsites * sizeof(double));
+    double *F1 = (double *)malloc(L->nsites * sizeof(double));
+    if (!F0 || !F1) { free(F0); free(F1); return ORC_ENOMEM; }
+    int st = ORC_OK;
+    for (int64_t k = 0; k < nsteps && st == ORC_OK; k++) st = one_step(L, F0, F1);
+    free(F0); free(F1);
+    return st;
+}
+
+/* Set the scalars of a stored state (t, a, a', step) and recompute the sums. */
+void orc_set_scalars(orc_lattice *L, double t, double a, double ad, int64_t step)
+{
+    L->t = t; L->a = a; L->ad = ad; L->step = step;
+    orc_sums(L);
+}
+
+/* ---------------------------------------------------------------- random numbers */
+
+/* Philox-4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
+ * multiplies with the Weyl key schedule. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* One standard normal per (seed, field, quantity, site): Philox output words
+ * 0 and 1 of counter (site, field, quantity, 0) under key (seed lo, seed hi),
+ * mapped to (0,1) as (u + 1/2) 2^-32, then Box-Muller's cosine branch. */
+double orc_normal(uint64_t seed, uint32_t field, uint32_t quantity, uint32_t site)
+{
+    uint32_t ctr[4] = {site, field, quantity, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    double u1 = ((double)o[0] + 0.5) * (1.0 / 4294967296.0);
+    double u2 = ((double)o[1] + 0.5) * (1.0 / 4294967296.0);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * ORC_PI * u2);
+}
+
+/* ---------------------------------------------------------------- FFT */
+
+/* Recursive mixed-radix Cooley-Tukey DFT of length n (any n >= 1):
+ * X[k] = sum_j x[j] exp(sign 2 pi i j k / n). Split by the smallest prime factor p,
+ * transform the p decimated subsequences, combine with twiddles. */
+static void dft1(int n, const double *xr, const double *xi, int stride, double *yr, double *yi, int sign)
+{
+    if (n == 1) { yr[0] = xr[0]; yi[0] = xi[0]; return; }
+    int p = n;
+    for (int d = 2; d * d <= n; d++) if (n % d == 0) { p = d; break; }
+    int m = n / p;
+    if (m == 1) {
+        for (int k = 0; k < n; k++) {
+            double sr = 0.0, si = 0.0;
+            for (int j = 0; j < n; j++) {
+                double ang = sign * 2.0 * ORC_PI * (double)(((long long)j * k) % n) / n;
+                double c = cos(ang), s = sin(ang);
+                sr += xr[j * stride] * c - xi[j * stride] * s;
+                si += xr[j * stride] * s + xi[j * stride] * c;
+            }
+            yr[k] = sr; yi[k] = si;
+        }
+        return;
+    }
+    double *tr = (double *)malloc(sizeof(double) * n), *ti = (double *)malloc(sizeof(double) * n);
+    for (int r = 0; r < p; r++) dft1(m, xr + r * stride, xi + r * stride, stride * p, tr + r * m, ti + r * m, sign);
+    for (int k = 0; k < n; k++) {
+        int kk = k % m;
+        double sr = 0.0, si = 0.0;
+        for (int r = 0; r < p; r++) {
+            double ang = sign * 2.0 * ORC_PI * (double)(((long long)r * k) % n) / n;
+            double c = cos(ang), s = sin(ang);
+            sr += tr[r * m + kk] * c - ti[r * m + kk] * s;
+            si += tr[r * m + kk] * s + ti[r * m + kk] * c;
+        }
+        yr[k] = sr; yi[k] = si;
+    }
+    free(tr); free(ti);
+}
+
+void orc_fft1(int n, const double *xr, const double *xi, double *yr, double *yi, int sign)
+{
+    dft1(n, xr, xi, 1, yr, yi, sign);
+}
+
+/* 3D DFT in place on (re, im), x fastest; sign -1 forward, +1 inverse (unnormalised) */
+void orc_fft3(int n, double *re, double *im, int sign)
+{
+    for (int axis = 0; axis < 3; axis++) {
+#pragma omp parallel
+        {
+            double *ar = (double *)malloc(sizeof(double) * n), *ai = (double *)malloc(sizeof(double) * n);
+            double *br = (double *)malloc(sizeof(double) * n), *bi = (double *)malloc(sizeof(double) * n);
+#pragma omp for schedule(static)
+            for (int line = 0; line < n * n; line++) {
+                int u = line % n, v = line / n;
+                for (int j = 0; j < n; j++) {
+                    size_t i = axis == 0 ? idx(n, j, u, v) : axis == 1 ? idx(n, u, j, v) : idx(n, u, v, j);
+                    ar[j] = re[i]; ai[j] = im[i];
+                }
+                dft1(n, ar, ai, 1, br, bi, sign);
+                for (int j = 0; j < n; j++) {
+                    size_t i = axis == 0 ? idx(n, j, u, v) : axis == 1 ? idx(n, u, j, v) : idx(n, u, v, j);
+                    re[i] = br[j]; im[i] = bi[j];
+                }
+            }
+            free(ar); free(ai); free(br); free(bi);
+        }
+    }
+}
+
+/* ---------------------------------------------------------------- initial conditions */
+
+static double kcut_of(const orc_lattice *L) { return L->p.kcut > 0.0 ? L->p.kcut : L->n / 4.0; }
+
+/* Gaussian fluctuation of one field (q = 0) or momentum (q = 1): filter white noise
+ * W(x) by s(k) in Fourier space. With F(k) = sum_x W(x) e^{-ikx} and the inverse
+ * (1/n^3) sum_k, white noise of unit variance has <|F_k|^2> = n^3, and a target
+ * per-mode variance P(k) / L^3 in the box needs s(k)^2 = P(k) / dx^3.
+ * Vacuum: P = 1/(2 omega) for fields, omega/2 for momenta, with
+ * omega^2 = k_lat^2 + m_eff^2 and k_lat^2 = sum_d (2/dx sin(pi n_d / n))^2. The
+ * program-unit amplitude carries the factor A B (f = A phi, x_pr = B x). Modes
+ * with |n| = 0 or |n| > kcut, and modes with omega^2 <= 0, are left empty. */
+static void fluctuation(const orc_lattice *L, int field, int q, double meff2, double *out)
+{
+    int n = L->n;
+    size_t N3 = L->nsites;
+    double *re = (double *)malloc(sizeof(double) * N3), *im = (double *)calloc(N3, sizeof(double));
+    for (size_t i = 0; i < N3; i++) re[i] = orc_normal(L->p.seed, (uint32_t)field, (uint32_t)q, (uint32_t)i);
+    orc_fft3(n, re, im, -1);
+    double amp = L->p.fluct * L->A * L->B * pow(L->dx, -1.5);
+    double kc = kcut_of(L);
+    for (int z = 0; z < n; z++)
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                int nx = x < n / 2 ? x : x - n, ny = y < n / 2 ? y : y - n, nz = z < n / 2 ? z : z - n;
+                double nmag = sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
+                double sx = 2.0 / L->dx * sin(ORC_PI * nx / n), sy = 2.0 / L->dx * sin(ORC_PI * ny / n),
+                       sz = 2.0 / L->dx * sin(ORC_PI * nz / n);
+                double w2 = sx * sx + sy * sy + sz * sz + meff2;
+                double scale = 0.0;
+                if (nmag > 0.0 && nmag <= kc && w2 > 0.0) {
+                    double w = sqrt(w2);
+                    scale = amp * (q == 0 ? 1.0 / sqrt(2.0 * w) : sqrt(0.5 * w));
+                }
+                size_t i = idx(n, x, y, z);
+                re[i] *= scale; im[i] *= scale;
+            }
+    orc_fft3(n, re, im, +1);
+    for (size_t i = 0; i < N3; i++) out[i] = re[i] / (double)N3;
+    free(re); free(im);
+}
+
+/* Sec. II.B, initial values: homogeneous phi0, dphi0 from input, H from the
+ * homogeneous energy density, conversion to program units, Gaussian vacuum
+ * fluctuations, then the fields (and a) advanced by dt/2. */
+int orc_init_fields(orc_lattice *L)
+{
+    const orc_params *p = &L->p;
+    L->t = 0.0; L->a = 1.0; L->step = 0;
+    double rho0 = 0.5 * (p->dphi0[0] * p->dphi0[0] + p->dphi0[1] * p->dphi0[1]) + V_phys(L, p->phi0[0], p->phi0[1]);
+    L->ad = 0.0;
+    if (p->expansion) {
+        if (!(rho0 > 0.0)) return ORC_EINVAL;
+        double H0 = sqrt(p->eight_pi_G * rho0 / 3.0);
+        L->ad = H0 / L->B;  /* a' = a^(1-s) H / B at a = 1 */
+    }
+    double h0 = L->ad;      /* a'/a at a = 1 */
+    double fh[2], ph[2];
+    for (int i = 0; i < 2; i++) {
+        fh[i] = L->A * p->phi0[i];
+        ph[i] = L->A / L->B * p->dphi0[i] + L->r * h0 * fh[i];
+    }
+    double meff2[2];
+    meff2[0] = L->cdom0 * (L->beta - 1.0) * pow(fh[0], L->beta - 2.0) + L->kappa0 * fh[1] * fh[1];
+    meff2[1] = L->kappa0 * fh[0] * fh[0];
+    double *df = (double *)malloc(sizeof(double) * L->nsites), *dp = (double *)malloc(sizeof(double) * L->nsites);
+    if (!df || !dp) { free(df); free(dp); return ORC_ENOMEM; }
+    for (int i = 0; i < 2; i++) {
+        if (p->fluct != 0.0) {
+            fluctuation(L, i, 0, meff2[i], df);
+            fluctuation(L, i, 1, meff2[i], dp);
+        } else {
+            memset(df, 0, sizeof(double) * L->nsites);
+            memset(dp, 0, sizeof(double) * L->nsites);
+        }
+        for (size_t k = 0; k < L->nsites; k++) {
+            L->f[i][k] = fh[i] + df[k];
+            L->pi[i][k] = ph[i] + dp[k] + L->r * h0 * df[k];
+        }
+    }
+    free(df); free(dp);
+    /* half-step desynchronisation: fields (and a) advanced by dt/2 */
+    double dt = p->dt;
+    for (int i = 0; i < 2; i++)
+        for (size_t k = 0; k < L->nsites; k++) L->f[i][k] += 0.5 * dt * L->pi[i][k];
+    if (p->expansion) L->a += 0.5 * dt * L->ad;
+    orc_sums(L);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Energies at the field time t_{n+1/2}: the momenta there are the average of
+ * pi_n and pi_{n+1} (a kick of dt/2 that is not committed), and a' there is the
+ * time-centred a'_{n+1/2}. Sec. II.B, eq. rho-pres, converted with
+ * phidot = (B/A) a^(s-r) (f' - r h f), grad_x phi = B grad f / (A a^r),
+ * V = (B^2/A^2) a^(2s-2r) V_pr:
+ *   rho = conv [ sum_i (1/2 (f_i' - r h f_i)^2 + 1/2 a^(-2s-2) |grad f_i|^2) + V_pr ]
+ *   p   = conv [ sum_i (1/2 (f_i' - r h f_i)^2 - 1/6 a^(-2s-2) |grad f_i|^2) - V_pr ]
+ * with conv = (B^2/A^2) a^(2s-2r). H = B a^s h; K/(a^2H^2) = 8piG<rho>/(3H^2) - 1.
+ * out: t, a, a', H, rho, p, w, curv, kin0, kin1, grad0, grad1, pot, mean0, mean1, var0, var1 */
+int orc_energies(orc_lattice *L, double out[17])
+{
+    double cL = 1.0, cF = 0.0, ad_next = 0.0, ad_half = 0.0, add = 0.0;
+    if (L->p.expansion) {
+        int st = orc_scale_update(L, &ad_next, &ad_half, &add);
+        if (st != ORC_OK) return st;
+        field_coefficients(L, L->a, ad_half, add, &cL, &cF);
+    }
+    double *F0 = (double *)malloc(L->nsites * sizeof(double)), *F1 = (double *)malloc(L->nsites * sizeof(double));
+    if (!F0 || !F1) { free(F0); free(F1); return ORC_ENOMEM; }
+    accelerations(L, cL, cF, F0, F1);
+    double a = L->a, h = L->p.expansion ? ad_half / a : 0.0, dt = L->p.dt;
+    double kin[2] = {0, 0}, mean[2] = {0, 0}, var[2] = {0, 0}, pot = 0.0;
+    for (int i = 0; i < 2; i++) {
+        const double *F = i == 0 ? F0 : F1;
+        double acc = 0.0, accm = 0.0;
+        for (size_t k = 0; k < L->nsites; k++) {
+            double pibar = L->pi[i][k] + 0.5 * dt * F[k];
+            double v = pibar - L->r * h * L->f[i][k];
+            acc += 0.5 * v * v;
+            accm += L->f[i][k];
+        }
+        kin[i] = acc / (double)L->nsites;
+        mean[i] = accm / (double)L->nsites;
+        double accv = 0.0;
+        for (size_t k = 0; k < L->nsites; k++) { double d = L->f[i][k] - mean[i]; accv += d * d; }
+        var[i] = accv / (double)L->nsites;
+    }
+    for (size_t k = 0; k < L->nsites; k++) pot += Vpr(L, a, L->f[0][k], L->f[1][k]);
+    pot /= (double)L->nsites;
+    free(F0); free(F1);
+    double cg = pow(a, -2.0 * L->s - 2.0);
+    double grad[2];
+    for (int i = 0; i < 2; i++) grad[i] = 0.5 * cg * orc_grad2_mean(L->n, L->dx, L->f[i]);
+    double conv = L->B * L->B / (L->A * L->A) * pow(a, 2.0 * L->s - 2.0 * L->r);
+    double rho = conv * (kin[0] + kin[1] + grad[0] + grad[1] + pot);
+    double pres = conv * (kin[0] + kin[1] - (grad[0] + grad[1]) / 3.0 - pot);
+    double H = L->B * pow(a, L->s) * h;
+    out[0] = L->t + 0.5 * dt;
+    out[1] = a;
+    out[2] = L->p.expansion ? ad_half : 0.0;
+    out[3] = H;
+    out[4] = rho;
+    out[5] = pres;
+    out[6] = pres / rho;
+    out[7] = H != 0.0 ? L->p.eight_pi_G * rho / (3.0 * H * H) - 1.0 : NAN;
+    out[8] = conv * kin[0]; out[9] = conv * kin[1];
+    out[10] = conv * grad[0]; out[11] = conv * grad[1];
+    out[12] = conv * pot;
+    out[13] = mean[0]; out[14] = mean[1];
+    out[15] = var[0]; out[16] = var[1];
+    return ORC_OK;
+}
+
+/* Shell-binned power spectrum of one field (Sec. IV names it as future work):
+ * bin b = round(|n|), n the integer wave vector; p_out[b] is the shell mean of
+ * |F_k|^2 / n^3 (F = forward DFT, so unit white noise gives 1), k_out[b] the shell
+ * mean of 2 pi |n| / L, count_out[b] the number of modes. */
+int orc_spectrum(orc_lattice *L, int field, int nbins, double *k_out, double *p_out, int64_t *count_out)
+{
+    int n = L->n;
+    size_t N3 = L->nsites;
+    double *re = (double *)malloc(sizeof(double) * N3), *im = (double *)calloc(N3, sizeof(double));
+    if (!re || !im) { free(re); free(im); return ORC_ENOMEM; }
+    memcpy(re, L->f[field], sizeof(double) * N3);
+    orc_fft3(n, re, im, -1);
+    for (int b = 0; b < nbins; b++) { k_out[b] = 0.0; p_out[b] = 0.0; count_out[b] = 0; }
+    for (int z = 0; z < n; z++)
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                int nx = x < n / 2 ? x : x - n, ny = y < n / 2 ? y : y - n, nz = z < n / 2 ? z : z - n;
+                double nmag = sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
+                int b = (int)floor(nmag + 0.5);
+                if (b >= nbins) continue;
+                size_t i = idx(n, x, y, z);
+                p_out[b] += (re[i] * re[i] + im[i] * im[i]) / (double)N3;
+                k_out[b] += 2.0 * ORC_PI * nmag / L->p.L;
+                count_out[b] += 1;
+            }
+    for (int b = 0; b < nbins; b++)
+        if (count_out[b] > 0) { p_out[b] /= (double)count_out[b]; k_out[b] /= (double)count_out[b]; }
+    free(re); free(im);
+    return ORC_OK;
+}
