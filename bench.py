@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused staggered-leapfrog step.
+
+`python bench.py --gpus N --steps K --warmup W` evolves one lattice per GPU
+(replicas, weak scaling: each rank runs its own independent lattice) for W
+untimed and K timed steps and prints one JSON line on rank 0:
+site-updates/s over all ranks, the step kernel's achieved HBM bandwidth against
+the measured copy peak, an end-to-end figure through the C ABI with host
+buffers, the FP64 oracle timed on the host cores, and SM clocks sampled during
+the timed region.
+
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only), each step a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lattice site-updates/s (2 fields, FP32) and % HBM roofline; adjoint/forward cost"
+UNIT = "site-updates/s"
+L2_BYTES = 129e6
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="m2phi2_256_fp32")
+    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 plain loads, 2 TMA")
+    ap.add_argument("--ty", type=int, default=0)
+    ap.add_argument("--zr", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_0911_5692_gb300.workloads import WORKLOADS
+    w = WORKLOADS[name]
+    p = dict(w["params"])
+    return p
+
+
+def model_name(p):
+    return "lphi4" if p["model"] == 0 else "m2phi2"
+
+
+def config_of(name, p, world):
+    n = p["n"]
+    esize = 4 if p["precision"] == 32 else 8
+    state = 8 * n ** 3 * esize
+    return {"workload": name, "model": model_name(p), "n": n, "sites": n ** 3, "precision": p["precision"],
+            "expansion": bool(p["expansion"]), "global_batch": world, "lattices_per_gpu": 1,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": f"inputs larger than L2: {state / 2 / 1e6:.0f} MB read + {state / 2 / 1e6:.0f} MB written per step"
+                  if state / 2 > L2_BYTES else "state fits in L2"}
+
+
+def kernel_source_hash():
+    d = os.path.join(ROOT, "paper_0911_5692_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def traffic_record(name, variant):
+    """DRAM bytes per launch of the step kernel from a committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    try:
+        recs = json.load(open(path))
+    except Exception:
+        return None
+    hsh = kernel_source_hash()
+    for r in recs.get("records", []):
+        if r.get("kernel_hash") == hsh and r.get("workload") == name and r.get("variant") == variant:
+            return r.get("dram_bytes_per_launch")
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu_id)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1])); mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(p, seconds):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded sample of
+    the workload: steps of the full lattice from a seeded synthetic state until
+    `seconds` have passed."""
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_0911_5692_gb300.workloads import random_state
+    n = p["n"]
+    st = random_state(n, 1, precision=p["precision"], f_mean=(1.0, 0.0), f_amp=(1e-3, 1e-4), pi_mean=(0.3, 0.0),
+                      pi_amp=(1e-3, 1e-2))
+    o = Oracle(p)
+    o.set_state(*st, t=0.0, a=1.0, ad=0.5)
+    del st
+    o.step(1)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cores = os.cpu_count()
+    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps of the full {n}^3 {model_name(p)} lattice from a seeded "
+                      f"synthetic state ({el:.1f} s, OpenMP over {cores} host cores)"}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle timed as the reference arm, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_0911_5692_gb300.workloads import random_state
+    p = workload(args.workload)
+    n_full = p["n"]
+    # per-site cost from a short calibration, then the sample lattice that keeps
+    # the whole (warmup + steps) run near 90 s
+    cal = dict(p, n=32)
+    o = Oracle(cal)
+    o.set_state(*random_state(32, 2, precision=64), t=0.0, a=1.0, ad=0.5)
+    o.step(2)
+    t0 = time.perf_counter(); o.step(10); per_site = (time.perf_counter() - t0) / (10 * 32 ** 3)
+    budget = 90.0 / max(1, args.steps + args.warmup)
+    ns = int((budget / per_site) ** (1 / 3)) // 4 * 4
+    ns = max(8, min(n_full, ns))
+    sp = dict(p, n=ns)
+    o = Oracle(sp)
+    o.set_state(*random_state(ns, 3, precision=p["precision"], f_mean=(1.0, 0.0), f_amp=(1e-3, 1e-4),
+                              pi_mean=(0.3, 0.0), pi_amp=(1e-3, 1e-2)), t=0.0, a=1.0, ad=0.5)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    value = ns ** 3 * args.steps / el
+    cores = os.cpu_count()
+    sample = (f"each step: one FP64 oracle leapfrog step of a {ns}^3 lattice with the {n_full}^3 workload's "
+              f"model, couplings, dx and dt (OpenMP over {cores} host cores)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args.workload, p, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import ctypes as C
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_0911_5692_gb300 import Lattice
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = workload(args.workload)
+    p["seed"] = p.get("seed", 0) + rank          # independent replica per rank
+    n = p["n"]
+    esize = 4 if p["precision"] == 32 else 8
+    lat = Lattice(p, device=local)
+    if args.variant or args.ty or args.zr:
+        lat.set_kernel(args.variant, args.ty, args.zr)
+    info = lat.kernel_info()
+    lat.init_fields()
+    lat.evolve(args.warmup)
+    lat.sync()
+
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else (gpu_id or local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record(lat.stream)
+    lat.evolve(args.steps)
+    end.record(lat.stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks.stop()
+    ms = start.elapsed_time(end)
+    lat.sync()   # raises on a sticky device error (non-finite fields)
+    t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    sec = ms_max / 1e3
+    value = world * n ** 3 * args.steps / sec
+    ms_per_step = ms_max / args.steps
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # state (4 arrays) from pinned host memory, advances one step and reads the
+    # scalars (t, a, a', step, sums) back.
+    E = max(1, args.e2e_steps)
+    host = []
+    for w in (0, 1):
+        for f in (0, 1):
+            d = lat.get_state_device(f, w)
+            hbuf = torch.empty_like(d, device="cpu").pin_memory()
+            hbuf.copy_(d)
+            host.append((f, w, hbuf))
+    lib, h = lat._L, lat._h
+    out8 = (C.c_double * 8)()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        for f, w, hbuf in host:
+            assert lib.lat_set_state(h, f, w, C.c_void_p(hbuf.data_ptr()), 0) == 0
+        assert lib.lat_evolve(h, 1) == 0
+        assert lib.lat_get_scalars(h, out8) == 0
+    e2e_sec = time.perf_counter() - t0
+    te = torch.tensor([e2e_sec], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * n ** 3 * E / float(te.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    if peaks and peaks.get("hbm_gbs"):
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = FALLBACK_HBM_GBS, "fallback"
+    bytes_per_launch = 32 * n ** 3 if esize == 4 else 64 * n ** 3
+    achieved = bytes_per_launch / (ms_per_step / 1e3) / 1e9
+    traffic = traffic_record(args.workload, info["variant"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if esize == 4 else "f64", "data": "synthetic",
+        "config": config_of(args.workload, p, world),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "kernel": f"fused step variant {info['variant']} ({info['blocks']} blocks x "
+                               f"{info['threads']} threads, ty={info['ty']}, zr={info['zr']})"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3 * esize,
+                "d2h_bytes_per_step": 8 * 8, "steps": E},
+        "gpu_launches": args.steps * info["launches_per_step"],
+        "clocks": clocks.summary(),
+        "context": {"paper_gtx260_256cubed_su_per_s": 7.6e8,
+                    "note": "paper: GTX 260, 27-point stencil, 0.022 s/step at 256^3 (not this workload)"},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

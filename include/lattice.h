@@ -1,0 +1,183 @@
+/*
+ * lattice.h -- C ABI of the GB300 lattice library: staggered-leapfrog evolution
+ * of two interacting scalar fields (phi, chi) on a periodic N^3 lattice in an
+ * expanding FRW universe, after J. Sainio, "CUDAEASY - a GPU Accelerated
+ * Cosmological Lattice Program" (arXiv:0911.5692).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns lat_status; nothing is thrown across the ABI.
+ *   - A handle is bound to the CUDA stream given at creation and is not
+ *     thread-safe. Calls that launch work are asynchronous on that stream
+ *     unless they say they synchronise.
+ *   - Errors detected on the device (non-finite sums, a failed scale-factor
+ *     solve, a wait that ran out of time) are sticky: the step kernels turn
+ *     into no-ops and the error is returned by the next synchronising call
+ *     (lat_energies, lat_sync, lat_get_scalars, lat_get_state).
+ *   - Arrays are SoA, one array per field and per quantity, x fastest:
+ *     element (x, y, z) is at ((z * n) + y) * n + x. Element type is float for
+ *     precision 32 and double for precision 64.
+ *   - Storage times follow the staggered leapfrog (Sec. II.B, eq. evo and the
+ *     half-step desynchronisation after initialisation): fields f and the scale
+ *     factor a live at t + dt/2, momenta f' and a' at t.
+ *   - All quantities are in program units (Sec. II.B): f = A a^r phi,
+ *     x_pr = B x, dt_pr = B a^s dt, with s - 2r + 3 = 0.
+ */
+#ifndef LATTICE_H
+#define LATTICE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lat_handle lat_handle;
+
+typedef enum {
+    LAT_OK = 0,
+    LAT_EINVAL = 1,       /* bad argument or parameter set */
+    LAT_ECFL = 2,         /* dt too large for the stencil and masses */
+    LAT_ENOMEM = 3,       /* device or host allocation failed */
+    LAT_ECUDA = 4,        /* a CUDA runtime or library call failed */
+    LAT_ENONFINITE = 5,   /* non-finite sums or no real root for a' (sticky) */
+    LAT_ETIMEOUT = 6,     /* a bounded device wait ran out (sticky) */
+    LAT_EUNSUPPORTED = 7, /* valid request this build cannot serve */
+    LAT_ESTATE = 8        /* call not valid in the handle's current state */
+} lat_status;
+
+/* Potentials, Sec. III and the lambda phi^4 lineage it compares with. */
+enum {
+    LAT_MODEL_LPHI4 = 0,  /* V = lambda/4 phi^4 + g2/2 phi^2 chi^2 */
+    LAT_MODEL_M2PHI2 = 1  /* V = m^2/2 phi^2   + g2/2 phi^2 chi^2 */
+};
+
+typedef struct {
+    int32_t n;            /* lattice side N (N^3 sites); 4 <= N <= 1024, N % 4 == 0 */
+    int32_t precision;    /* 32 or 64: storage and arithmetic of fields and momenta */
+    int32_t model;        /* LAT_MODEL_* */
+    int32_t expansion;    /* 0: static space (a = 1, a' = 0); 1: FRW, eq. scale */
+    double L;             /* box side, program units; dx = L / N */
+    double dt;            /* time step, program units */
+    double lambda, m, g2; /* physical couplings (Planck units fixed by eight_pi_G) */
+    double phi0[2];       /* homogeneous phi, chi at t = 0 (physical) */
+    double dphi0[2];      /* their physical-time derivatives */
+    double eight_pi_G;    /* 1: reduced Planck units; 8 pi: non-reduced */
+    double A, B, r, s;    /* rescaling; all four zero: derived from the dominant
+                             term as in Sec. II.B (A = 1/phi0, B = sqrt(cpl)
+                             phi0^(beta/2-1), r = 6/(2+beta), s = 3(2-beta)/(2+beta)) */
+    double kcut;          /* initial fluctuations cut above |n| > kcut (units of
+                             2 pi / L); 0: N/4 */
+    double fluct;         /* multiplier on the vacuum fluctuation amplitude (1 = vacuum) */
+    uint64_t seed;        /* seed of the counter-based generator for the initial state */
+} lat_params;
+
+/* Volume averages at the field time, in physical units (Sec. II.B, eq. rho-pres;
+ * residual curvature and w as in Sec. III). kin, grad and pot are the kinetic,
+ * gradient and potential parts of rho (rho = sum kin + sum grad + pot); mean and
+ * var are of the program-unit fields. */
+typedef struct {
+    double t, a, ad, H, rho, p, w, curv_resid;
+    double kin[2], grad[2], pot, mean[2], var[2];
+} lat_energy_report;
+
+/* Create a lattice on `cuda_stream` (a cudaStream_t; NULL = legacy default
+ * stream) with library-owned device buffers (8 arrays of N^3 elements: f and
+ * f' of both fields, twice for the leapfrog's ping-pong). Validates the
+ * parameters and the stability bound of the leapfrog (LAT_ECFL when
+ * dt^2 (12 a^(-2s-2)/dx^2 + m_eff^2) > 4 at the initial state). The fields
+ * start at zero; call lat_init_fields or lat_set_state. On error *out is NULL. */
+lat_status lat_create(const lat_params* params, void* cuda_stream, lat_handle** out);
+
+/* As lat_create, with caller-owned device buffers (e.g. torch tensors):
+ * dev_bufs[0..7] = f_phi, f_chi, pi_phi, pi_chi of ping-pong set 0, then the
+ * same four of set 1. Each holds N^3 elements of the chosen precision, 16-byte
+ * aligned. They must outlive the handle; lat_destroy does not free them. */
+lat_status lat_create_with_buffers(const lat_params* params, void* cuda_stream,
+                                   void* const dev_bufs[8], lat_handle** out);
+
+/* DEFROST-style initial conditions (Sec. II.B, last paragraph): homogeneous
+ * values from params plus Gaussian vacuum fluctuations of every field and
+ * momentum (white noise from Philox-4x32-10 keyed by the seed, filtered in
+ * Fourier space to |f_k|^2 = 1/(2 w_k), |f'_k|^2 = w_k/2, w_k^2 = k_lat^2 +
+ * m_eff^2), converted to program units (f = A a^r phi, f' = (A/B) a^(r-s) phidot
+ * + r (a'/a) f), then the fields and a advanced by dt/2. Runs on the device with
+ * temporary buffers; synchronises the stream. */
+lat_status lat_init_fields(lat_handle* h);
+
+/* Advance n_steps leapfrog steps (Sec. II.B, eq. evo with eq. scalar-evo and
+ * eq. scale). Each step is one fused kernel: 7-point Laplacian, potential
+ * derivative, kick and drift of both fields, the <|grad f|^2> and <V> sums of
+ * the new fields, and (in its last block) the FP64 scale-factor update that sets
+ * the coefficients of the next step. Asynchronous; no host synchronisation.
+ * n_steps >= 0. */
+lat_status lat_evolve(lat_handle* h, int64_t n_steps);
+
+/* Energy density, pressure, w, H, residual curvature, per-field kinetic /
+ * gradient / potential parts, means and variances at the field time (Sec. II.B,
+ * eq. rho-pres; Sec. III). Momenta at the field time are the average of those
+ * at t and t + dt. Synchronises; returns a sticky device error if one is set. */
+lat_status lat_energies(lat_handle* h, lat_energy_report* out);
+
+/* Shell-binned power spectrum of field `field` (0 = phi, 1 = chi), the
+ * diagnostic Sec. IV names as future work: bin b = round(|n|), n the integer
+ * wave vector; p_out[b] = shell mean of |F_k|^2 / N^3 (F the forward DFT),
+ * k_out[b] = shell mean of 2 pi |n| / L, count_out[b] = modes in the shell.
+ * Host arrays of nbins entries, 1 <= nbins <= 4096. Synchronises. */
+lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, double* p_out,
+                        int64_t* count_out);
+
+/* Copy one array out: field 0/1, what 0 = f (at t + dt/2), 1 = f' (at t).
+ * dst holds N^3 elements of the handle's precision, on the device if
+ * dst_is_device, else host memory (pinned or pageable). Synchronises. */
+lat_status lat_get_state(lat_handle* h, int field, int what, void* dst, int dst_is_device);
+
+/* Copy one array in (same layout as lat_get_state). The sums and scale-factor
+ * coefficients are recomputed before the next step or diagnostic. */
+lat_status lat_set_state(lat_handle* h, int field, int what, const void* src, int src_is_device);
+
+/* Scalars: out[0] = t (time of the momenta), out[1] = a (at t + dt/2),
+ * out[2] = a' (at t), out[3] = step count, out[4..7] = the volume averages
+ * <|grad f_phi|^2>, <|grad f_chi|^2>, <f_phi^beta/beta>, <f_phi^2 f_chi^2/2> at the
+ * field time. Synchronises; returns a sticky device error if one is set. */
+lat_status lat_get_scalars(lat_handle* h, double out[8]);
+
+/* Set t, a (at t + dt/2), a' (at t) and the step count from in[0..3]; the sums
+ * and coefficients are recomputed before the next step. */
+lat_status lat_set_scalars(lat_handle* h, const double in[4]);
+
+/* Wait for the handle's stream; return a sticky device error if one is set. */
+lat_status lat_sync(lat_handle* h);
+
+/* Checkpoint and resume (the paper has none; LATTICEEASY-style runs are long).
+ * A checkpoint is a host blob: a header with the parameters, the FP64 scalar
+ * block exactly as the device holds it (t, a, a', the sums and coefficients of
+ * the next step) and the four state arrays. Loading it into a handle created
+ * with the same parameters continues bit-identically to an uninterrupted run.
+ * lat_checkpoint_bytes gives the blob size; save and load synchronise and
+ * return LAT_EINVAL on a size or parameter mismatch. */
+lat_status lat_checkpoint_bytes(lat_handle* h, uint64_t* bytes);
+lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes);
+lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
+
+/* Choose the step kernel: variant 0 = automatic, 1 = plain-load kernel,
+ * 2 = TMA plane-ring kernel (FP32 and FP64); ty = rows per tile, zr = planes per
+ * z-chunk (0 = automatic). LAT_EUNSUPPORTED if the variant cannot run this
+ * lattice. */
+lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr);
+
+/* Launch geometry of the current step kernel: out[0] = variant, out[1] = blocks
+ * per step, out[2] = threads per block, out[3] = dynamic shared memory bytes,
+ * out[4] = kernels launched per step, out[5] = ty, out[6] = zr. */
+lat_status lat_kernel_info(lat_handle* h, int64_t out[7]);
+
+/* Release the handle and the buffers it owns. NULL is accepted. */
+void lat_destroy(lat_handle* h);
+
+/* Static description of a status code. */
+const char* lat_status_string(lat_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LATTICE_H */

@@ -1,0 +1,707 @@
+// lat_abi.cu -- the C ABI of include/lattice.h: parameter validation and the
+// program-unit rescaling (Sec. II.B), buffer ownership, the graph-captured
+// evolution loop, initial conditions and diagnostics.
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lat_kernels.h"
+
+using namespace lat;
+
+struct lat_handle {
+    lat_params p;
+    Model M;
+    int prec;
+    size_t esize;
+    size_t nsites;
+    cudaStream_t stream;
+    void* buf[8];        // f0, f1, p0, p1 of set 0, then of set 1
+    bool owns;
+    DevScalars* sc;      // device
+    double* partials;    // device, per-block sums
+    size_t partials_cap; // doubles
+    double* means;       // device, 2 doubles
+    bool dirty;          // sums and coefficients must be recomputed
+    int variant;         // 1 = plain loads, 2 = TMA
+    int ty, zr;
+    TmaConfig tcfg;
+    alignas(64) unsigned char tmaps[8 * 128];
+    cudaGraphExec_t graph;
+    int graph_steps;
+};
+
+namespace {
+
+constexpr int kGraphChunk = 32;
+
+lat_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LAT_OK : LAT_ECUDA; }
+
+#define LAT_TRY(expr)                          \
+    do {                                       \
+        lat_status _s = (expr);                \
+        if (_s != LAT_OK) return _s;           \
+    } while (0)
+#define LAT_CUDA(expr)                                   \
+    do {                                                 \
+        cudaError_t _e = (expr);                         \
+        if (_e != cudaSuccess) return LAT_ECUDA;         \
+    } while (0)
+
+// Sec. II.B: rescaling for a dominant term cpl/beta phi^beta and the program-unit
+// potential V_pr = (A^2/B^2) a^(2r-2s) V(f / (A a^r)), which for
+// V = cpl/beta phi^beta + g2/2 phi^2 chi^2 is
+// cdom0 a^pdom f^beta/beta + kappa0 a^pint f^2 chi^2/2 with
+// cdom0 = cpl A^(2-beta)/B^2, pdom = 2r - 2s - beta r, kappa0 = g2/(A^2 B^2),
+// pint = -2r - 2s.
+lat_status derive_model(const lat_params& p, Model* M)
+{
+    if (p.n < 4 || p.n > 1024 || (p.n % 4) != 0) return LAT_EINVAL;
+    if (p.precision != 32 && p.precision != 64) return LAT_EINVAL;
+    if (!(p.L > 0.0) || !(p.dt > 0.0) || !std::isfinite(p.L) || !std::isfinite(p.dt)) return LAT_EINVAL;
+    if (p.expansion != 0 && p.expansion != 1) return LAT_EINVAL;
+    double cpl, beta;
+    if (p.model == LAT_MODEL_LPHI4) { cpl = p.lambda; beta = 4.0; }
+    else if (p.model == LAT_MODEL_M2PHI2) { cpl = p.m * p.m; beta = 2.0; }
+    else return LAT_EINVAL;
+    if (!(cpl > 0.0) || p.phi0[0] == 0.0 || !(p.g2 >= 0.0)) return LAT_EINVAL;
+    double A, B, r, s;
+    if (p.A == 0.0 && p.B == 0.0 && p.r == 0.0 && p.s == 0.0) {
+        A = 1.0 / p.phi0[0];
+        B = std::sqrt(cpl) * std::pow(std::fabs(p.phi0[0]), beta / 2.0 - 1.0);
+        r = 6.0 / (2.0 + beta);
+        s = 3.0 * (2.0 - beta) / (2.0 + beta);
+    } else {
+        A = p.A; B = p.B; r = p.r; s = p.s;
+    }
+    if (A == 0.0 || !(B > 0.0) || std::fabs(s - 2.0 * r + 3.0) > 1e-12) return LAT_EINVAL;
+    if (p.expansion && !(p.eight_pi_G > 0.0)) return LAT_EINVAL;
+    std::memset(M, 0, sizeof(*M));
+    M->n = p.n;
+    M->expansion = p.expansion;
+    M->beta = (int)beta;
+    M->dx = p.L / p.n;
+    M->dt = p.dt;
+    M->inv_dx2 = 1.0 / (M->dx * M->dx);
+    M->A = A; M->B = B; M->r = r; M->s = s;
+    M->cdom0 = cpl * std::pow(A, 2.0 - beta) / (B * B);
+    M->pdom = 2.0 * r - 2.0 * s - beta * r;
+    M->kappa0 = p.g2 / (A * A * B * B);
+    M->pint = -2.0 * r - 2.0 * s;
+    M->eight_pi_G = p.eight_pi_G;
+    M->inv_sites = 1.0 / ((double)p.n * p.n * p.n);
+    return LAT_OK;
+}
+
+// Effective masses^2 of the two fields at the homogeneous initial values (a = 1).
+void meff2_initial(const lat_params& p, const Model& M, double out[2])
+{
+    const double fh = M.A * p.phi0[0], ch = M.A * p.phi0[1];
+    out[0] = M.cdom0 * (M.beta - 1) * std::pow(fh, M.beta - 2) + M.kappa0 * ch * ch;
+    out[1] = M.kappa0 * fh * fh;
+}
+
+// Stability of the leapfrog for the 7-point stencil: the largest lattice
+// frequency must satisfy w dt < 2, w^2 = 12/dx^2 + m_eff^2 (a = 1).
+lat_status check_cfl(const lat_params& p, const Model& M)
+{
+    double m2[2];
+    meff2_initial(p, M, m2);
+    const double mmax = std::max(0.0, std::max(m2[0], m2[1]));
+    const double w2 = 12.0 * M.inv_dx2 + mmax;
+    if (!(p.dt * p.dt * w2 <= 4.0)) return LAT_ECFL;
+    return LAT_OK;
+}
+
+size_t partials_needed(int n)
+{
+    size_t need = (size_t)std::max(simple_grid_blocks(n, std::min(n, 32)), sums_grid_blocks(n)) * kSums;
+    need = std::max(need, (size_t)energies_grid_blocks(n) * kEnergySums);
+    // TMA grids are bounded by (N/ty) * (N/zr) <= N * N / 4 blocks
+    need = std::max(need, (size_t)n * n / 4 * kSums + 1024);
+    return need;
+}
+
+template <typename T>
+Bufs<T> bufs_of(const lat_handle* h)
+{
+    Bufs<T> b;
+    for (int par = 0; par < 2; par++)
+        for (int f = 0; f < 2; f++) {
+            b.f[par][f] = (T*)h->buf[4 * par + f];
+            b.p[par][f] = (T*)h->buf[4 * par + 2 + f];
+        }
+    return b;
+}
+
+lat_status launch_prepare(lat_handle* h)
+{
+    cudaError_t e = h->prec == 32 ? launch_sums<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->stream)
+                                  : launch_sums<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->stream);
+    return cuda_status(e);
+}
+
+lat_status launch_one_step(lat_handle* h)
+{
+    cudaError_t e;
+    if (h->variant == 2) {
+        e = h->prec == 32
+                ? launch_step_tma<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->tcfg, h->tmaps, h->stream)
+                : launch_step_tma<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->tcfg, h->tmaps,
+                                          h->stream);
+    } else {
+        e = h->prec == 32 ? launch_step_simple<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->zr, h->stream)
+                          : launch_step_simple<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->zr,
+                                                       h->stream);
+    }
+    return cuda_status(e);
+}
+
+void drop_graph(lat_handle* h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_steps = 0;
+}
+
+lat_status ensure_prepared(lat_handle* h)
+{
+    if (!h->dirty) return LAT_OK;
+    LAT_TRY(launch_prepare(h));
+    h->dirty = false;
+    return LAT_OK;
+}
+
+lat_status read_scalars(lat_handle* h, DevScalars* out)
+{
+    LAT_CUDA(cudaMemcpyAsync(out, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    return LAT_OK;
+}
+
+lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr)
+{
+    const int n = h->p.n;
+    if (variant < 0 || variant > 2) return LAT_EINVAL;
+    int chosen = 1;
+    if (variant == 0 || variant == 2) {
+        TmaConfig cfg;
+        if (tma_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr, &cfg) &&
+            (size_t)cfg.blocks * kSums <= h->partials_cap) {
+            const void* ptrs[8];
+            for (int i = 0; i < 8; i++) ptrs[i] = h->buf[i];
+            LAT_CUDA(tma_encode_maps(ptrs, n, (int)h->esize, h->tmaps));
+            h->tcfg = cfg;
+            h->ty = cfg.ty;
+            h->zr = cfg.zr;
+            chosen = 2;
+        } else if (variant == 2) {
+            return LAT_EUNSUPPORTED;
+        }
+    }
+    if (chosen == 1) {
+        const int zrr = (variant == 1 && zr > 0) ? std::min(zr, n) : std::min(n, 32);
+        if ((size_t)simple_grid_blocks(n, zrr) * kSums > h->partials_cap) return LAT_EUNSUPPORTED;
+        h->ty = kSimpleTY;
+        h->zr = zrr;
+    }
+    h->variant = chosen;
+    drop_graph(h);
+    return LAT_OK;
+}
+
+lat_status create_common(const lat_params* params, void* stream, void* const bufs[8], lat_handle** out)
+{
+    if (!out) return LAT_EINVAL;
+    *out = nullptr;
+    if (!params) return LAT_EINVAL;
+    Model M;
+    LAT_TRY(derive_model(*params, &M));
+    LAT_TRY(check_cfl(*params, M));
+    lat_handle* h = new (std::nothrow) lat_handle();
+    if (!h) return LAT_ENOMEM;
+    h->p = *params;
+    h->M = M;
+    h->prec = params->precision;
+    h->esize = params->precision == 32 ? 4 : 8;
+    h->nsites = (size_t)params->n * params->n * params->n;
+    h->stream = (cudaStream_t)stream;
+    h->owns = bufs == nullptr;
+    lat_status st = LAT_OK;
+    for (int i = 0; i < 8 && st == LAT_OK; i++) {
+        if (bufs) {
+            h->buf[i] = bufs[i];
+            if (!bufs[i] || ((uintptr_t)bufs[i] & 15u)) st = LAT_EINVAL;
+        } else if (cudaMalloc(&h->buf[i], h->nsites * h->esize) != cudaSuccess) {
+            h->buf[i] = nullptr;
+            st = LAT_ENOMEM;
+        } else if (cudaMemsetAsync(h->buf[i], 0, h->nsites * h->esize, h->stream) != cudaSuccess) {
+            st = LAT_ECUDA;
+        }
+    }
+    h->partials_cap = partials_needed(params->n);
+    if (st == LAT_OK && cudaMalloc((void**)&h->sc, sizeof(DevScalars)) != cudaSuccess) st = LAT_ENOMEM;
+    if (st == LAT_OK && cudaMalloc((void**)&h->partials, h->partials_cap * sizeof(double)) != cudaSuccess)
+        st = LAT_ENOMEM;
+    if (st == LAT_OK && cudaMalloc((void**)&h->means, 2 * sizeof(double)) != cudaSuccess) st = LAT_ENOMEM;
+    if (st == LAT_OK) {
+        DevScalars s;
+        std::memset(&s, 0, sizeof(s));
+        s.a = 1.0;
+        if (cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            st = LAT_ECUDA;
+    }
+    h->dirty = true;
+    if (st == LAT_OK) st = configure_kernel(h, 0, 0, 0);
+    if (st != LAT_OK) {
+        lat_destroy(h);
+        return st;
+    }
+    *out = h;
+    return LAT_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char* lat_status_string(lat_status st)
+{
+    switch (st) {
+    case LAT_OK: return "ok";
+    case LAT_EINVAL: return "invalid argument or parameters";
+    case LAT_ECFL: return "time step violates the leapfrog stability bound";
+    case LAT_ENOMEM: return "out of memory";
+    case LAT_ECUDA: return "CUDA runtime or library error";
+    case LAT_ENONFINITE: return "non-finite sums or no real root for the scale-factor update";
+    case LAT_ETIMEOUT: return "a bounded device wait timed out";
+    case LAT_EUNSUPPORTED: return "unsupported configuration";
+    case LAT_ESTATE: return "call not valid in the current state";
+    }
+    return "unknown status";
+}
+
+lat_status lat_create(const lat_params* params, void* cuda_stream, lat_handle** out)
+{
+    return create_common(params, cuda_stream, nullptr, out);
+}
+
+lat_status lat_create_with_buffers(const lat_params* params, void* cuda_stream, void* const dev_bufs[8],
+                                   lat_handle** out)
+{
+    if (!dev_bufs) return LAT_EINVAL;
+    return create_common(params, cuda_stream, dev_bufs, out);
+}
+
+void lat_destroy(lat_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    drop_graph(h);
+    if (h->owns)
+        for (int i = 0; i < 8; i++)
+            if (h->buf[i]) cudaFree(h->buf[i]);
+    if (h->sc) cudaFree(h->sc);
+    if (h->partials) cudaFree(h->partials);
+    if (h->means) cudaFree(h->means);
+    delete h;
+}
+
+lat_status lat_sync(lat_handle* h)
+{
+    if (!h) return LAT_EINVAL;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    return (lat_status)s.status;
+}
+
+lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr)
+{
+    if (!h || variant < 0 || variant > 2 || ty < 0 || zr < 0) return LAT_EINVAL;
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    return configure_kernel(h, variant, ty, zr);
+}
+
+lat_status lat_kernel_info(lat_handle* h, int64_t out[7])
+{
+    if (!h || !out) return LAT_EINVAL;
+    out[0] = h->variant;
+    if (h->variant == 2) {
+        out[1] = h->tcfg.blocks; out[2] = h->tcfg.threads; out[3] = (int64_t)h->tcfg.smem;
+    } else {
+        out[1] = simple_grid_blocks(h->p.n, h->zr); out[2] = kSimpleTX * kSimpleTY; out[3] = 0;
+    }
+    out[4] = 1;
+    out[5] = h->ty;
+    out[6] = h->zr;
+    return LAT_OK;
+}
+
+lat_status lat_evolve(lat_handle* h, int64_t n_steps)
+{
+    if (!h || n_steps < 0) return LAT_EINVAL;
+    LAT_TRY(ensure_prepared(h));
+    int64_t left = n_steps;
+    // Chunks of kGraphChunk steps replay one captured graph; the step kernels read
+    // the ping-pong parity and the coefficients from device memory, so the same
+    // graph is valid at any step. The legacy default stream cannot be captured.
+    if (h->stream != nullptr && left >= kGraphChunk) {
+        if (!h->graph) {
+            cudaGraph_t g;
+            LAT_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            lat_status st = LAT_OK;
+            for (int i = 0; i < kGraphChunk && st == LAT_OK; i++) st = launch_one_step(h);
+            cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+            if (st != LAT_OK) return st;
+            if (e != cudaSuccess) return LAT_ECUDA;
+            e = cudaGraphInstantiate(&h->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { h->graph = nullptr; return LAT_ECUDA; }
+            h->graph_steps = kGraphChunk;
+        }
+        while (left >= h->graph_steps) {
+            LAT_CUDA(cudaGraphLaunch(h->graph, h->stream));
+            left -= h->graph_steps;
+        }
+    }
+    for (; left > 0; left--) LAT_TRY(launch_one_step(h));
+    return LAT_OK;
+}
+
+lat_status lat_get_scalars(lat_handle* h, double out[8])
+{
+    if (!h || !out) return LAT_EINVAL;
+    LAT_TRY(ensure_prepared(h));
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    out[0] = s.t; out[1] = s.a; out[2] = s.ad; out[3] = (double)s.step;
+    for (int k = 0; k < 4; k++) out[4 + k] = s.S[k];
+    return (lat_status)s.status;
+}
+
+lat_status lat_set_scalars(lat_handle* h, const double in[4])
+{
+    if (!h || !in) return LAT_EINVAL;
+    if (!std::isfinite(in[0]) || !(in[1] > 0.0) || !std::isfinite(in[2]) || !(in[3] >= 0.0)) return LAT_EINVAL;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    s.t = in[0];
+    s.a = h->M.expansion ? in[1] : 1.0;
+    s.ad = h->M.expansion ? in[2] : 0.0;
+    s.step = (long long)in[3];
+    s.ticket = 0;
+    s.ticket2 = 0;
+    LAT_CUDA(cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    h->dirty = true;
+    return LAT_OK;
+}
+
+lat_status lat_get_state(lat_handle* h, int field, int what, void* dst, int dst_is_device)
+{
+    if (!h || !dst || field < 0 || field > 1 || what < 0 || what > 1) return LAT_EINVAL;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    const int par = (int)(s.step & 1);
+    const void* src = h->buf[4 * par + 2 * what + field];
+    LAT_CUDA(cudaMemcpyAsync(dst, src, h->nsites * h->esize,
+                             dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    return (lat_status)s.status;
+}
+
+lat_status lat_set_state(lat_handle* h, int field, int what, const void* src, int src_is_device)
+{
+    if (!h || !src || field < 0 || field > 1 || what < 0 || what > 1) return LAT_EINVAL;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    const int par = (int)(s.step & 1);
+    void* dst = h->buf[4 * par + 2 * what + field];
+    LAT_CUDA(cudaMemcpyAsync(dst, src, h->nsites * h->esize,
+                             src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    h->dirty = true;
+    return LAT_OK;
+}
+
+lat_status lat_init_fields(lat_handle* h)
+{
+    if (!h) return LAT_EINVAL;
+    const lat_params& p = h->p;
+    const Model& M = h->M;
+    const int n = p.n;
+    // homogeneous state at t = 0, a = 1 (Sec. II.B): H from the homogeneous energy
+    const double cpl = p.model == LAT_MODEL_LPHI4 ? p.lambda : p.m * p.m;
+    const double beta = (double)M.beta;
+    const double V0 = cpl / beta * std::pow(p.phi0[0], beta) + 0.5 * p.g2 * p.phi0[0] * p.phi0[0] * p.phi0[1] * p.phi0[1];
+    const double rho0 = 0.5 * (p.dphi0[0] * p.dphi0[0] + p.dphi0[1] * p.dphi0[1]) + V0;
+    double ad = 0.0;
+    if (p.expansion) {
+        if (!(rho0 > 0.0)) return LAT_EINVAL;
+        ad = std::sqrt(p.eight_pi_G * rho0 / 3.0) / M.B;   // a' = a^(1-s) H / B at a = 1
+    }
+    const double h0 = ad;
+    double fh[2], ph[2], m2[2];
+    for (int i = 0; i < 2; i++) {
+        fh[i] = M.A * p.phi0[i];
+        ph[i] = M.A / M.B * p.dphi0[i] + M.r * h0 * fh[i];
+    }
+    meff2_initial(p, M, m2);
+    const double amp = p.fluct * M.A * M.B * std::pow(M.dx, -1.5);
+    const double kcut = p.kcut > 0.0 ? p.kcut : n / 4.0;
+
+    lat_status st = LAT_OK;
+    double *re = nullptr, *df = nullptr, *dp = nullptr;
+    void* spec = nullptr;
+    cufftHandle fwd = 0, inv = 0;
+    bool have_fwd = false, have_inv = false;
+    const size_t nspec = (size_t)n * n * (n / 2 + 1);
+    if (p.fluct != 0.0) {
+        if (cudaMalloc((void**)&re, h->nsites * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&df, h->nsites * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&dp, h->nsites * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&spec, nspec * sizeof(cufftDoubleComplex)) != cudaSuccess)
+            st = LAT_ENOMEM;
+        if (st == LAT_OK) {
+            if (cufftPlan3d(&fwd, n, n, n, CUFFT_D2Z) != CUFFT_SUCCESS) st = LAT_ECUDA;
+            else have_fwd = true;
+        }
+        if (st == LAT_OK) {
+            if (cufftPlan3d(&inv, n, n, n, CUFFT_Z2D) != CUFFT_SUCCESS) st = LAT_ECUDA;
+            else have_inv = true;
+        }
+        if (st == LAT_OK && (cufftSetStream(fwd, h->stream) != CUFFT_SUCCESS ||
+                             cufftSetStream(inv, h->stream) != CUFFT_SUCCESS))
+            st = LAT_ECUDA;
+    }
+    for (int field = 0; field < 2 && st == LAT_OK; field++) {
+        if (p.fluct != 0.0) {
+            for (int q = 0; q < 2 && st == LAT_OK; q++) {
+                double* outq = q == 0 ? df : dp;
+                if (launch_white_noise(re, n, p.seed, (uint32_t)field, (uint32_t)q, h->stream) != cudaSuccess) st = LAT_ECUDA;
+                else if (cufftExecD2Z(fwd, re, (cufftDoubleComplex*)spec) != CUFFT_SUCCESS) st = LAT_ECUDA;
+                else if (launch_spectral_scale(spec, n, M.dx, m2[field], amp, kcut, q, h->stream) != cudaSuccess) st = LAT_ECUDA;
+                else if (cufftExecZ2D(inv, (cufftDoubleComplex*)spec, outq) != CUFFT_SUCCESS) st = LAT_ECUDA;
+            }
+        }
+        if (st != LAT_OK) break;
+        cudaError_t e = h->prec == 32
+                            ? launch_init_combine<float>(bufs_of<float>(h), field, df, dp, fh[field], ph[field],
+                                                         M.r * h0, 0.5 * p.dt, n, h->stream)
+                            : launch_init_combine<double>(bufs_of<double>(h), field, df, dp, fh[field], ph[field],
+                                                          M.r * h0, 0.5 * p.dt, n, h->stream);
+        if (e != cudaSuccess) st = LAT_ECUDA;
+    }
+    if (st == LAT_OK) {
+        DevScalars s;
+        std::memset(&s, 0, sizeof(s));
+        s.t = 0.0;
+        s.ad = ad;
+        s.a = 1.0 + (p.expansion ? 0.5 * p.dt * ad : 0.0);
+        s.step = 0;
+        if (cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) st = LAT_ECUDA;
+    }
+    if (st == LAT_OK) {
+        h->dirty = true;
+        st = ensure_prepared(h);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
+    if (have_fwd) cufftDestroy(fwd);
+    if (have_inv) cufftDestroy(inv);
+    cudaFree(re); cudaFree(df); cudaFree(dp); cudaFree(spec);
+    return st;
+}
+
+lat_status lat_energies(lat_handle* h, lat_energy_report* out)
+{
+    if (!h || !out) return LAT_EINVAL;
+    LAT_TRY(ensure_prepared(h));
+    const Model& M = h->M;
+    const int nb = energies_grid_blocks(M.n);
+    std::vector<double> part((size_t)nb * kEnergySums);
+    double tot[kEnergySums];
+    for (int pass = 0; pass < 2; pass++) {
+        cudaError_t e = h->prec == 32 ? launch_energies<float>(bufs_of<float>(h), M, h->sc, h->partials, h->means, pass, h->stream)
+                                      : launch_energies<double>(bufs_of<double>(h), M, h->sc, h->partials, h->means, pass, h->stream);
+        LAT_CUDA(e);
+        LAT_CUDA(cudaMemcpyAsync(part.data(), h->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+        LAT_CUDA(cudaStreamSynchronize(h->stream));
+        double acc[kEnergySums] = {0, 0, 0, 0, 0, 0, 0};
+        for (int b = 0; b < nb; b++)
+            for (int k = 0; k < kEnergySums; k++) acc[k] += part[(size_t)b * kEnergySums + k];
+        if (pass == 0) {
+            for (int k = 0; k < kEnergySums; k++) tot[k] = acc[k] * M.inv_sites;
+            LAT_CUDA(cudaMemcpyAsync(h->means, &tot[5], 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        } else {
+            out->var[0] = acc[5] * M.inv_sites;
+            out->var[1] = acc[6] * M.inv_sites;
+        }
+    }
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    const double a = s.a;
+    const double hh = M.expansion ? s.ad_half / a : 0.0;
+    const double cg = std::pow(a, -2.0 * M.s - 2.0);
+    const double conv = M.B * M.B / (M.A * M.A) * std::pow(a, 2.0 * M.s - 2.0 * M.r);
+    const double kin0 = tot[0], kin1 = tot[1], pot = tot[4];
+    const double gr0 = 0.5 * cg * tot[2] * M.inv_dx2, gr1 = 0.5 * cg * tot[3] * M.inv_dx2;
+    out->t = s.t + 0.5 * M.dt;
+    out->a = a;
+    out->ad = M.expansion ? s.ad_half : 0.0;
+    out->H = M.B * std::pow(a, M.s) * hh;
+    out->rho = conv * (kin0 + kin1 + gr0 + gr1 + pot);
+    out->p = conv * (kin0 + kin1 - (gr0 + gr1) / 3.0 - pot);
+    out->w = out->p / out->rho;
+    out->curv_resid = out->H != 0.0 ? M.eight_pi_G * out->rho / (3.0 * out->H * out->H) - 1.0 : NAN;
+    out->kin[0] = conv * kin0; out->kin[1] = conv * kin1;
+    out->grad[0] = conv * gr0; out->grad[1] = conv * gr1;
+    out->pot = conv * pot;
+    out->mean[0] = tot[5]; out->mean[1] = tot[6];
+    return (lat_status)s.status;
+}
+
+lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, double* p_out, int64_t* count_out)
+{
+    if (!h || field < 0 || field > 1 || nbins < 1 || nbins > 4096 || !k_out || !p_out || !count_out)
+        return LAT_EINVAL;
+    const int n = h->p.n;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    const int par = (int)(s.step & 1);
+    const size_t nspec = (size_t)n * n * (n / 2 + 1);
+    const int nb = spectrum_grid_blocks(n);
+    double* re = nullptr;
+    void* spec = nullptr;
+    double* part = nullptr;
+    lat_status st = LAT_OK;
+    cufftHandle fwd = 0;
+    bool have = false;
+    if (cudaMalloc((void**)&re, h->nsites * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&spec, nspec * sizeof(cufftDoubleComplex)) != cudaSuccess ||
+        cudaMalloc((void**)&part, (size_t)nb * 3 * nbins * sizeof(double)) != cudaSuccess)
+        st = LAT_ENOMEM;
+    if (st == LAT_OK) {
+        const void* src = h->buf[4 * par + field];
+        cudaError_t e = h->prec == 32 ? launch_to_double<float>((const float*)src, re, h->nsites, h->stream)
+                                      : launch_to_double<double>((const double*)src, re, h->nsites, h->stream);
+        if (e != cudaSuccess) st = LAT_ECUDA;
+    }
+    if (st == LAT_OK) {
+        if (cufftPlan3d(&fwd, n, n, n, CUFFT_D2Z) != CUFFT_SUCCESS) st = LAT_ECUDA;
+        else have = true;
+    }
+    if (st == LAT_OK && cufftSetStream(fwd, h->stream) != CUFFT_SUCCESS) st = LAT_ECUDA;
+    if (st == LAT_OK && cufftExecD2Z(fwd, re, (cufftDoubleComplex*)spec) != CUFFT_SUCCESS) st = LAT_ECUDA;
+    if (st == LAT_OK && launch_spectrum_bins(spec, n, h->p.L, nbins, part, h->stream) != cudaSuccess) st = LAT_ECUDA;
+    std::vector<double> hp;
+    if (st == LAT_OK) {
+        hp.resize((size_t)nb * 3 * nbins);
+        if (cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            st = LAT_ECUDA;
+    }
+    if (st == LAT_OK) {
+        for (int b = 0; b < nbins; b++) {
+            double pp = 0.0, kk = 0.0, cc = 0.0;
+            for (int blk = 0; blk < nb; blk++) {
+                const double* row = hp.data() + (size_t)blk * 3 * nbins;
+                pp += row[b]; kk += row[nbins + b]; cc += row[2 * nbins + b];
+            }
+            count_out[b] = (int64_t)std::llround(cc);
+            p_out[b] = cc > 0.0 ? pp / cc : 0.0;
+            k_out[b] = cc > 0.0 ? kk / cc : 0.0;
+        }
+    }
+    if (have) cufftDestroy(fwd);
+    cudaFree(re); cudaFree(spec); cudaFree(part);
+    if (st != LAT_OK) return st;
+    return (lat_status)s.status;
+}
+
+} // extern "C"
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];       // "LATCKPT1"
+    uint64_t bytes;      // whole blob
+    uint32_t scalars_bytes;
+    uint32_t esize;
+    lat_params params;
+};
+
+uint64_t ckpt_bytes(const lat_handle* h)
+{
+    return sizeof(CkptHeader) + sizeof(DevScalars) + 4 * h->nsites * h->esize;
+}
+
+} // namespace
+
+extern "C" {
+
+lat_status lat_checkpoint_bytes(lat_handle* h, uint64_t* bytes)
+{
+    if (!h || !bytes) return LAT_EINVAL;
+    *bytes = ckpt_bytes(h);
+    return LAT_OK;
+}
+
+lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes)
+{
+    if (!h || !dst || bytes != ckpt_bytes(h)) return LAT_EINVAL;
+    LAT_TRY(ensure_prepared(h));
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    if (s.status != LAT_OK) return (lat_status)s.status;
+    CkptHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "LATCKPT1", 8);
+    hd.bytes = bytes;
+    hd.scalars_bytes = sizeof(DevScalars);
+    hd.esize = (uint32_t)h->esize;
+    hd.params = h->p;
+    unsigned char* out = (unsigned char*)dst;
+    std::memcpy(out, &hd, sizeof(hd));
+    std::memcpy(out + sizeof(hd), &s, sizeof(s));
+    unsigned char* arr = out + sizeof(hd) + sizeof(s);
+    const int par = (int)(s.step & 1);
+    for (int k = 0; k < 4; k++)
+        LAT_CUDA(cudaMemcpyAsync(arr + k * h->nsites * h->esize, h->buf[4 * par + k], h->nsites * h->esize,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    return LAT_OK;
+}
+
+lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes)
+{
+    if (!h || !src || bytes != ckpt_bytes(h)) return LAT_EINVAL;
+    CkptHeader hd;
+    std::memcpy(&hd, src, sizeof(hd));
+    if (std::memcmp(hd.magic, "LATCKPT1", 8) != 0 || hd.bytes != bytes || hd.scalars_bytes != sizeof(DevScalars) ||
+        hd.esize != h->esize || std::memcmp(&hd.params, &h->p, sizeof(lat_params)) != 0)
+        return LAT_EINVAL;
+    DevScalars s;
+    std::memcpy(&s, (const unsigned char*)src + sizeof(hd), sizeof(s));
+    s.ticket = 0;
+    s.ticket2 = 0;
+    const unsigned char* arr = (const unsigned char*)src + sizeof(hd) + sizeof(s);
+    const int par = (int)(s.step & 1);
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 4; k++)
+        LAT_CUDA(cudaMemcpyAsync(h->buf[4 * par + k], arr + k * h->nsites * h->esize, h->nsites * h->esize,
+                                 cudaMemcpyHostToDevice, h->stream));
+    LAT_CUDA(cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    h->dirty = false;
+    return LAT_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,179 @@
+// lat_diag.cu -- diagnostics off the timed path: energy density and pressure
+// parts (Sec. II.B, eq. rho-pres) and the shell-binned power spectrum that
+// Sec. IV names as future work.
+#include <cufft.h>
+
+#include "lat_kernels.h"
+
+namespace lat {
+
+namespace {
+
+__device__ __forceinline__ size_t sidx(int n, int x, int y, int z) { return ((size_t)z * n + y) * n + x; }
+
+// Per-block FP64 partials (one thread per (x, y) column, z marched in order):
+// pass 0: [kin0, kin1, grad0, grad1, pot, sum f0, sum f1], where the momenta at
+// the field time are f' + (dt/2) F(f) (the average of the stored f' and the
+// next kick's), kin_i = (f'_i - r h f_i)^2 / 2 with h = a'/a at the field time,
+// grad_i = sum_d (forward difference)^2 (unscaled), pot = V_pr;
+// pass 1: [0, 0, 0, 0, 0, sum (f0 - mean0)^2, sum (f1 - mean1)^2].
+template <typename T>
+__global__ void __launch_bounds__(256) energies_kernel(Bufs<T> B, Model M, const DevScalars* sc, double* partials,
+                                                       const double* means, int pass)
+{
+    __shared__ double red[32][kEnergySums];
+    const int n = M.n;
+    const int par = (int)(sc->step & 1);
+    const T* f0 = B.f[par][0];
+    const T* f1 = B.f[par][1];
+    const T* p0 = B.p[par][0];
+    const T* p1 = B.p[par][1];
+    const double cL = sc->cL, cF = sc->cF, cdom = sc->cdom, kap = sc->kappa, dt = M.dt;
+    const double h = M.expansion ? sc->ad_half / sc->a : 0.0;
+    double acc[kEnergySums] = {0, 0, 0, 0, 0, 0, 0};
+    const long long cols = (long long)n * n;
+    for (long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
+         col += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(col % n), y = (int)(col / n);
+        const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+        for (int z = 0; z < n; z++) {
+            const size_t c = sidx(n, x, y, z);
+            const double a0 = (double)f0[c], a1 = (double)f1[c];
+            if (pass == 1) {
+                const double d0 = a0 - means[0], d1 = a1 - means[1];
+                acc[5] += d0 * d0;
+                acc[6] += d1 * d1;
+                continue;
+            }
+            const int zm = z == 0 ? n - 1 : z - 1, zp = z == n - 1 ? 0 : z + 1;
+            const double fx0 = (double)f0[sidx(n, xp, y, z)], fy0 = (double)f0[sidx(n, x, yp, z)],
+                         fz0 = (double)f0[sidx(n, x, y, zp)];
+            const double fx1 = (double)f1[sidx(n, xp, y, z)], fy1 = (double)f1[sidx(n, x, yp, z)],
+                         fz1 = (double)f1[sidx(n, x, y, zp)];
+            const double lap0 = (((fx0 - a0) + ((double)f0[sidx(n, xm, y, z)] - a0)) + ((fy0 - a0) + ((double)f0[sidx(n, x, ym, z)] - a0))
+                                 + ((fz0 - a0) + ((double)f0[sidx(n, x, y, zm)] - a0))) * M.inv_dx2;
+            const double lap1 = (((fx1 - a1) + ((double)f1[sidx(n, xm, y, z)] - a1)) + ((fy1 - a1) + ((double)f1[sidx(n, x, ym, z)] - a1))
+                                 + ((fz1 - a1) + ((double)f1[sidx(n, x, y, zm)] - a1))) * M.inv_dx2;
+            const double a0b = M.beta == 4 ? a0 * a0 * a0 : a0;
+            const double F0 = cL * lap0 + cF * a0 - (cdom * a0b + kap * a0 * a1 * a1);
+            const double F1 = cL * lap1 + cF * a1 - kap * a0 * a0 * a1;
+            const double q0 = (double)p0[c] + 0.5 * dt * F0 - M.r * h * a0;
+            const double q1 = (double)p1[c] + 0.5 * dt * F1 - M.r * h * a1;
+            acc[0] += 0.5 * q0 * q0;
+            acc[1] += 0.5 * q1 * q1;
+            acc[2] += (fx0 - a0) * (fx0 - a0) + (fy0 - a0) * (fy0 - a0) + (fz0 - a0) * (fz0 - a0);
+            acc[3] += (fx1 - a1) * (fx1 - a1) + (fy1 - a1) * (fy1 - a1) + (fz1 - a1) * (fz1 - a1);
+            const double sq = a0 * a0;
+            acc[4] += cdom * (M.beta == 4 ? 0.25 * sq * sq : 0.5 * sq) + 0.5 * kap * sq * a1 * a1;
+            acc[5] += a0;
+            acc[6] += a1;
+        }
+    }
+    // deterministic block reduction: shuffle tree, then warp totals in order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = 0; k < kEnergySums; k++) {
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+        if (lane == 0) red[warp][k] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < kEnergySums) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; w++) s += red[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * kEnergySums + threadIdx.x] = s;
+    }
+}
+
+template <typename T>
+__global__ void to_double_kernel(const T* src, double* dst, size_t count)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+// Shell binning of the R2C half spectrum ([kz][ky][kx], kx in [0, N/2]). Modes
+// with 0 < kx < N/2 stand for themselves and their conjugate partner (weight 2).
+// Each block accumulates into shared-memory bins and writes its own row of
+// partials [p(nbins), k(nbins), count(nbins)]; the host folds the rows in block
+// order.
+__global__ void spectrum_bins_kernel(const cufftDoubleComplex* spec, int n, double L, int nbins, double* partials)
+{
+    extern __shared__ double sb[];
+    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) sb[i] = 0.0;
+    __syncthreads();
+    const int nh = n / 2 + 1;
+    const size_t count = (size_t)n * n * nh;
+    const double inv_n3 = 1.0 / ((double)n * n * n);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % nh);
+        const int ky = (int)((i / nh) % n);
+        const int kz = (int)(i / ((size_t)nh * n));
+        const int nx = kx < n / 2 ? kx : kx - n;
+        const int ny = ky < n / 2 ? ky : ky - n;
+        const int nz = kz < n / 2 ? kz : kz - n;
+        const double nmag = sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
+        const int b = (int)floor(nmag + 0.5);
+        if (b >= nbins) continue;
+        const double w = (kx == 0 || 2 * kx == n) ? 1.0 : 2.0;
+        const double pw = (spec[i].x * spec[i].x + spec[i].y * spec[i].y) * inv_n3;
+        atomicAdd(&sb[b], w * pw);
+        atomicAdd(&sb[nbins + b], w * 2.0 * 3.14159265358979323846 * nmag / L);
+        atomicAdd(&sb[2 * nbins + b], w);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) partials[(size_t)blockIdx.x * 3 * nbins + i] = sb[i];
+}
+
+} // namespace
+
+int energies_grid_blocks(int n)
+{
+    const long long cols = (long long)n * n;
+    long long blocks = (cols + 255) / 256;
+    return (int)(blocks < 1024 ? blocks : 1024);
+}
+
+template <typename T>
+cudaError_t launch_energies(const Bufs<T>& b, const Model& M, const DevScalars* sc, double* partials,
+                            const double* means, int pass, cudaStream_t st)
+{
+    energies_kernel<T><<<energies_grid_blocks(M.n), 256, 0, st>>>(b, M, sc, partials, means, pass);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_to_double(const T* src, double* dst, size_t count, cudaStream_t st)
+{
+    size_t blocks = (count + 255) / 256;
+    to_double_kernel<T><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+int spectrum_grid_blocks(int n)
+{
+    const size_t count = (size_t)n * n * (n / 2 + 1);
+    size_t blocks = (count + 255) / 256;
+    return (int)(blocks < 256 ? blocks : 256);
+}
+
+cudaError_t launch_spectrum_bins(const void* spec, int n, double L, int nbins, double* partials, cudaStream_t st)
+{
+    const size_t smem = (size_t)3 * nbins * sizeof(double);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(spectrum_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    spectrum_bins_kernel<<<spectrum_grid_blocks(n), 256, smem, st>>>((const cufftDoubleComplex*)spec, n, L, nbins,
+                                                                     partials);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_energies<float>(const Bufs<float>&, const Model&, const DevScalars*, double*,
+                                            const double*, int, cudaStream_t);
+template cudaError_t launch_energies<double>(const Bufs<double>&, const Model&, const DevScalars*, double*,
+                                             const double*, int, cudaStream_t);
+template cudaError_t launch_to_double<float>(const float*, double*, size_t, cudaStream_t);
+template cudaError_t launch_to_double<double>(const double*, double*, size_t, cudaStream_t);
+
+} // namespace lat

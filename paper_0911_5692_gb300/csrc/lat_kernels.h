@@ -1,0 +1,75 @@
+// lat_kernels.h -- host-side launchers of the lattice kernels (internal to the
+// library; the public ABI is include/lattice.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lat_common.cuh"
+
+namespace lat {
+
+// Device buffers of one lattice: [parity][field] for fields f and momenta f'.
+template <typename T>
+struct Bufs {
+    T* f[2][2];
+    T* p[2][2];
+};
+
+// Plain-load fused step (both precisions, any N % 4 == 0).
+constexpr int kSimpleTX = 32, kSimpleTY = 8;
+int simple_grid_blocks(int n, int zr);
+template <typename T>
+cudaError_t launch_step_simple(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, int zr,
+                               cudaStream_t st);
+
+// Sums of the current fields (no step) followed by the scale-factor solve.
+int sums_grid_blocks(int n);
+template <typename T>
+cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, cudaStream_t st);
+
+// TMA plane-ring fused step.
+struct TmaConfig {
+    int ty;        // owned rows per tile
+    int zr;        // planes per z-chunk
+    int depth;     // planes prefetched ahead
+    int threads;   // threads per block
+    size_t smem;   // dynamic shared memory bytes
+    int blocks;    // blocks per step
+};
+bool tma_config(int n, int elem_bytes, int ty, int zr, TmaConfig* cfg);
+template <typename T>
+cudaError_t launch_step_tma(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
+                            const TmaConfig& cfg, const void* tmaps, cudaStream_t st);
+// Encode the 8 tensor maps (one per array) for the TMA kernel into `out`
+// (8 * 128 bytes, 64-byte aligned host memory).
+cudaError_t tma_encode_maps(const void* const ptrs[8], int n, int elem_bytes, void* out);
+
+// Initial conditions (off the timed path).
+struct InitWork {
+    double* re;      // N^3 doubles
+    double* keep;    // N^3 doubles
+    void* spec;      // N*N*(N/2+1) complex doubles
+    int fft_fwd, fft_inv;  // cufft handles
+};
+template <typename T>
+cudaError_t launch_init_combine(const Bufs<T>& b, int field, const double* df, const double* dp, double fh,
+                                double ph, double r_h0, double half_dt, int n, cudaStream_t st);
+cudaError_t launch_white_noise(double* out, int n, uint64_t seed, uint32_t field, uint32_t quantity,
+                               cudaStream_t st);
+cudaError_t launch_spectral_scale(void* spec, int n, double dx, double meff2, double amp, double kcut,
+                                  int quantity, cudaStream_t st);
+
+// Diagnostics (off the timed path).
+constexpr int kEnergySums = 7;
+int energies_grid_blocks(int n);
+template <typename T>
+cudaError_t launch_energies(const Bufs<T>& b, const Model& M, const DevScalars* sc, double* partials,
+                            const double* means, int pass, cudaStream_t st);
+template <typename T>
+cudaError_t launch_to_double(const T* src, double* dst, size_t count, cudaStream_t st);
+int spectrum_grid_blocks(int n);
+cudaError_t launch_spectrum_bins(const void* spec, int n, double L, int nbins, double* partials,
+                                 cudaStream_t st);
+
+} // namespace lat

@@ -1,0 +1,268 @@
+"""Python binding of the lattice C ABI (include/lattice.h).
+
+Argument marshalling only: every step of the evolution, the initial conditions
+and the diagnostics run in the CUDA library. PyTorch supplies device memory
+(the eight state buffers can be torch tensors) and the CUDA stream. There is no
+CPU fallback: if the compiled library cannot be loaded, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LAT_OK = 0
+STATUS_NAMES = {0: "LAT_OK", 1: "LAT_EINVAL", 2: "LAT_ECFL", 3: "LAT_ENOMEM", 4: "LAT_ECUDA",
+                5: "LAT_ENONFINITE", 6: "LAT_ETIMEOUT", 7: "LAT_EUNSUPPORTED", 8: "LAT_ESTATE"}
+
+EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evolve", "lat_energies",
+            "lat_spectrum", "lat_get_state", "lat_set_state", "lat_get_scalars", "lat_set_scalars",
+            "lat_sync", "lat_set_kernel", "lat_kernel_info", "lat_destroy", "lat_status_string",
+            "lat_checkpoint_bytes", "lat_save_checkpoint", "lat_load_checkpoint")
+
+
+class LatParams(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32), ("expansion", C.c_int32),
+        ("L", C.c_double), ("dt", C.c_double),
+        ("lam", C.c_double), ("m", C.c_double), ("g2", C.c_double),
+        ("phi0", C.c_double * 2), ("dphi0", C.c_double * 2),
+        ("eight_pi_G", C.c_double),
+        ("A", C.c_double), ("B", C.c_double), ("r", C.c_double), ("s", C.c_double),
+        ("kcut", C.c_double), ("fluct", C.c_double),
+        ("seed", C.c_uint64),
+    ]
+
+
+class LatEnergyReport(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("t", "a", "ad", "H", "rho", "p", "w", "curv_resid")] + [
+        ("kin", C.c_double * 2), ("grad", C.c_double * 2), ("pot", C.c_double),
+        ("mean", C.c_double * 2), ("var", C.c_double * 2)]
+
+
+class LatticeError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load liblattice.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"lattice library not built: {path}")
+            L = C.CDLL(path)
+            P, dp = C.c_void_p, C.POINTER(C.c_double)
+            i64p = C.POINTER(C.c_int64)
+            L.lat_create.argtypes = [C.POINTER(LatParams), P, C.POINTER(P)]
+            L.lat_create_with_buffers.argtypes = [C.POINTER(LatParams), P, C.POINTER(P), C.POINTER(P)]
+            L.lat_init_fields.argtypes = [P]
+            L.lat_evolve.argtypes = [P, C.c_int64]
+            L.lat_energies.argtypes = [P, C.POINTER(LatEnergyReport)]
+            L.lat_spectrum.argtypes = [P, C.c_int, C.c_int, dp, dp, i64p]
+            L.lat_get_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
+            L.lat_set_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
+            L.lat_get_scalars.argtypes = [P, dp]
+            L.lat_set_scalars.argtypes = [P, dp]
+            L.lat_sync.argtypes = [P]
+            L.lat_set_kernel.argtypes = [P, C.c_int, C.c_int, C.c_int]
+            L.lat_kernel_info.argtypes = [P, i64p]
+            L.lat_checkpoint_bytes.argtypes = [P, C.POINTER(C.c_uint64)]
+            L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
+            L.lat_load_checkpoint.argtypes = [P, P, C.c_uint64]
+            L.lat_destroy.argtypes = [P]
+            L.lat_destroy.restype = None
+            L.lat_status_string.argtypes = [C.c_int]
+            L.lat_status_string.restype = C.c_char_p
+            for name in EXPORTED:
+                if name not in ("lat_destroy", "lat_status_string"):
+                    getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def make_params(d: dict) -> LatParams:
+    p = LatParams()
+    p.n = int(d["n"]); p.precision = int(d.get("precision", 32))
+    p.model = int(d.get("model", 0)); p.expansion = int(d.get("expansion", 1))
+    p.L = float(d.get("L", 10.0)); p.dt = float(d["dt"])
+    p.lam = float(d.get("lam", 0.0)); p.m = float(d.get("m", 0.0)); p.g2 = float(d.get("g2", 0.0))
+    phi0 = d.get("phi0", (1.0, 0.0)); dphi0 = d.get("dphi0", (0.0, 0.0))
+    p.phi0[0], p.phi0[1] = float(phi0[0]), float(phi0[1])
+    p.dphi0[0], p.dphi0[1] = float(dphi0[0]), float(dphi0[1])
+    p.eight_pi_G = float(d.get("eight_pi_G", 1.0))
+    p.A = float(d.get("A", 0.0)); p.B = float(d.get("B", 0.0))
+    p.r = float(d.get("r", 0.0)); p.s = float(d.get("s", 0.0))
+    p.kcut = float(d.get("kcut", 0.0)); p.fluct = float(d.get("fluct", 1.0))
+    p.seed = int(d.get("seed", 0))
+    return p
+
+
+def _check(st: int, what: str):
+    if st != LAT_OK:
+        raise LatticeError(st, what)
+
+
+class Lattice:
+    """One N^3 lattice of (phi, chi) on the GPU, driven through the C ABI.
+
+    ``params`` is a dict with the keys of ``lat_params`` (see workloads.py for
+    presets). State buffers are torch tensors on ``device`` (owned by this
+    object) unless ``torch_buffers`` is False, in which case the library
+    allocates them. Work is issued on ``stream`` (a torch.cuda.Stream; default
+    a new non-default stream so evolution can be graph-captured).
+    """
+
+    def __init__(self, params: dict, device: int = 0, stream=None, torch_buffers: bool = True):
+        import torch
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Lattice needs a CUDA device; the library has no CPU path")
+        self._L = load_library()
+        self.params = dict(params)
+        self.n = int(params["n"])
+        self.precision = int(params.get("precision", 32))
+        self.dtype = torch.float32 if self.precision == 32 else torch.float64
+        self.np_dtype = np.float32 if self.precision == 32 else np.float64
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self._p = make_params(params)
+        h = C.c_void_p()
+        sptr = C.c_void_p(self.stream.cuda_stream)
+        self.buffers = None
+        if torch_buffers:
+            n3 = self.n ** 3
+            self.buffers = [torch.zeros(n3, dtype=self.dtype, device=self.device) for _ in range(8)]
+            torch.cuda.synchronize(self.device)
+            arr = (C.c_void_p * 8)(*[b.data_ptr() for b in self.buffers])
+            _check(self._L.lat_create_with_buffers(C.byref(self._p), sptr, arr, C.byref(h)), "lat_create_with_buffers")
+        else:
+            _check(self._L.lat_create(C.byref(self._p), sptr, C.byref(h)), "lat_create")
+        self._h = h
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lat_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- evolution
+    def init_fields(self):
+        _check(self._L.lat_init_fields(self._h), "lat_init_fields")
+
+    def evolve(self, n_steps: int):
+        _check(self._L.lat_evolve(self._h, int(n_steps)), "lat_evolve")
+
+    def sync(self):
+        _check(self._L.lat_sync(self._h), "lat_sync")
+
+    def set_kernel(self, variant: int = 0, ty: int = 0, zr: int = 0):
+        _check(self._L.lat_set_kernel(self._h, int(variant), int(ty), int(zr)), "lat_set_kernel")
+
+    def kernel_info(self) -> dict:
+        out = (C.c_int64 * 7)()
+        _check(self._L.lat_kernel_info(self._h, out), "lat_kernel_info")
+        keys = ("variant", "blocks", "threads", "smem", "launches_per_step", "ty", "zr")
+        return dict(zip(keys, [int(v) for v in out]))
+
+    # -- state
+    def get_state_host(self, field: int, what: int) -> np.ndarray:
+        out = np.empty((self.n, self.n, self.n), dtype=self.np_dtype)
+        _check(self._L.lat_get_state(self._h, field, what, out.ctypes.data_as(C.c_void_p), 0), "lat_get_state")
+        return out
+
+    def get_state(self):
+        """(f_phi, f_chi, pi_phi, pi_chi) as float64 numpy arrays [z][y][x]."""
+        return tuple(self.get_state_host(i, w).astype(np.float64) for w in (0, 1) for i in (0, 1))
+
+    def set_state_host(self, field: int, what: int, arr: np.ndarray):
+        a = np.ascontiguousarray(arr, dtype=self.np_dtype).reshape(self.n, self.n, self.n)
+        _check(self._L.lat_set_state(self._h, field, what, a.ctypes.data_as(C.c_void_p), 0), "lat_set_state")
+
+    def set_state(self, f0, f1, pi0, pi1, t=0.0, a=1.0, ad=0.0, step=0):
+        # scalars first: the step count selects which ping-pong set is current
+        self.set_scalars(t, a, ad, step)
+        for i, arr in enumerate((f0, f1)):
+            self.set_state_host(i, 0, arr)
+        for i, arr in enumerate((pi0, pi1)):
+            self.set_state_host(i, 1, arr)
+
+    def set_state_device(self, field: int, what: int, tensor):
+        t = tensor.contiguous()
+        assert t.dtype == self.dtype and t.numel() == self.n ** 3 and t.is_cuda
+        _check(self._L.lat_set_state(self._h, field, what, C.c_void_p(t.data_ptr()), 1), "lat_set_state")
+
+    def get_state_device(self, field: int, what: int, out=None):
+        torch = self._torch
+        if out is None:
+            out = torch.empty(self.n ** 3, dtype=self.dtype, device=self.device)
+        _check(self._L.lat_get_state(self._h, field, what, C.c_void_p(out.data_ptr()), 1), "lat_get_state")
+        return out
+
+    def scalars(self) -> dict:
+        out = (C.c_double * 8)()
+        _check(self._L.lat_get_scalars(self._h, out), "lat_get_scalars")
+        return {"t": out[0], "a": out[1], "ad": out[2], "step": int(out[3]), "S": list(out[4:8])}
+
+    def set_scalars(self, t=0.0, a=1.0, ad=0.0, step=0):
+        v = (C.c_double * 4)(float(t), float(a), float(ad), float(step))
+        _check(self._L.lat_set_scalars(self._h, v), "lat_set_scalars")
+
+    # -- checkpoints
+    def save_checkpoint(self) -> bytes:
+        """Exact checkpoint (parameters, FP64 scalar block, state arrays) as bytes."""
+        nb = C.c_uint64()
+        _check(self._L.lat_checkpoint_bytes(self._h, C.byref(nb)), "lat_checkpoint_bytes")
+        buf = (C.c_ubyte * nb.value)()
+        _check(self._L.lat_save_checkpoint(self._h, buf, nb.value), "lat_save_checkpoint")
+        return bytes(buf)
+
+    def load_checkpoint(self, blob: bytes):
+        buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+        _check(self._L.lat_load_checkpoint(self._h, buf, len(blob)), "lat_load_checkpoint")
+
+    # -- diagnostics
+    ENERGY_KEYS = ("t", "a", "ad", "H", "rho", "p", "w", "curv_resid", "kin0", "kin1",
+                   "grad0", "grad1", "pot", "mean0", "mean1", "var0", "var1")
+
+    def energies(self) -> dict:
+        r = LatEnergyReport()
+        _check(self._L.lat_energies(self._h, C.byref(r)), "lat_energies")
+        vals = [r.t, r.a, r.ad, r.H, r.rho, r.p, r.w, r.curv_resid, r.kin[0], r.kin[1], r.grad[0], r.grad[1],
+                r.pot, r.mean[0], r.mean[1], r.var[0], r.var[1]]
+        return dict(zip(self.ENERGY_KEYS, vals))
+
+    def spectrum(self, field: int, nbins: int):
+        k = np.zeros(nbins); p = np.zeros(nbins); c = np.zeros(nbins, dtype=np.int64)
+        _check(self._L.lat_spectrum(self._h, field, nbins, k.ctypes.data_as(C.POINTER(C.c_double)),
+                                    p.ctypes.data_as(C.POINTER(C.c_double)),
+                                    c.ctypes.data_as(C.POINTER(C.c_int64))), "lat_spectrum")
+        return k, p, c

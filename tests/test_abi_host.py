@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every entry point include/lattice.h declares, the
+ctypes structs match the C layout, and parameter validation (which runs before
+any CUDA call) rejects bad inputs with the documented status codes."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_0911_5692_gb300 as pkg
+from paper_0911_5692_gb300 import lattice as lat
+from paper_0911_5692_gb300.workloads import lphi4, m2phi2
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lattice.h")
+
+
+def declared_symbols():
+    hdr = open(HEADER).read()
+    return set(re.findall(r"^(?:lat_status|void|const char\*)\s+(lat_\w+)\(", hdr, re.M))
+
+
+def test_library_exports_every_declared_symbol():
+    L = pkg.load_library()
+    decl = declared_symbols()
+    assert decl == set(pkg.EXPORTED)
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.library_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (lat_\w+)$", out, re.M))
+    assert decl <= exported, decl - exported
+    for name in decl:
+        assert getattr(L, name) is not None
+
+
+def test_struct_layouts_match_header(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lattice.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(lat_params), '
+                   'offsetof(lat_params, seed), offsetof(lat_params, fluct), sizeof(lat_energy_report), '
+                   'offsetof(lat_energy_report, var));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [C.sizeof(lat.LatParams), lat.LatParams.seed.offset, lat.LatParams.fluct.offset,
+                    C.sizeof(lat.LatEnergyReport), lat.LatEnergyReport.var.offset]
+
+
+def test_status_strings():
+    L = pkg.load_library()
+    for code in range(9):
+        assert L.lat_status_string(code)
+    assert L.lat_status_string(0) == b"ok"
+
+
+def _create_status(params):
+    L = pkg.load_library()
+    p = lat.make_params(params)
+    h = C.c_void_p()
+    st = L.lat_create(C.byref(p), None, C.byref(h))
+    if st == 0:
+        L.lat_destroy(h)
+    else:
+        assert h.value is None
+    return st
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=30),               # N must be a multiple of 4
+    dict(n=2),                # too small
+    dict(n=2048),             # too large
+    dict(precision=16),
+    dict(model=7),
+    dict(dt=-1.0),
+    dict(L=0.0),
+    dict(phi0=(0.0, 0.0)),    # A = 1/phi0 undefined
+    dict(A=1.0, B=1.0, r=1.0, s=0.0),   # violates s - 2r + 3 = 0
+    dict(expansion=3),
+])
+def test_validation_rejects_bad_parameters(bad):
+    p = dict(lphi4(16), **bad)
+    assert _create_status(p) == 1  # LAT_EINVAL
+
+
+def test_validation_rejects_unstable_time_step():
+    p = lphi4(16)
+    p["dt"] = 2.5 * p["L"] / 16   # dt > 2 dx / sqrt(12)
+    assert _create_status(p) == 2  # LAT_ECFL
+    q = m2phi2(64, g2=2.5e-5)     # heavy chi at dt = 2^-10: w dt > 2
+    assert _create_status(q) == 2
+
+
+def test_null_arguments():
+    L = pkg.load_library()
+    assert L.lat_create(None, None, None) == 1
+    assert L.lat_evolve(None, 1) == 1
+    assert L.lat_sync(None) == 1
+    L.lat_destroy(None)
