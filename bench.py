@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 plain loads, 2 TMA")
     ap.add_argument("--ty", type=int, default=0)
     ap.add_argument("--zr", type=int, default=0)
+    ap.add_argument("--depth", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -246,8 +247,8 @@ def run_ours(args):
     n = p["n"]
     esize = 4 if p["precision"] == 32 else 8
     lat = Lattice(p, device=local)
-    if args.variant or args.ty or args.zr:
-        lat.set_kernel(args.variant, args.ty, args.zr)
+    if args.variant or args.ty or args.zr or args.depth:
+        lat.set_kernel(args.variant, args.ty, args.zr, args.depth)
     info = lat.kernel_info()
     lat.init_fields()
     lat.evolve(args.warmup)
@@ -331,7 +332,7 @@ def run_ours(args):
                      "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "kernel": f"fused step variant {info['variant']} ({info['blocks']} blocks x "
-                               f"{info['threads']} threads, ty={info['ty']}, zr={info['zr']})"},
+                               f"{info['threads']} threads, ty={info['ty']}, zr={info['zr']}, depth={info['depth']})"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3 * esize,
                 "d2h_bytes_per_step": 8 * 8, "steps": E},
         "gpu_launches": args.steps * info["launches_per_step"],

@@ -159,16 +159,19 @@ lat_status lat_checkpoint_bytes(lat_handle* h, uint64_t* bytes);
 lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes);
 lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
 
-/* Choose the step kernel: variant 0 = automatic, 1 = plain-load kernel,
- * 2 = TMA plane-ring kernel (FP32 and FP64); ty = rows per tile, zr = planes per
- * z-chunk (0 = automatic). LAT_EUNSUPPORTED if the variant cannot run this
- * lattice. */
-lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr);
+/* Choose the step kernel (all compute the same step): variant 0 = automatic
+ * (2 where it fits, else 1), 1 = one site per thread with cached loads,
+ * 2 = z-march through a shared-memory plane ring filled by per-thread
+ * asynchronous copies (the fast path), 3 = plane ring filled by TMA boxes;
+ * ty = owned rows per tile, zr = planes per z-chunk (variant 3: planes per
+ * block), depth = planes prefetched ahead (variants 2 and 3), 0 = automatic.
+ * LAT_EUNSUPPORTED if the variant cannot run this lattice. */
+lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth);
 
 /* Launch geometry of the current step kernel: out[0] = variant, out[1] = blocks
  * per step, out[2] = threads per block, out[3] = dynamic shared memory bytes,
- * out[4] = kernels launched per step, out[5] = ty, out[6] = zr. */
-lat_status lat_kernel_info(lat_handle* h, int64_t out[7]);
+ * out[4] = kernels launched per step, out[5] = ty, out[6] = zr, out[7] = depth. */
+lat_status lat_kernel_info(lat_handle* h, int64_t out[8]);
 
 /* Release the handle and the buffers it owns. NULL is accepted. */
 void lat_destroy(lat_handle* h);

@@ -28,10 +28,11 @@ struct lat_handle {
     size_t partials_cap; // doubles
     double* means;       // device, 2 doubles
     bool dirty;          // sums and coefficients must be recomputed
-    int variant;         // 1 = plain loads, 2 = TMA
+    int variant;         // 1 = plain per-site loads, 2 = register-prefetch z-march, 3 = TMA ring
     int ty, zr;
+    MarchConfig mcfg;
     TmaConfig tcfg;
-    alignas(64) unsigned char tmaps[8 * 128];
+    alignas(64) unsigned char tmaps[kTmaMaps * 128];
     cudaGraphExec_t graph;
     int graph_steps;
 };
@@ -150,6 +151,10 @@ lat_status launch_one_step(lat_handle* h)
 {
     cudaError_t e;
     if (h->variant == 2) {
+        e = h->prec == 32 ? launch_step_march<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->mcfg, h->stream)
+                          : launch_step_march<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->mcfg,
+                                                      h->stream);
+    } else if (h->variant == 3) {
         e = h->prec == 32
                 ? launch_step_tma<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->tcfg, h->tmaps, h->stream)
                 : launch_step_tma<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->tcfg, h->tmaps,
@@ -184,19 +189,17 @@ lat_status read_scalars(lat_handle* h, DevScalars* out)
     return LAT_OK;
 }
 
-lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr)
+lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
 {
     const int n = h->p.n;
-    if (variant < 0 || variant > 2) return LAT_EINVAL;
-    int chosen = 1;
+    if (variant < 0 || variant > 3) return LAT_EINVAL;
+    int chosen = 0;
     if (variant == 0 || variant == 2) {
-        TmaConfig cfg;
-        if (tma_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr, &cfg) &&
+        MarchConfig cfg;
+        if (march_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr, variant == 0 ? 0 : depth,
+                         &cfg) &&
             (size_t)cfg.blocks * kSums <= h->partials_cap) {
-            const void* ptrs[8];
-            for (int i = 0; i < 8; i++) ptrs[i] = h->buf[i];
-            LAT_CUDA(tma_encode_maps(ptrs, n, (int)h->esize, h->tmaps));
-            h->tcfg = cfg;
+            h->mcfg = cfg;
             h->ty = cfg.ty;
             h->zr = cfg.zr;
             chosen = 2;
@@ -204,11 +207,24 @@ lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr)
             return LAT_EUNSUPPORTED;
         }
     }
-    if (chosen == 1) {
+    if (variant == 3) {
+        TmaConfig cfg;
+        if (!tma_config(n, (int)h->esize, ty, zr, &cfg) || (size_t)cfg.blocks * kSums > h->partials_cap)
+            return LAT_EUNSUPPORTED;
+        const void* ptrs[8];
+        for (int i = 0; i < 8; i++) ptrs[i] = h->buf[i];
+        LAT_CUDA(tma_encode_maps(ptrs, n, (int)h->esize, cfg.ty, h->tmaps));
+        h->tcfg = cfg;
+        h->ty = cfg.ty;
+        h->zr = cfg.zr;
+        chosen = 3;
+    }
+    if (chosen == 0) {
         const int zrr = (variant == 1 && zr > 0) ? std::min(zr, n) : std::min(n, 32);
         if ((size_t)simple_grid_blocks(n, zrr) * kSums > h->partials_cap) return LAT_EUNSUPPORTED;
         h->ty = kSimpleTY;
         h->zr = zrr;
+        chosen = 1;
     }
     h->variant = chosen;
     drop_graph(h);
@@ -258,7 +274,7 @@ lat_status create_common(const lat_params* params, void* stream, void* const buf
             st = LAT_ECUDA;
     }
     h->dirty = true;
-    if (st == LAT_OK) st = configure_kernel(h, 0, 0, 0);
+    if (st == LAT_OK) st = configure_kernel(h, 0, 0, 0, 0);
     if (st != LAT_OK) {
         lat_destroy(h);
         return st;
@@ -322,18 +338,20 @@ lat_status lat_sync(lat_handle* h)
     return (lat_status)s.status;
 }
 
-lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr)
+lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
 {
-    if (!h || variant < 0 || variant > 2 || ty < 0 || zr < 0) return LAT_EINVAL;
+    if (!h || variant < 0 || variant > 3 || ty < 0 || zr < 0 || depth < 0) return LAT_EINVAL;
     LAT_CUDA(cudaStreamSynchronize(h->stream));
-    return configure_kernel(h, variant, ty, zr);
+    return configure_kernel(h, variant, ty, zr, depth);
 }
 
-lat_status lat_kernel_info(lat_handle* h, int64_t out[7])
+lat_status lat_kernel_info(lat_handle* h, int64_t out[8])
 {
     if (!h || !out) return LAT_EINVAL;
     out[0] = h->variant;
     if (h->variant == 2) {
+        out[1] = h->mcfg.blocks; out[2] = h->mcfg.threads; out[3] = (int64_t)h->mcfg.smem;
+    } else if (h->variant == 3) {
         out[1] = h->tcfg.blocks; out[2] = h->tcfg.threads; out[3] = (int64_t)h->tcfg.smem;
     } else {
         out[1] = simple_grid_blocks(h->p.n, h->zr); out[2] = kSimpleTX * kSimpleTY; out[3] = 0;
@@ -341,6 +359,7 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[7])
     out[4] = 1;
     out[5] = h->ty;
     out[6] = h->zr;
+    out[7] = h->variant == 2 ? h->mcfg.depth : h->variant == 3 ? h->tcfg.depth : 0;
     return LAT_OK;
 }
 

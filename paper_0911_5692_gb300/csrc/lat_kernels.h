@@ -28,22 +28,50 @@ int sums_grid_blocks(int n);
 template <typename T>
 cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, cudaStream_t st);
 
-// TMA plane-ring fused step.
-struct TmaConfig {
+// Register-prefetch z-march fused step (the default fast path).
+struct MarchConfig {
     int ty;        // owned rows per tile
     int zr;        // planes per z-chunk
+    int depth;     // planes prefetched ahead (1..4)
+    int threads;   // threads per block ((ty + 3) rows x 16-byte vectors)
+    int maxt;      // launch-bound instance
+    size_t smem;   // dynamic shared memory bytes
+    int nyt;       // y tiles
+    int blocks;    // blocks per step
+};
+bool march_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
+template <typename T>
+cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
+                              const MarchConfig& cfg, cudaStream_t st);
+
+// TMA plane-ring fused step.
+struct TmaGeom {
+    int n, ty, zr, depth;
+    int bw, nbx;   // TMA box width (elements) and x chunks per row
+    int rs;        // shared-memory row stride in bytes (a multiple of 128)
+    int tall;      // 1: one multi-row box per field and x chunk where y does not wrap
+    int nyt;       // y tiles
+    int rf, rp;    // ring slots for f planes and for momentum planes
+    int items;     // (ty + 1) * n / (16 / element bytes)
+};
+struct TmaConfig {
+    int ty;        // owned rows per tile
+    int zr;        // requested (y tile, z) planes per block; 0 = one resident wave
     int depth;     // planes prefetched ahead
     int threads;   // threads per block
     size_t smem;   // dynamic shared memory bytes
-    int blocks;    // blocks per step
+    int blocks;    // blocks per step (persistent: each marches a contiguous run)
+    TmaGeom geom;
 };
 bool tma_config(int n, int elem_bytes, int ty, int zr, TmaConfig* cfg);
 template <typename T>
 cudaError_t launch_step_tma(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                             const TmaConfig& cfg, const void* tmaps, cudaStream_t st);
-// Encode the 8 tensor maps (one per array) for the TMA kernel into `out`
-// (8 * 128 bytes, 64-byte aligned host memory).
-cudaError_t tma_encode_maps(const void* const ptrs[8], int n, int elem_bytes, void* out);
+// Encode the 16 tensor maps of the TMA kernel into `out` (16 * 128 bytes,
+// 64-byte aligned host memory): one-row boxes for the 8 arrays, then multi-row
+// boxes (ty + 3 rows for fields, ty + 1 for momenta).
+constexpr int kTmaMaps = 16;
+cudaError_t tma_encode_maps(const void* const ptrs[8], int n, int elem_bytes, int ty, void* out);
 
 // Initial conditions (off the timed path).
 struct InitWork {

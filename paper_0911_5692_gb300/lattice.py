@@ -80,7 +80,7 @@ def load_library(build_if_missing: bool = True):
             L.lat_get_scalars.argtypes = [P, dp]
             L.lat_set_scalars.argtypes = [P, dp]
             L.lat_sync.argtypes = [P]
-            L.lat_set_kernel.argtypes = [P, C.c_int, C.c_int, C.c_int]
+            L.lat_set_kernel.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int]
             L.lat_kernel_info.argtypes = [P, i64p]
             L.lat_checkpoint_bytes.argtypes = [P, C.POINTER(C.c_uint64)]
             L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
@@ -184,13 +184,13 @@ class Lattice:
     def sync(self):
         _check(self._L.lat_sync(self._h), "lat_sync")
 
-    def set_kernel(self, variant: int = 0, ty: int = 0, zr: int = 0):
-        _check(self._L.lat_set_kernel(self._h, int(variant), int(ty), int(zr)), "lat_set_kernel")
+    def set_kernel(self, variant: int = 0, ty: int = 0, zr: int = 0, depth: int = 0):
+        _check(self._L.lat_set_kernel(self._h, int(variant), int(ty), int(zr), int(depth)), "lat_set_kernel")
 
     def kernel_info(self) -> dict:
-        out = (C.c_int64 * 7)()
+        out = (C.c_int64 * 8)()
         _check(self._L.lat_kernel_info(self._h, out), "lat_kernel_info")
-        keys = ("variant", "blocks", "threads", "smem", "launches_per_step", "ty", "zr")
+        keys = ("variant", "blocks", "threads", "smem", "launches_per_step", "ty", "zr", "depth")
         return dict(zip(keys, [int(v) for v in out]))
 
     # -- state

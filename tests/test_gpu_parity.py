@@ -18,7 +18,7 @@ from paper_0911_5692_gb300.workloads import lphi4, m2phi2, random_state
 pytestmark = pytest.mark.gpu
 
 TOL = {32: 2e-6, 64: 1e-12}
-VARIANTS = [1, 2]
+VARIANTS = [1, 2, 3]
 
 
 def _params(model, n, prec, expansion):
@@ -299,3 +299,24 @@ def test_full_size_step_parity(n, model):
     g.evolve(1)
     o.step(1)
     compare_states(g, o, TOL[32], f"full size {n}")
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3, 4])
+@pytest.mark.parametrize("ty,zr", [(1, 5), (2, 7), (4, 16)])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_march_geometries(prec, ty, zr, depth):
+    """The plane-ring z-march at every prefetch depth and with ragged z-chunks:
+    ten steps against the oracle."""
+    n = 36 if ty != 4 else 32
+    p = lphi4(n, precision=prec)
+    st = _state("lphi4", n, prec, seed=ty * 10 + depth)
+    g, o = paired(p, st, (0.0, 1.1, 0.45, 0))
+    try:
+        g.set_kernel(2, ty, zr, depth)
+    except LatticeError:
+        pytest.skip("geometry does not fit")
+    assert g.kernel_info()["depth"] == depth
+    g.set_state(*st, t=0.0, a=1.1, ad=0.45, step=0)
+    g.evolve(10)
+    o.step(10)
+    compare_states(g, o, 10 * TOL[prec], f"march ty={ty} zr={zr} depth={depth} fp{prec}")
