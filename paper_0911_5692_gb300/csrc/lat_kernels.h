@@ -31,14 +31,21 @@ cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double
 // Register-prefetch z-march fused step (the default fast path).
 struct MarchConfig {
     int ty;        // owned rows per tile
-    int zr;        // planes per z-chunk
+    int zr;        // planes per z-chunk (the longest)
+    int nzc;       // z-chunks (balanced lengths)
     int depth;     // planes prefetched ahead (1..4)
     int threads;   // threads per block ((ty + 3) rows x 16-byte vectors)
     int maxt;      // launch-bound instance
     size_t smem;   // dynamic shared memory bytes
     int nyt;       // y tiles
     int blocks;    // blocks per step
+    int fast;      // 1: the instance specialised for this (N, ty) at depth 1
 };
+// kernel specialised for (element bytes, N, ty) at prefetch depth 1, or null
+const void* fast_kernel(int elem_bytes, int n, int ty);
+template <typename T>
+cudaError_t launch_step_fast(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
+                             const MarchConfig& cfg, cudaStream_t st);
 bool march_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
 template <typename T>
 cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,

@@ -25,36 +25,18 @@
 #include <algorithm>
 
 #include "lat_kernels.h"
+#include "lat_async.cuh"
 #include "lat_pairs.cuh"
 
 namespace lat {
 
 namespace {
 
-__device__ __forceinline__ int wrapn(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 
 struct MarchArgs {
-    int ty, zr, nyt, depth;
+    int ty, nzc, nyt, depth;
 };
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most `pending` of the most recent groups are still in flight
-__device__ __forceinline__ void cp_async_wait(int pending)
-{
-    switch (pending) {
-    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-    }
-}
 
 // Shared ring of the march for prefetch depth D: D+3 field-plane slots
 // [slot][field][ty+3 rows][n] (planes z-1, z, z+1 in use, D planes in flight),
@@ -82,7 +64,7 @@ __device__ __forceinline__ RingGeom ring_geom(int n, int ty, int depth)
 }
 
 template <typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT) step_march_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials,
+__global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1)) step_march_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials,
                                                           MarchArgs G)
 {
     typedef typename PK<T>::P P;
@@ -109,15 +91,18 @@ __global__ void __launch_bounds__(MAXT) step_march_kernel(Bufs<T> B, Model M, De
     const uint32_t offP = (uint32_t)(comp ? rho - 1 : 0) * n + x;   // in a momentum / new-field plane
 
     const int yt = blockIdx.x % G.nyt, zc = blockIdx.x / G.nyt;
-    const int y0 = yt * ty, z0 = zc * G.zr;
-    const int nz = min(z0 + G.zr, n) - z0;
+    // z chunks of balanced length: chunk c covers [c n / nzc, (c+1) n / nzc)
+    const int y0 = yt * ty, z0 = zc * n / G.nzc;
+    const int nz = (zc + 1) * n / G.nzc - z0;
     const uint32_t nn = (uint32_t)n * n;
     const uint32_t rowg = (uint32_t)wrapn(y0 - 1 + rho, n) * n + x;
-    const int par = (int)(sc->step & 1);
-    const T* const f0 = B.f[par][0];
-    const T* const f1 = B.f[par][1];
-    const T* const p0 = B.p[par][0];
-    const T* const p1 = B.p[par][1];
+    // ping-pong parity; buffers are selected with constant indices (a runtime
+    // index into the parameter block would copy it to local memory)
+    const bool par = (sc->step & 1) != 0;
+    const T* const f0 = par ? B.f[1][0] : B.f[0][0];
+    const T* const f1 = par ? B.f[1][1] : B.f[0][1];
+    const T* const p0 = par ? B.p[1][0] : B.p[0][0];
+    const T* const p1 = par ? B.p[1][1] : B.p[0][1];
 
     // f' += dt (cL Lap f + cF f - dV/df), f += dt f', with the 1/dx^2 of the
     // Laplacian folded into dt cL
@@ -128,16 +113,17 @@ __global__ void __launch_bounds__(MAXT) step_march_kernel(Bufs<T> B, Model M, De
     P accg0 = mk2(T(0), T(0)), accg1 = accg0, accvd = accg0, accvi = accg0;
 
     // copies of this thread's vectors of plane z0 + zrel: f into field slot
-    // (zrel + 1) mod (D+3), momenta into momentum slot zrel mod (D+1)
-    auto fetch_f = [&](int zrel) {          // zrel in [-1, nz + 1]
+    // (zrel + 1) mod (D+3), momenta into momentum slot zrel mod (D+1); the slot
+    // is passed in (kept as running counters, no division in the loop)
+    auto fetch_f = [&](int zrel, int slot) {          // zrel in [-1, nz + 1]
         const uint32_t gi = (uint32_t)wrapn(z0 + zrel, n) * nn + rowg;
-        T* d = S + (uint32_t)((zrel + 1) % R.rf) * R.slotF + offF;
+        T* d = S + (uint32_t)slot * R.slotF + offF;
         cp_async16(d, f0 + gi);
         cp_async16(d + R.fieldF, f1 + gi);
     };
-    auto fetch_p = [&](int zrel) {          // zrel in [0, nz]
+    auto fetch_p = [&](int zrel, int slot) {          // zrel in [0, nz]
         const uint32_t gi = (uint32_t)wrapn(z0 + zrel, n) * nn + rowg;
-        T* d = S + R.p0 + (uint32_t)(zrel % R.rp) * R.slotP + offP;
+        T* d = S + R.p0 + (uint32_t)slot * R.slotP + offP;
         cp_async16(d, p0 + gi);
         cp_async16(d + R.fieldP, p1 + gi);
     };
@@ -145,17 +131,23 @@ __global__ void __launch_bounds__(MAXT) step_march_kernel(Bufs<T> B, Model M, De
     // plane z0+1+j and momenta of z0+j. Iteration k then commits group D+k
     // (plane z0+1+D+k, momenta z0+D+k) and waits for group k first.
     if (live) {
-        fetch_f(-1);
-        fetch_f(0);
-        fetch_f(1);
-        if (comp) fetch_p(0);
+        fetch_f(-1, 0);
+        fetch_f(0, 1);
+        fetch_f(1, 2);
+        if (comp) fetch_p(0, 0);
     }
     cp_async_commit();
     for (int j = 1; j < D; j++) {
-        if (live && 1 + j <= nz + 1) fetch_f(1 + j);
-        if (comp && j <= nz) fetch_p(j);
+        if (live && 1 + j <= nz + 1) fetch_f(1 + j, 2 + j);
+        if (comp && j <= nz) fetch_p(j, j);
         cp_async_commit();
     }
+    // x neighbours in the adjacent lanes (same row, not wrapped), else shared memory
+    const int lane = t & 31;
+    const int qv = x / VW;
+    const bool nbl = qv > 0 && lane > 0, nbr = qv < Q - 1 && lane < 31;
+    int sf = 0, sp = 0;          // k mod (D+3), k mod (D+1)
+    auto addm = [](int a, int b, int m) { return a + b >= m ? a + b - m : a + b; };
 
     for (int k = 0; k <= nz; k++) {
         const bool ahead = k == nz;
@@ -164,31 +156,45 @@ __global__ void __launch_bounds__(MAXT) step_march_kernel(Bufs<T> B, Model M, De
         __syncthreads();
         // prefetch into the slots released by plane k-1 (every thread has passed
         // the barrier above)
-        if (live && k + 1 + D <= nz + 1) fetch_f(k + 1 + D);
-        if (comp && k + D <= nz) fetch_p(k + D);
+        if (live && k + 1 + D <= nz + 1) fetch_f(k + 1 + D, addm(sf, D + 2, R.rf));
+        if (comp && k + D <= nz) fetch_p(k + D, addm(sp, D, R.rp));
         cp_async_commit();
 
-        const T* Fm = S + (uint32_t)(k % R.rf) * R.slotF;
-        const T* Fc = S + (uint32_t)((k + 1) % R.rf) * R.slotF;
-        const T* Fp = S + (uint32_t)((k + 2) % R.rf) * R.slotF;
-        const T* Pc = S + R.p0 + (uint32_t)(k % R.rp) * R.slotP;
+        const T* Fm = S + (uint32_t)sf * R.slotF;
+        const T* Fc = S + (uint32_t)addm(sf, 1, R.rf) * R.slotF;
+        const T* Fp = S + (uint32_t)addm(sf, 2, R.rf) * R.slotF;
+        const T* Pc = S + R.p0 + (uint32_t)sp * R.slotP;
+        sf = addm(sf, 1, R.rf);
+        sp = addm(sp, 1, R.rp);
         T* Gw = S + R.g0 + (k & 1) * R.planeG;
         const T* Gr = S + R.g0 + ((k + 1) & 1) * R.planeG;
 
+        // centre vectors and their x neighbours (every lane takes part in the
+        // shuffles; halo rows load harmlessly)
+        P cen[2][NP];
+        T lefts[2], rights[2];
+#pragma unroll
+        for (int f = 0; f < 2; f++) {
+            const T* Ff = Fc + f * R.fieldF + offF;
+            PK<T>::ld(Ff, cen[f]);
+            lefts[f] = __shfl_up_sync(0xffffffffu, hi2(cen[f][NP - 1]), 1);
+            rights[f] = __shfl_down_sync(0xffffffffu, lo2(cen[f][0]), 1);
+            if (!nbl) lefts[f] = Ff[dl];
+            if (!nbr) rights[f] = Ff[dr];
+        }
         P g[2][NP];
         if (comp && !(ahead && rho == ty + 1)) {
-            P pn[2][NP], cen[2][NP];
+            P pn[2][NP];
 #pragma unroll
             for (int f = 0; f < 2; f++) {
                 const T* Ff = Fc + f * R.fieldF + offF;
                 P up[NP], dn[NP], zm[NP], zp[NP], pv[NP], lft[NP], rgt[NP];
-                PK<T>::ld(Ff, cen[f]);
                 PK<T>::ld(Ff - n, up);
                 PK<T>::ld(Ff + n, dn);
                 PK<T>::ld(Fm + f * R.fieldF + offF, zm);
                 PK<T>::ld(Fp + f * R.fieldF + offF, zp);
                 PK<T>::ld(Pc + f * R.fieldP + offP, pv);
-                const T left = Ff[dl], right = Ff[dr];
+                const T left = lefts[f], right = rights[f];
                 if constexpr (NP == 2) {
                     T c0, c1, c2, c3;
                     un2(cen[f][0], c0, c1);
@@ -228,10 +234,10 @@ __global__ void __launch_bounds__(MAXT) step_march_kernel(Bufs<T> B, Model M, De
             if (!ahead) {
                 if (own) {
                     const uint32_t gi = (uint32_t)z * nn + rowg;
-                    PK<T>::st(B.p[par ^ 1][0] + gi, pn[0]);
-                    PK<T>::st(B.p[par ^ 1][1] + gi, pn[1]);
-                    PK<T>::st(B.f[par ^ 1][0] + gi, g[0]);
-                    PK<T>::st(B.f[par ^ 1][1] + gi, g[1]);
+                    PK<T>::st((par ? B.p[0][0] : B.p[1][0]) + gi, pn[0]);
+                    PK<T>::st((par ? B.p[0][1] : B.p[1][1]) + gi, pn[1]);
+                    PK<T>::st((par ? B.f[0][0] : B.f[1][0]) + gi, g[0]);
+                    PK<T>::st((par ? B.f[0][1] : B.f[1][1]) + gi, g[1]);
                 }
                 PK<T>::st(Gw + offP, g[0]);
                 PK<T>::st(Gw + R.fieldG + offP, g[1]);
@@ -240,15 +246,23 @@ __global__ void __launch_bounds__(MAXT) step_march_kernel(Bufs<T> B, Model M, De
 
         // sums over the owned rows of plane k-1 (x and y pairs, potential) and the
         // z pair (k-1, k), from the new fields written one plane ago
-        if (k > 0 && own) {
+        if (k > 0) {
             P gq[2][NP];
+            T xnexts[2];
+#pragma unroll
+            for (int f = 0; f < 2; f++) {
+                const T* Gf = Gr + f * R.fieldG + offP;
+                PK<T>::ld(Gf, gq[f]);
+                xnexts[f] = __shfl_down_sync(0xffffffffu, lo2(gq[f][0]), 1);
+                if (!nbr) xnexts[f] = Gf[dr];
+            }
+            if (own) {
 #pragma unroll
             for (int f = 0; f < 2; f++) {
                 const T* Gf = Gr + f * R.fieldG + offP;
                 P yn[NP], xn[NP];
-                PK<T>::ld(Gf, gq[f]);
                 PK<T>::ld(Gf + n, yn);
-                const T xnext = Gf[dr];
+                const T xnext = xnexts[f];
                 if constexpr (NP == 2) {
                     T a, b, c, d;
                     un2(gq[f][0], a, b);
@@ -272,6 +286,7 @@ __global__ void __launch_bounds__(MAXT) step_march_kernel(Bufs<T> B, Model M, De
                 const P sq = mul2(gq[0][v], gq[0][v]);
                 accvd = quartic ? fma2(sq, sq, accvd) : add2(sq, accvd);
                 accvi = fma2(sq, mul2(gq[1][v], gq[1][v]), accvi);
+            }
             }
         }
     }
@@ -321,19 +336,41 @@ bool march_geom(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     const size_t smem = march_smem(n, esize, ty, depth);
     if (smem > 220 * 1024) return false;
     const int maxt = maxt_for(threads);
-    const void* fn = esize == 4 ? march_fn<float>(maxt) : march_fn<double>(maxt);
+    const void* fast = depth == 1 ? fast_kernel(esize, n, ty) : nullptr;
+    const void* fn = fast ? fast : esize == 4 ? march_fn<float>(maxt) : march_fn<double>(maxt);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
-    const int z = zr > 0 ? std::min(zr, n) : std::min(n, 32);
+    // z chunks: for a requested length zr, ceil(n / zr) balanced chunks; else the
+    // count that fills whole waves of resident blocks (nyt * nzc a multiple of
+    // the slots), weighing the per-chunk cost of its halo planes
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return false;
+    const long long slots = (long long)sms * occ;
+    const int nyt = n / ty;
+    int nzc = 1;
+    if (zr > 0) {
+        nzc = (n + std::min(zr, n) - 1) / std::min(zr, n);
+    } else {
+        double best = 1e30;
+        for (int c = 1; c <= std::max(1, n / 8); c++) {
+            const long long b = (long long)nyt * c;
+            const double waves = (double)((b + slots - 1) / slots);
+            const double score = waves * slots / b * (1.0 + 2.0 / ((double)n / c));
+            if (score < best - 1e-12) { best = score; nzc = c; }
+        }
+    }
     cfg->ty = ty;
-    cfg->zr = z;
+    cfg->zr = (n + nzc - 1) / nzc;
+    cfg->nzc = nzc;
     cfg->depth = depth;
     cfg->threads = threads;
     cfg->maxt = maxt;
+    cfg->fast = fast ? 1 : 0;
     cfg->smem = smem;
-    cfg->nyt = n / ty;
-    cfg->blocks = (n / ty) * ((n + z - 1) / z);
+    cfg->nyt = nyt;
+    cfg->blocks = nyt * nzc;
     return true;
 }
 
@@ -343,7 +380,7 @@ bool march_geom(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
 // row) whose block fits in 1024 threads.
 bool march_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg)
 {
-    const int d = depth > 0 ? depth : 2;
+    const int d = depth > 0 ? depth : 1;
     if (ty > 0) return march_geom(n, elem_bytes, ty, zr, d, cfg);
     const int tys[] = {16, 8, 4, 2, 1};
     for (int t : tys)
@@ -355,7 +392,8 @@ template <typename T>
 cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                               const MarchConfig& cfg, cudaStream_t st)
 {
-    MarchArgs G{cfg.ty, cfg.zr, cfg.nyt, cfg.depth};
+    if (cfg.fast) return launch_step_fast<T>(b, M, sc, partials, cfg, st);
+    MarchArgs G{cfg.ty, cfg.nzc, cfg.nyt, cfg.depth};
     switch (cfg.maxt) {
     case 448: step_march_kernel<T, 448><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
     case 512: step_march_kernel<T, 512><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
