@@ -173,6 +173,30 @@ lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
  * out[4] = kernels launched per step, out[5] = ty, out[6] = zr, out[7] = depth. */
 lat_status lat_kernel_info(lat_handle* h, int64_t out[8]);
 
+/* Volume sums of two field arrays without allocating device memory. The paper
+ * has no counterpart; this is for callers that cannot call cudaMalloc (device
+ * memory already reserved by another allocator such as a framework's caching
+ * pool, a fixed memory budget, or code that cannot take cudaMalloc's implicit
+ * device-wide synchronisation).
+ * f_phi, f_chi: device arrays of n^3 elements (float for precision 32, double
+ * for 64), layout as in lat_get_state; model: LAT_MODEL_*; L: box side. Writes
+ * to out_dev (device, 4 doubles, caller-owned) the averages <|grad f_phi|^2>,
+ * <|grad f_chi|^2> (forward differences / dx^2), <f_phi^beta/beta> and
+ * <f_phi^2 f_chi^2 / 2>: the same values lat_get_scalars reports in out[4..7]
+ * for a handle holding these fields. Asynchronous on cuda_stream (a
+ * cudaStream_t; NULL = legacy default stream).
+ * Scratch: one static device array per GPU (about 33 KB, held by every GPU that
+ * loads the library until the process exits); it calls no cudaMalloc, cudaFree
+ * or allocating library routine. The first call on a device looks the array up
+ * with cudaGetSymbolAddress and clears it, synchronously; make that first call
+ * before any stream capture. Every call shares the array, so calls that overlap
+ * on the GPU (different streams or threads without ordering) race and give
+ * wrong sums. Errors: LAT_EINVAL for null pointers or n not a multiple of 4 in
+ * [4, ...], bad precision, model or L; LAT_EUNSUPPORTED for n > 1024 (the
+ * largest lattice this scratch serves); LAT_ECUDA if the set-up or launch fails. */
+lat_status lat_field_sums_static(const void* f_phi, const void* f_chi, int n, int precision, int model, double L,
+                                 double* out_dev, void* cuda_stream);
+
 /* Release the handle and the buffers it owns. NULL is accepted. */
 void lat_destroy(lat_handle* h);
 

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "LAT_OK", 1: "LAT_EINVAL", 2: "LAT_ECFL", 3: "LAT_ENOMEM", 4:
 EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evolve", "lat_energies",
             "lat_spectrum", "lat_get_state", "lat_set_state", "lat_get_scalars", "lat_set_scalars",
             "lat_sync", "lat_set_kernel", "lat_kernel_info", "lat_destroy", "lat_status_string",
-            "lat_checkpoint_bytes", "lat_save_checkpoint", "lat_load_checkpoint")
+            "lat_checkpoint_bytes", "lat_save_checkpoint", "lat_load_checkpoint", "lat_field_sums_static")
 
 
 class LatParams(C.Structure):
@@ -85,6 +85,7 @@ def load_library(build_if_missing: bool = True):
             L.lat_checkpoint_bytes.argtypes = [P, C.POINTER(C.c_uint64)]
             L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
             L.lat_load_checkpoint.argtypes = [P, P, C.c_uint64]
+            L.lat_field_sums_static.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_double, P, P]
             L.lat_destroy.argtypes = [P]
             L.lat_destroy.restype = None
             L.lat_status_string.argtypes = [C.c_int]
@@ -94,6 +95,20 @@ def load_library(build_if_missing: bool = True):
                     getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
+
+
+def field_sums_static(f_phi, f_chi, n: int, precision: int, model: int, L: float, out, stream=None):
+    """Marshal lat_field_sums_static: torch CUDA tensors in, a CUDA float64 tensor
+    of 4 elements out (written asynchronously on ``stream``, a torch.cuda.Stream
+    or None for the current stream). The call allocates no device memory; see
+    include/lattice.h for its scratch rules."""
+    import torch
+    L_ = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = L_.lat_field_sums_static(C.c_void_p(f_phi.data_ptr()), C.c_void_p(f_chi.data_ptr()), int(n),
+                                  int(precision), int(model), float(L), C.c_void_p(out.data_ptr()),
+                                  C.c_void_p(s.cuda_stream))
+    _check(st, "lat_field_sums_static")
 
 
 def make_params(d: dict) -> LatParams:
