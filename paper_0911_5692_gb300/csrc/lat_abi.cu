@@ -650,7 +650,7 @@ lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, doub
 namespace {
 
 struct CkptHeader {
-    char magic[8];       // "LATCKPT1"
+    char magic[8];       // "LATCKPT2"
     uint64_t bytes;      // whole blob
     uint32_t scalars_bytes;
     uint32_t esize;
@@ -682,7 +682,7 @@ lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes)
     if (s.status != LAT_OK) return (lat_status)s.status;
     CkptHeader hd;
     std::memset(&hd, 0, sizeof(hd));
-    std::memcpy(hd.magic, "LATCKPT1", 8);
+    std::memcpy(hd.magic, "LATCKPT2", 8);
     hd.bytes = bytes;
     hd.scalars_bytes = sizeof(DevScalars);
     hd.esize = (uint32_t)h->esize;
@@ -704,7 +704,7 @@ lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes)
     if (!h || !src || bytes != ckpt_bytes(h)) return LAT_EINVAL;
     CkptHeader hd;
     std::memcpy(&hd, src, sizeof(hd));
-    if (std::memcmp(hd.magic, "LATCKPT1", 8) != 0 || hd.bytes != bytes || hd.scalars_bytes != sizeof(DevScalars) ||
+    if (std::memcmp(hd.magic, "LATCKPT2", 8) != 0 || hd.bytes != bytes || hd.scalars_bytes != sizeof(DevScalars) ||
         hd.esize != h->esize || std::memcmp(&hd.params, &h->p, sizeof(lat_params)) != 0)
         return LAT_EINVAL;
     DevScalars s;

@@ -43,7 +43,18 @@ struct DevScalars {
     unsigned int ticket; // last-block counter of the step kernel
     unsigned int ticket2;
     int pad;
+    double kd[5];    // step coefficients dt cL/dx^2, dt cF, -dt cdom, -dt kappa, dt
+    float kf[5];     // the same rounded once to FP32 for the FP32 kernels
+    int pad2;
 };
+
+// Step coefficient i for element type T (kd / kf above).
+template <typename T>
+__device__ __forceinline__ T step_coef(const DevScalars* sc, int i);
+template <>
+__device__ __forceinline__ float step_coef<float>(const DevScalars* sc, int i) { return sc->kf[i]; }
+template <>
+__device__ __forceinline__ double step_coef<double>(const DevScalars* sc, int i) { return sc->kd[i]; }
 
 // Number of sums reduced per block: grad^2 of each field (unscaled by 1/dx^2),
 // sum f0^beta/beta, sum f0^2 f1^2 / 2.
@@ -73,6 +84,71 @@ __device__ __forceinline__ void block_reduce(double v[kSums], double* red)
     __syncthreads();
 }
 
+// Block reduction of FP32 per-thread sums: a fixed FP32 shuffle tree within
+// each warp (32 terms, relative rounding error a few FP32 ulp, far below that
+// of the per-thread accumulations), then warp 0 folds the warp totals in FP64 in
+// warp order. FP64 arithmetic runs at a small fraction of the FP32 rate, so
+// only one warp of the block touches it. Result in out[] of thread 0.
+__device__ __forceinline__ void block_reduce(float v[kSums], double* red, double out[kSums])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < kSums; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kSums; k++) red[warp * kSums + k] = (double)v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < kSums; k++) {
+            double w = lane < nwarps ? red[lane * kSums + k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+            out[k] = w;
+        }
+    }
+}
+
+// FP64 per-thread sums: block_reduce above in FP64 throughout.
+__device__ __forceinline__ void block_reduce(double v[kSums], double* red, double out[kSums])
+{
+    block_reduce(v, red);
+#pragma unroll
+    for (int k = 0; k < kSums; k++) out[k] = v[k];
+}
+
+// a^p. The exponents of the two models' rescalings (Sec. II.B) are integers
+// for which repeated multiplication is exact to a few ulp and costs a handful
+// of FP64 multiplies instead of a general pow on the slow FP64 pipe.
+__device__ inline double apow(double a, double p)
+{
+    if (p == rint(p) && fabs(p) <= 16.0) {
+        int e = (int)fabs(p);
+        double r = 1.0, b = a;
+        while (e) {
+            if (e & 1) r *= b;
+            b *= b;
+            e >>= 1;
+        }
+        return p < 0.0 ? 1.0 / r : r;
+    }
+    return pow(a, p);
+}
+
+// The per-step coefficients of eq. scalar-evo as the step kernels use them.
+__device__ inline void step_coefficients(const Model& M, DevScalars* sc)
+{
+    sc->kd[0] = M.dt * sc->cL * M.inv_dx2;
+    sc->kd[1] = M.dt * sc->cF;
+    sc->kd[2] = -M.dt * sc->cdom;
+    sc->kd[3] = -M.dt * sc->kappa;
+    sc->kd[4] = M.dt;
+    for (int i = 0; i < 5; i++) sc->kf[i] = (float)sc->kd[i];
+}
+
 // Scale-factor update of Sec. II.B, eq. scale, with the staggered a':
 // a''_{n+1/2} = q a'_{n+1/2}^2 + c, q = -(s+2)/a, a'_{n+1/2} = (a'_n + a'_{n+1})/2,
 // c = (8piG/A^2) a^(-2s-2r-1) ((S0+S1)/3 + a^(2s+2) <V_pr>).
@@ -84,16 +160,17 @@ __device__ __forceinline__ void block_reduce(double v[kSums], double* red)
 __device__ inline void scale_solve(const Model& M, DevScalars* sc)
 {
     const double a = sc->a;
-    sc->cdom = M.cdom0 * pow(a, M.pdom);
-    sc->kappa = M.kappa0 * pow(a, M.pint);
+    sc->cdom = M.cdom0 * apow(a, M.pdom);
+    sc->kappa = M.kappa0 * apow(a, M.pint);
     if (!M.expansion) {
         sc->ad_next = 0.0; sc->ad_half = 0.0; sc->add = 0.0;
         sc->cL = 1.0; sc->cF = 0.0;
+        step_coefficients(M, sc);
         return;
     }
     const double vpr = sc->cdom * sc->S[2] + sc->kappa * sc->S[3];
-    const double c = M.eight_pi_G / (M.A * M.A) * pow(a, -2.0 * M.s - 2.0 * M.r - 1.0)
-                   * ((sc->S[0] + sc->S[1]) / 3.0 + pow(a, 2.0 * M.s + 2.0) * vpr);
+    const double c = M.eight_pi_G / (M.A * M.A) * apow(a, -2.0 * M.s - 2.0 * M.r - 1.0)
+                   * ((sc->S[0] + sc->S[1]) / 3.0 + apow(a, 2.0 * M.s + 2.0) * vpr);
     const double q = -(M.s + 2.0) / a;
     const double alpha = M.dt * q * 0.25;
     const double gamma = 2.0 * sc->ad + M.dt * c;
@@ -106,21 +183,26 @@ __device__ inline void scale_solve(const Model& M, DevScalars* sc)
     sc->ad_half = 0.5 * y;
     sc->ad_next = y - sc->ad;
     sc->add = q * sc->ad_half * sc->ad_half + c;
-    sc->cL = pow(a, -2.0 * M.s - 2.0);
+    sc->cL = apow(a, -2.0 * M.s - 2.0);
     const double h = sc->ad_half / a;
     sc->cF = M.r * (M.s - M.r + 2.0) * h * h + M.r * sc->add / a;
+    step_coefficients(M, sc);
 }
 
-// Fixed-order reduction of the per-block partials by the block that finished
-// last; writes the averages at the new field time into sc->S.
-__device__ inline void reduce_partials(const Model& M, const double* partials, int nblocks, double* red,
-                                       double out[kSums])
+// Fixed-order reduction of the per-block partials by warp 0 of the block that
+// finished last (lane l folds blocks l, l+32, ..., then a fixed shuffle tree);
+// writes the averages at the new field time into out[] of thread 0.
+__device__ inline void reduce_partials(const Model& M, const double* partials, int nblocks, double out[kSums])
 {
+    if (threadIdx.x >= 32) return;
     double v[kSums] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int b = threadIdx.x; b < nblocks; b += 32)
 #pragma unroll
         for (int k = 0; k < kSums; k++) v[k] += __ldcg(partials + (size_t)b * kSums + k);
-    block_reduce(v, red);
+#pragma unroll
+    for (int k = 0; k < kSums; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if (threadIdx.x == 0) {
         out[0] = v[0] * M.inv_dx2 * M.inv_sites;
         out[1] = v[1] * M.inv_dx2 * M.inv_sites;
@@ -132,16 +214,19 @@ __device__ inline void reduce_partials(const Model& M, const double* partials, i
 // Write this block's partial sums, and let the last block of the launch fold
 // all partials and advance the FP64 scalars: a_{n+3/2} = a_{n+1/2} + dt a'_{n+1},
 // then the a' solve and coefficients for the next step. `advance` is false for
-// the sums-only pass that follows initialisation or a state upload.
-__device__ inline void finish_block(const Model& M, DevScalars* sc, double* partials, double v[kSums],
+// the sums-only pass that follows initialisation or a state upload. The
+// per-thread sums are float (FP32 kernels) or double.
+template <typename A>
+__device__ inline void finish_block(const Model& M, DevScalars* sc, double* partials, A v[kSums],
                                     double* red, bool advance)
 {
     const int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    block_reduce(v, red);
+    double bs[kSums];
+    block_reduce(v, red, bs);
     __shared__ unsigned int is_last;
     if (threadIdx.x == 0) {
-        for (int k = 0; k < kSums; k++) partials[(size_t)bid * kSums + k] = v[k];
+        for (int k = 0; k < kSums; k++) partials[(size_t)bid * kSums + k] = bs[k];
         __threadfence();
         unsigned int t = atomicAdd(&sc->ticket, 1u);
         is_last = (t == (unsigned int)nblocks - 1u);
@@ -150,7 +235,7 @@ __device__ inline void finish_block(const Model& M, DevScalars* sc, double* part
     if (!is_last) return;
     __threadfence();
     double S[kSums];
-    reduce_partials(M, partials, nblocks, red, S);
+    reduce_partials(M, partials, nblocks, S);
     if (threadIdx.x == 0) {
         sc->ticket = 0u;
         bool finite = true;

@@ -39,10 +39,11 @@ struct MarchConfig {
     size_t smem;   // dynamic shared memory bytes
     int nyt;       // y tiles
     int blocks;    // blocks per step
-    int fast;      // 1: the instance specialised for this (N, ty) at depth 1
+    int fast;      // 1: the instance specialised for this (N, ty, depth)
 };
-// kernel specialised for (element bytes, N, ty) at prefetch depth 1, or null
-const void* fast_kernel(int elem_bytes, int n, int ty);
+// kernel specialised for (element bytes, N, ty, depth), or null; *smem gets its
+// dynamic shared memory in bytes
+const void* fast_kernel(int elem_bytes, int n, int ty, int depth, size_t* smem);
 template <typename T>
 cudaError_t launch_step_fast(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                              const MarchConfig& cfg, cudaStream_t st);

@@ -1,16 +1,15 @@
 // lat_step_fast.cu -- the z-march step of lat_step_march.cu specialised for a
-// lattice side N, a tile height TY and a prefetch depth of one plane known at
-// compile time.
+// lattice side N, a tile height TY and a prefetch depth D (planes in flight
+// ahead of the one being computed) known at compile time.
 //
-// Same algorithm, same shared-memory ring and the same results as the general
-// kernel (Sec. II.B, eq. evo with eq. scalar-evo and the sums for eq. scale).
-// With N and TY constant, every shared-memory stride folds into an immediate
-// offset; the plane loop is unrolled by the ring period (4 field slots,
-// 2 momentum slots, 2 new-field buffers) so every slot index is a constant;
-// and because a row of 16-byte vectors spans whole warps (N/4 or N/2 a multiple
-// of 32), each warp has one role (halo row, owned row or look-ahead row) and
-// its branches are uniform. This removes the integer and bookkeeping work that
-// dominated the general kernel's instruction count.
+// Same algorithm and the same results as the general kernel (Sec. II.B, eq. evo
+// with eq. scalar-evo and the sums for eq. scale). With N and TY constant every
+// shared-memory stride folds into an immediate offset; the ring holds RF field
+// slots (D + 3 planes in use, padded so the ring period is small), RP = D + 1
+// momentum slots and 2 new-field buffers, and the plane loop is unrolled by the
+// period lcm(RF, RP, 2) so every slot index is a constant; and because a row of
+// 16-byte vectors spans whole warps (N/4 or N/2 a multiple of 32), each warp has
+// one role (halo row, owned row or look-ahead row) and its branches are uniform.
 #include "lat_async.cuh"
 #include "lat_kernels.h"
 #include "lat_pairs.cuh"
@@ -19,9 +18,18 @@ namespace lat {
 
 namespace {
 
-template <typename T, int N, int TY>
+template <int D>
+struct Ring {
+    static constexpr int RF = D == 1 ? 4 : (D == 2 ? 6 : 6);   // field plane slots (>= D + 3)
+    static constexpr int RP = D + 1;                           // momentum plane slots
+    static constexpr int PERIOD = D == 1 ? 4 : 6;              // lcm(RF, RP, 2)
+    static_assert(RF >= D + 3 && PERIOD % RF == 0 && PERIOD % RP == 0 && PERIOD % 2 == 0, "ring period");
+};
+
+template <typename T, int N, int TY, int D>
 struct Fast {
     typedef typename PK<T>::P P;
+    static constexpr int RF = Ring<D>::RF, RP = Ring<D>::RP, PERIOD = Ring<D>::PERIOD;
     static constexpr int NP = PK<T>::NP;
     static constexpr int VW = 2 * NP;
     static constexpr int Q = N / VW;               // vectors per row
@@ -29,7 +37,8 @@ struct Fast {
     static constexpr int THREADS = (TY + 3) * Q;
     static constexpr uint32_t FIELDF = (TY + 3) * N, SLOTF = 2 * FIELDF;   // field slot [field][TY+3][N]
     static constexpr uint32_t FIELDP = (TY + 1) * N, SLOTP = 2 * FIELDP;   // momentum slot / new-field plane
-    static constexpr uint32_t P0 = 4 * SLOTF, G0 = P0 + 2 * SLOTP;
+    static constexpr uint32_t P0 = RF * SLOTF, G0 = P0 + RP * SLOTP;
+    static constexpr size_t SMEM = sizeof(T) * (size_t)(G0 + 2 * SLOTP);
     static constexpr uint32_t NN = (uint32_t)N * N;
     static_assert(Q % 32 == 0, "rows must span whole warps");
 
@@ -59,25 +68,28 @@ struct Fast {
         cp_async16(d + FIELDP, C.p1 + gi);
     }
 
-    // plane k = 4m + J of the chunk
+    // plane k = PERIOD m + J of the chunk. Field plane z0 + j lives in slot
+    // (j + 1) % RF, momentum plane z0 + j in slot j % RP; plane k fetches the
+    // fields of k + D + 1 and the momenta of k + D, after waiting for the group
+    // committed D planes ago (fields k + 1, momenta k).
     template <int J>
     static __device__ __forceinline__ void plane(Ctx& C, int k)
     {
         const bool ahead = k == C.nz;
         const bool comp = C.rho >= 1 && C.rho <= TY + 1;   // warp-uniform
         const bool own = C.rho >= 1 && C.rho <= TY;
-        cp_async_wait(0);
+        cp_async_wait(D - 1);
         __syncthreads();
-        if (k < C.nz) {
-            fetch_f(C, k + 2, (J + 3) & 3);
-            if (comp) fetch_p(C, k + 1, (J + 1) & 1);
+        if (k + D <= C.nz) {
+            fetch_f(C, k + D + 1, (J + D + 2) % RF);
+            if (comp) fetch_p(C, k + D, (J + D) % RP);
         }
         cp_async_commit();
 
-        const T* Fm = C.S + J * SLOTF;
-        const T* Fc = C.S + ((J + 1) & 3) * SLOTF;
-        const T* Fp = C.S + ((J + 2) & 3) * SLOTF;
-        const T* Pc = C.S + P0 + (J & 1) * SLOTP;
+        const T* Fm = C.S + (J % RF) * SLOTF;
+        const T* Fc = C.S + ((J + 1) % RF) * SLOTF;
+        const T* Fp = C.S + ((J + 2) % RF) * SLOTF;
+        const T* Pc = C.S + P0 + (J % RP) * SLOTP;
         T* Gw = C.S + G0 + (J & 1) * SLOTP;
         const T* Gr = C.S + G0 + ((J + 1) & 1) * SLOTP;
 
@@ -188,13 +200,23 @@ struct Fast {
             }
         }
     }
+
+    // planes k + J .. k + PERIOD - 1; false once the look-ahead plane is done
+    template <int J>
+    static __device__ __forceinline__ bool planes(Ctx& C, int k)
+    {
+        plane<J>(C, k + J);
+        if (k + J + 1 > C.nz) return false;
+        if constexpr (J + 1 < PERIOD) return planes<J + 1>(C, k);
+        else return true;
+    }
 };
 
-template <typename T, int N, int TY>
-__global__ void __launch_bounds__(Fast<T, N, TY>::THREADS, (Fast<T, N, TY>::THREADS <= 512 ? 2 : 1))
-    step_fast_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, int nzc, int nyt)
+template <typename T, int N, int TY, int D>
+__global__ void __launch_bounds__(Fast<T, N, TY, D>::THREADS, (Fast<T, N, TY, D>::THREADS <= 512 ? 2 : 1))
+    step_fast_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials)
 {
-    typedef Fast<T, N, TY> F;
+    typedef Fast<T, N, TY, D> F;
     typedef typename F::P P;
     constexpr int VW = F::VW;
     __shared__ double red[32 * kSums];
@@ -211,12 +233,6 @@ __global__ void __launch_bounds__(Fast<T, N, TY>::THREADS, (Fast<T, N, TY>::THRE
     C.dr = x + VW == N ? VW - N : VW;                        // right neighbour of the last site
     C.offF = (uint32_t)C.rho * N + x;
     C.offP = (uint32_t)(C.rho >= 1 && C.rho <= TY + 1 ? C.rho - 1 : 0) * N + x;
-    const int yt = blockIdx.x % nyt, zc = blockIdx.x / nyt;
-    const int y0 = yt * TY;
-    // z chunks of balanced length: chunk c covers [c N / nzc, (c+1) N / nzc)
-    C.z0 = zc * N / nzc;
-    C.nz = (zc + 1) * N / nzc - C.z0;
-    C.rowg = (uint32_t)wrapn(y0 - 1 + C.rho, N) * N + x;
     // buffers selected with constant indices (a runtime index into the
     // parameter block would copy it to local memory)
     const bool par = (sc->step & 1) != 0;
@@ -229,9 +245,9 @@ __global__ void __launch_bounds__(Fast<T, N, TY>::THREADS, (Fast<T, N, TY>::THRE
     C.op0 = par ? B.p[0][0] : B.p[1][0];
     C.op1 = par ? B.p[0][1] : B.p[1][1];
     // f' += dt (cL Lap f + cF f - dV/df), f += dt f', with 1/dx^2 folded into dt cL
-    const T dt_s = (T)M.dt;
-    const T dtcl = (T)(M.dt * sc->cL * M.inv_dx2), dtcf = (T)(M.dt * sc->cF);
-    const T mdtcdom = (T)(-M.dt * sc->cdom), mdtkap = (T)(-M.dt * sc->kappa);
+    const T dt_s = step_coef<T>(sc, 4);
+    const T dtcl = step_coef<T>(sc, 0), dtcf = step_coef<T>(sc, 1);
+    const T mdtcdom = step_coef<T>(sc, 2), mdtkap = step_coef<T>(sc, 3);
     C.dtcl2 = mk2(dtcl, dtcl);
     C.dtcf2 = mk2(dtcf, dtcf);
     C.dt2 = mk2(dt_s, dt_s);
@@ -240,46 +256,69 @@ __global__ void __launch_bounds__(Fast<T, N, TY>::THREADS, (Fast<T, N, TY>::THRE
     C.quartic = M.beta == 4;
     C.accg0 = C.accg1 = C.accvd = C.accvi = mk2(T(0), T(0));
 
-    // prologue: planes z0-1, z0, z0+1 into field slots 0..2, momenta of z0 into slot 0
-    F::fetch_f(C, -1, 0);
-    F::fetch_f(C, 0, 1);
-    F::fetch_f(C, 1, 2);
-    if (C.rho >= 1 && C.rho <= TY + 1) F::fetch_p(C, 0, 0);
-    cp_async_commit();
-    for (int k = 0;; k += 4) {
-        F::template plane<0>(C, k);
-        if (k + 1 > C.nz) break;
-        F::template plane<1>(C, k + 1);
-        if (k + 2 > C.nz) break;
-        F::template plane<2>(C, k + 2);
-        if (k + 3 > C.nz) break;
-        F::template plane<3>(C, k + 3);
-        if (k + 4 > C.nz) break;
+    // Work: the (N / TY) * N (y tile, z plane) units in tile-major order; block
+    // b takes units [b U / B, (b+1) U / B) and marches them as one segment per y
+    // tile it touches (B = (N / TY) * c gives c balanced z chunks per tile).
+    constexpr long long U = (long long)(N / TY) * N;
+    long long u = (long long)blockIdx.x * U / gridDim.x;
+    const long long uend = ((long long)blockIdx.x + 1) * U / gridDim.x;
+    const bool comp = C.rho >= 1 && C.rho <= TY + 1;
+    for (bool first = true; u < uend; first = false) {
+        const int yt = (int)(u / N);
+        C.z0 = (int)(u - (long long)yt * N);
+        C.nz = (int)min((long long)(N - C.z0), uend - u);
+        u += C.nz;
+        C.rowg = (uint32_t)wrapn(yt * TY - 1 + C.rho, N) * N + x;
+        // the previous segment's last plane is read by every thread before the
+        // prologue refills the ring
+        if (!first) __syncthreads();
+        // prologue: group 0 holds field planes z0-1, z0, z0+1 and momenta z0;
+        // group j (1 <= j < D) the fields of z0+1+j and the momenta of z0+j
+        // (planes past the segment wrap harmlessly and go unused)
+        F::fetch_f(C, -1, 0);
+        F::fetch_f(C, 0, 1);
+        F::fetch_f(C, 1, 2);
+        if (comp) F::fetch_p(C, 0, 0);
+        cp_async_commit();
+#pragma unroll
+        for (int j = 1; j < D; j++) {
+            F::fetch_f(C, j + 1, j + 2);
+            if (comp) F::fetch_p(C, j, j);
+            cp_async_commit();
+        }
+        for (int k = 0; F::template planes<0>(C, k); k += F::PERIOD) {}
     }
 
-    double v[kSums] = {(double)lo2(C.accg0) + (double)hi2(C.accg0), (double)lo2(C.accg1) + (double)hi2(C.accg1),
-                       ((double)lo2(C.accvd) + (double)hi2(C.accvd)) * (C.quartic ? 0.25 : 0.5),
-                       0.5 * ((double)lo2(C.accvi) + (double)hi2(C.accvi))};
+    // per-thread sums in the element type (the 1/beta and 1/2 factors are
+    // powers of two, exact); the block folds them as finish_block describes
+    T v[kSums] = {lo2(C.accg0) + hi2(C.accg0), lo2(C.accg1) + hi2(C.accg1),
+                  (lo2(C.accvd) + hi2(C.accvd)) * (C.quartic ? T(0.25) : T(0.5)),
+                  T(0.5) * (lo2(C.accvi) + hi2(C.accvi))};
     finish_block(M, sc, partials, v, red, true);
 }
 
-// Specialised instances: (element bytes, N, TY).
+// Specialised instances: (element bytes, N, TY, D).
 struct FastKey {
-    int esize, n, ty;
+    int esize, n, ty, depth;
 };
-constexpr FastKey kFast[] = {{4, 128, 4}, {4, 128, 8}, {4, 256, 4}, {4, 256, 8}, {4, 512, 2}, {4, 512, 4},
-                             {8, 256, 4}, {8, 512, 1}};
+constexpr FastKey kFast[] = {{4, 128, 4, 1}, {4, 128, 8, 1}, {4, 256, 4, 1}, {4, 256, 8, 1}, {4, 512, 2, 1},
+                             {4, 512, 4, 1}, {4, 128, 8, 2}, {4, 256, 4, 2}, {4, 256, 8, 2}, {4, 512, 2, 2},
+                             {8, 256, 4, 1}, {8, 512, 1, 1}};
 
 template <typename T>
-const void* fast_fn(int n, int ty)
+const void* fast_fn(int n, int ty, int depth, size_t* smem)
 {
-#define LAT_FAST_CASE(NN, TT) \
-    if (n == NN && ty == TT) return (const void*)step_fast_kernel<T, NN, TT>;
+#define LAT_FAST_CASE(NN, TT, DD)                                  \
+    if (n == NN && ty == TT && depth == DD) {                      \
+        *smem = Fast<T, NN, TT, DD>::SMEM;                         \
+        return (const void*)step_fast_kernel<T, NN, TT, DD>;       \
+    }
     if constexpr (sizeof(T) == 4) {
-        LAT_FAST_CASE(128, 4) LAT_FAST_CASE(128, 8) LAT_FAST_CASE(256, 4) LAT_FAST_CASE(256, 8)
-        LAT_FAST_CASE(512, 2) LAT_FAST_CASE(512, 4)
+        LAT_FAST_CASE(128, 4, 1) LAT_FAST_CASE(128, 8, 1) LAT_FAST_CASE(256, 4, 1) LAT_FAST_CASE(256, 8, 1)
+        LAT_FAST_CASE(512, 2, 1) LAT_FAST_CASE(512, 4, 1)
+        LAT_FAST_CASE(128, 8, 2) LAT_FAST_CASE(256, 4, 2) LAT_FAST_CASE(256, 8, 2) LAT_FAST_CASE(512, 2, 2)
     } else {
-        LAT_FAST_CASE(256, 4) LAT_FAST_CASE(512, 1)
+        LAT_FAST_CASE(256, 4, 1) LAT_FAST_CASE(512, 1, 1)
     }
 #undef LAT_FAST_CASE
     return nullptr;
@@ -287,11 +326,11 @@ const void* fast_fn(int n, int ty)
 
 } // namespace
 
-const void* fast_kernel(int elem_bytes, int n, int ty)
+const void* fast_kernel(int elem_bytes, int n, int ty, int depth, size_t* smem)
 {
     for (const FastKey& k : kFast)
-        if (k.esize == elem_bytes && k.n == n && k.ty == ty)
-            return elem_bytes == 4 ? fast_fn<float>(n, ty) : fast_fn<double>(n, ty);
+        if (k.esize == elem_bytes && k.n == n && k.ty == ty && k.depth == depth)
+            return elem_bytes == 4 ? fast_fn<float>(n, ty, depth, smem) : fast_fn<double>(n, ty, depth, smem);
     return nullptr;
 }
 
@@ -299,9 +338,10 @@ template <typename T>
 cudaError_t launch_step_fast(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                              const MarchConfig& cfg, cudaStream_t st)
 {
-    const void* fn = fast_fn<T>(M.n, cfg.ty);
+    size_t smem = 0;
+    const void* fn = fast_fn<T>(M.n, cfg.ty, cfg.depth, &smem);
     if (!fn) return cudaErrorInvalidValue;
-    void* args[] = {(void*)&b, (void*)&M, (void*)&sc, (void*)&partials, (void*)&cfg.nzc, (void*)&cfg.nyt};
+    void* args[] = {(void*)&b, (void*)&M, (void*)&sc, (void*)&partials};
     return cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
 }
 

@@ -90,12 +90,15 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1)) step_march_kernel
     const uint32_t offF = (uint32_t)rho * n + x;            // this vector in a field plane
     const uint32_t offP = (uint32_t)(comp ? rho - 1 : 0) * n + x;   // in a momentum / new-field plane
 
-    const int yt = blockIdx.x % G.nyt, zc = blockIdx.x / G.nyt;
-    // z chunks of balanced length: chunk c covers [c n / nzc, (c+1) n / nzc)
-    const int y0 = yt * ty, z0 = zc * n / G.nzc;
-    const int nz = (zc + 1) * n / G.nzc - z0;
+    // Work: the nyt * n (y tile, z plane) units in tile-major order; block b
+    // takes units [b U / B, (b+1) U / B) and marches them as one segment per y
+    // tile it touches (B = nyt * c gives c balanced z chunks per tile).
+    const long long U = (long long)G.nyt * n;
+    long long u = (long long)blockIdx.x * U / gridDim.x;
+    const long long uend = ((long long)blockIdx.x + 1) * U / gridDim.x;
+    int z0 = 0, nz = 0;
+    uint32_t rowg = 0;
     const uint32_t nn = (uint32_t)n * n;
-    const uint32_t rowg = (uint32_t)wrapn(y0 - 1 + rho, n) * n + x;
     // ping-pong parity; buffers are selected with constant indices (a runtime
     // index into the parameter block would copy it to local memory)
     const bool par = (sc->step & 1) != 0;
@@ -106,9 +109,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1)) step_march_kernel
 
     // f' += dt (cL Lap f + cF f - dV/df), f += dt f', with the 1/dx^2 of the
     // Laplacian folded into dt cL
-    const T dt_s = (T)M.dt;
-    const T dtcl = (T)(M.dt * sc->cL * M.inv_dx2), dtcf = (T)(M.dt * sc->cF);
-    const T mdtcdom = (T)(-M.dt * sc->cdom), mdtkap = (T)(-M.dt * sc->kappa);
+    const T dt_s = step_coef<T>(sc, 4);
+    const T dtcl = step_coef<T>(sc, 0), dtcf = step_coef<T>(sc, 1);
+    const T mdtcdom = step_coef<T>(sc, 2), mdtkap = step_coef<T>(sc, 3);
     const bool quartic = M.beta == 4;
     P accg0 = mk2(T(0), T(0)), accg1 = accg0, accvd = accg0, accvi = accg0;
 
@@ -127,173 +130,186 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1)) step_march_kernel
         cp_async16(d, p0 + gi);
         cp_async16(d + R.fieldP, p1 + gi);
     };
-    // prologue: group 0 = planes z0-1, z0, z0+1 and momenta of z0; group j < D =
-    // plane z0+1+j and momenta of z0+j. Iteration k then commits group D+k
-    // (plane z0+1+D+k, momenta z0+D+k) and waits for group k first.
-    if (live) {
-        fetch_f(-1, 0);
-        fetch_f(0, 1);
-        fetch_f(1, 2);
-        if (comp) fetch_p(0, 0);
-    }
-    cp_async_commit();
-    for (int j = 1; j < D; j++) {
-        if (live && 1 + j <= nz + 1) fetch_f(1 + j, 2 + j);
-        if (comp && j <= nz) fetch_p(j, j);
-        cp_async_commit();
-    }
     // x neighbours in the adjacent lanes (same row, not wrapped), else shared memory
     const int lane = t & 31;
     const int qv = x / VW;
     const bool nbl = qv > 0 && lane > 0, nbr = qv < Q - 1 && lane < 31;
-    int sf = 0, sp = 0;          // k mod (D+3), k mod (D+1)
     auto addm = [](int a, int b, int m) { return a + b >= m ? a + b - m : a + b; };
 
-    for (int k = 0; k <= nz; k++) {
-        const bool ahead = k == nz;
-        const int z = z0 + k;                 // == n only on the look-ahead plane of the last chunk
-        cp_async_wait(D - 1);
-        __syncthreads();
-        // prefetch into the slots released by plane k-1 (every thread has passed
-        // the barrier above)
-        if (live && k + 1 + D <= nz + 1) fetch_f(k + 1 + D, addm(sf, D + 2, R.rf));
-        if (comp && k + D <= nz) fetch_p(k + D, addm(sp, D, R.rp));
-        cp_async_commit();
-
-        const T* Fm = S + (uint32_t)sf * R.slotF;
-        const T* Fc = S + (uint32_t)addm(sf, 1, R.rf) * R.slotF;
-        const T* Fp = S + (uint32_t)addm(sf, 2, R.rf) * R.slotF;
-        const T* Pc = S + R.p0 + (uint32_t)sp * R.slotP;
-        sf = addm(sf, 1, R.rf);
-        sp = addm(sp, 1, R.rp);
-        T* Gw = S + R.g0 + (k & 1) * R.planeG;
-        const T* Gr = S + R.g0 + ((k + 1) & 1) * R.planeG;
-
-        // centre vectors and their x neighbours (every lane takes part in the
-        // shuffles; halo rows load harmlessly)
-        P cen[2][NP];
-        T lefts[2], rights[2];
-#pragma unroll
-        for (int f = 0; f < 2; f++) {
-            const T* Ff = Fc + f * R.fieldF + offF;
-            PK<T>::ld(Ff, cen[f]);
-            lefts[f] = __shfl_up_sync(0xffffffffu, hi2(cen[f][NP - 1]), 1);
-            rights[f] = __shfl_down_sync(0xffffffffu, lo2(cen[f][0]), 1);
-            if (!nbl) lefts[f] = Ff[dl];
-            if (!nbr) rights[f] = Ff[dr];
+    for (bool first = true; u < uend; first = false) {
+        const int yt = (int)(u / n);
+        z0 = (int)(u - (long long)yt * n);
+        nz = (int)min((long long)(n - z0), uend - u);
+        u += nz;
+        rowg = (uint32_t)wrapn(yt * ty - 1 + rho, n) * n + x;
+        // the previous segment's last plane is read by every thread before the
+        // prologue below refills the ring
+        if (!first) __syncthreads();
+        // prologue: group 0 = planes z0-1, z0, z0+1 and momenta of z0; group j < D =
+        // plane z0+1+j and momenta of z0+j. Iteration k then commits group D+k
+        // (plane z0+1+D+k, momenta z0+D+k) and waits for group k first.
+        if (live) {
+            fetch_f(-1, 0);
+            fetch_f(0, 1);
+            fetch_f(1, 2);
+            if (comp) fetch_p(0, 0);
         }
-        P g[2][NP];
-        if (comp && !(ahead && rho == ty + 1)) {
-            P pn[2][NP];
+        cp_async_commit();
+        for (int j = 1; j < D; j++) {
+            if (live && 1 + j <= nz + 1) fetch_f(1 + j, 2 + j);
+            if (comp && j <= nz) fetch_p(j, j);
+            cp_async_commit();
+        }
+        int sf = 0, sp = 0;          // k mod (D+3), k mod (D+1)
+
+        for (int k = 0; k <= nz; k++) {
+            const bool ahead = k == nz;
+            const int z = z0 + k;                 // == n only on the look-ahead plane of the last chunk
+            cp_async_wait(D - 1);
+            __syncthreads();
+            // prefetch into the slots released by plane k-1 (every thread has passed
+            // the barrier above)
+            if (live && k + 1 + D <= nz + 1) fetch_f(k + 1 + D, addm(sf, D + 2, R.rf));
+            if (comp && k + D <= nz) fetch_p(k + D, addm(sp, D, R.rp));
+            cp_async_commit();
+
+            const T* Fm = S + (uint32_t)sf * R.slotF;
+            const T* Fc = S + (uint32_t)addm(sf, 1, R.rf) * R.slotF;
+            const T* Fp = S + (uint32_t)addm(sf, 2, R.rf) * R.slotF;
+            const T* Pc = S + R.p0 + (uint32_t)sp * R.slotP;
+            sf = addm(sf, 1, R.rf);
+            sp = addm(sp, 1, R.rp);
+            T* Gw = S + R.g0 + (k & 1) * R.planeG;
+            const T* Gr = S + R.g0 + ((k + 1) & 1) * R.planeG;
+
+            // centre vectors and their x neighbours (every lane takes part in the
+            // shuffles; halo rows load harmlessly)
+            P cen[2][NP];
+            T lefts[2], rights[2];
 #pragma unroll
             for (int f = 0; f < 2; f++) {
                 const T* Ff = Fc + f * R.fieldF + offF;
-                P up[NP], dn[NP], zm[NP], zp[NP], pv[NP], lft[NP], rgt[NP];
-                PK<T>::ld(Ff - n, up);
-                PK<T>::ld(Ff + n, dn);
-                PK<T>::ld(Fm + f * R.fieldF + offF, zm);
-                PK<T>::ld(Fp + f * R.fieldF + offF, zp);
-                PK<T>::ld(Pc + f * R.fieldP + offP, pv);
-                const T left = lefts[f], right = rights[f];
-                if constexpr (NP == 2) {
-                    T c0, c1, c2, c3;
-                    un2(cen[f][0], c0, c1);
-                    un2(cen[f][1], c2, c3);
-                    lft[0] = mk2(left, c0);
-                    lft[1] = mk2(c1, c2);
-                    rgt[0] = lft[1];
-                    rgt[1] = mk2(c3, right);
-                } else {
-                    lft[0] = mk2(left, lo2(cen[f][0]));
-                    rgt[0] = mk2(hi2(cen[f][0]), right);
+                PK<T>::ld(Ff, cen[f]);
+                lefts[f] = __shfl_up_sync(0xffffffffu, hi2(cen[f][NP - 1]), 1);
+                rights[f] = __shfl_down_sync(0xffffffffu, lo2(cen[f][0]), 1);
+                if (!nbl) lefts[f] = Ff[dl];
+                if (!nbr) rights[f] = Ff[dr];
+            }
+            P g[2][NP];
+            if (comp && !(ahead && rho == ty + 1)) {
+                P pn[2][NP];
+#pragma unroll
+                for (int f = 0; f < 2; f++) {
+                    const T* Ff = Fc + f * R.fieldF + offF;
+                    P up[NP], dn[NP], zm[NP], zp[NP], pv[NP], lft[NP], rgt[NP];
+                    PK<T>::ld(Ff - n, up);
+                    PK<T>::ld(Ff + n, dn);
+                    PK<T>::ld(Fm + f * R.fieldF + offF, zm);
+                    PK<T>::ld(Fp + f * R.fieldF + offF, zp);
+                    PK<T>::ld(Pc + f * R.fieldP + offP, pv);
+                    const T left = lefts[f], right = rights[f];
+                    if constexpr (NP == 2) {
+                        T c0, c1, c2, c3;
+                        un2(cen[f][0], c0, c1);
+                        un2(cen[f][1], c2, c3);
+                        lft[0] = mk2(left, c0);
+                        lft[1] = mk2(c1, c2);
+                        rgt[0] = lft[1];
+                        rgt[1] = mk2(c3, right);
+                    } else {
+                        lft[0] = mk2(left, lo2(cen[f][0]));
+                        rgt[0] = mk2(hi2(cen[f][0]), right);
+                    }
+                    const P dtcl2 = mk2(dtcl, dtcl), dtcf2 = mk2(dtcf, dtcf);
+#pragma unroll
+                    for (int v = 0; v < NP; v++) {
+                        const P c = cen[f][v];
+                        // Laplacian as a sum of neighbour differences: exact differences
+                        // for f = const + small (Sterbenz)
+                        const P lapu = add2(add2(add2(sub2(lft[v], c), sub2(rgt[v], c)),
+                                                 add2(sub2(up[v], c), sub2(dn[v], c))),
+                                            add2(sub2(zm[v], c), sub2(zp[v], c)));
+                        pn[f][v] = fma2(dtcl2, lapu, fma2(dtcf2, c, pv[v]));
+                    }
                 }
-                const P dtcl2 = mk2(dtcl, dtcl), dtcf2 = mk2(dtcf, dtcf);
+                const P mdtcdom2 = mk2(mdtcdom, mdtcdom), mdtkap2 = mk2(mdtkap, mdtkap), dt2 = mk2(dt_s, dt_s);
 #pragma unroll
                 for (int v = 0; v < NP; v++) {
-                    const P c = cen[f][v];
-                    // Laplacian as a sum of neighbour differences: exact differences
-                    // for f = const + small (Sterbenz)
-                    const P lapu = add2(add2(add2(sub2(lft[v], c), sub2(rgt[v], c)),
-                                             add2(sub2(up[v], c), sub2(dn[v], c))),
-                                        add2(sub2(zm[v], c), sub2(zp[v], c)));
-                    pn[f][v] = fma2(dtcl2, lapu, fma2(dtcf2, c, pv[v]));
+                    // potential: f0 gets -dt (cdom f0^(beta-1) + kappa f0 f1^2), f1 gets -dt kappa f0^2 f1
+                    const P a0 = cen[0][v], a1 = cen[1][v];
+                    const P a0a1 = mul2(a0, a1);
+                    const P dom = quartic ? mul2(mul2(a0, a0), a0) : a0;
+                    pn[0][v] = fma2(mdtcdom2, dom, fma2(mdtkap2, mul2(a0a1, a1), pn[0][v]));
+                    pn[1][v] = fma2(mdtkap2, mul2(a0a1, a0), pn[1][v]);
+                    g[0][v] = fma2(dt2, pn[0][v], a0);
+                    g[1][v] = fma2(dt2, pn[1][v], a1);
+                }
+                if (!ahead) {
+                    if (own) {
+                        const uint32_t gi = (uint32_t)z * nn + rowg;
+                        PK<T>::st((par ? B.p[0][0] : B.p[1][0]) + gi, pn[0]);
+                        PK<T>::st((par ? B.p[0][1] : B.p[1][1]) + gi, pn[1]);
+                        PK<T>::st((par ? B.f[0][0] : B.f[1][0]) + gi, g[0]);
+                        PK<T>::st((par ? B.f[0][1] : B.f[1][1]) + gi, g[1]);
+                    }
+                    PK<T>::st(Gw + offP, g[0]);
+                    PK<T>::st(Gw + R.fieldG + offP, g[1]);
                 }
             }
-            const P mdtcdom2 = mk2(mdtcdom, mdtcdom), mdtkap2 = mk2(mdtkap, mdtkap), dt2 = mk2(dt_s, dt_s);
+
+            // sums over the owned rows of plane k-1 (x and y pairs, potential) and the
+            // z pair (k-1, k), from the new fields written one plane ago
+            if (k > 0) {
+                P gq[2][NP];
+                T xnexts[2];
 #pragma unroll
-            for (int v = 0; v < NP; v++) {
-                // potential: f0 gets -dt (cdom f0^(beta-1) + kappa f0 f1^2), f1 gets -dt kappa f0^2 f1
-                const P a0 = cen[0][v], a1 = cen[1][v];
-                const P a0a1 = mul2(a0, a1);
-                const P dom = quartic ? mul2(mul2(a0, a0), a0) : a0;
-                pn[0][v] = fma2(mdtcdom2, dom, fma2(mdtkap2, mul2(a0a1, a1), pn[0][v]));
-                pn[1][v] = fma2(mdtkap2, mul2(a0a1, a0), pn[1][v]);
-                g[0][v] = fma2(dt2, pn[0][v], a0);
-                g[1][v] = fma2(dt2, pn[1][v], a1);
-            }
-            if (!ahead) {
+                for (int f = 0; f < 2; f++) {
+                    const T* Gf = Gr + f * R.fieldG + offP;
+                    PK<T>::ld(Gf, gq[f]);
+                    xnexts[f] = __shfl_down_sync(0xffffffffu, lo2(gq[f][0]), 1);
+                    if (!nbr) xnexts[f] = Gf[dr];
+                }
                 if (own) {
-                    const uint32_t gi = (uint32_t)z * nn + rowg;
-                    PK<T>::st((par ? B.p[0][0] : B.p[1][0]) + gi, pn[0]);
-                    PK<T>::st((par ? B.p[0][1] : B.p[1][1]) + gi, pn[1]);
-                    PK<T>::st((par ? B.f[0][0] : B.f[1][0]) + gi, g[0]);
-                    PK<T>::st((par ? B.f[0][1] : B.f[1][1]) + gi, g[1]);
-                }
-                PK<T>::st(Gw + offP, g[0]);
-                PK<T>::st(Gw + R.fieldG + offP, g[1]);
-            }
-        }
-
-        // sums over the owned rows of plane k-1 (x and y pairs, potential) and the
-        // z pair (k-1, k), from the new fields written one plane ago
-        if (k > 0) {
-            P gq[2][NP];
-            T xnexts[2];
 #pragma unroll
-            for (int f = 0; f < 2; f++) {
-                const T* Gf = Gr + f * R.fieldG + offP;
-                PK<T>::ld(Gf, gq[f]);
-                xnexts[f] = __shfl_down_sync(0xffffffffu, lo2(gq[f][0]), 1);
-                if (!nbr) xnexts[f] = Gf[dr];
-            }
-            if (own) {
+                for (int f = 0; f < 2; f++) {
+                    const T* Gf = Gr + f * R.fieldG + offP;
+                    P yn[NP], xn[NP];
+                    PK<T>::ld(Gf + n, yn);
+                    const T xnext = xnexts[f];
+                    if constexpr (NP == 2) {
+                        T a, b, c, d;
+                        un2(gq[f][0], a, b);
+                        un2(gq[f][1], c, d);
+                        xn[0] = mk2(b, c);
+                        xn[1] = mk2(d, xnext);
+                    } else {
+                        xn[0] = mk2(hi2(gq[f][0]), xnext);
+                    }
+                    P acc = f == 0 ? accg0 : accg1;
 #pragma unroll
-            for (int f = 0; f < 2; f++) {
-                const T* Gf = Gr + f * R.fieldG + offP;
-                P yn[NP], xn[NP];
-                PK<T>::ld(Gf + n, yn);
-                const T xnext = xnexts[f];
-                if constexpr (NP == 2) {
-                    T a, b, c, d;
-                    un2(gq[f][0], a, b);
-                    un2(gq[f][1], c, d);
-                    xn[0] = mk2(b, c);
-                    xn[1] = mk2(d, xnext);
-                } else {
-                    xn[0] = mk2(hi2(gq[f][0]), xnext);
+                    for (int v = 0; v < NP; v++) {
+                        const P dxv = sub2(xn[v], gq[f][v]), dyv = sub2(yn[v], gq[f][v]), dzv = sub2(g[f][v], gq[f][v]);
+                        acc = fma2(dxv, dxv, fma2(dyv, dyv, fma2(dzv, dzv, acc)));
+                    }
+                    if (f == 0) accg0 = acc;
+                    else accg1 = acc;
                 }
-                P acc = f == 0 ? accg0 : accg1;
 #pragma unroll
                 for (int v = 0; v < NP; v++) {
-                    const P dxv = sub2(xn[v], gq[f][v]), dyv = sub2(yn[v], gq[f][v]), dzv = sub2(g[f][v], gq[f][v]);
-                    acc = fma2(dxv, dxv, fma2(dyv, dyv, fma2(dzv, dzv, acc)));
+                    const P sq = mul2(gq[0][v], gq[0][v]);
+                    accvd = quartic ? fma2(sq, sq, accvd) : add2(sq, accvd);
+                    accvi = fma2(sq, mul2(gq[1][v], gq[1][v]), accvi);
                 }
-                if (f == 0) accg0 = acc;
-                else accg1 = acc;
-            }
-#pragma unroll
-            for (int v = 0; v < NP; v++) {
-                const P sq = mul2(gq[0][v], gq[0][v]);
-                accvd = quartic ? fma2(sq, sq, accvd) : add2(sq, accvd);
-                accvi = fma2(sq, mul2(gq[1][v], gq[1][v]), accvi);
-            }
+                }
             }
         }
-    }
+    } // segments
 
-    double v[kSums] = {(double)lo2(accg0) + (double)hi2(accg0), (double)lo2(accg1) + (double)hi2(accg1),
-                       ((double)lo2(accvd) + (double)hi2(accvd)) * (quartic ? 0.25 : 0.5),
-                       0.5 * ((double)lo2(accvi) + (double)hi2(accvi))};
+    // per-thread sums in the element type (the 1/beta and 1/2 factors are
+    // powers of two, exact); the block folds them as finish_block describes
+    T v[kSums] = {lo2(accg0) + hi2(accg0), lo2(accg1) + hi2(accg1),
+                  (lo2(accvd) + hi2(accvd)) * (quartic ? T(0.25) : T(0.5)),
+                  T(0.5) * (lo2(accvi) + hi2(accvi))};
     finish_block(M, sc, partials, v, red, true);
 }
 
@@ -333,44 +349,37 @@ bool march_geom(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     threads = ((threads + 31) / 32) * 32;
     if (threads > 1024) return false;
     if (depth < 1 || depth > 4) return false;
-    const size_t smem = march_smem(n, esize, ty, depth);
-    if (smem > 220 * 1024) return false;
+    size_t fast_smem = 0;
+    const void* fast = fast_kernel(esize, n, ty, depth, &fast_smem);
+    const size_t smem = fast ? fast_smem : march_smem(n, esize, ty, depth);
+    if (smem > 227 * 1024 - 2048) return false;   // the opt-in limit less the static arrays
     const int maxt = maxt_for(threads);
-    const void* fast = depth == 1 ? fast_kernel(esize, n, ty) : nullptr;
     const void* fn = fast ? fast : esize == 4 ? march_fn<float>(maxt) : march_fn<double>(maxt);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
-    // z chunks: for a requested length zr, ceil(n / zr) balanced chunks; else the
-    // count that fills whole waves of resident blocks (nyt * nzc a multiple of
-    // the slots), weighing the per-chunk cost of its halo planes
+    // blocks: for a requested z length zr, nyt * ceil(n / zr) blocks (balanced
+    // z chunks of each y tile); else one resident wave, each block taking an
+    // equal share of the (y tile, z plane) units
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return false;
     const long long slots = (long long)sms * occ;
     const int nyt = n / ty;
-    int nzc = 1;
-    if (zr > 0) {
-        nzc = (n + std::min(zr, n) - 1) / std::min(zr, n);
-    } else {
-        double best = 1e30;
-        for (int c = 1; c <= std::max(1, n / 8); c++) {
-            const long long b = (long long)nyt * c;
-            const double waves = (double)((b + slots - 1) / slots);
-            const double score = waves * slots / b * (1.0 + 2.0 / ((double)n / c));
-            if (score < best - 1e-12) { best = score; nzc = c; }
-        }
-    }
+    const long long units = (long long)nyt * n;
+    long long blocks = 0;
+    if (zr > 0) blocks = (long long)nyt * ((n + std::min(zr, n) - 1) / std::min(zr, n));
+    else blocks = std::min(slots, units);
     cfg->ty = ty;
-    cfg->zr = (n + nzc - 1) / nzc;
-    cfg->nzc = nzc;
+    cfg->zr = (int)((units + blocks - 1) / blocks);
+    cfg->nzc = (int)((blocks + nyt - 1) / nyt);
     cfg->depth = depth;
     cfg->threads = threads;
     cfg->maxt = maxt;
     cfg->fast = fast ? 1 : 0;
     cfg->smem = smem;
     cfg->nyt = nyt;
-    cfg->blocks = nyt * nzc;
+    cfg->blocks = (int)blocks;
     return true;
 }
 

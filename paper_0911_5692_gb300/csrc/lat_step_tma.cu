@@ -196,9 +196,9 @@ __global__ void __launch_bounds__(kMaxThreads) step_tma_kernel(const __grid_cons
     const int par = (int)(sc->step & 1);
     // f' += dt (cL Lap f + cF f - dV/df), f += dt f': coefficients folded so that
     // the unscaled neighbour-difference sum multiplies dt cL / dx^2 directly
-    const T dt_s = (T)M.dt;
-    const T dtcl = (T)(M.dt * sc->cL * M.inv_dx2), dtcf = (T)(M.dt * sc->cF);
-    const T mdtcdom = (T)(-M.dt * sc->cdom), mdtkap = (T)(-M.dt * sc->kappa);
+    const T dt_s = step_coef<T>(sc, 4);
+    const T dtcl = step_coef<T>(sc, 0), dtcf = step_coef<T>(sc, 1);
+    const T mdtcdom = step_coef<T>(sc, 2), mdtkap = step_coef<T>(sc, 3);
     const bool quartic = M.beta == 4;
 
     if (threadIdx.x == 0) {
@@ -432,11 +432,10 @@ __global__ void __launch_bounds__(kMaxThreads) step_tma_kernel(const __grid_cons
     }
     // per-thread sums to the block: gradient sums go to the thread's field,
     // the potential sums (with their 1/beta and 1/2 factors) come from field 0
-    const double gsum = (double)lo2(accg) + (double)hi2(accg);
+    const T gsum = lo2(accg) + hi2(accg);
     const bool f0t = (io[0].flags & 1) == 0;
-    double v[kSums] = {f0t ? gsum : 0.0, f0t ? 0.0 : gsum,
-                       ((double)lo2(accvd) + (double)hi2(accvd)) * (quartic ? 0.25 : 0.5),
-                       0.5 * ((double)lo2(accvi) + (double)hi2(accvi))};
+    T v[kSums] = {f0t ? gsum : T(0), f0t ? T(0) : gsum, (lo2(accvd) + hi2(accvd)) * (quartic ? T(0.25) : T(0.5)),
+                  T(0.5) * (lo2(accvi) + hi2(accvi))};
     finish_block(M, sc, A.partials, v, red, true);
 }
 

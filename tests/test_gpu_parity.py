@@ -322,20 +322,26 @@ def test_march_geometries(prec, ty, zr, depth):
     compare_states(g, o, 10 * TOL[prec], f"march ty={ty} zr={zr} depth={depth} fp{prec}")
 
 
-@pytest.mark.parametrize("prec,n,ty", [(32, 128, 4), (32, 128, 8), (32, 256, 4), (32, 256, 8), (32, 512, 2),
-                                       (32, 512, 4), (64, 256, 4), (64, 512, 1)])
-def test_specialised_instances(prec, n, ty):
-    """The compile-time-geometry instances of the z-march (one per (N, ty) the
-    automatic choice can pick), against the oracle; z chunks that do not divide N
-    exercise the unrolled plane loop's early exits."""
+@pytest.mark.parametrize("prec,n,ty,depth,zr", [(32, 128, 4, 1, 23), (32, 128, 8, 1, 23), (32, 256, 4, 1, 23),
+                                                (32, 256, 8, 1, 23), (32, 512, 2, 1, 23), (32, 512, 4, 1, 23),
+                                                (32, 128, 8, 2, 23), (32, 256, 4, 2, 23), (32, 256, 8, 2, 23),
+                                                (32, 512, 2, 2, 23), (32, 128, 8, 2, 1), (32, 128, 8, 2, 2),
+                                                (32, 128, 8, 1, 1), (64, 256, 4, 1, 23), (64, 512, 1, 1, 23)])
+def test_specialised_instances(prec, n, ty, depth, zr):
+    """The compile-time-geometry instances of the z-march (one per (N, ty, depth)
+    the automatic choice can pick), against the oracle; z chunks that do not
+    divide N exercise the unrolled plane loop's early exits, chunks of one or two
+    planes the prologue of the deeper ring."""
     p = lphi4(n, precision=prec)
     st = _state("lphi4", n, prec, seed=n + ty)
     g, o = paired(p, st, (0.0, 1.05, 0.5, 0))
-    g.set_kernel(2, ty, 23, 1)
+    g.set_kernel(2, ty, zr, depth)
+    info = g.kernel_info()
+    assert (info["ty"], info["depth"]) == (ty, depth)
     steps = 2 if n >= 512 else 3
     g.set_state(*st, t=0.0, a=1.05, ad=0.5, step=0)
     g.evolve(steps)
     o.step(steps)
-    compare_states(g, o, steps * TOL[prec], f"fast N={n} ty={ty} fp{prec}")
+    compare_states(g, o, steps * TOL[prec], f"fast N={n} ty={ty} depth={depth} zr={zr} fp{prec}")
     gs, os_ = g.scalars(), o.scalars()
     assert abs(gs["a"] / os_["a"] - 1) <= (1e-13 if prec == 64 else 1e-7)
