@@ -671,3 +671,231 @@ int orc_spectrum(orc_lattice *L, int field, int nbins, double *k_out, double *p_
     free(re); free(im);
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------- coupling */
+
+/* Change g^2 (and with it kappa0 = g^2 / (A^2 B^2)) of an existing lattice; the
+ * state and the sums (which do not involve g^2) are kept. */
+int orc_set_g2(orc_lattice *L, double g2)
+{
+    L->p.g2 = g2;
+    return orc_derive(L);
+}
+
+/* ---------------------------------------------------------------- adjoint */
+
+/*
+ * Reverse-mode derivative (vector-Jacobian product) of nsteps leapfrog steps of
+ * one_step above, taken exactly through every dependence of the discrete step:
+ * the kick's Laplacian, potential and cF f terms, the drift, the a / a' update,
+ * and the dependence of a'', cF, cdom, kappa (and so of every later step) on the
+ * volume sums S of the fields, i.e. the coupling of the fields to a(t) through
+ * eq. scale. kappa0 (hence g^2) is an input too.
+ *
+ * Forward step k, state (f_k, pi_k, a_k, a'_k), sums S_k = S(f_k):
+ *   c = K a^e1 ((S0+S1)/3 + a^e2 (cdom(a) S2 + kappa(a) S3)), K = 8piG/A^2,
+ *       e1 = -2s-2r-1, e2 = 2s+2
+ *   q = -(s+2)/a, alpha = dt q/4, gamma = 2a'_k + dt c, y = root of
+ *       alpha y^2 - y + gamma = 0, a'_half = y/2, a'' = q a'_half^2 + c
+ *   cL = a^(-2s-2), cF = r(s-r+2) (a'_half/a)^2 + r a''/a
+ *   pi_{k+1} = pi_k + dt (cL Lap f_k + cF f_k - dV_pr/df(f_k; cdom, kappa))
+ *   f_{k+1} = f_k + dt pi_{k+1}
+ *   a'_{k+1} = y - a'_k, a_{k+1} = a_k + dt a'_{k+1}
+ * (expansion off: a, a' fixed, cL = 1, cF = 0.)
+ *
+ * The reverse sweep walks the steps backwards; within a step it reverses the
+ * statements above in the opposite order. The adjoint of the global sums S_k
+ * feeds back to every site through dS/df:
+ *   dS0/df0 = -2 Lap f0 / N^3, dS1/df1 = -2 Lap f1 / N^3,
+ *   dS2/df0 = f0^(beta-1) / N^3, dS3/df0 = f0 f1^2 / N^3, dS3/df1 = f0^2 f1 / N^3
+ * (the first two by the summation-by-parts identity of Sec. II.B).
+ *
+ * In:  fbar[2], pibar[2] (nsites each): the adjoint of the final f and pi;
+ *      sbar[0..1]: the adjoint of the final a and a'.
+ * Out: fbar, pibar overwritten by the adjoint of the initial f and pi;
+ *      sbar[0..1] the adjoint of the initial a and a', sbar[2] dJ/dkappa0 and
+ *      sbar[3] dJ/dg^2 = dJ/dkappa0 / (A^2 B^2).
+ * The lattice itself ends advanced by nsteps (as after orc_step). All states
+ * are kept in memory: this is meant for small lattices.
+ */
+
+/* forward scalars of one step from (a, a', S) */
+typedef struct {
+    double c, q, alpha, gamma, y, ah, add, cL, cF, cd, kp, vpr, e1v, e2v;
+} orc_coefs;
+
+static int step_coefs(const orc_lattice *L, double a, double ad, const double S[4], orc_coefs *o)
+{
+    memset(o, 0, sizeof(*o));
+    o->cd = cdom_at(L, a);
+    o->kp = kappa_at(L, a);
+    o->cL = 1.0;
+    o->cF = 0.0;
+    if (!L->p.expansion) return ORC_OK;
+    double dt = L->p.dt, r = L->r, s = L->s;
+    o->vpr = o->cd * S[2] + o->kp * S[3];
+    o->e1v = pow(a, -2.0 * s - 2.0 * r - 1.0);
+    o->e2v = pow(a, 2.0 * s + 2.0);
+    o->c = L->p.eight_pi_G / (L->A * L->A) * o->e1v * ((S[0] + S[1]) / 3.0 + o->e2v * o->vpr);
+    o->q = -(s + 2.0) / a;
+    o->alpha = dt * o->q / 4.0;
+    o->gamma = 2.0 * ad + dt * o->c;
+    double disc = 1.0 - 4.0 * o->alpha * o->gamma;
+    if (!(disc >= 0.0)) return ORC_ENONFINITE;
+    o->y = 2.0 * o->gamma / (1.0 + sqrt(disc));
+    o->ah = 0.5 * o->y;
+    o->add = o->q * o->ah * o->ah + o->c;
+    o->cL = pow(a, -2.0 * s - 2.0);
+    double h = o->ah / a;
+    o->cF = r * (s - r + 2.0) * h * h + r * o->add / a;
+    return ORC_OK;
+}
+
+/* Reverse of step_coefs: from the adjoints of cL, cF, cdom, kappa and y, add to
+ * the adjoints of a, a', S[0..3] and kappa0. */
+static void step_coefs_adjoint(const orc_lattice *L, double a, const double S[4], const orc_coefs *o,
+                               double bcL, double bcF, double bcd, double bkp, double by,
+                               double *ba, double *bad, double bS[4], double *bk0)
+{
+    double r = L->r, s = L->s, dt = L->p.dt;
+    if (L->p.expansion) {
+        double h = o->ah / a;
+        /* cF = r (s-r+2) h^2 + r add / a */
+        double bh = bcF * 2.0 * r * (s - r + 2.0) * h;
+        double badd = bcF * r / a;
+        *ba -= bcF * r * o->add / (a * a);
+        /* h = ah / a */
+        double bah = bh / a;
+        *ba -= bh * o->ah / (a * a);
+        /* add = q ah^2 + c */
+        double bq = badd * o->ah * o->ah;
+        bah += badd * 2.0 * o->q * o->ah;
+        double bc = badd;
+        /* ah = y / 2 */
+        by += 0.5 * bah;
+        /* alpha y^2 - y + gamma = 0: dy = (y^2 dalpha + dgamma) / (1 - 2 alpha y) */
+        double den = 1.0 - 2.0 * o->alpha * o->y;
+        double bgamma = by / den, balpha = by * o->y * o->y / den;
+        /* alpha = dt q / 4, gamma = 2 a' + dt c */
+        bq += balpha * dt / 4.0;
+        *bad += 2.0 * bgamma;
+        bc += dt * bgamma;
+        /* q = -(s+2)/a */
+        *ba += bq * (s + 2.0) / (a * a);
+        /* cL = a^(-2s-2) */
+        *ba += bcL * (-2.0 * s - 2.0) * pow(a, -2.0 * s - 3.0);
+        /* c = K e1v (T + e2v vpr), T = (S0+S1)/3 */
+        double K = L->p.eight_pi_G / (L->A * L->A);
+        double T = (S[0] + S[1]) / 3.0;
+        double be1 = bc * K * (T + o->e2v * o->vpr);
+        double bT = bc * K * o->e1v;
+        double be2 = bc * K * o->e1v * o->vpr;
+        double bvpr = bc * K * o->e1v * o->e2v;
+        *ba += be1 * (-2.0 * s - 2.0 * r - 1.0) * pow(a, -2.0 * s - 2.0 * r - 2.0);
+        *ba += be2 * (2.0 * s + 2.0) * pow(a, 2.0 * s + 1.0);
+        bS[0] += bT / 3.0;
+        bS[1] += bT / 3.0;
+        /* vpr = cdom S2 + kappa S3 */
+        bcd += bvpr * S[2];
+        bkp += bvpr * S[3];
+        bS[2] += bvpr * o->cd;
+        bS[3] += bvpr * o->kp;
+    }
+    /* cdom = cdom0 a^pdom, kappa = kappa0 a^pint */
+    *ba += bcd * L->cdom0 * L->pdom * pow(a, L->pdom - 1.0) + bkp * L->kappa0 * L->pint * pow(a, L->pint - 1.0);
+    *bk0 += bkp * pow(a, L->pint);
+}
+
+/* sum over all sites of an array, plane by plane in z order */
+static double volume_sum(int n, const double *v)
+{
+    size_t plane = (size_t)n * n;
+    double tot = 0.0;
+    for (int z = 0; z < n; z++) {
+        double acc = 0.0;
+        for (size_t k = 0; k < plane; k++) acc += v[(size_t)z * plane + k];
+        tot += acc;
+    }
+    return tot;
+}
+
+int orc_adjoint(orc_lattice *L, int64_t nsteps, double *fbar[2], double *pibar[2], double sbar[4])
+{
+    const size_t N3 = L->nsites;
+    const int n = L->n;
+    const double dt = L->p.dt, beta = L->beta;
+    if (nsteps < 0) return ORC_EINVAL;
+    /* forward: keep f_k (both fields) and (a_k, a'_k, S_k) of every step */
+    double *fs = (double *)malloc(sizeof(double) * 2 * N3 * (size_t)(nsteps + 1));
+    double *sc = (double *)malloc(sizeof(double) * 6 * (size_t)(nsteps + 1));
+    double *w = (double *)malloc(sizeof(double) * 8 * N3);
+    if (!fs || !sc || !w) { free(fs); free(sc); free(w); return ORC_ENOMEM; }
+    int st = ORC_OK;
+    for (int64_t k = 0; k <= nsteps && st == ORC_OK; k++) {
+        memcpy(fs + (size_t)k * 2 * N3, L->f[0], sizeof(double) * N3);
+        memcpy(fs + (size_t)k * 2 * N3 + N3, L->f[1], sizeof(double) * N3);
+        sc[6 * k + 0] = L->a;
+        sc[6 * k + 1] = L->ad;
+        for (int i = 0; i < 4; i++) sc[6 * k + 2 + i] = L->S[i];
+        if (k < nsteps) st = orc_step(L, 1);
+    }
+    double *pt0 = w, *pt1 = w + N3, *lp0 = w + 2 * N3, *lp1 = w + 3 * N3;
+    double *lf0 = w + 4 * N3, *lf1 = w + 5 * N3, *t0 = w + 6 * N3, *t1 = w + 7 * N3;
+    double ba = sbar[0], bad = sbar[1], bk0 = 0.0;
+    const double inv_n3 = 1.0 / (double)N3;
+    for (int64_t k = nsteps - 1; k >= 0 && st == ORC_OK; k--) {
+        const double *f0 = fs + (size_t)k * 2 * N3, *f1 = f0 + N3;
+        const double a = sc[6 * k + 0], ad = sc[6 * k + 1], *S = sc + 6 * k + 2;
+        orc_coefs o;
+        st = step_coefs(L, a, ad, S, &o);
+        if (st != ORC_OK) break;
+        /* drift f_{k+1} = f_k + dt pi_{k+1}: pi_{k+1} sees pibar + dt fbar */
+        for (size_t i = 0; i < N3; i++) {
+            pt0[i] = pibar[0][i] + dt * fbar[0][i];
+            pt1[i] = pibar[1][i] + dt * fbar[1][i];
+        }
+        /* a_{k+1} = a_k + dt a'_{k+1}, a'_{k+1} = y - a'_k */
+        double by = 0.0;
+        if (L->p.expansion) {
+            by = bad + dt * ba;
+            bad = -by;
+        }
+        /* kick pi_{k+1} = pi_k + dt (cL Lap f + cF f - dV/df): adjoints of the
+         * step coefficients are volume sums */
+        orc_laplacian(n, L->dx, f0, lf0);
+        orc_laplacian(n, L->dx, f1, lf1);
+        for (size_t i = 0; i < N3; i++) t0[i] = pt0[i] * lf0[i] + pt1[i] * lf1[i];
+        double bcL = dt * volume_sum(n, t0);
+        for (size_t i = 0; i < N3; i++) t0[i] = pt0[i] * f0[i] + pt1[i] * f1[i];
+        double bcF = dt * volume_sum(n, t0);
+        for (size_t i = 0; i < N3; i++) t0[i] = pt0[i] * pow(f0[i], beta - 1.0);
+        double bcd = -dt * volume_sum(n, t0);
+        for (size_t i = 0; i < N3; i++) t0[i] = pt0[i] * f0[i] * f1[i] * f1[i] + pt1[i] * f0[i] * f0[i] * f1[i];
+        double bkp = -dt * volume_sum(n, t0);
+        double bS[4] = {0.0, 0.0, 0.0, 0.0};
+        step_coefs_adjoint(L, a, S, &o, bcL, bcF, bcd, bkp, by, &ba, &bad, bS, &bk0);
+        /* field adjoints: fbar_k = fbar_{k+1} + dt (dF/df)^T pt + sum_j bS_j dS_j/df */
+        orc_laplacian(n, L->dx, pt0, lp0);
+        orc_laplacian(n, L->dx, pt1, lp1);
+        for (size_t i = 0; i < N3; i++) {
+            double p0 = f0[i], p1 = f1[i];
+            double h00 = o.cd * (beta - 1.0) * pow(p0, beta - 2.0) + o.kp * p1 * p1;
+            double h01 = 2.0 * o.kp * p0 * p1;
+            double h11 = o.kp * p0 * p0;
+            double g0 = o.cL * lp0[i] + o.cF * pt0[i] - h00 * pt0[i] - h01 * pt1[i];
+            double g1 = o.cL * lp1[i] + o.cF * pt1[i] - h01 * pt0[i] - h11 * pt1[i];
+            double s0 = bS[0] * (-2.0 * lf0[i]) + bS[2] * pow(p0, beta - 1.0) + bS[3] * p0 * p1 * p1;
+            double s1 = bS[1] * (-2.0 * lf1[i]) + bS[3] * p0 * p0 * p1;
+            fbar[0][i] += dt * g0 + s0 * inv_n3;
+            fbar[1][i] += dt * g1 + s1 * inv_n3;
+            pibar[0][i] = pt0[i];
+            pibar[1][i] = pt1[i];
+        }
+    }
+    sbar[0] = ba;
+    sbar[1] = bad;
+    sbar[2] = bk0;
+    sbar[3] = bk0 / (L->A * L->A * L->B * L->B);
+    free(fs); free(sc); free(w);
+    return st;
+}

@@ -82,6 +82,8 @@ def lib():
             L.orc_normal.restype = C.c_double
             L.orc_fft1.argtypes = [C.c_int, dp, dp, dp, dp, C.c_int]
             L.orc_fft3.argtypes = [C.c_int, dp, dp, C.c_int]
+            L.orc_set_g2.argtypes = [P, C.c_double]
+            L.orc_adjoint.argtypes = [P, C.c_int64, C.POINTER(dp), C.POINTER(dp), dp]
             _lib = L
     return _lib
 
@@ -185,6 +187,46 @@ class Oracle:
         out = (C.c_double * 17)()
         _check(self._L.orc_energies(self._h, out), "orc_energies")
         return dict(zip(self.ENERGY_KEYS, list(out)))
+
+    def set_g2(self, g2: float):
+        """Change the coupling g^2 (kappa0 follows); the state is kept."""
+        _check(self._L.orc_set_g2(self._h, float(g2)), "orc_set_g2")
+        self.params["g2"] = float(g2)
+
+    def vjp(self, nsteps: int, fbar, pibar, abar: float = 0.0, adbar: float = 0.0):
+        """Reverse-mode product of nsteps steps with the adjoint (fbar, pibar,
+        abar, adbar) of the final state. Returns (fbar0, pibar0, abar0, adbar0,
+        dkappa0, dg2): the adjoint of the state at the start, of kappa0 and of
+        g^2. The lattice ends advanced by nsteps."""
+        n3 = self.n ** 3
+        fb = [np.ascontiguousarray(np.asarray(fbar[i], dtype=np.float64).reshape(n3)).copy() for i in (0, 1)]
+        pb = [np.ascontiguousarray(np.asarray(pibar[i], dtype=np.float64).reshape(n3)).copy() for i in (0, 1)]
+        fps = (C.POINTER(C.c_double) * 2)(_dp(fb[0]), _dp(fb[1]))
+        pps = (C.POINTER(C.c_double) * 2)(_dp(pb[0]), _dp(pb[1]))
+        sb = np.array([abar, adbar, 0.0, 0.0], dtype=np.float64)
+        _check(self._L.orc_adjoint(self._h, int(nsteps), fps, pps, _dp(sb)), "orc_adjoint")
+        shp = (self.n,) * 3
+        return ([f.reshape(shp) for f in fb], [q.reshape(shp) for q in pb], sb[0], sb[1], sb[2], sb[3])
+
+    def chi2_mean(self) -> float:
+        """Observable J = <f1^2>, the volume mean of the squared program-unit chi."""
+        f1 = self.array(1, 0)
+        return float(np.sum(f1 * f1, dtype=np.float64) / f1.size)
+
+    def chi2_gradient(self, nsteps: int):
+        """J = <f1^2> after nsteps steps from the current state, and its gradient
+        with respect to the current (f, pi) and g^2. Returns (J, dJ/df [2 arrays],
+        dJ/dpi [2 arrays], dJ/dg2). The lattice ends advanced by nsteps."""
+        n = self.n
+        st = self.get_state()
+        sc = self.scalars()
+        self.step(nsteps)
+        J = self.chi2_mean()
+        f1 = self.array(1, 0).copy()
+        self.set_state(*st, t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
+        zeros = np.zeros((n, n, n))
+        fb, pb, _, _, _, dg2 = self.vjp(nsteps, [zeros, 2.0 * f1 / n ** 3], [zeros, zeros])
+        return J, fb, pb, dg2
 
     def spectrum(self, field: int, nbins: int):
         k = np.zeros(nbins); p = np.zeros(nbins); c = np.zeros(nbins, dtype=np.int64)
