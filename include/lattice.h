@@ -197,6 +197,47 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8]);
 lat_status lat_field_sums_static(const void* f_phi, const void* f_chi, int n, int precision, int model, double L,
                                  double* out_dev, void* cuda_stream);
 
+/* Change the coupling g^2 of an existing handle (Sec. II.B: it enters the
+ * program-unit potential as kappa0 = g^2 / (A^2 B^2)); the state is kept and the
+ * next step's coefficients are recomputed. LAT_EINVAL for g2 < 0 or not finite,
+ * LAT_ECFL if the new effective mass breaks the leapfrog stability bound. */
+lat_status lat_set_g2(lat_handle* h, double g2);
+
+/* Reverse-mode derivative (vector-Jacobian product) of n_steps leapfrog steps
+ * (Sec. II.B, eq. evo with eq. scalar-evo and eq. scale) from the handle's
+ * current state, exact for the discrete scheme: it includes the dependence of
+ * a'', the field-equation coefficients and every later step on the volume sums
+ * of gradient and potential energy (eq. scale). The paper has no derivative;
+ * this is the differentiation the reference method is extended with.
+ *   fbar_dev, pibar_dev: device arrays of 2 n^3 elements each (phi block then
+ *     chi block, layout of lat_get_state, element type of the handle), caller-
+ *     owned. In: the adjoint of f and pi after n_steps. Out: the adjoint of f and
+ *     pi of the starting state.
+ *   sbar[4]: in: sbar[0], sbar[1] = adjoint of a and a' after n_steps; out:
+ *     sbar[0], sbar[1] = adjoint of the starting a and a', sbar[2] = derivative
+ *     with respect to kappa0, sbar[3] = with respect to g^2.
+ *   ckpt_every: steps between stored checkpoints; 0 = ceil(sqrt(n_steps)). The
+ *     forward pass stores one checkpoint (three field pairs) per ckpt_every
+ *     steps, the reverse pass recomputes each segment into ckpt_every field
+ *     pairs; device memory grows as (3 n_steps / ckpt_every + 2 ckpt_every + 8)
+ *     arrays.
+ * The handle ends at the state after n_steps (as after lat_evolve). Handles
+ * configured for the TMA step kernel take the plane-ring kernel in both passes.
+ * Synchronises. LAT_ENOMEM if the checkpoints do not fit; sticky device errors
+ * of the forward or reverse pass are returned. */
+lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fbar_dev, void* pibar_dev,
+                   double sbar[4]);
+
+/* Value and gradient of an observable of the state after n_steps with respect
+ * to the starting f, pi and g^2, by lat_vjp. observable 0: J = <chi^2>, the
+ * volume mean of the squared program-unit chi (f_1). J_out (host, may be NULL)
+ * gets J; dJ_dg2 (host, may be NULL) gets dJ/dg^2; dJ_df_dev and dJ_dpi_dev
+ * (device, 2 n^3 elements each, as in lat_vjp) get dJ/df and dJ/dpi of the
+ * starting state. n_steps = 0 gives J and its gradient at the current state.
+ * LAT_EUNSUPPORTED for any other observable. Synchronises. */
+lat_status lat_adjoint(lat_handle* h, int64_t n_steps, int observable, int64_t ckpt_every, double* J_out,
+                       double* dJ_dg2, void* dJ_df_dev, void* dJ_dpi_dev);
+
 /* Release the handle and the buffers it owns. NULL is accepted. */
 void lat_destroy(lat_handle* h);
 

@@ -10,49 +10,16 @@
 #include <new>
 #include <vector>
 
-#include "lat_kernels.h"
+#include "lat_internal.h"
 
 using namespace lat;
 
-struct lat_handle {
-    lat_params p;
-    Model M;
-    int prec;
-    size_t esize;
-    size_t nsites;
-    cudaStream_t stream;
-    void* buf[8];        // f0, f1, p0, p1 of set 0, then of set 1
-    bool owns;
-    DevScalars* sc;      // device
-    double* partials;    // device, per-block sums
-    size_t partials_cap; // doubles
-    double* means;       // device, 2 doubles
-    bool dirty;          // sums and coefficients must be recomputed
-    int variant;         // 1 = plain per-site loads, 2 = register-prefetch z-march, 3 = TMA ring
-    int ty, zr;
-    MarchConfig mcfg;
-    TmaConfig tcfg;
-    alignas(64) unsigned char tmaps[kTmaMaps * 128];
-    cudaGraphExec_t graph;
-    int graph_steps;
-};
 
-namespace {
+namespace lat {
 
 constexpr int kGraphChunk = 32;
 
 lat_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LAT_OK : LAT_ECUDA; }
-
-#define LAT_TRY(expr)                          \
-    do {                                       \
-        lat_status _s = (expr);                \
-        if (_s != LAT_OK) return _s;           \
-    } while (0)
-#define LAT_CUDA(expr)                                   \
-    do {                                                 \
-        cudaError_t _e = (expr);                         \
-        if (_e != cudaSuccess) return LAT_ECUDA;         \
-    } while (0)
 
 // Sec. II.B: rescaling for a dominant term cpl/beta phi^beta and the program-unit
 // potential V_pr = (A^2/B^2) a^(2r-2s) V(f / (A a^r)), which for
@@ -128,17 +95,6 @@ size_t partials_needed(int n)
     return need;
 }
 
-template <typename T>
-Bufs<T> bufs_of(const lat_handle* h)
-{
-    Bufs<T> b;
-    for (int par = 0; par < 2; par++)
-        for (int f = 0; f < 2; f++) {
-            b.f[par][f] = (T*)h->buf[4 * par + f];
-            b.p[par][f] = (T*)h->buf[4 * par + 2 + f];
-        }
-    return b;
-}
 
 lat_status launch_prepare(lat_handle* h)
 {
@@ -147,23 +103,33 @@ lat_status launch_prepare(lat_handle* h)
     return cuda_status(e);
 }
 
+// One step of the configured kernel on the given buffers (the handle's own for
+// lat_evolve; per-step storage for the recomputation of the reverse pass). The
+// TMA ring is bound to the handle's buffers by its tensor maps, so other buffers
+// take the plane-ring kernel instead.
+template <typename T>
+cudaError_t launch_step_with(lat_handle* h, const Bufs<T>& b, bool own_buffers)
+{
+    if (h->variant == 2) return launch_step_march<T>(b, h->M, h->sc, h->partials, h->mcfg, h->stream);
+    if (h->variant == 3) {
+        if (own_buffers) return launch_step_tma<T>(b, h->M, h->sc, h->partials, h->tcfg, h->tmaps, h->stream);
+        if (!h->alt_ok) {
+            if (!march_config(h->p.n, (int)h->esize, 0, 0, 0, &h->alt_mcfg) ||
+                (size_t)h->alt_mcfg.blocks * kSums > h->partials_cap)
+                return cudaErrorInvalidConfiguration;
+            h->alt_ok = true;
+        }
+        return launch_step_march<T>(b, h->M, h->sc, h->partials, h->alt_mcfg, h->stream);
+    }
+    return launch_step_simple<T>(b, h->M, h->sc, h->partials, h->zr, h->stream);
+}
+template cudaError_t launch_step_with<float>(lat_handle*, const Bufs<float>&, bool);
+template cudaError_t launch_step_with<double>(lat_handle*, const Bufs<double>&, bool);
+
 lat_status launch_one_step(lat_handle* h)
 {
-    cudaError_t e;
-    if (h->variant == 2) {
-        e = h->prec == 32 ? launch_step_march<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->mcfg, h->stream)
-                          : launch_step_march<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->mcfg,
-                                                      h->stream);
-    } else if (h->variant == 3) {
-        e = h->prec == 32
-                ? launch_step_tma<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->tcfg, h->tmaps, h->stream)
-                : launch_step_tma<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->tcfg, h->tmaps,
-                                          h->stream);
-    } else {
-        e = h->prec == 32 ? launch_step_simple<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->zr, h->stream)
-                          : launch_step_simple<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->zr,
-                                                       h->stream);
-    }
+    cudaError_t e = h->prec == 32 ? launch_step_with<float>(h, bufs_of<float>(h), true)
+                                  : launch_step_with<double>(h, bufs_of<double>(h), true);
     return cuda_status(e);
 }
 
@@ -283,7 +249,7 @@ lat_status create_common(const lat_params* params, void* stream, void* const buf
     return LAT_OK;
 }
 
-} // namespace
+} // namespace lat
 
 extern "C" {
 
@@ -336,6 +302,22 @@ lat_status lat_sync(lat_handle* h)
     DevScalars s;
     LAT_TRY(read_scalars(h, &s));
     return (lat_status)s.status;
+}
+
+lat_status lat_set_g2(lat_handle* h, double g2)
+{
+    if (!h || !(g2 >= 0.0) || !std::isfinite(g2)) return LAT_EINVAL;
+    lat_params p = h->p;
+    p.g2 = g2;
+    Model M;
+    LAT_TRY(derive_model(p, &M));
+    LAT_TRY(check_cfl(p, M));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    h->p = p;
+    h->M = M;
+    drop_graph(h);      // the captured launches carry the old constants
+    h->dirty = true;    // coefficients of the next step follow kappa
+    return LAT_OK;
 }
 
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth)

@@ -1,0 +1,497 @@
+// lat_adjoint.cu -- reverse-mode derivative of the leapfrog evolution (the
+// adjoint of Sec. II.B, eq. evo with eq. scalar-evo and eq. scale), with
+// sqrt(n) checkpointing and recomputation.
+//
+// Forward step k (state f_k, pi_k, a_k, a'_k; volume sums S_k of f_k):
+//   a'' and the coefficients cL, cF, cdom, kappa from (a_k, a'_k, S_k) (the
+//   implicit a' update of eq. scale, solved as a quadratic in y = a'_k + a'_{k+1})
+//   pi_{k+1} = pi_k + dt (cL Lap f_k + cF f_k - dV/df(f_k))
+//   f_{k+1}  = f_k + dt pi_{k+1},  a'_{k+1} = y - a'_k,  a_{k+1} = a_k + dt a'_{k+1}
+// Reverse step k, from the adjoint (fb, pb) of (f_{k+1}, pi_{k+1}):
+//   pt = pb + dt fb                                  (drift)
+//   fb_k = fb + dt (cL Lap pt + cF pt - Hess V(f_k) pt) + sum_j Sb_j dS_j/df(f_k)
+//   pb_k = pt
+// where Sb, the adjoint of the volume sums S_k, comes from the FP64 reverse of
+// the scalar update, whose inputs are four volume sums of pt against f_k:
+//   dt <pt, Lap f_k>, dt <pt, f_k>, -dt <pt0, f0^(beta-1)>, -dt <pt0 f0 f1^2 + pt1 f0^2 f1>.
+// One kernel per reverse step does the field update of step k and, from the
+// pt it has just formed, the four sums of step k-1; its last block runs the
+// scalar reverse of step k-1. Memory traffic per reverse step: read f_k,
+// f_{k-1} and the incoming adjoints, write the outgoing adjoints.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lat_internal.h"
+
+namespace lat {
+
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+// Adjoint scalars carried between reverse steps (FP64, device).
+struct AdjScalars {
+    double ba, bad, bk0;     // adjoints of a, a' of the state being reached, and of kappa0
+    double cL, cF, cd, kp;   // forward coefficients of the step the next field update reverses
+    double bS[4];            // adjoint of that step's volume sums
+    int status;
+    unsigned int ticket;
+};
+
+template <typename T>
+struct AdjBufs {
+    const T* f[2];    // f_k, the fields the reversed step started from
+    const T* fm[2];   // f_{k-1}, or null when there is no earlier step
+    const T* fb[2];   // adjoint of f_{k+1}
+    const T* pb[2];   // adjoint of pi_{k+1}
+    T* fbo[2];        // adjoint of f_k (out)
+    T* pbo[2];        // adjoint of pi_k (out)
+};
+
+// Intermediate values of the forward scalar update of one step.
+struct ScaleFwd {
+    double c, q, alpha, y, ah, add, vpr, ea, eb;
+};
+
+// Recompute the forward scalar update from the scalars the step started from
+// (same formulas as scale_solve, with the intermediates kept).
+__device__ void scale_forward(const Model& M, const DevScalars& s, ScaleFwd& o)
+{
+    const double a = s.a;
+    o.vpr = s.cdom * s.S[2] + s.kappa * s.S[3];
+    o.ea = apow(a, -2.0 * M.s - 2.0 * M.r - 1.0);
+    o.eb = apow(a, 2.0 * M.s + 2.0);
+    o.c = M.eight_pi_G / (M.A * M.A) * o.ea * ((s.S[0] + s.S[1]) / 3.0 + o.eb * o.vpr);
+    o.q = -(M.s + 2.0) / a;
+    o.alpha = M.dt * o.q * 0.25;
+    o.y = 2.0 * s.ad_half;
+    o.ah = s.ad_half;
+    o.add = s.add;
+}
+
+// Reverse of the scalar update of one step: given the adjoints of the
+// coefficients the kick used (bcL, bcF, bcd, bkp) and of y (from the a, a'
+// update), add to the adjoints of a, a', kappa0 and produce those of S.
+__device__ void scale_reverse(const Model& M, const DevScalars& s, double bcL, double bcF, double bcd, double bkp,
+                              double by, AdjScalars* as, double bS[4])
+{
+    const double a = s.a;
+    double ba = 0.0, bad = 0.0;
+    for (int k = 0; k < 4; k++) bS[k] = 0.0;
+    if (M.expansion) {
+        ScaleFwd o;
+        scale_forward(M, s, o);
+        const double r = M.r, sx = M.s;
+        const double hh = o.ah / a;
+        // cF = r(s-r+2) h^2 + r a''/a, h = a'_half / a
+        const double bh = bcF * 2.0 * r * (sx - r + 2.0) * hh;
+        const double badd = bcF * r / a;
+        ba -= bcF * r * o.add / (a * a);
+        double bah = bh / a;
+        ba -= bh * o.ah / (a * a);
+        // a'' = q a'_half^2 + c
+        double bq = badd * o.ah * o.ah;
+        bah += badd * 2.0 * o.q * o.ah;
+        double bc = badd;
+        // a'_half = y / 2; y solves alpha y^2 - y + gamma = 0 with gamma = 2a' + dt c
+        by += 0.5 * bah;
+        const double den = 1.0 - 2.0 * o.alpha * o.y;
+        const double bgamma = by / den, balpha = by * o.y * o.y / den;
+        bq += balpha * M.dt * 0.25;
+        bad += 2.0 * bgamma;
+        bc += M.dt * bgamma;
+        ba += bq * (sx + 2.0) / (a * a);
+        // cL = a^(-2s-2)
+        ba += bcL * (-2.0 * sx - 2.0) * apow(a, -2.0 * sx - 3.0);
+        // c = K ea (T + eb vpr)
+        const double K = M.eight_pi_G / (M.A * M.A);
+        const double T = (s.S[0] + s.S[1]) / 3.0;
+        const double bea = bc * K * (T + o.eb * o.vpr);
+        const double bT = bc * K * o.ea;
+        const double beb = bc * K * o.ea * o.vpr;
+        const double bvpr = bc * K * o.ea * o.eb;
+        ba += bea * (-2.0 * sx - 2.0 * r - 1.0) * apow(a, -2.0 * sx - 2.0 * r - 2.0);
+        ba += beb * (2.0 * sx + 2.0) * apow(a, 2.0 * sx + 1.0);
+        bS[0] = bT / 3.0;
+        bS[1] = bT / 3.0;
+        bcd += bvpr * s.S[2];
+        bkp += bvpr * s.S[3];
+        bS[2] = bvpr * s.cdom;
+        bS[3] = bvpr * s.kappa;
+    }
+    // cdom = cdom0 a^pdom, kappa = kappa0 a^pint
+    ba += bcd * M.cdom0 * M.pdom * apow(a, M.pdom - 1.0) + bkp * M.kappa0 * M.pint * apow(a, M.pint - 1.0);
+    as->bk0 += bkp * apow(a, M.pint);
+    as->ba += ba;
+    as->bad += bad;
+}
+
+template <typename T>
+__device__ __forceinline__ T powb1(T f, int beta)   // f^(beta-1), beta in {2, 4}
+{
+    return beta == 4 ? f * f * f : f;
+}
+
+// Reverse step kernel. UPDATE: reverse the field update of step k (outputs fbo,
+// pbo); always: if fm is given, the four sums of step k-1 from pt' = pb_k + dt fb_k
+// (without UPDATE, pb + dt fb of the inputs), folded by the last block into the
+// scalar reverse of step k-1 (hist = the scalars step k-1 started from).
+template <typename T, bool UPDATE>
+__global__ void __launch_bounds__(kAdjThreads) adj_step_kernel(AdjBufs<T> B, Model M, AdjScalars* as,
+                                                               const DevScalars* hist, double* partials)
+{
+    __shared__ double red[32 * kSums];
+    if (as->status != LAT_OK) return;
+    const int n = M.n;
+    const long long nn = (long long)n * n, n3 = nn * n;
+    const T dt = (T)M.dt;
+    const T cLs = (T)(as->cL * M.inv_dx2), cF = (T)as->cF, cd = (T)as->cd, kp = (T)as->kp;
+    const T sg0 = (T)(-2.0 * as->bS[0] * M.inv_dx2 * M.inv_sites), sg1 = (T)(-2.0 * as->bS[1] * M.inv_dx2 * M.inv_sites);
+    const T sv2 = (T)(as->bS[2] * M.inv_sites), sv3 = (T)(as->bS[3] * M.inv_sites);
+    const int beta = M.beta;
+    const bool sums = B.fm[0] != nullptr;
+    T acc[kSums] = {T(0), T(0), T(0), T(0)};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / nn);
+        const long long ixm = i + ((x == 0 ? n - 1 : x - 1) - x), ixp = i + ((x == n - 1 ? 0 : x + 1) - x);
+        const long long iym = i + (long long)((y == 0 ? n - 1 : y - 1) - y) * n;
+        const long long iyp = i + (long long)((y == n - 1 ? 0 : y + 1) - y) * n;
+        const long long izm = i + ((z == 0 ? n - 1 : z - 1) - z) * nn;
+        const long long izp = i + ((z == n - 1 ? 0 : z + 1) - z) * nn;
+        T ptn[2];   // pt' of step k-1 at this site
+        if (UPDATE) {
+            T pt[2], lpt[2], lf[2];
+#pragma unroll
+            for (int f = 0; f < 2; f++) {
+                const T* pb = B.pb[f];
+                const T* fb = B.fb[f];
+                const T c = __ldg(pb + i) + dt * __ldg(fb + i);
+                pt[f] = c;
+                lpt[f] = ((__ldg(pb + ixm) + dt * __ldg(fb + ixm)) - c) + ((__ldg(pb + ixp) + dt * __ldg(fb + ixp)) - c) +
+                         ((__ldg(pb + iym) + dt * __ldg(fb + iym)) - c) + ((__ldg(pb + iyp) + dt * __ldg(fb + iyp)) - c) +
+                         ((__ldg(pb + izm) + dt * __ldg(fb + izm)) - c) + ((__ldg(pb + izp) + dt * __ldg(fb + izp)) - c);
+                const T* ff = B.f[f];
+                const T fc = __ldg(ff + i);
+                lf[f] = (__ldg(ff + ixm) - fc) + (__ldg(ff + ixp) - fc) + (__ldg(ff + iym) - fc) + (__ldg(ff + iyp) - fc) +
+                        (__ldg(ff + izm) - fc) + (__ldg(ff + izp) - fc);
+            }
+            const T f0 = __ldg(B.f[0] + i), f1 = __ldg(B.f[1] + i);
+            // Hessian of V_pr = cdom f0^beta/beta + kappa f0^2 f1^2/2
+            const T h00 = (beta == 4 ? T(3) * cd * f0 * f0 : cd) + kp * f1 * f1;
+            const T h01 = T(2) * kp * f0 * f1;
+            const T h11 = kp * f0 * f0;
+            const T g0 = cLs * lpt[0] + cF * pt[0] - h00 * pt[0] - h01 * pt[1];
+            const T g1 = cLs * lpt[1] + cF * pt[1] - h01 * pt[0] - h11 * pt[1];
+            const T s0 = sg0 * lf[0] + sv2 * powb1(f0, beta) + sv3 * f0 * f1 * f1;
+            const T s1 = sg1 * lf[1] + sv3 * f0 * f0 * f1;
+            const T nf0 = __ldg(B.fb[0] + i) + dt * g0 + s0;
+            const T nf1 = __ldg(B.fb[1] + i) + dt * g1 + s1;
+            B.fbo[0][i] = nf0;
+            B.fbo[1][i] = nf1;
+            B.pbo[0][i] = pt[0];
+            B.pbo[1][i] = pt[1];
+            ptn[0] = pt[0] + dt * nf0;
+            ptn[1] = pt[1] + dt * nf1;
+        } else {
+            ptn[0] = __ldg(B.pb[0] + i) + dt * __ldg(B.fb[0] + i);
+            ptn[1] = __ldg(B.pb[1] + i) + dt * __ldg(B.fb[1] + i);
+        }
+        if (sums) {
+            T lm[2];
+#pragma unroll
+            for (int f = 0; f < 2; f++) {
+                const T* ff = B.fm[f];
+                const T fc = __ldg(ff + i);
+                lm[f] = (__ldg(ff + ixm) - fc) + (__ldg(ff + ixp) - fc) + (__ldg(ff + iym) - fc) + (__ldg(ff + iyp) - fc) +
+                        (__ldg(ff + izm) - fc) + (__ldg(ff + izp) - fc);
+            }
+            const T m0 = __ldg(B.fm[0] + i), m1 = __ldg(B.fm[1] + i);
+            acc[0] += ptn[0] * lm[0] + ptn[1] * lm[1];
+            acc[1] += ptn[0] * m0 + ptn[1] * m1;
+            acc[2] += ptn[0] * powb1(m0, beta);
+            acc[3] += ptn[0] * m0 * m1 * m1 + ptn[1] * m0 * m0 * m1;
+        }
+    }
+    if (!sums) return;
+    double bs[kSums];
+    block_reduce(acc, red, bs);
+    __shared__ unsigned int is_last;
+    const int nblocks = gridDim.x;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kSums; k++) partials[(size_t)blockIdx.x * kSums + k] = bs[k];
+        __threadfence();
+        is_last = atomicAdd(&as->ticket, 1u) == (unsigned int)nblocks - 1u;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x >= 32) return;
+    double v[kSums] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += 32)
+#pragma unroll
+        for (int k = 0; k < kSums; k++) v[k] += __ldcg(partials + (size_t)b * kSums + k);
+#pragma unroll
+    for (int k = 0; k < kSums; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (threadIdx.x != 0) return;
+    as->ticket = 0u;
+    const DevScalars s = *hist;
+    // reverse of a_{k} = a_{k-1} + dt a'_{k}, a'_{k} = y - a'_{k-1}
+    double by = 0.0;
+    if (M.expansion) {
+        by = as->bad + M.dt * as->ba;
+        as->bad = -by;
+    }
+    const double bcL = M.dt * v[0] * M.inv_dx2, bcF = M.dt * v[1], bcd = -M.dt * v[2], bkp = -M.dt * v[3];
+    double bS[4];
+    scale_reverse(M, s, bcL, bcF, bcd, bkp, by, as, bS);
+    bool finite = isfinite(as->ba) && isfinite(as->bad) && isfinite(as->bk0);
+    for (int k = 0; k < 4; k++) {
+        as->bS[k] = bS[k];
+        finite = finite && isfinite(bS[k]);
+    }
+    as->cL = s.cL;
+    as->cF = s.cF;
+    as->cd = s.cdom;
+    as->kp = s.kappa;
+    if (!finite) as->status = LAT_ENONFINITE;
+    __threadfence();
+}
+
+// J = <f1^2> (volume mean of chi squared) per block, and its gradient 2 f1 / N^3.
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads) chi2_kernel(const T* __restrict__ f1, T* __restrict__ grad, long long n3,
+                                                           double inv_sites, double* partials)
+{
+    __shared__ double red[32 * kSums];
+    T acc[kSums] = {T(0), T(0), T(0), T(0)};
+    const T two_over = (T)(2.0 * inv_sites);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+        const T v = f1[i];
+        acc[0] += v * v;
+        if (grad) grad[i] = two_over * v;
+    }
+    double bs[kSums];
+    block_reduce(acc, red, bs);
+    if (threadIdx.x == 0) partials[blockIdx.x] = bs[0];
+}
+
+int adj_blocks(long long n3)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long need = (n3 + kAdjThreads - 1) / kAdjThreads;
+    return (int)std::max<long long>(1, std::min<long long>(need, (long long)sms * 8));
+}
+
+// Device allocations of one reverse-mode call, freed together.
+struct Scratch {
+    std::vector<void*> ptrs;
+    ~Scratch()
+    {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename P>
+    bool alloc(P** out, size_t bytes)
+    {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+        ptrs.push_back(p);
+        *out = static_cast<P*>(p);
+        return true;
+    }
+};
+
+// Reverse-mode product of n steps. If observable >= 0 the adjoint of the final
+// state is that of the observable (0: <chi^2>), written into fb/pb after the
+// forward pass, and *J_out receives its value; otherwise fb, pb and sbar[0..1]
+// carry the adjoint of the final state in.
+template <typename T>
+lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T* pb_user, double sbar[4],
+                    int observable, double* J_out)
+{
+    const Model& M = h->M;
+    const size_t N3 = h->nsites, ab = N3 * sizeof(T);
+    cudaStream_t st = h->stream;
+    lat_status rs = ensure_prepared(h);
+    if (rs != LAT_OK) return rs;
+    DevScalars s0;
+    rs = read_scalars(h, &s0);
+    if (rs != LAT_OK) return rs;
+    if (s0.status != LAT_OK) return (lat_status)s0.status;
+    const int64_t K = ckpt_every > 0 ? std::min<int64_t>(ckpt_every, std::max<int64_t>(n, 1))
+                                     : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)n)));
+    const int64_t nck = n > 0 ? (n + K - 1) / K : 0;
+    const int nb = adj_blocks((long long)N3);
+
+    Scratch S;
+    T *ck = nullptr, *seg = nullptr, *adj1 = nullptr, *fin = nullptr;
+    DevScalars *ck_sc = nullptr, *hist = nullptr, *fin_sc = nullptr;
+    AdjScalars* as = nullptr;
+    double* part = nullptr;
+    if (!S.alloc(&ck, (size_t)nck * 6 * ab) || !S.alloc(&ck_sc, (size_t)nck * sizeof(DevScalars)) ||
+        !S.alloc(&hist, (size_t)std::max<int64_t>(n, 1) * sizeof(DevScalars)) || !S.alloc(&seg, (size_t)K * 2 * ab) ||
+        !S.alloc(&adj1, 4 * ab) || !S.alloc(&fin, 4 * ab) || !S.alloc(&fin_sc, sizeof(DevScalars)) ||
+        !S.alloc(&as, sizeof(AdjScalars)) || !S.alloc(&part, (size_t)nb * kSums * sizeof(double)))
+        return LAT_ENOMEM;
+    Bufs<T> hb = bufs_of<T>(h);
+    auto arr = [&](T* base, size_t i) { return base + i * N3; };
+
+    // forward pass: checkpoints (f_c, pi_c, f_{c-1}, scalars) every K steps and
+    // the scalars every step started from
+    for (int64_t k = 0; k < n; k++) {
+        const int par = (int)((s0.step + k) & 1);
+        if (k % K == 0) {
+            T* c = arr(ck, (size_t)(k / K) * 6);
+            for (int f = 0; f < 2; f++) {
+                LAT_CUDA(cudaMemcpyAsync(c + f * N3, hb.f[par][f], ab, cudaMemcpyDeviceToDevice, st));
+                LAT_CUDA(cudaMemcpyAsync(c + (2 + f) * N3, hb.p[par][f], ab, cudaMemcpyDeviceToDevice, st));
+                if (k > 0) LAT_CUDA(cudaMemcpyAsync(c + (4 + f) * N3, hb.f[1 - par][f], ab, cudaMemcpyDeviceToDevice, st));
+            }
+            LAT_CUDA(cudaMemcpyAsync(ck_sc + k / K, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
+        }
+        LAT_CUDA(cudaMemcpyAsync(hist + k, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
+        LAT_CUDA(launch_step_with<T>(h, hb, false));
+    }
+    const int parN = (int)((s0.step + n) & 1);
+    for (int f = 0; f < 2; f++) {
+        LAT_CUDA(cudaMemcpyAsync(fin + f * N3, hb.f[parN][f], ab, cudaMemcpyDeviceToDevice, st));
+        LAT_CUDA(cudaMemcpyAsync(fin + (2 + f) * N3, hb.p[parN][f], ab, cudaMemcpyDeviceToDevice, st));
+    }
+    LAT_CUDA(cudaMemcpyAsync(fin_sc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
+
+    // adjoint of the final state
+    AdjScalars a0;
+    std::memset(&a0, 0, sizeof(a0));
+    if (observable == 0) {
+        LAT_CUDA(cudaMemsetAsync(fb_user, 0, ab, st));
+        LAT_CUDA(cudaMemsetAsync(pb_user, 0, 2 * ab, st));
+        chi2_kernel<T><<<nb, kAdjThreads, 0, st>>>(hb.f[parN][1], fb_user + N3, (long long)N3, M.inv_sites, part);
+        LAT_CUDA(cudaGetLastError());
+        std::vector<double> hp(nb);
+        LAT_CUDA(cudaMemcpyAsync(hp.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LAT_CUDA(cudaStreamSynchronize(st));
+        double J = 0.0;
+        for (int b = 0; b < nb; b++) J += hp[b];
+        if (J_out) *J_out = J * M.inv_sites;
+    } else {
+        a0.ba = sbar[0];
+        a0.bad = sbar[1];
+    }
+    LAT_CUDA(cudaMemcpyAsync(as, &a0, sizeof(a0), cudaMemcpyHostToDevice, st));
+
+    T* setF[2] = {fb_user, adj1};
+    T* setP[2] = {pb_user, adj1 + 2 * N3};
+    int cur = 0;
+    auto adj_bufs = [&](const T* fk0, const T* fm0) {
+        AdjBufs<T> b;
+        for (int f = 0; f < 2; f++) {
+            b.f[f] = fk0 ? fk0 + f * N3 : nullptr;
+            b.fm[f] = fm0 ? fm0 + f * N3 : nullptr;
+            b.fb[f] = setF[cur] + f * N3;
+            b.pb[f] = setP[cur] + f * N3;
+            b.fbo[f] = setF[1 - cur] + f * N3;
+            b.pbo[f] = setP[1 - cur] + f * N3;
+        }
+        return b;
+    };
+    if (n > 0) {
+        // sums of the last step from the final adjoint and f_{n-1}, still in
+        // the other ping-pong buffer
+        T* fm_last = seg;   // f_{n-1} copied next to the segment storage
+        for (int f = 0; f < 2; f++)
+            LAT_CUDA(cudaMemcpyAsync(fm_last + f * N3, hb.f[1 - parN][f], ab, cudaMemcpyDeviceToDevice, st));
+        adj_step_kernel<T, false><<<nb, kAdjThreads, 0, st>>>(adj_bufs(nullptr, fm_last), M, as, hist + (n - 1), part);
+        LAT_CUDA(cudaGetLastError());
+    }
+    for (int64_t sgi = nck - 1; sgi >= 0; sgi--) {
+        const int64_t c = sgi * K, e = std::min<int64_t>(c + K, n);
+        const T* cp = arr(ck, (size_t)sgi * 6);
+        // restore the checkpoint and recompute f_c .. f_{e-1} into the segment storage
+        const int parc = (int)((s0.step + c) & 1);
+        for (int f = 0; f < 2; f++) {
+            LAT_CUDA(cudaMemcpyAsync(seg + f * N3, cp + f * N3, ab, cudaMemcpyDeviceToDevice, st));
+            LAT_CUDA(cudaMemcpyAsync(hb.p[parc][f], cp + (2 + f) * N3, ab, cudaMemcpyDeviceToDevice, st));
+        }
+        LAT_CUDA(cudaMemcpyAsync(h->sc, ck_sc + sgi, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
+        for (int64_t k = c; k + 1 < e; k++) {
+            const int par = (int)((s0.step + k) & 1);
+            Bufs<T> b = hb;
+            for (int f = 0; f < 2; f++) {
+                b.f[par][f] = arr(seg, (size_t)(k - c) * 2 + f);
+                b.f[1 - par][f] = arr(seg, (size_t)(k - c + 1) * 2 + f);
+            }
+            LAT_CUDA(launch_step_with<T>(h, b, false));
+        }
+        // reverse steps e-1 .. c
+        for (int64_t k = e - 1; k >= c; k--) {
+            const T* fk = arr(seg, (size_t)(k - c) * 2);
+            const T* fm = k > c ? arr(seg, (size_t)(k - c - 1) * 2) : (k > 0 ? cp + 4 * N3 : nullptr);
+            adj_step_kernel<T, true><<<nb, kAdjThreads, 0, st>>>(adj_bufs(fk, fm), M, as, k > 0 ? hist + (k - 1) : hist,
+                                                                 part);
+            LAT_CUDA(cudaGetLastError());
+            cur = 1 - cur;
+        }
+    }
+    if (cur != 0) {
+        LAT_CUDA(cudaMemcpyAsync(fb_user, setF[cur], 2 * ab, cudaMemcpyDeviceToDevice, st));
+        LAT_CUDA(cudaMemcpyAsync(pb_user, setP[cur], 2 * ab, cudaMemcpyDeviceToDevice, st));
+    }
+    // the handle ends at the final state
+    for (int f = 0; f < 2; f++) {
+        LAT_CUDA(cudaMemcpyAsync(hb.f[parN][f], fin + f * N3, ab, cudaMemcpyDeviceToDevice, st));
+        LAT_CUDA(cudaMemcpyAsync(hb.p[parN][f], fin + (2 + f) * N3, ab, cudaMemcpyDeviceToDevice, st));
+    }
+    LAT_CUDA(cudaMemcpyAsync(h->sc, fin_sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
+    AdjScalars out;
+    LAT_CUDA(cudaMemcpyAsync(&out, as, sizeof(out), cudaMemcpyDeviceToHost, st));
+    DevScalars sN;
+    LAT_CUDA(cudaMemcpyAsync(&sN, fin_sc, sizeof(sN), cudaMemcpyDeviceToHost, st));
+    LAT_CUDA(cudaStreamSynchronize(st));
+    if (sN.status != LAT_OK) return (lat_status)sN.status;
+    if (out.status != LAT_OK) return (lat_status)out.status;
+    sbar[0] = out.ba;
+    sbar[1] = out.bad;
+    sbar[2] = out.bk0;
+    sbar[3] = out.bk0 / (M.A * M.A * M.B * M.B);
+    return LAT_OK;
+}
+
+} // namespace
+
+} // namespace lat
+
+using namespace lat;
+
+extern "C" {
+
+lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fbar_dev, void* pibar_dev,
+                   double sbar[4])
+{
+    if (!h || n_steps < 0 || ckpt_every < 0 || !fbar_dev || !pibar_dev || !sbar) return LAT_EINVAL;
+    if (((uintptr_t)fbar_dev | (uintptr_t)pibar_dev) % h->esize != 0) return LAT_EINVAL;
+    return h->prec == 32 ? vjp_impl<float>(h, n_steps, ckpt_every, (float*)fbar_dev, (float*)pibar_dev, sbar, -1, nullptr)
+                         : vjp_impl<double>(h, n_steps, ckpt_every, (double*)fbar_dev, (double*)pibar_dev, sbar, -1,
+                                            nullptr);
+}
+
+lat_status lat_adjoint(lat_handle* h, int64_t n_steps, int observable, int64_t ckpt_every, double* J_out,
+                       double* dJ_dg2, void* dJ_df_dev, void* dJ_dpi_dev)
+{
+    if (!h || n_steps < 0 || ckpt_every < 0 || !dJ_df_dev || !dJ_dpi_dev) return LAT_EINVAL;
+    if (observable != 0) return LAT_EUNSUPPORTED;
+    if (((uintptr_t)dJ_df_dev | (uintptr_t)dJ_dpi_dev) % h->esize != 0) return LAT_EINVAL;
+    double sbar[4] = {0.0, 0.0, 0.0, 0.0};
+    const lat_status st =
+        h->prec == 32 ? vjp_impl<float>(h, n_steps, ckpt_every, (float*)dJ_df_dev, (float*)dJ_dpi_dev, sbar, observable, J_out)
+                      : vjp_impl<double>(h, n_steps, ckpt_every, (double*)dJ_df_dev, (double*)dJ_dpi_dev, sbar, observable,
+                                         J_out);
+    if (st == LAT_OK && dJ_dg2) *dJ_dg2 = sbar[3];
+    return st;
+}
+
+} // extern "C"

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "LAT_OK", 1: "LAT_EINVAL", 2: "LAT_ECFL", 3: "LAT_ENOMEM", 4:
 EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evolve", "lat_energies",
             "lat_spectrum", "lat_get_state", "lat_set_state", "lat_get_scalars", "lat_set_scalars",
             "lat_sync", "lat_set_kernel", "lat_kernel_info", "lat_destroy", "lat_status_string",
-            "lat_checkpoint_bytes", "lat_save_checkpoint", "lat_load_checkpoint", "lat_field_sums_static")
+            "lat_checkpoint_bytes", "lat_save_checkpoint", "lat_load_checkpoint", "lat_field_sums_static",
+            "lat_set_g2", "lat_vjp", "lat_adjoint")
 
 
 class LatParams(C.Structure):
@@ -86,6 +87,9 @@ def load_library(build_if_missing: bool = True):
             L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
             L.lat_load_checkpoint.argtypes = [P, P, C.c_uint64]
             L.lat_field_sums_static.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_double, P, P]
+            L.lat_set_g2.argtypes = [P, C.c_double]
+            L.lat_vjp.argtypes = [P, C.c_int64, C.c_int64, P, P, dp]
+            L.lat_adjoint.argtypes = [P, C.c_int64, C.c_int, C.c_int64, dp, dp, P, P]
             L.lat_destroy.argtypes = [P]
             L.lat_destroy.restype = None
             L.lat_status_string.argtypes = [C.c_int]
@@ -281,3 +285,40 @@ class Lattice:
                                     p.ctypes.data_as(C.POINTER(C.c_double)),
                                     c.ctypes.data_as(C.POINTER(C.c_int64))), "lat_spectrum")
         return k, p, c
+
+    # -- derivatives
+    def set_g2(self, g2: float):
+        """Change the coupling g^2 (the state is kept)."""
+        _check(self._L.lat_set_g2(self._h, float(g2)), "lat_set_g2")
+        self.params["g2"] = float(g2)
+
+    def vjp(self, n_steps: int, fbar, pibar, abar: float = 0.0, adbar: float = 0.0, ckpt_every: int = 0):
+        """Reverse-mode product of n_steps steps from the current state (lat_vjp).
+        fbar, pibar: CUDA tensors of 2*n^3 elements of the lattice dtype (phi then
+        chi), the adjoint of the final f and pi; overwritten in place with the
+        adjoint of the starting f and pi. Returns (abar0, adbar0, dkappa0, dg2).
+        The lattice ends advanced by n_steps."""
+        for t in (fbar, pibar):
+            assert t.is_cuda and t.dtype == self.dtype and t.numel() == 2 * self.n ** 3 and t.is_contiguous()
+        sb = (C.c_double * 4)(float(abar), float(adbar), 0.0, 0.0)
+        self._torch.cuda.current_stream(self.device).synchronize()
+        _check(self._L.lat_vjp(self._h, int(n_steps), int(ckpt_every), C.c_void_p(fbar.data_ptr()),
+                               C.c_void_p(pibar.data_ptr()), sb), "lat_vjp")
+        return sb[0], sb[1], sb[2], sb[3]
+
+    def adjoint(self, n_steps: int, observable: int = 0, ckpt_every: int = 0):
+        """J = <chi^2> after n_steps and its gradient with respect to the current
+        state and g^2 (lat_adjoint). Returns (J, dJ/df, dJ/dpi, dJ/dg2) with the
+        gradients as CUDA tensors of shape (2, n, n, n). The lattice ends advanced
+        by n_steps."""
+        torch = self._torch
+        n3 = self.n ** 3
+        df = torch.empty(2 * n3, dtype=self.dtype, device=self.device)
+        dp = torch.empty(2 * n3, dtype=self.dtype, device=self.device)
+        J, dg2 = C.c_double(), C.c_double()
+        torch.cuda.current_stream(self.device).synchronize()
+        _check(self._L.lat_adjoint(self._h, int(n_steps), int(observable), int(ckpt_every), C.byref(J),
+                                   C.byref(dg2), C.c_void_p(df.data_ptr()), C.c_void_p(dp.data_ptr())),
+               "lat_adjoint")
+        shp = (2, self.n, self.n, self.n)
+        return J.value, df.view(shp), dp.view(shp), dg2.value
