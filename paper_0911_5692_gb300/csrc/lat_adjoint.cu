@@ -134,7 +134,63 @@ __device__ __forceinline__ T powb1(T f, int beta)   // f^(beta-1), beta in {2, 4
     return beta == 4 ? f * f * f : f;
 }
 
-// Reverse step kernel. UPDATE: reverse the field update of step k (outputs fbo,
+// Fold the per-thread sums of a reverse-step kernel (block reduction, then the
+// last block of the launch in fixed order) and run the FP64 scalar reverse of
+// step k-1 from them; hist = the scalars step k-1 started from. Writes the
+// coefficients and the adjoint of the sums that the next field update uses.
+template <typename T>
+__device__ void adj_finish(T acc[kSums], double* red, AdjScalars* as, const DevScalars* hist, double* partials,
+                           const Model& M)
+{
+    double bs[kSums];
+    block_reduce(acc, red, bs);
+    __shared__ unsigned int is_last;
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if (tid == 0) {
+        for (int k = 0; k < kSums; k++) partials[(size_t)bid * kSums + k] = bs[k];
+        __threadfence();
+        is_last = atomicAdd(&as->ticket, 1u) == (unsigned int)nblocks - 1u;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (tid >= 32) return;
+    double v[kSums] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = tid; b < nblocks; b += 32)
+#pragma unroll
+        for (int k = 0; k < kSums; k++) v[k] += __ldcg(partials + (size_t)b * kSums + k);
+#pragma unroll
+    for (int k = 0; k < kSums; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (tid != 0) return;
+    as->ticket = 0u;
+    const DevScalars s = *hist;
+    // reverse of a_{k} = a_{k-1} + dt a'_{k}, a'_{k} = y - a'_{k-1}
+    double by = 0.0;
+    if (M.expansion) {
+        by = as->bad + M.dt * as->ba;
+        as->bad = -by;
+    }
+    const double bcL = M.dt * v[0] * M.inv_dx2, bcF = M.dt * v[1], bcd = -M.dt * v[2], bkp = -M.dt * v[3];
+    double bS[4];
+    scale_reverse(M, s, bcL, bcF, bcd, bkp, by, as, bS);
+    bool finite = isfinite(as->ba) && isfinite(as->bad) && isfinite(as->bk0);
+    for (int k = 0; k < 4; k++) {
+        as->bS[k] = bS[k];
+        finite = finite && isfinite(bS[k]);
+    }
+    as->cL = s.cL;
+    as->cF = s.cF;
+    as->cd = s.cdom;
+    as->kp = s.kappa;
+    if (!finite) as->status = LAT_ENONFINITE;
+    __threadfence();
+}
+
+// Reverse step kernel, one site per thread (any N). UPDATE: reverse the field update of step k (outputs fbo,
 // pbo); always: if fm is given, the four sums of step k-1 from pt' = pb_k + dt fb_k
 // (without UPDATE, pb + dt fb of the inputs), folded by the last block into the
 // scalar reverse of step k-1 (hist = the scalars step k-1 started from).
@@ -215,50 +271,148 @@ __global__ void __launch_bounds__(kAdjThreads) adj_step_kernel(AdjBufs<T> B, Mod
         }
     }
     if (!sums) return;
-    double bs[kSums];
-    block_reduce(acc, red, bs);
-    __shared__ unsigned int is_last;
-    const int nblocks = gridDim.x;
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < kSums; k++) partials[(size_t)blockIdx.x * kSums + k] = bs[k];
-        __threadfence();
-        is_last = atomicAdd(&as->ticket, 1u) == (unsigned int)nblocks - 1u;
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    if (threadIdx.x >= 32) return;
-    double v[kSums] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nblocks; b += 32)
+    adj_finish(acc, red, as, hist, partials, M);
+}
+
+// Reverse step kernel as a z-march (N a multiple of 32): a 32 x 8 tile of
+// threads walks a run of z planes; each thread keeps the z-1, z, z+1 values of
+// the six stencil arrays (pt = pb + dt fb, f_k and f_{k-1} of both fields) in
+// registers and takes its x and y neighbours from a shared-memory copy of the
+// current plane with a one-site halo (two copies used alternately, so one
+// barrier per plane suffices). The loads for plane z+1 (its z+2 values and its
+// halo) are issued one plane ahead, so their latency overlaps the arithmetic of
+// plane z. Same arithmetic as adj_step_kernel.
+constexpr int kMX = 32, kMY = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kMX * kMY, sizeof(T) == 4 ? 3 : 2)
+    adj_march_kernel(AdjBufs<T> B, Model M, AdjScalars* as, const DevScalars* hist, double* partials, int nzc)
+{
+    __shared__ double red[32 * kSums];
+    __shared__ T tiles[2][6][kMY + 2][kMX + 2];
+    if (as->status != LAT_OK) return;
+    const int n = M.n;
+    const uint32_t nn = (uint32_t)n * n;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = blockIdx.x * kMX + tx, y = blockIdx.y * kMY + ty;
+    const int z0 = (int)((long long)blockIdx.z * n / nzc);
+    const int nz = (int)((long long)(blockIdx.z + 1) * n / nzc) - z0;
+    const T dt = (T)M.dt;
+    const T cLs = (T)(as->cL * M.inv_dx2), cF = (T)as->cF, cd = (T)as->cd, kp = (T)as->kp;
+    const T sg0 = (T)(-2.0 * as->bS[0] * M.inv_dx2 * M.inv_sites), sg1 = (T)(-2.0 * as->bS[1] * M.inv_dx2 * M.inv_sites);
+    const T sv2 = (T)(as->bS[2] * M.inv_sites), sv3 = (T)(as->bS[3] * M.inv_sites);
+    const int beta = M.beta;
+    const bool sums = B.fm[0] != nullptr;
+    // raw arrays: 0,1 pb; 2,3 fb; 4,5 f_k; 6,7 f_{k-1}
+    const T* R[8] = {B.pb[0], B.pb[1], B.fb[0], B.fb[1], B.f[0], B.f[1], B.fm[0], B.fm[1]};
+    const int nraw = sums ? 8 : 6;
+    const uint32_t col = (uint32_t)y * n + x;
+    // the one halo site this thread also fetches in x and in y (edge threads)
+    const bool hx = tx == 0 || tx == kMX - 1, hy = ty == 0 || ty == kMY - 1;
+    const uint32_t colx = (uint32_t)y * n + (tx == 0 ? (x == 0 ? n - 1 : x - 1) : (x == n - 1 ? 0 : x + 1));
+    const uint32_t coly = (uint32_t)(ty == 0 ? (y == 0 ? n - 1 : y - 1) : (y == n - 1 ? 0 : y + 1)) * n + x;
+    const int sx = tx == 0 ? 0 : kMX + 1, sy = ty == 0 ? 0 : kMY + 1;
+    auto plane_of = [&](int z) -> uint32_t { return (uint32_t)(z < 0 ? z + n : (z >= n ? z - n : z)) * nn; };
+    // stencil value a (0..5) from raw values
+    auto st = [&](const T* r, int a) -> T { return a < 2 ? r[a] + dt * r[a + 2] : r[a + 2]; };
+
+    T w[6][3];           // stencil arrays at z-1, z, z+1
+    T fbz[2][2];         // raw fb at z, z+1
+    T nr[8], hxr[8], hyr[8];
+    {
+        T r0[8], r1[8];
+        const uint32_t pm = plane_of(z0 - 1) + col, pc = plane_of(z0) + col;
 #pragma unroll
-        for (int k = 0; k < kSums; k++) v[k] += __ldcg(partials + (size_t)b * kSums + k);
+        for (int q = 0; q < 8; q++)
+            if (q < nraw) {
+                r0[q] = __ldg(R[q] + pm);
+                r1[q] = __ldg(R[q] + pc);
+            }
 #pragma unroll
-    for (int k = 0; k < kSums; k++)
+        for (int a = 0; a < 6; a++)
+            if (a + 2 < nraw) {
+                w[a][0] = st(r0, a);
+                w[a][1] = st(r1, a);
+            }
+        fbz[0][0] = r1[2];
+        fbz[1][0] = r1[3];
+        // plane z0+1 and the halo of plane z0
+        const uint32_t pn = plane_of(z0 + 1);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (threadIdx.x != 0) return;
-    as->ticket = 0u;
-    const DevScalars s = *hist;
-    // reverse of a_{k} = a_{k-1} + dt a'_{k}, a'_{k} = y - a'_{k-1}
-    double by = 0.0;
-    if (M.expansion) {
-        by = as->bad + M.dt * as->ba;
-        as->bad = -by;
+        for (int q = 0; q < 8; q++)
+            if (q < nraw) {
+                nr[q] = __ldg(R[q] + pn + col);
+                if (hx) hxr[q] = __ldg(R[q] + pc - col + colx);
+                if (hy) hyr[q] = __ldg(R[q] + pc - col + coly);
+            }
     }
-    const double bcL = M.dt * v[0] * M.inv_dx2, bcF = M.dt * v[1], bcd = -M.dt * v[2], bkp = -M.dt * v[3];
-    double bS[4];
-    scale_reverse(M, s, bcL, bcF, bcd, bkp, by, as, bS);
-    bool finite = isfinite(as->ba) && isfinite(as->bad) && isfinite(as->bk0);
-    for (int k = 0; k < 4; k++) {
-        as->bS[k] = bS[k];
-        finite = finite && isfinite(bS[k]);
+    T acc[kSums] = {T(0), T(0), T(0), T(0)};
+    for (int k = 0; k < nz; k++) {
+        const int z = z0 + k;
+        T(*tile)[kMY + 2][kMX + 2] = tiles[k & 1];
+#pragma unroll
+        for (int a = 0; a < 6; a++)
+            if (a + 2 < nraw) {
+                w[a][2] = st(nr, a);
+                tile[a][ty + 1][tx + 1] = w[a][1];
+                if (hx) tile[a][ty + 1][sx] = st(hxr, a);
+                if (hy) tile[a][sy][tx + 1] = st(hyr, a);
+            }
+        fbz[0][1] = nr[2];
+        fbz[1][1] = nr[3];
+        // next plane's loads: z+2 values and the halo of plane z+1
+        if (k + 1 < nz) {
+            const uint32_t p2 = plane_of(z + 2), p1 = plane_of(z + 1);
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (q < nraw) {
+                    nr[q] = __ldg(R[q] + p2 + col);
+                    if (hx) hxr[q] = __ldg(R[q] + p1 + colx);
+                    if (hy) hyr[q] = __ldg(R[q] + p1 + coly);
+                }
+        }
+        __syncthreads();
+        T lap[6];
+#pragma unroll
+        for (int a = 0; a < 6; a++)
+            if (a + 2 < nraw) {
+                const T c = w[a][1];
+                lap[a] = (tile[a][ty + 1][tx] - c) + (tile[a][ty + 1][tx + 2] - c) + (tile[a][ty][tx + 1] - c) +
+                         (tile[a][ty + 2][tx + 1] - c) + (w[a][0] - c) + (w[a][2] - c);
+            }
+        const T pt0 = w[0][1], pt1 = w[1][1], f0 = w[2][1], f1 = w[3][1];
+        const T h00 = (beta == 4 ? T(3) * cd * f0 * f0 : cd) + kp * f1 * f1;
+        const T h01 = T(2) * kp * f0 * f1;
+        const T h11 = kp * f0 * f0;
+        const T g0 = cLs * lap[0] + cF * pt0 - h00 * pt0 - h01 * pt1;
+        const T g1 = cLs * lap[1] + cF * pt1 - h01 * pt0 - h11 * pt1;
+        const T s0 = sg0 * lap[2] + sv2 * powb1(f0, beta) + sv3 * f0 * f1 * f1;
+        const T s1 = sg1 * lap[3] + sv3 * f0 * f0 * f1;
+        const T nf0 = fbz[0][0] + dt * g0 + s0;
+        const T nf1 = fbz[1][0] + dt * g1 + s1;
+        const uint32_t i = (uint32_t)z * nn + col;
+        B.fbo[0][i] = nf0;
+        B.fbo[1][i] = nf1;
+        B.pbo[0][i] = pt0;
+        B.pbo[1][i] = pt1;
+        if (sums) {
+            const T q0 = pt0 + dt * nf0, q1 = pt1 + dt * nf1;
+            const T m0 = w[4][1], m1 = w[5][1];
+            acc[0] += q0 * lap[4] + q1 * lap[5];
+            acc[1] += q0 * m0 + q1 * m1;
+            acc[2] += q0 * powb1(m0, beta);
+            acc[3] += q0 * m0 * m1 * m1 + q1 * m0 * m0 * m1;
+        }
+#pragma unroll
+        for (int a = 0; a < 6; a++) {
+            w[a][0] = w[a][1];
+            w[a][1] = w[a][2];
+        }
+        fbz[0][0] = fbz[0][1];
+        fbz[1][0] = fbz[1][1];
     }
-    as->cL = s.cL;
-    as->cF = s.cF;
-    as->cd = s.cdom;
-    as->kp = s.kappa;
-    if (!finite) as->status = LAT_ENONFINITE;
-    __threadfence();
+    if (!sums) return;
+    adj_finish(acc, red, as, hist, partials, M);
 }
 
 // J = <f1^2> (volume mean of chi squared) per block, and its gradient 2 f1 / N^3.
@@ -286,6 +440,18 @@ int adj_blocks(long long n3)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long need = (n3 + kAdjThreads - 1) / kAdjThreads;
     return (int)std::max<long long>(1, std::min<long long>(need, (long long)sms * 8));
+}
+
+// z chunks of the z-march reverse kernel: enough blocks for four per SM, runs
+// of at least 8 planes.
+int adj_march_nzc(int n)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = (n / kMX) * (n / kMY);
+    const int want = (4 * sms + tiles - 1) / tiles;
+    return std::max(1, std::min(want, std::max(1, n / 8)));
 }
 
 // Device allocations of one reverse-mode call, freed together.
@@ -327,6 +493,10 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
                                      : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)n)));
     const int64_t nck = n > 0 ? (n + K - 1) / K : 0;
     const int nb = adj_blocks((long long)N3);
+    const bool march = M.n % kMX == 0;
+    const int nzc = march ? adj_march_nzc(M.n) : 0;
+    const dim3 mgrid(march ? M.n / kMX : 1, march ? M.n / kMY : 1, march ? nzc : 1);
+    const size_t nparts = std::max<size_t>(nb, (size_t)mgrid.x * mgrid.y * mgrid.z);
 
     Scratch S;
     T *ck = nullptr, *seg = nullptr, *adj1 = nullptr, *fin = nullptr;
@@ -336,7 +506,7 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
     if (!S.alloc(&ck, (size_t)nck * 6 * ab) || !S.alloc(&ck_sc, (size_t)nck * sizeof(DevScalars)) ||
         !S.alloc(&hist, (size_t)std::max<int64_t>(n, 1) * sizeof(DevScalars)) || !S.alloc(&seg, (size_t)K * 2 * ab) ||
         !S.alloc(&adj1, 4 * ab) || !S.alloc(&fin, 4 * ab) || !S.alloc(&fin_sc, sizeof(DevScalars)) ||
-        !S.alloc(&as, sizeof(AdjScalars)) || !S.alloc(&part, (size_t)nb * kSums * sizeof(double)))
+        !S.alloc(&as, sizeof(AdjScalars)) || !S.alloc(&part, nparts * kSums * sizeof(double)))
         return LAT_ENOMEM;
     Bufs<T> hb = bufs_of<T>(h);
     auto arr = [&](T* base, size_t i) { return base + i * N3; };
@@ -431,8 +601,12 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
         for (int64_t k = e - 1; k >= c; k--) {
             const T* fk = arr(seg, (size_t)(k - c) * 2);
             const T* fm = k > c ? arr(seg, (size_t)(k - c - 1) * 2) : (k > 0 ? cp + 4 * N3 : nullptr);
-            adj_step_kernel<T, true><<<nb, kAdjThreads, 0, st>>>(adj_bufs(fk, fm), M, as, k > 0 ? hist + (k - 1) : hist,
-                                                                 part);
+            if (march)
+                adj_march_kernel<T><<<mgrid, dim3(kMX, kMY), 0, st>>>(adj_bufs(fk, fm), M, as,
+                                                                      k > 0 ? hist + (k - 1) : hist, part, nzc);
+            else
+                adj_step_kernel<T, true><<<nb, kAdjThreads, 0, st>>>(adj_bufs(fk, fm), M, as,
+                                                                     k > 0 ? hist + (k - 1) : hist, part);
             LAT_CUDA(cudaGetLastError());
             cur = 1 - cur;
         }

@@ -60,13 +60,20 @@ __device__ __forceinline__ double step_coef<double>(const DevScalars* sc, int i)
 // sum f0^beta/beta, sum f0^2 f1^2 / 2.
 constexpr int kSums = 4;
 
-// Deterministic reduction of kSums doubles over a block: a fixed shuffle tree
-// within warps, then warp 0 folds the warp totals in warp order. Result valid in
-// thread 0. `red` must hold 32 * kSums doubles.
+// Deterministic reduction of kSums doubles over a block (any block shape; warps
+// and lanes follow the linear thread index): a fixed shuffle tree within warps,
+// then warp 0 folds the warp totals in warp order. Result valid in thread 0.
+// `red` must hold 32 * kSums doubles.
+__device__ __forceinline__ int linear_tid()
+{
+    return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+__device__ __forceinline__ int block_warps() { return (blockDim.x * blockDim.y * blockDim.z + 31) >> 5; }
+
 __device__ __forceinline__ void block_reduce(double v[kSums], double* red)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
+    const int tid = linear_tid(), lane = tid & 31, warp = tid >> 5;
+    const int nwarps = block_warps();
 #pragma unroll
     for (int k = 0; k < kSums; k++)
 #pragma unroll
@@ -91,8 +98,8 @@ __device__ __forceinline__ void block_reduce(double v[kSums], double* red)
 // only one warp of the block touches it. Result in out[] of thread 0.
 __device__ __forceinline__ void block_reduce(float v[kSums], double* red, double out[kSums])
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
+    const int tid = linear_tid(), lane = tid & 31, warp = tid >> 5;
+    const int nwarps = block_warps();
 #pragma unroll
     for (int k = 0; k < kSums; k++)
 #pragma unroll
@@ -194,16 +201,17 @@ __device__ inline void scale_solve(const Model& M, DevScalars* sc)
 // writes the averages at the new field time into out[] of thread 0.
 __device__ inline void reduce_partials(const Model& M, const double* partials, int nblocks, double out[kSums])
 {
-    if (threadIdx.x >= 32) return;
+    const int tid = linear_tid();
+    if (tid >= 32) return;
     double v[kSums] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nblocks; b += 32)
+    for (int b = tid; b < nblocks; b += 32)
 #pragma unroll
         for (int k = 0; k < kSums; k++) v[k] += __ldcg(partials + (size_t)b * kSums + k);
 #pragma unroll
     for (int k = 0; k < kSums; k++)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         out[0] = v[0] * M.inv_dx2 * M.inv_sites;
         out[1] = v[1] * M.inv_dx2 * M.inv_sites;
         out[2] = v[2] * M.inv_sites;
@@ -222,10 +230,11 @@ __device__ inline void finish_block(const Model& M, DevScalars* sc, double* part
 {
     const int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int tid = linear_tid();
     double bs[kSums];
     block_reduce(v, red, bs);
     __shared__ unsigned int is_last;
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         for (int k = 0; k < kSums; k++) partials[(size_t)bid * kSums + k] = bs[k];
         __threadfence();
         unsigned int t = atomicAdd(&sc->ticket, 1u);
@@ -236,7 +245,7 @@ __device__ inline void finish_block(const Model& M, DevScalars* sc, double* part
     __threadfence();
     double S[kSums];
     reduce_partials(M, partials, nblocks, S);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         sc->ticket = 0u;
         bool finite = true;
         for (int k = 0; k < kSums; k++) finite = finite && isfinite(S[k]);

@@ -61,6 +61,20 @@ def test_adjoint_fp64_matches_oracle(model, expansion):
         assert normwise(dp[i], dpo[i]) <= 1e-10, ("dp", i)
 
 
+@pytest.mark.parametrize("n,steps", [(32, 9), (64, 6), (96, 3)])
+def test_adjoint_march_kernel_fp64(n, steps):
+    """N a multiple of 32 takes the z-march reverse kernel (several z chunks)."""
+    p, st, sc = _case("lphi4", n, 64)
+    g = _gpu(p, st, sc)
+    J, df, dp, dg2 = g.adjoint(steps)
+    Jo, dfo, dpo, dg2o = _oracle_grad(p, st, sc, steps)
+    assert abs(dg2 - dg2o) <= 1e-10 * abs(dg2o)
+    df, dp = df.cpu().numpy(), dp.cpu().numpy()
+    for i in (0, 1):
+        assert normwise(df[i], dfo[i]) <= 1e-10, ("df", i)
+        assert normwise(dp[i], dpo[i]) <= 1e-10, ("dp", i)
+
+
 def test_adjoint_ends_at_final_state():
     n, steps = 16, 25
     p, st, sc = _case("lphi4", n, 64)
