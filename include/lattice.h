@@ -238,6 +238,60 @@ lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fba
 lat_status lat_adjoint(lat_handle* h, int64_t n_steps, int observable, int64_t ckpt_every, double* J_out,
                        double* dJ_dg2, void* dJ_df_dev, void* dJ_dpi_dev);
 
+/* ---- Ensembles: independent lattices of uneven size and coupling stepped
+ * together by one persistent launch. The paper evolves one lattice at a time
+ * (Sec. II.C); every member here follows the same step (Sec. II.B, eq. evo with
+ * eq. scalar-evo and eq. scale) with its own N, dt, couplings and a(t). */
+typedef struct lat_batch lat_batch;
+
+/* Create `count` members from params[0..count-1] (all of one precision; each
+ * member owns its buffers), bound to cuda_stream. The launch shape comes from
+ * the process's autotuner cache for this set of sizes and precision, else a
+ * default. LAT_EINVAL for mixed precisions or a bad member (its lat_create
+ * status is returned), LAT_EUNSUPPORTED if a member size fits no block shape. */
+lat_status lat_batch_create(const lat_params* params, int count, void* cuda_stream, lat_batch** out);
+
+/* lat_init_fields on every member (each with its own seed). Synchronises. */
+lat_status lat_batch_init_fields(lat_batch* b);
+
+/* Advance every member by n_steps (0 <= n_steps < 2^31) in one cooperative
+ * launch (every block resident; the runtime refuses the launch otherwise),
+ * captured in a CUDA graph per step count. Between steps the blocks meet at a
+ * grid barrier whose waits are bounded by the global timer: a wait that runs out
+ * makes every block leave and lat_batch_sync return LAT_ETIMEOUT. Asynchronous. */
+lat_status lat_batch_evolve(lat_batch* b, int64_t n_steps);
+
+/* Wait for the stream; return the first sticky error of the launch or of a
+ * member. */
+lat_status lat_batch_sync(lat_batch* b);
+
+/* Autotune the launch shape: time `steps` steps for each candidate block size
+ * (tile heights follow from it) on the ensemble itself, keep the fastest and
+ * cache it for this process per (sizes, precision). Member states are saved
+ * before and restored after. Synchronises. */
+lat_status lat_batch_tune(lat_batch* b, int steps);
+
+/* Self-test of the bounded grid barrier (failure detection without a fault):
+ * launches the ensemble kernel so that its barrier waits for one block more
+ * than the launch has; every block's wait runs out after timeout_ns
+ * (1 ms .. 2 s) and the call returns LAT_ETIMEOUT with the context still
+ * usable. Member states are not touched. Synchronises. */
+lat_status lat_batch_check_barrier(lat_batch* b, int64_t timeout_ns);
+
+/* Borrow member i's handle (owned by the batch; do not destroy it) for state
+ * access, energies, spectra or checkpoints. Do not evolve it on its own while
+ * batch work is in flight. */
+lat_status lat_batch_member(lat_batch* b, int i, lat_handle** out);
+
+/* Launch shape: out[0] = blocks, out[1] = threads per block, out[2] = dynamic
+ * shared memory bytes, out[3] = work ranges, out[4] = 1 if the last evolve ran
+ * as a captured graph, out[5] = total sites, out[6] = members, out[7] = launches
+ * per evolve call. */
+lat_status lat_batch_info(lat_batch* b, int64_t out[8]);
+
+/* Release the ensemble and its members. NULL is accepted. */
+void lat_batch_destroy(lat_batch* b);
+
 /* Release the handle and the buffers it owns. NULL is accepted. */
 void lat_destroy(lat_handle* h);
 

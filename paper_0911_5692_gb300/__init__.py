@@ -5,7 +5,7 @@ The compute path is the CUDA library built from csrc/ (C ABI in
 include/lattice.h); this package holds its Python binding and the workload
 presets.
 """
-from .lattice import EXPORTED, Lattice, LatticeError, load_library, library_path, make_params  # noqa: F401
+from .lattice import EXPORTED, Ensemble, Lattice, LatticeError, load_library, library_path, make_params  # noqa: F401
 from . import workloads  # noqa: F401
 
-__all__ = ["Lattice", "LatticeError", "load_library", "library_path", "make_params", "workloads", "EXPORTED"]
+__all__ = ["Ensemble", "Lattice", "LatticeError", "load_library", "library_path", "make_params", "workloads", "EXPORTED"]

@@ -196,6 +196,29 @@ __device__ inline void scale_solve(const Model& M, DevScalars* sc)
     step_coefficients(M, sc);
 }
 
+// The scalars after one step, from those before it and the volume sums S of the
+// new fields: a_{n+3/2} = a_{n+1/2} + dt a'_{n+1}, a' <- a'_{n+1}, t += dt, then
+// the a' solve and coefficients for the next step (scale_solve). `advance` is
+// false for the sums-only pass after initialisation or a state upload.
+__device__ inline void advance_scalars(const Model& M, DevScalars& s, const double S[kSums], bool advance)
+{
+    bool finite = true;
+    for (int k = 0; k < kSums; k++) {
+        finite = finite && isfinite(S[k]);
+        s.S[k] = S[k];
+    }
+    if (advance) {
+        if (M.expansion) {
+            s.a = s.a + M.dt * s.ad_next;
+            s.ad = s.ad_next;
+        }
+        s.t = s.t + M.dt;
+        s.step = s.step + 1;
+    }
+    if (!finite) s.status = LAT_ENONFINITE;
+    else scale_solve(M, &s);
+}
+
 // Fixed-order reduction of the per-block partials by warp 0 of the block that
 // finished last (lane l folds blocks l, l+32, ..., then a fixed shuffle tree);
 // writes the averages at the new field time into out[] of thread 0.
@@ -246,20 +269,11 @@ __device__ inline void finish_block(const Model& M, DevScalars* sc, double* part
     double S[kSums];
     reduce_partials(M, partials, nblocks, S);
     if (tid == 0) {
-        sc->ticket = 0u;
-        bool finite = true;
-        for (int k = 0; k < kSums; k++) finite = finite && isfinite(S[k]);
-        for (int k = 0; k < kSums; k++) sc->S[k] = S[k];
-        if (advance) {
-            if (M.expansion) {
-                sc->a = sc->a + M.dt * sc->ad_next;
-                sc->ad = sc->ad_next;
-            }
-            sc->t = sc->t + M.dt;
-            sc->step = sc->step + 1;
-        }
-        if (!finite) sc->status = LAT_ENONFINITE;
-        else scale_solve(M, sc);
+        // every other block has taken its ticket: the whole block can be rewritten
+        DevScalars s = *sc;
+        s.ticket = 0u;
+        advance_scalars(M, s, S, advance);
+        *sc = s;
         __threadfence();
     }
 }

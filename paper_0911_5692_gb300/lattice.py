@@ -23,7 +23,9 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_spectrum", "lat_get_state", "lat_set_state", "lat_get_scalars", "lat_set_scalars",
             "lat_sync", "lat_set_kernel", "lat_kernel_info", "lat_destroy", "lat_status_string",
             "lat_checkpoint_bytes", "lat_save_checkpoint", "lat_load_checkpoint", "lat_field_sums_static",
-            "lat_set_g2", "lat_vjp", "lat_adjoint")
+            "lat_set_g2", "lat_vjp", "lat_adjoint", "lat_batch_create", "lat_batch_init_fields",
+            "lat_batch_evolve", "lat_batch_sync", "lat_batch_tune", "lat_batch_member", "lat_batch_info",
+            "lat_batch_destroy", "lat_batch_check_barrier")
 
 
 class LatParams(C.Structure):
@@ -90,12 +92,22 @@ def load_library(build_if_missing: bool = True):
             L.lat_set_g2.argtypes = [P, C.c_double]
             L.lat_vjp.argtypes = [P, C.c_int64, C.c_int64, P, P, dp]
             L.lat_adjoint.argtypes = [P, C.c_int64, C.c_int, C.c_int64, dp, dp, P, P]
+            L.lat_batch_create.argtypes = [C.POINTER(LatParams), C.c_int, P, C.POINTER(P)]
+            L.lat_batch_init_fields.argtypes = [P]
+            L.lat_batch_evolve.argtypes = [P, C.c_int64]
+            L.lat_batch_sync.argtypes = [P]
+            L.lat_batch_tune.argtypes = [P, C.c_int]
+            L.lat_batch_member.argtypes = [P, C.c_int, C.POINTER(P)]
+            L.lat_batch_info.argtypes = [P, i64p]
+            L.lat_batch_check_barrier.argtypes = [P, C.c_int64]
+            L.lat_batch_destroy.argtypes = [P]
+            L.lat_batch_destroy.restype = None
             L.lat_destroy.argtypes = [P]
             L.lat_destroy.restype = None
             L.lat_status_string.argtypes = [C.c_int]
             L.lat_status_string.restype = C.c_char_p
             for name in EXPORTED:
-                if name not in ("lat_destroy", "lat_status_string"):
+                if name not in ("lat_destroy", "lat_status_string", "lat_batch_destroy"):
                     getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -175,8 +187,32 @@ class Lattice:
             _check(self._L.lat_create(C.byref(self._p), sptr, C.byref(h)), "lat_create")
         self._h = h
 
+    @classmethod
+    def _borrow(cls, lib, handle, params: dict, device, stream, owner):
+        """A view of a handle owned elsewhere (an ensemble member); closing it
+        does not destroy the handle."""
+        import torch
+        self = cls.__new__(cls)
+        self._torch = torch
+        self._L = lib
+        self.params = dict(params)
+        self.n = int(params["n"])
+        self.precision = int(params.get("precision", 32))
+        self.dtype = torch.float32 if self.precision == 32 else torch.float64
+        self.np_dtype = np.float32 if self.precision == 32 else np.float64
+        self.device = device
+        self.stream = stream
+        self.buffers = None
+        self._p = make_params(params)
+        self._h = handle
+        self._owner = owner   # keeps the ensemble alive while the view exists
+        return self
+
     # -- lifecycle
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self._h = None
+            return
         if getattr(self, "_h", None):
             self._L.lat_destroy(self._h)
             self._h = None
@@ -322,3 +358,68 @@ class Lattice:
                "lat_adjoint")
         shp = (2, self.n, self.n, self.n)
         return J.value, df.view(shp), dp.view(shp), dg2.value
+
+
+class Ensemble:
+    """Independent lattices of uneven size and coupling stepped together by one
+    persistent launch per evolve call (lat_batch_*). ``params_list`` holds one
+    parameter dict per member (one precision for all)."""
+
+    def __init__(self, params_list, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Ensemble needs a CUDA device; the library has no CPU path")
+        self._torch = torch
+        self._L = load_library()
+        self.params = [dict(p) for p in params_list]
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        arr = (LatParams * len(self.params))(*[make_params(p) for p in self.params])
+        h = C.c_void_p()
+        _check(self._L.lat_batch_create(arr, len(self.params), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+               "lat_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lat_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.params)
+
+    def init_fields(self):
+        _check(self._L.lat_batch_init_fields(self._h), "lat_batch_init_fields")
+
+    def evolve(self, n_steps: int):
+        _check(self._L.lat_batch_evolve(self._h, int(n_steps)), "lat_batch_evolve")
+
+    def sync(self):
+        _check(self._L.lat_batch_sync(self._h), "lat_batch_sync")
+
+    def tune(self, steps: int = 10):
+        _check(self._L.lat_batch_tune(self._h, int(steps)), "lat_batch_tune")
+
+    def check_barrier(self, timeout_ns: int = 200_000_000) -> int:
+        """Run the bounded-barrier self-test; returns the lat_status it ends with
+        (LAT_ETIMEOUT = 6 when the timeout works)."""
+        return int(self._L.lat_batch_check_barrier(self._h, int(timeout_ns)))
+
+    def info(self) -> dict:
+        out = (C.c_int64 * 8)()
+        _check(self._L.lat_batch_info(self._h, out), "lat_batch_info")
+        keys = ("blocks", "threads", "smem", "ranges", "graph", "sites", "members", "launches")
+        return dict(zip(keys, [int(v) for v in out]))
+
+    def member(self, i: int) -> Lattice:
+        """Borrowed Lattice view of member i (state access, energies, spectra)."""
+        h = C.c_void_p()
+        _check(self._L.lat_batch_member(self._h, int(i), C.byref(h)), "lat_batch_member")
+        return Lattice._borrow(self._L, h, self.params[i], self.device, self.stream, self)
