@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint, ensemble and FP32-vs-FP64 measurements")
     return ap.parse_args()
 
 
@@ -182,6 +184,102 @@ def cpu_baseline(p, seconds):
     return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} FP64 oracle steps of the full {n}^3 {model_name(p)} lattice from a seeded "
                       f"synthetic state ({el:.1f} s, OpenMP over {cores} host cores)"}
+
+
+def measure_adjoint(local, name="lphi4_128_fp32"):
+    """Cost of the reverse-mode derivative on the 128^3 lambda phi^4 workload:
+    J = <chi^2> after its 2000 steps and dJ/d(f, pi, g^2) by lat_adjoint
+    (sqrt(n) checkpointing), against the plain forward evolution of the same
+    steps. ratio_total = adjoint call / forward; ratio_backward = (adjoint call -
+    forward) / forward, the recomputation plus reverse sweep per forward step."""
+    import torch
+    from paper_0911_5692_gb300 import Lattice
+    from paper_0911_5692_gb300.workloads import WORKLOADS
+    w = WORKLOADS[name]
+    p, steps = dict(w["params"]), int(w["steps"])
+    g = Lattice(p, device=local)
+    g.init_fields()
+    g.sync()
+    blob = g.save_checkpoint()
+    g.evolve(64)
+    g.sync()
+    res = {}
+    for rep in range(2):
+        g.load_checkpoint(blob)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.evolve(steps)
+        g.sync()
+        tf = time.perf_counter() - t0
+        g.load_checkpoint(blob)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, _, _, dg2 = g.adjoint(steps)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t0
+        res = {"workload": name, "n": p["n"], "steps": steps, "forward_s": tf, "adjoint_s": ta,
+               "ratio_total": ta / tf, "ratio_backward": (ta - tf) / tf, "J": J, "dJ_dg2": dg2,
+               "checkpoint_every": int(math.ceil(math.sqrt(steps))), "timing": "wall clock, second of two runs"}
+    return res
+
+
+def measure_ensemble(local, steps=200):
+    """The 64-member ensemble (N in 32, 48, 64, 96; g^2/lambda log-uniform in
+    [50, 500]; FP32) in one persistent launch per evolve call, after autotuning."""
+    import torch
+    from paper_0911_5692_gb300 import Ensemble
+    from paper_0911_5692_gb300.workloads import ensemble_64
+    ens = Ensemble(ensemble_64(), device=local)
+    ens.init_fields()
+    ens.tune(20)
+    ens.evolve(5)
+    ens.sync()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(ens.stream)
+    ens.evolve(steps)
+    e.record(ens.stream)
+    ens.sync()
+    ms = s.elapsed_time(e) / steps
+    info = ens.info()
+    su = info["sites"] / (ms / 1e3)
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and peaks.get("hbm_gbs") else FALLBACK_HBM_GBS
+    return {"workload": "ensemble_64", "members": info["members"], "sites": info["sites"], "steps": steps,
+            "ms_per_step": ms, "value": su, "unit": UNIT, "hbm_frac": su * 32 / 1e9 / peak,
+            "launch": {"blocks": info["blocks"], "threads": info["threads"], "graph": bool(info["graph"]),
+                       "launches_per_evolve": info["launches"]}}
+
+
+def measure_fp32_error(local, name, steps=200):
+    """FP32 against FP64 on the GPU for the benchmark workload: both precisions
+    from the same initial state (FP64 initialisation rounded to FP32), `steps`
+    steps, normwise error on the strided subset of 32^3 sites."""
+    import numpy as np
+    from paper_0911_5692_gb300 import Lattice
+    p = workload(name)
+    n = p["n"]
+    g64 = Lattice(dict(p, precision=64), device=local)
+    g64.init_fields()
+    st = g64.get_state()
+    sc = g64.scalars()
+    g32 = Lattice(dict(p, precision=32), device=local)
+    g32.set_state(*[a.astype(np.float32) for a in st], t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
+    g64.set_state(*[a.astype(np.float32).astype(np.float64) for a in st], t=sc["t"], a=sc["a"], ad=sc["ad"],
+                  step=sc["step"])
+    g32.evolve(steps)
+    g64.evolve(steps)
+    stride = max(1, n // 32)
+    names = ("f_phi", "f_chi", "pi_phi", "pi_chi")
+    err = {}
+    for k, (a, b) in enumerate(zip(g32.get_state(), g64.get_state())):
+        a, b = a[::stride, ::stride, ::stride], b[::stride, ::stride, ::stride]
+        d = b - b.mean() if k in (0, 2) else b
+        err[names[k]] = float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+        err[names[k] + "_fluct"] = float(np.max(np.abs(a - b)) / max(np.max(np.abs(d)), 1e-300))
+    s32, s64 = g32.scalars(), g64.scalars()
+    return {"steps": steps, "subset": f"every {stride}th site per axis", "normwise": err,
+            "a_rel": abs(s32["a"] / s64["a"] - 1)}
 
 
 def run_reference(args):
@@ -340,6 +438,11 @@ def run_ours(args):
         "context": {"paper_gtx260_256cubed_su_per_s": 7.6e8,
                     "note": "paper: GTX 260, 27-point stencil, 0.022 s/step at 256^3 (not this workload)"},
     }
+    if not args.no_extras and world == 1:
+        lat.close()
+        line["fp32_vs_fp64"] = measure_fp32_error(local, args.workload)
+        line["adjoint"] = measure_adjoint(local)
+        line["ensemble"] = measure_ensemble(local)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     print(json.dumps(line), flush=True)
