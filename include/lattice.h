@@ -238,6 +238,42 @@ lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fba
 lat_status lat_adjoint(lat_handle* h, int64_t n_steps, int observable, int64_t ckpt_every, double* J_out,
                        double* dJ_dg2, void* dJ_df_dev, void* dJ_dpi_dev);
 
+/* ---- One lattice split into z-slabs (one slab per GPU; the paper leaves
+ * multi-GPU runs as future work, Sec. IV). A slab handle owns planes
+ * [z0, z0 + nzl) of the N^3 lattice described by params (n = N). Its eight
+ * caller-owned device arrays (same order as lat_create_with_buffers) hold
+ * nzl + 3 planes of N^2 elements each: stored plane p is global plane
+ * z0 - 1 + p (mod N), so p = 0 is the halo below, 1..nzl the owned planes,
+ * nzl + 1 and nzl + 2 the halos above. One step of the whole lattice is, on
+ * every slab: (1) the caller fills the halos of the current ping-pong set
+ * (set = step & 1): f_phi and f_chi planes 0, nzl + 1, nzl + 2 and pi_phi,
+ * pi_chi plane nzl + 1 from the neighbouring slabs; (2) lat_slab_step; (3) the
+ * caller adds the four shares of every slab (an allreduce); (4)
+ * lat_slab_advance(advance = 1) with the total. Before the first step (and
+ * after any state upload): halos, lat_slab_sums, allreduce,
+ * lat_slab_advance(advance = 0). lat_get_state / lat_set_state /
+ * lat_get_scalars / lat_set_scalars act on the slab's stored arrays; the
+ * whole-lattice calls (evolve, init, energies, spectrum, checkpoints,
+ * derivative, set_kernel) return LAT_ESTATE on a slab. nzl >= 2. */
+lat_status lat_slab_create(const lat_params* params, int z0, int nzl, void* cuda_stream, void* const dev_bufs[8],
+                           lat_handle** out);
+
+/* Shares of the four volume averages of the slab's current fields (sums over
+ * its owned sites / N^3, in the order of lat_get_scalars out[4..7]) into
+ * sums_dev (device, 4 doubles). Needs the halos above. Asynchronous. */
+lat_status lat_slab_sums(lat_handle* h, double* sums_dev);
+
+/* The fused step on the owned planes (reads the current set including its
+ * halos, writes the other set) and the shares of the averages of the new
+ * fields into sums_dev (device, 4 doubles). Asynchronous. */
+lat_status lat_slab_step(lat_handle* h, double* sums_dev);
+
+/* The FP64 scale-factor update (eq. scale) from the total of all slabs'
+ * shares (sums_dev: device, 4 doubles): advance = 1 after a step (a, a', t and
+ * the step count advance), 0 to set the coefficients of the first step.
+ * Asynchronous. */
+lat_status lat_slab_advance(lat_handle* h, const double* sums_dev, int advance);
+
 /* ---- Ensembles: independent lattices of uneven size and coupling stepped
  * together by one persistent launch. The paper evolves one lattice at a time
  * (Sec. II.C); every member here follows the same step (Sec. II.B, eq. evo with

@@ -899,3 +899,15 @@ int orc_adjoint(orc_lattice *L, int64_t nsteps, double *fbar[2], double *pibar[2
     free(fs); free(sc); free(w);
     return st;
 }
+
+/* Coefficients of one step from the scalars it starts from (a, a' and the
+ * volume averages S of its fields): out = (cL, cF, cdom, kappa, y) with
+ * y = a'_n + a'_{n+1} (0 without expansion). For drivers that assemble the
+ * averages themselves (domain-decomposed runs in the tests). */
+int orc_step_coefs(const orc_lattice *L, double a, double ad, const double S[4], double out[5])
+{
+    orc_coefs o;
+    int st = step_coefs(L, a, ad, S, &o);
+    out[0] = o.cL; out[1] = o.cF; out[2] = o.cd; out[3] = o.kp; out[4] = o.y;
+    return st;
+}

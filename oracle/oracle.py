@@ -84,6 +84,7 @@ def lib():
             L.orc_fft3.argtypes = [C.c_int, dp, dp, C.c_int]
             L.orc_set_g2.argtypes = [P, C.c_double]
             L.orc_adjoint.argtypes = [P, C.c_int64, C.POINTER(dp), C.POINTER(dp), dp]
+            L.orc_step_coefs.argtypes = [P, C.c_double, C.c_double, dp, dp]
             _lib = L
     return _lib
 
@@ -207,6 +208,14 @@ class Oracle:
         _check(self._L.orc_adjoint(self._h, int(nsteps), fps, pps, _dp(sb)), "orc_adjoint")
         shp = (self.n,) * 3
         return ([f.reshape(shp) for f in fb], [q.reshape(shp) for q in pb], sb[0], sb[1], sb[2], sb[3])
+
+    def step_coefs(self, a: float, ad: float, S) -> dict:
+        """Coefficients of a step from its starting scalars (a, a', averages S):
+        cL, cF, cdom, kappa and y = a'_n + a'_{n+1}."""
+        s = np.ascontiguousarray(np.asarray(S, dtype=np.float64))
+        out = np.zeros(5)
+        _check(self._L.orc_step_coefs(self._h, float(a), float(ad), _dp(s), _dp(out)), "orc_step_coefs")
+        return dict(zip(("cL", "cF", "cdom", "kappa", "y"), out.tolist()))
 
     def chi2_mean(self) -> float:
         """Observable J = <f1^2>, the volume mean of the squared program-unit chi."""

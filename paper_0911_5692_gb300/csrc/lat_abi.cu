@@ -14,7 +14,6 @@
 
 using namespace lat;
 
-
 namespace lat {
 
 constexpr int kGraphChunk = 32;
@@ -95,7 +94,6 @@ size_t partials_needed(int n)
     return need;
 }
 
-
 lat_status launch_prepare(lat_handle* h)
 {
     cudaError_t e = h->prec == 32 ? launch_sums<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->stream)
@@ -142,6 +140,10 @@ void drop_graph(lat_handle* h)
 
 lat_status ensure_prepared(lat_handle* h)
 {
+    if (h->slab) {   // a slab's coefficients come from lat_slab_advance
+        h->dirty = false;
+        return LAT_OK;
+    }
     if (!h->dirty) return LAT_OK;
     LAT_TRY(launch_prepare(h));
     h->dirty = false;
@@ -323,6 +325,7 @@ lat_status lat_set_g2(lat_handle* h, double g2)
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
 {
     if (!h || variant < 0 || variant > 3 || ty < 0 || zr < 0 || depth < 0) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     return configure_kernel(h, variant, ty, zr, depth);
 }
@@ -348,6 +351,7 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8])
 lat_status lat_evolve(lat_handle* h, int64_t n_steps)
 {
     if (!h || n_steps < 0) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
     LAT_TRY(ensure_prepared(h));
     int64_t left = n_steps;
     // Chunks of kGraphChunk steps replay one captured graph; the step kernels read
@@ -435,6 +439,7 @@ lat_status lat_set_state(lat_handle* h, int field, int what, const void* src, in
 lat_status lat_init_fields(lat_handle* h)
 {
     if (!h) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
     const lat_params& p = h->p;
     const Model& M = h->M;
     const int n = p.n;
@@ -523,6 +528,7 @@ lat_status lat_init_fields(lat_handle* h)
 lat_status lat_energies(lat_handle* h, lat_energy_report* out)
 {
     if (!h || !out) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
     LAT_TRY(ensure_prepared(h));
     const Model& M = h->M;
     const int nb = energies_grid_blocks(M.n);
@@ -573,6 +579,7 @@ lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, doub
 {
     if (!h || field < 0 || field > 1 || nbins < 1 || nbins > 4096 || !k_out || !p_out || !count_out)
         return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
     const int n = h->p.n;
     DevScalars s;
     LAT_TRY(read_scalars(h, &s));
@@ -658,6 +665,7 @@ lat_status lat_checkpoint_bytes(lat_handle* h, uint64_t* bytes)
 lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes)
 {
     if (!h || !dst || bytes != ckpt_bytes(h)) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
     LAT_TRY(ensure_prepared(h));
     DevScalars s;
     LAT_TRY(read_scalars(h, &s));
@@ -684,6 +692,7 @@ lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes)
 lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes)
 {
     if (!h || !src || bytes != ckpt_bytes(h)) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
     CkptHeader hd;
     std::memcpy(&hd, src, sizeof(hd));
     if (std::memcmp(hd.magic, "LATCKPT2", 8) != 0 || hd.bytes != bytes || hd.scalars_bytes != sizeof(DevScalars) ||

@@ -199,6 +199,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 3 : (MAXT <= 512 ? 2 : 1))
                 L.mdtkap = step_coef<T>(&cur, 3);
                 L.dt = step_coef<T>(&cur, 4);
                 L.quartic = BL.M.beta == 4;
+                L.periodic = true;
+                L.zbase = 0;
                 MarchSums<T> A;
                 A.zero();
                 march_segment(L, g.yt, g.z0, g.nz, S, A, s == sb);

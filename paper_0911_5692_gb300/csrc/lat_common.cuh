@@ -278,4 +278,35 @@ __device__ inline void finish_block(const Model& M, DevScalars* sc, double* part
     }
 }
 
+// As finish_block, for a domain that is part of a larger lattice (a z-slab):
+// the last block writes the domain's share of the volume averages (sums over
+// its sites / N^3) to sums_out and leaves the scalars alone; the scalars advance
+// once the shares of every domain are added (advance_scalars).
+template <typename A>
+__device__ inline void finish_block_sums(const Model& M, DevScalars* sc, double* partials, A v[kSums], double* red,
+                                         double* sums_out)
+{
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int tid = linear_tid();
+    double bs[kSums];
+    block_reduce(v, red, bs);
+    __shared__ unsigned int is_last_s;
+    if (tid == 0) {
+        for (int k = 0; k < kSums; k++) partials[(size_t)bid * kSums + k] = bs[k];
+        __threadfence();
+        is_last_s = atomicAdd(&sc->ticket, 1u) == (unsigned int)nblocks - 1u;
+    }
+    __syncthreads();
+    if (!is_last_s) return;
+    __threadfence();
+    double S[kSums];
+    reduce_partials(M, partials, nblocks, S);
+    if (tid == 0) {
+        sc->ticket = 0u;
+        for (int k = 0; k < kSums; k++) sums_out[k] = S[k];
+        __threadfence();
+    }
+}
+
 } // namespace lat

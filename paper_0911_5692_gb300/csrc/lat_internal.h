@@ -27,6 +27,8 @@ struct lat_handle {
     int graph_steps;
     lat::MarchConfig alt_mcfg; // plane-ring geometry for buffers other than the handle's (TMA handles)
     bool alt_ok;
+    bool slab;           // a z-slab of a larger lattice (lat_slab_create)
+    int slab_z0, slab_nzl;
 };
 
 #define LAT_TRY(expr)                          \

@@ -40,6 +40,8 @@ struct MarchConfig {
     int nyt;       // y tiles
     int blocks;    // blocks per step
     int fast;      // 1: the instance specialised for this (N, ty, depth)
+    int nzl = 0;   // z-slab: owned planes (0: a whole periodic lattice)
+    int zbase = 0; // z-slab: stored plane of z = z + zbase
 };
 // kernel specialised for (element bytes, N, ty, depth), or null; *smem gets its
 // dynamic shared memory in bytes
@@ -48,9 +50,12 @@ template <typename T>
 cudaError_t launch_step_fast(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                              const MarchConfig& cfg, cudaStream_t st);
 bool march_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
+// geometry of the general plane-ring kernel over a z-slab of nzl owned planes
+// (arrays store plane z at z + 1); one resident wave
+bool march_slab_config(int n, int elem_bytes, int nzl, MarchConfig* cfg);
 template <typename T>
 cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
-                              const MarchConfig& cfg, cudaStream_t st);
+                              const MarchConfig& cfg, cudaStream_t st, double* sums_out = nullptr);
 
 // TMA plane-ring fused step.
 struct TmaGeom {

@@ -59,6 +59,14 @@ struct MarchLattice {
     int n, ty, depth;
     T dtcl, dtcf, mdtcdom, mdtkap, dt;   // dt cL / dx^2, dt cF, -dt cdom, -dt kappa, dt
     bool quartic;                        // beta == 4
+    // z storage: periodic (plane z stored at z mod n) or a z-slab whose arrays
+    // hold plane z at z + zbase (halo planes below and above the owned ones)
+    bool periodic;
+    int zbase;
+    __device__ __forceinline__ uint32_t plane(int z) const
+    {
+        return (uint32_t)(periodic ? wrapn(z, n) : z + zbase);
+    }
 };
 
 // Per-thread sums of the new fields (packed pairs): forward-difference
@@ -114,13 +122,13 @@ __device__ void march_segment(const MarchLattice<T>& L, int yt, int z0, int nz, 
     // (zrel + 1) mod (D+3), momenta into momentum slot zrel mod (D+1); the slot
     // is passed in (kept as running counters, no division in the loop)
     auto fetch_f = [&](int zrel, int slot) {          // zrel in [-1, nz + 1]
-        const uint32_t gi = (uint32_t)wrapn(z0 + zrel, n) * nn + rowg;
+        const uint32_t gi = L.plane(z0 + zrel) * nn + rowg;
         T* d = S + (uint32_t)slot * R.slotF + offF;
         cp_async16(d, L.f0 + gi);
         cp_async16(d + R.fieldF, L.f1 + gi);
     };
     auto fetch_p = [&](int zrel, int slot) {          // zrel in [0, nz]
-        const uint32_t gi = (uint32_t)wrapn(z0 + zrel, n) * nn + rowg;
+        const uint32_t gi = L.plane(z0 + zrel) * nn + rowg;
         T* d = S + R.p0 + (uint32_t)slot * R.slotP + offP;
         cp_async16(d, L.p0 + gi);
         cp_async16(d + R.fieldP, L.p1 + gi);
@@ -235,7 +243,7 @@ __device__ void march_segment(const MarchLattice<T>& L, int yt, int z0, int nz, 
             }
             if (!ahead) {
                 if (own) {
-                    const uint32_t gi = (uint32_t)z * nn + rowg;
+                    const uint32_t gi = L.plane(z) * nn + rowg;
                     PK<T>::st(L.op0 + gi, pn[0]);
                     PK<T>::st(L.op1 + gi, pn[1]);
                     PK<T>::st(L.of0 + gi, g[0]);

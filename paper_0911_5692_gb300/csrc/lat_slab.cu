@@ -1,0 +1,152 @@
+// lat_slab.cu -- one lattice split into z-slabs, one slab per handle (the
+// multi-GPU form the paper leaves as future work, Sec. IV).
+//
+// A slab handle owns planes [z0, z0 + nzl) of an N^3 lattice. Its eight arrays
+// hold nzl + 3 planes each: stored plane p is global plane z0 - 1 + p (mod N),
+// so p = 0 is the halo below, 1 .. nzl the owned planes and nzl + 1, nzl + 2
+// the halos above (the second for the look-ahead rim of the step's sums).
+// One step of the whole lattice is then, per slab:
+//   1. halo exchange (by the caller): f planes 0, nzl+1, nzl+2 and pi plane
+//      nzl+1 of the current ping-pong set from the neighbouring slabs;
+//   2. lat_slab_step: the fused step (Sec. II.B, eq. evo with eq. scalar-evo) on
+//      the owned planes, writing the slab's share of the volume averages of the
+//      new fields (sums over its sites / N^3);
+//   3. the shares of all slabs added (an allreduce of four FP64 numbers);
+//   4. lat_slab_advance: the FP64 scale-factor update (eq. scale) from the
+//      total, identical on every slab.
+// Before the first step, lat_slab_sums + lat_slab_advance(advance = 0) set the
+// coefficients from the starting fields.
+#include <algorithm>
+
+#include "lat_internal.h"
+
+namespace lat {
+
+namespace {
+
+// Shares of the four volume averages of the current fields over the owned
+// sites (forward differences; the +z neighbour of the top plane is the halo).
+template <typename T>
+__global__ void __launch_bounds__(256) slab_sums_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials,
+                                                        int nzl, double* sums_out)
+{
+    __shared__ double red[32 * kSums];
+    const int n = M.n;
+    const int par = (int)(sc->step & 1);
+    const T* __restrict__ f0 = par ? B.f[1][0] : B.f[0][0];
+    const T* __restrict__ f1 = par ? B.f[1][1] : B.f[0][1];
+    double acc[kSums] = {0.0, 0.0, 0.0, 0.0};
+    const size_t nn = (size_t)n * n;
+    const long long cols = (long long)n * n;
+    for (long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
+         col += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(col % n), y = (int)(col / n);
+        const int xp = x == n - 1 ? 0 : x + 1, yp = y == n - 1 ? 0 : y + 1;
+        for (int z = 0; z < nzl; z++) {
+            const size_t pl = (size_t)(z + 1) * nn, pu = (size_t)(z + 2) * nn;
+            const size_t c = pl + (size_t)y * n + x;
+            const double a0 = (double)f0[c], a1 = (double)f1[c];
+            const double e0 = (double)f0[pl + (size_t)y * n + xp] - a0, e1 = (double)f0[pl + (size_t)yp * n + x] - a0,
+                         e2 = (double)f0[pu + (size_t)y * n + x] - a0;
+            const double h0 = (double)f1[pl + (size_t)y * n + xp] - a1, h1 = (double)f1[pl + (size_t)yp * n + x] - a1,
+                         h2 = (double)f1[pu + (size_t)y * n + x] - a1;
+            acc[0] += e0 * e0 + e1 * e1 + e2 * e2;
+            acc[1] += h0 * h0 + h1 * h1 + h2 * h2;
+            const double sq = a0 * a0;
+            acc[2] += M.beta == 4 ? 0.25 * sq * sq : 0.5 * sq;
+            acc[3] += 0.5 * sq * a1 * a1;
+        }
+    }
+    finish_block_sums(M, sc, partials, acc, red, sums_out);
+}
+
+// The scalars after one step (or, advance = 0, the coefficients of the first
+// step) from the total of all slabs' shares.
+__global__ void slab_advance_kernel(Model M, DevScalars* sc, const double* sums, int advance)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    DevScalars s = *sc;
+    if (s.status != LAT_OK) return;
+    const double S[kSums] = {sums[0], sums[1], sums[2], sums[3]};
+    advance_scalars(M, s, S, advance != 0);
+    s.ticket = 0u;
+    *sc = s;
+}
+
+int slab_sum_blocks(int n)
+{
+    const long long cols = (long long)n * n;
+    return (int)std::max<long long>(1, std::min<long long>((cols + 255) / 256, 1024));
+}
+
+} // namespace
+
+} // namespace lat
+
+using namespace lat;
+
+extern "C" {
+
+lat_status lat_slab_create(const lat_params* params, int z0, int nzl, void* cuda_stream, void* const dev_bufs[8],
+                           lat_handle** out)
+{
+    if (!out) return LAT_EINVAL;
+    *out = nullptr;
+    if (!params || !dev_bufs) return LAT_EINVAL;
+    if (z0 < 0 || z0 >= params->n || nzl < 2 || nzl > params->n) return LAT_EINVAL;
+    lat_handle* h = nullptr;
+    LAT_TRY(lat_create_with_buffers(params, cuda_stream, dev_bufs, &h));
+    h->slab = true;
+    h->slab_z0 = z0;
+    h->slab_nzl = nzl;
+    h->nsites = (size_t)(nzl + 3) * params->n * params->n;
+    h->dirty = false;
+    MarchConfig cfg;
+    if (!march_slab_config(params->n, (int)h->esize, nzl, &cfg) || (size_t)cfg.blocks * kSums > h->partials_cap ||
+        (size_t)slab_sum_blocks(params->n) * kSums > h->partials_cap) {
+        lat_destroy(h);
+        return LAT_EUNSUPPORTED;
+    }
+    h->mcfg = cfg;
+    h->variant = 2;
+    h->ty = cfg.ty;
+    h->zr = cfg.zr;
+    drop_graph(h);
+    *out = h;
+    return LAT_OK;
+}
+
+lat_status lat_slab_sums(lat_handle* h, double* sums_dev)
+{
+    if (!h || !sums_dev) return LAT_EINVAL;
+    if (!h->slab) return LAT_ESTATE;
+    const int nb = slab_sum_blocks(h->M.n);
+    if (h->prec == 32)
+        slab_sums_kernel<float><<<nb, 256, 0, h->stream>>>(bufs_of<float>(h), h->M, h->sc, h->partials, h->slab_nzl,
+                                                           sums_dev);
+    else
+        slab_sums_kernel<double><<<nb, 256, 0, h->stream>>>(bufs_of<double>(h), h->M, h->sc, h->partials,
+                                                            h->slab_nzl, sums_dev);
+    return cuda_status(cudaGetLastError());
+}
+
+lat_status lat_slab_step(lat_handle* h, double* sums_dev)
+{
+    if (!h || !sums_dev) return LAT_EINVAL;
+    if (!h->slab) return LAT_ESTATE;
+    cudaError_t e = h->prec == 32 ? launch_step_march<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->mcfg,
+                                                             h->stream, sums_dev)
+                                  : launch_step_march<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->mcfg,
+                                                              h->stream, sums_dev);
+    return cuda_status(e);
+}
+
+lat_status lat_slab_advance(lat_handle* h, const double* sums_dev, int advance)
+{
+    if (!h || !sums_dev) return LAT_EINVAL;
+    if (!h->slab) return LAT_ESTATE;
+    slab_advance_kernel<<<1, 32, 0, h->stream>>>(h->M, h->sc, sums_dev, advance);
+    return cuda_status(cudaGetLastError());
+}
+
+} // extern "C"

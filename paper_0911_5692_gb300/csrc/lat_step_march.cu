@@ -21,11 +21,14 @@ namespace {
 
 struct MarchArgs {
     int ty, nzc, nyt, depth;
+    int nzl;        // planes of the z domain: n, or the owned planes of a z-slab
+    int zbase;      // slab: stored plane of z = z + zbase (0 when periodic)
+    int periodic;   // 1: periodic z (a whole lattice); 0: z-slab with halo planes
 };
 
 template <typename T, int MAXT>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
-    step_march_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, MarchArgs G)
+    step_march_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, MarchArgs G, double* sums_out)
 {
     __shared__ double red[32 * kSums];
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -56,25 +59,29 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
     L.mdtcdom = step_coef<T>(sc, 2);
     L.mdtkap = step_coef<T>(sc, 3);
     L.quartic = M.beta == 4;
+    L.periodic = G.periodic != 0;
+    L.zbase = G.zbase;
     MarchSums<T> A;
     A.zero();
 
-    // Work: the nyt * n (y tile, z plane) units in tile-major order; block b
+    // Work: the nyt * nzl (y tile, z plane) units in tile-major order; block b
     // takes units [b U / B, (b+1) U / B) and marches them as one segment per y
     // tile it touches (B = nyt * c gives c balanced z chunks per tile).
-    const long long U = (long long)G.nyt * n;
+    const int nzl = G.nzl;
+    const long long U = (long long)G.nyt * nzl;
     long long u = (long long)blockIdx.x * U / gridDim.x;
     const long long uend = ((long long)blockIdx.x + 1) * U / gridDim.x;
     for (bool first = true; u < uend; first = false) {
-        const int yt = (int)(u / n);
-        const int z0 = (int)(u - (long long)yt * n);
-        const int nz = (int)min((long long)(n - z0), uend - u);
+        const int yt = (int)(u / nzl);
+        const int z0 = (int)(u - (long long)yt * nzl);
+        const int nz = (int)min((long long)(nzl - z0), uend - u);
         u += nz;
         march_segment(L, yt, z0, nz, S, A, first);
     }
     T v[kSums];
     A.totals(L.quartic, v);
-    finish_block(M, sc, partials, v, red, true);
+    if (sums_out) finish_block_sums(M, sc, partials, v, red, sums_out);
+    else finish_block(M, sc, partials, v, red, true);
 }
 
 
@@ -152,6 +159,42 @@ bool march_geom(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
 
 // Default geometry: the tallest tile (fewest halo and look-ahead rows per owned
 // row) whose block fits in 1024 threads.
+bool march_slab_config(int n, int elem_bytes, int nzl, MarchConfig* cfg)
+{
+    if (nzl < 1) return false;
+    const int vw = 16 / elem_bytes;
+    for (int ty : {16, 8, 4, 2, 1}) {
+        if (ty > n || n % ty != 0) continue;
+        int threads = ((ty + 3) * (n / vw) + 31) / 32 * 32;
+        if (threads > 1024) continue;
+        const size_t smem = march_smem(n, elem_bytes, ty, 1);
+        if (smem > 227 * 1024 - 2048) continue;
+        const int maxt = maxt_for(threads);
+        const void* fn = elem_bytes == 4 ? march_fn<float>(maxt) : march_fn<double>(maxt);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) continue;
+        int occ = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) continue;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return false;
+        const long long units = (long long)(n / ty) * nzl;
+        const long long blocks = std::min<long long>((long long)sms * occ, units);
+        cfg->ty = ty;
+        cfg->zr = (int)((units + blocks - 1) / blocks);
+        cfg->nzc = 0;
+        cfg->depth = 1;
+        cfg->threads = threads;
+        cfg->maxt = maxt;
+        cfg->fast = 0;
+        cfg->smem = smem;
+        cfg->nyt = n / ty;
+        cfg->blocks = (int)blocks;
+        cfg->nzl = nzl;
+        cfg->zbase = 1;
+        return true;
+    }
+    return false;
+}
+
 bool march_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg)
 {
     const int d = depth > 0 ? depth : 1;
@@ -164,24 +207,25 @@ bool march_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig*
 
 template <typename T>
 cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
-                              const MarchConfig& cfg, cudaStream_t st)
+                              const MarchConfig& cfg, cudaStream_t st, double* sums_out)
 {
-    if (cfg.fast) return launch_step_fast<T>(b, M, sc, partials, cfg, st);
-    MarchArgs G{cfg.ty, cfg.nzc, cfg.nyt, cfg.depth};
+    if (cfg.fast && !sums_out && cfg.nzl == 0) return launch_step_fast<T>(b, M, sc, partials, cfg, st);
+    MarchArgs G{cfg.ty, cfg.nzc, cfg.nyt, cfg.depth, cfg.nzl > 0 ? cfg.nzl : M.n, cfg.zbase, cfg.nzl > 0 ? 0 : 1};
+    double* so = sums_out;
     switch (cfg.maxt) {
-    case 448: step_march_kernel<T, 448><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
-    case 512: step_march_kernel<T, 512><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
-    case 704: step_march_kernel<T, 704><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
-    case 768: step_march_kernel<T, 768><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
-    case 896: step_march_kernel<T, 896><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
-    default: step_march_kernel<T, 1024><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
+    case 448: step_march_kernel<T, 448><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
+    case 512: step_march_kernel<T, 512><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
+    case 704: step_march_kernel<T, 704><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
+    case 768: step_march_kernel<T, 768><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
+    case 896: step_march_kernel<T, 896><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
+    default: step_march_kernel<T, 1024><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
     }
     return cudaGetLastError();
 }
 
 template cudaError_t launch_step_march<float>(const Bufs<float>&, const Model&, DevScalars*, double*,
-                                              const MarchConfig&, cudaStream_t);
+                                              const MarchConfig&, cudaStream_t, double*);
 template cudaError_t launch_step_march<double>(const Bufs<double>&, const Model&, DevScalars*, double*,
-                                               const MarchConfig&, cudaStream_t);
+                                               const MarchConfig&, cudaStream_t, double*);
 
 } // namespace lat

@@ -25,7 +25,8 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_checkpoint_bytes", "lat_save_checkpoint", "lat_load_checkpoint", "lat_field_sums_static",
             "lat_set_g2", "lat_vjp", "lat_adjoint", "lat_batch_create", "lat_batch_init_fields",
             "lat_batch_evolve", "lat_batch_sync", "lat_batch_tune", "lat_batch_member", "lat_batch_info",
-            "lat_batch_destroy", "lat_batch_check_barrier")
+            "lat_batch_destroy", "lat_batch_check_barrier", "lat_slab_create", "lat_slab_sums", "lat_slab_step",
+            "lat_slab_advance")
 
 
 class LatParams(C.Structure):
@@ -100,6 +101,10 @@ def load_library(build_if_missing: bool = True):
             L.lat_batch_member.argtypes = [P, C.c_int, C.POINTER(P)]
             L.lat_batch_info.argtypes = [P, i64p]
             L.lat_batch_check_barrier.argtypes = [P, C.c_int64]
+            L.lat_slab_create.argtypes = [C.POINTER(LatParams), C.c_int, C.c_int, P, C.POINTER(P), C.POINTER(P)]
+            L.lat_slab_sums.argtypes = [P, P]
+            L.lat_slab_step.argtypes = [P, P]
+            L.lat_slab_advance.argtypes = [P, P, C.c_int]
             L.lat_batch_destroy.argtypes = [P]
             L.lat_batch_destroy.restype = None
             L.lat_destroy.argtypes = [P]

@@ -1,0 +1,284 @@
+"""One lattice split into z-slabs (the multi-GPU form of the evolution).
+
+The paper runs one lattice on one GPU and names multi-GPU runs as future work
+(Sec. IV). Here a lattice of N^3 sites is cut into contiguous z ranges, one per
+slab. Per step (Sec. II.B, eq. evo with eq. scalar-evo and eq. scale):
+
+1. halo exchange of the current ping-pong set: every slab receives the f
+   plane just below its range, the two f planes just above (the second for the
+   look-ahead rim of the sums) and the pi plane just above;
+2. the fused step on the owned planes (CUDA, ``lat_slab_step``), which writes
+   the slab's share of the four volume averages of the new fields;
+3. an allreduce adds the shares (four FP64 numbers);
+4. the FP64 scale-factor update from the total (``lat_slab_advance``),
+   identical on every slab.
+
+This module is host-side orchestration only: the compute of each slab runs in
+the CUDA library. Halo planes move by torch.distributed point-to-point calls
+(one slab per rank; NCCL between GPUs) or, for slabs held by one process, by
+device copies. The exchange and allreduce logic takes any slab object with the
+interface of ``SlabGPU`` (views of its stored planes, ``local_sums``,
+``local_step``, ``advance``).
+
+Stored plane p of a slab with owned range [z0, z0 + nzl) is global plane
+z0 - 1 + p (mod N): p = 0 halo below, 1..nzl owned, nzl + 1, nzl + 2 halos above.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from .lattice import LatticeError, _check, load_library, make_params
+
+# array index within a ping-pong set: f_phi, f_chi, pi_phi, pi_chi
+F0, F1, P0, P1 = 0, 1, 2, 3
+
+
+def slab_ranges(n: int, parts: int):
+    """Balanced contiguous z ranges [(z0, nzl)] of `parts` slabs; every slab
+    needs at least two planes (its two lowest planes are a neighbour's halo)."""
+    out = [(r * n // parts, (r + 1) * n // parts - r * n // parts) for r in range(parts)]
+    if min(nz for _, nz in out) < 2:
+        raise ValueError(f"{parts} slabs of a {n}^3 lattice leave a slab with fewer than 2 planes")
+    return out
+
+
+def halo_plan():
+    """Point-to-point messages of one exchange as (direction, tag, array, k):
+    'down' messages go to the slab below and carry the sender's owned plane k
+    (stored plane k = 1, 2: its two lowest) into the receiver's halo above
+    (stored plane nzl + k); 'up' messages go to the slab above and carry the
+    sender's top owned plane (stored nzl) into the receiver's halo below
+    (stored 0). f of both fields goes down twice and up once; pi goes down once."""
+    msgs, tag = [], 0
+    for k in (1, 2):
+        for a in (F0, F1):
+            msgs.append(("down", tag, a, k))
+            tag += 1
+    for a in (P0, P1):
+        msgs.append(("down", tag, a, 1))
+        tag += 1
+    for a in (F0, F1):
+        msgs.append(("up", tag, a, 0))
+        tag += 1
+    return msgs
+
+
+def send_plane(msg, nzl_sender: int) -> int:
+    direction, _, _, k = msg
+    return k if direction == "down" else nzl_sender
+
+
+def recv_plane(msg, nzl_receiver: int) -> int:
+    direction, _, _, k = msg
+    return nzl_receiver + k if direction == "down" else 0
+
+
+class SlabGPU:
+    """One z-slab on the GPU, driven through lat_slab_* (device memory from torch)."""
+
+    def __init__(self, params: dict, z0: int, nzl: int, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("SlabGPU needs a CUDA device; the library has no CPU path")
+        self._torch = torch
+        self._L = load_library()
+        self.params = dict(params)
+        self.n = int(params["n"])
+        self.z0, self.nzl = int(z0), int(nzl)
+        self.precision = int(params.get("precision", 32))
+        self.dtype = torch.float32 if self.precision == 32 else torch.float64
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        n = self.n
+        self.buffers = [torch.zeros((self.nzl + 3, n, n), dtype=self.dtype, device=self.device) for _ in range(8)]
+        self.shares = torch.zeros(4, dtype=torch.float64, device=self.device)
+        torch.cuda.synchronize(self.device)
+        self._p = make_params(params)
+        arr = (C.c_void_p * 8)(*[b.data_ptr() for b in self.buffers])
+        h = C.c_void_p()
+        _check(self._L.lat_slab_create(C.byref(self._p), self.z0, self.nzl, C.c_void_p(self.stream.cuda_stream), arr,
+                                       C.byref(h)), "lat_slab_create")
+        self._h = h
+        self.step_count = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lat_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # stored planes of the current ping-pong set
+    def current_set(self) -> int:
+        return self.step_count & 1
+
+    def plane(self, a: int, p: int):
+        return self.buffers[4 * self.current_set() + a][p]
+
+    def load(self, f0, f1, pi0, pi1, t=0.0, a=1.0, ad=0.0, step=0):
+        """Upload this slab's part (with its halos) of full-lattice arrays [z][y][x]."""
+        torch = self._torch
+        self.step_count = int(step)
+        v = (C.c_double * 4)(float(t), float(a), float(ad), float(step))
+        _check(self._L.lat_set_scalars(self._h, v), "lat_set_scalars")
+        idx = [(self.z0 - 1 + p) % self.n for p in range(self.nzl + 3)]
+        s = self.current_set()
+        with torch.cuda.stream(self.stream):
+            for k, arr in enumerate((f0, f1, pi0, pi1)):
+                part = np.ascontiguousarray(np.asarray(arr)[idx])
+                self.buffers[4 * s + k].copy_(torch.from_numpy(part).to(self.dtype))
+        self.stream.synchronize()
+
+    def owned(self):
+        """Owned planes of the current set as float64 numpy arrays (f0, f1, pi0, pi1)."""
+        self.stream.synchronize()
+        s = self.current_set()
+        return tuple(self.buffers[4 * s + k][1:self.nzl + 1].double().cpu().numpy() for k in range(4))
+
+    def scalars(self) -> dict:
+        out = (C.c_double * 8)()
+        _check(self._L.lat_get_scalars(self._h, out), "lat_get_scalars")
+        return {"t": out[0], "a": out[1], "ad": out[2], "step": int(out[3]), "S": list(out[4:8])}
+
+    def local_sums(self):
+        _check(self._L.lat_slab_sums(self._h, C.c_void_p(self.shares.data_ptr())), "lat_slab_sums")
+        return self.shares
+
+    def local_step(self):
+        _check(self._L.lat_slab_step(self._h, C.c_void_p(self.shares.data_ptr())), "lat_slab_step")
+        return self.shares
+
+    def advance(self, total, advance: bool):
+        _check(self._L.lat_slab_advance(self._h, C.c_void_p(total.data_ptr()), 1 if advance else 0),
+               "lat_slab_advance")
+        if advance:
+            self.step_count += 1
+
+    def sync(self):
+        self.stream.synchronize()
+
+
+class LocalComm:
+    """All slabs of the lattice in this process: halos by device copies, the
+    allreduce by adding the shares on the device."""
+
+    def exchange(self, slabs):
+        import torch
+        P = len(slabs)
+        for i, s in enumerate(slabs):
+            above, below = slabs[(i + 1) % P], slabs[(i - 1) % P]
+            s.stream.wait_stream(above.stream)
+            s.stream.wait_stream(below.stream)
+            with torch.cuda.stream(s.stream):
+                for msg in halo_plan():
+                    src = above if msg[0] == "down" else below
+                    s.plane(msg[2], recv_plane(msg, s.nzl)).copy_(src.plane(msg[2], send_plane(msg, src.nzl)))
+        # a slab's planes are read above before it may write them again
+        for i, s in enumerate(slabs):
+            s.stream.wait_stream(slabs[(i + 1) % P].stream)
+            s.stream.wait_stream(slabs[(i - 1) % P].stream)
+
+    def allreduce(self, slabs, shares):
+        import torch
+        s0 = slabs[0]
+        for s in slabs[1:]:
+            s0.stream.wait_stream(s.stream)
+        with torch.cuda.stream(s0.stream):
+            total = torch.stack(list(shares)).sum(dim=0)
+        for s in slabs[1:]:
+            s.stream.wait_stream(s0.stream)
+            total.record_stream(s.stream)
+        return [total] * len(slabs)
+
+
+class DistComm:
+    """One slab per rank of a torch.distributed group: halos by point-to-point
+    messages with the ranks above and below (modulo the group size), the
+    allreduce by all_reduce. Works with any backend (NCCL with device tensors,
+    gloo with host tensors)."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+        self.rank = dist.get_rank(group)
+        self.world = dist.get_world_size(group)
+
+    def _global(self, r):
+        return self.dist.get_global_rank(self.group, r) if self.group is not None else r
+
+    def exchange(self, slabs):
+        (s,) = slabs
+        dist = self.dist
+        with _stream_ctx(s):
+            if self.world == 1:          # the whole lattice: halos are its own planes
+                for msg in halo_plan():
+                    s.plane(msg[2], recv_plane(msg, s.nzl)).copy_(s.plane(msg[2], send_plane(msg, s.nzl)))
+                return
+            up, down = self._global((self.rank + 1) % self.world), self._global((self.rank - 1) % self.world)
+            reqs = []
+            for msg in halo_plan():      # receive 'down' messages from above, 'up' ones from below
+                reqs.append(dist.irecv(s.plane(msg[2], recv_plane(msg, s.nzl)), src=up if msg[0] == "down" else down,
+                                       tag=msg[1], group=self.group))
+            for msg in halo_plan():      # send 'down' messages below, 'up' ones above
+                reqs.append(dist.isend(s.plane(msg[2], send_plane(msg, s.nzl)), dst=down if msg[0] == "down" else up,
+                                       tag=msg[1], group=self.group))
+            for r in reqs:
+                r.wait()
+
+    def allreduce(self, slabs, shares):
+        (sh,) = shares
+        with _stream_ctx(slabs[0]):
+            total = sh.clone()
+            self.dist.all_reduce(total, group=self.group)
+        return [total]
+
+
+def _stream_ctx(slab):
+    import contextlib
+    stream = getattr(slab, "stream", None)
+    if stream is None:
+        return contextlib.nullcontext()
+    import torch
+    return torch.cuda.stream(stream)
+
+
+class SlabEvolution:
+    """Steps the slabs of one lattice together: ``slabs`` are the slabs this
+    process holds (all of them with LocalComm, one with DistComm)."""
+
+    def __init__(self, slabs, comm):
+        self.slabs = list(slabs)
+        self.comm = comm
+
+    def prepare(self):
+        """Coefficients of the first step from the current fields (after a load)."""
+        self.comm.exchange(self.slabs)
+        shares = [s.local_sums() for s in self.slabs]
+        totals = self.comm.allreduce(self.slabs, shares)
+        for s, t in zip(self.slabs, totals):
+            s.advance(t, False)
+
+    def step(self, n_steps: int = 1):
+        for _ in range(int(n_steps)):
+            self.comm.exchange(self.slabs)
+            shares = [s.local_step() for s in self.slabs]
+            totals = self.comm.allreduce(self.slabs, shares)
+            for s, t in zip(self.slabs, totals):
+                s.advance(t, True)
+
+    def gather(self):
+        """Full-lattice arrays (f0, f1, pi0, pi1) from the slabs of this process
+        (LocalComm: all of them) in z order."""
+        parts = [s.owned() for s in sorted(self.slabs, key=lambda s: s.z0)]
+        return tuple(np.concatenate([p[k] for p in parts], axis=0) for k in range(4))
+
+
+__all__ = ["slab_ranges", "halo_plan", "send_plane", "recv_plane", "SlabGPU", "LocalComm", "DistComm", "SlabEvolution",
+           "LatticeError"]
