@@ -23,6 +23,7 @@
 #include <cstring>
 #include <vector>
 
+#include "lat_async.cuh"
 #include "lat_internal.h"
 
 namespace lat {
@@ -279,21 +280,32 @@ __global__ void __launch_bounds__(kAdjThreads) adj_step_kernel(AdjBufs<T> B, Mod
 // the six stencil arrays (pt = pb + dt fb, f_k and f_{k-1} of both fields) in
 // registers and takes its x and y neighbours from a shared-memory copy of the
 // current plane with a one-site halo (two copies used alternately, so one
-// barrier per plane suffices). The loads for plane z+1 (its z+2 values and its
-// halo) are issued one plane ahead, so their latency overlaps the arithmetic of
-// plane z. Same arithmetic as adj_step_kernel.
-constexpr int kMX = 32, kMY = 8;
+// barrier per plane suffices). Each thread stages the raw values of its own
+// site for the planes two and three ahead in shared memory by asynchronous
+// copies (no registers held while they are in flight, and no barrier: a thread
+// reads back only what it copied); halo values are loaded one plane ahead.
+// Same arithmetic as adj_step_kernel.
+constexpr int kMX = 32, kMY = 8, kStage = 3;
+
+template <typename T>
+constexpr size_t adj_march_smem()
+{
+    return sizeof(T) * ((size_t)kStage * 8 * kMX * kMY + 2 * 6 * (kMY + 2) * (kMX + 2));
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kMX * kMY, sizeof(T) == 4 ? 3 : 2)
     adj_march_kernel(AdjBufs<T> B, Model M, AdjScalars* as, const DevScalars* hist, double* partials, int nzc)
 {
     __shared__ double red[32 * kSums];
-    __shared__ T tiles[2][6][kMY + 2][kMX + 2];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*stage)[8][kMX * kMY] = reinterpret_cast<T (*)[8][kMX * kMY]>(smem_raw);
+    T (*tiles)[6][kMY + 2][kMX + 2] =
+        reinterpret_cast<T (*)[6][kMY + 2][kMX + 2]>(smem_raw + sizeof(T) * kStage * 8 * kMX * kMY);
     if (as->status != LAT_OK) return;
     const int n = M.n;
     const uint32_t nn = (uint32_t)n * n;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kMX + tx;
     const int x = blockIdx.x * kMX + tx, y = blockIdx.y * kMY + ty;
     const int z0 = (int)((long long)blockIdx.z * n / nzc);
     const int nz = (int)((long long)(blockIdx.z + 1) * n / nzc) - z0;
@@ -315,10 +327,17 @@ __global__ void __launch_bounds__(kMX * kMY, sizeof(T) == 4 ? 3 : 2)
     auto plane_of = [&](int z) -> uint32_t { return (uint32_t)(z < 0 ? z + n : (z >= n ? z - n : z)) * nn; };
     // stencil value a (0..5) from raw values
     auto st = [&](const T* r, int a) -> T { return a < 2 ? r[a] + dt * r[a + 2] : r[a + 2]; };
+    // copies of this site's raw values of plane z into stage slot s
+    auto stage_plane = [&](int z, int s) {
+        const uint32_t o = plane_of(z) + col;
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (q < nraw) cp_async_small<sizeof(T)>(&stage[s][q][tid], R[q] + o);
+    };
 
     T w[6][3];           // stencil arrays at z-1, z, z+1
     T fbz[2][2];         // raw fb at z, z+1
-    T nr[8], hxr[8], hyr[8];
+    T hxr[8], hyr[8];    // raw halo values of the next plane
     {
         T r0[8], r1[8];
         const uint32_t pm = plane_of(z0 - 1) + col, pc = plane_of(z0) + col;
@@ -327,6 +346,8 @@ __global__ void __launch_bounds__(kMX * kMY, sizeof(T) == 4 ? 3 : 2)
             if (q < nraw) {
                 r0[q] = __ldg(R[q] + pm);
                 r1[q] = __ldg(R[q] + pc);
+                if (hx) hxr[q] = __ldg(R[q] + pc - col + colx);
+                if (hy) hyr[q] = __ldg(R[q] + pc - col + coly);
             }
 #pragma unroll
         for (int a = 0; a < 6; a++)
@@ -336,37 +357,43 @@ __global__ void __launch_bounds__(kMX * kMY, sizeof(T) == 4 ? 3 : 2)
             }
         fbz[0][0] = r1[2];
         fbz[1][0] = r1[3];
-        // plane z0+1 and the halo of plane z0
-        const uint32_t pn = plane_of(z0 + 1);
-#pragma unroll
-        for (int q = 0; q < 8; q++)
-            if (q < nraw) {
-                nr[q] = __ldg(R[q] + pn + col);
-                if (hx) hxr[q] = __ldg(R[q] + pc - col + colx);
-                if (hy) hyr[q] = __ldg(R[q] + pc - col + coly);
-            }
     }
+    // group j (j = 0, 1) stages plane z0+1+j into slot j; plane k then stages
+    // z0+k+3 into slot (k+2) % 3 after reading slot k % 3 (waiting for group k)
+    stage_plane(z0 + 1, 0);
+    cp_async_commit();
+    if (nz > 1) stage_plane(z0 + 2, 1);
+    cp_async_commit();
     T acc[kSums] = {T(0), T(0), T(0), T(0)};
+    int sr = 0, sw = 2;   // k % 3, (k + 2) % 3
     for (int k = 0; k < nz; k++) {
         const int z = z0 + k;
         T(*tile)[kMY + 2][kMX + 2] = tiles[k & 1];
+        cp_async_wait(1);
+        T raw[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (q < nraw) raw[q] = stage[sr][q][tid];
+        if (k + 2 < nz) stage_plane(z + 3, sw);
+        cp_async_commit();
+        sr = sr == 2 ? 0 : sr + 1;
+        sw = sw == 2 ? 0 : sw + 1;
 #pragma unroll
         for (int a = 0; a < 6; a++)
             if (a + 2 < nraw) {
-                w[a][2] = st(nr, a);
+                w[a][2] = st(raw, a);
                 tile[a][ty + 1][tx + 1] = w[a][1];
                 if (hx) tile[a][ty + 1][sx] = st(hxr, a);
                 if (hy) tile[a][sy][tx + 1] = st(hyr, a);
             }
-        fbz[0][1] = nr[2];
-        fbz[1][1] = nr[3];
-        // next plane's loads: z+2 values and the halo of plane z+1
+        fbz[0][1] = raw[2];
+        fbz[1][1] = raw[3];
+        // halo of the next plane
         if (k + 1 < nz) {
-            const uint32_t p2 = plane_of(z + 2), p1 = plane_of(z + 1);
+            const uint32_t p1 = plane_of(z + 1);
 #pragma unroll
             for (int q = 0; q < 8; q++)
                 if (q < nraw) {
-                    nr[q] = __ldg(R[q] + p2 + col);
                     if (hx) hxr[q] = __ldg(R[q] + p1 + colx);
                     if (hy) hyr[q] = __ldg(R[q] + p1 + coly);
                 }
@@ -411,6 +438,7 @@ __global__ void __launch_bounds__(kMX * kMY, sizeof(T) == 4 ? 3 : 2)
         fbz[0][0] = fbz[0][1];
         fbz[1][0] = fbz[1][1];
     }
+    cp_async_wait(0);
     if (!sums) return;
     adj_finish(acc, red, as, hist, partials, M);
 }
@@ -493,7 +521,9 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
                                      : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)n)));
     const int64_t nck = n > 0 ? (n + K - 1) / K : 0;
     const int nb = adj_blocks((long long)N3);
-    const bool march = M.n % kMX == 0;
+    const bool march = M.n % kMX == 0 &&
+                       cudaFuncSetAttribute(adj_march_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)adj_march_smem<T>()) == cudaSuccess;
     const int nzc = march ? adj_march_nzc(M.n) : 0;
     const dim3 mgrid(march ? M.n / kMX : 1, march ? M.n / kMY : 1, march ? nzc : 1);
     const size_t nparts = std::max<size_t>(nb, (size_t)mgrid.x * mgrid.y * mgrid.z);
@@ -602,8 +632,8 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
             const T* fk = arr(seg, (size_t)(k - c) * 2);
             const T* fm = k > c ? arr(seg, (size_t)(k - c - 1) * 2) : (k > 0 ? cp + 4 * N3 : nullptr);
             if (march)
-                adj_march_kernel<T><<<mgrid, dim3(kMX, kMY), 0, st>>>(adj_bufs(fk, fm), M, as,
-                                                                      k > 0 ? hist + (k - 1) : hist, part, nzc);
+                adj_march_kernel<T><<<mgrid, dim3(kMX, kMY), adj_march_smem<T>(), st>>>(
+                    adj_bufs(fk, fm), M, as, k > 0 ? hist + (k - 1) : hist, part, nzc);
             else
                 adj_step_kernel<T, true><<<nb, kAdjThreads, 0, st>>>(adj_bufs(fk, fm), M, as,
                                                                      k > 0 ? hist + (k - 1) : hist, part);

@@ -16,6 +16,15 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
                  "l"(gmem)
                  : "memory");
 }
+// 4- or 8-byte copy through L1 (ca); both addresses aligned to the size
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem)
+{
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // wait until at most `pending` of the most recent groups are still in flight
 __device__ __forceinline__ void cp_async_wait(int pending)
