@@ -21,10 +21,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "lat_async.cuh"
 #include "lat_internal.h"
+#include "lat_pairs.cuh"
 
 namespace lat {
 
@@ -443,6 +445,203 @@ __global__ void __launch_bounds__(kMX * kMY, sizeof(T) == 4 ? 3 : 2)
     adj_finish(acc, red, as, hist, partials, M);
 }
 
+// FP32 reverse step with two x sites per thread (N a multiple of 64): the
+// z-march of adj_march_kernel on a 64 x 8 site tile, with packed f32x2
+// arithmetic (one instruction updates both sites) and 8-byte staged copies, so
+// the per-site instruction count (addresses, loop, barriers) is halved. Each
+// thread stages the raw values of its site pair for the next plane, and edge
+// threads the halo values of the next plane, in shared memory by asynchronous
+// copies; halos are written into the next plane's copy of the tile right after
+// the current plane's barrier (that copy was last read before it).
+constexpr int kPX = 32, kPY = 8, kPW = 2 * kPX + 4;   // threads in x, y; tile row (halo + 64 + halo + pad)
+
+struct AdjPairSmem {
+    F2 stage[2][8][kPX * kPY];       // raw values of each thread's site pair, by plane parity
+    float sx[2][8][kPY][2];          // x-halo raw values (left of lane 0, right of lane 31)
+    F2 sy[2][8][2][kPX];             // y-halo raw pairs (below warp 0, above warp kPY-1)
+    float tile[2][6][kPY + 2][kPW];  // stencil values of the current plane with a one-site halo
+};
+
+__global__ void __launch_bounds__(kPX * kPY, 2)
+    adj_pair_kernel(AdjBufs<float> B, Model M, AdjScalars* as, const DevScalars* hist, double* partials, int nzc)
+{
+    __shared__ double red[32 * kSums];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AdjPairSmem& SM = *reinterpret_cast<AdjPairSmem*>(smem_raw);
+    if (as->status != LAT_OK) return;
+    const int n = M.n;
+    const uint32_t nn = (uint32_t)n * n;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
+    const int x0 = blockIdx.x * (2 * kPX) + 2 * tx, y = blockIdx.y * kPY + ty;
+    const int z0 = (int)((long long)blockIdx.z * n / nzc);
+    const int nz = (int)((long long)(blockIdx.z + 1) * n / nzc) - z0;
+    const float dts = (float)M.dt;
+    const F2 dt = mk2(dts, dts);
+    const float cLv = (float)(as->cL * M.inv_dx2);
+    const F2 cLs = mk2(cLv, cLv), cF = mk2((float)as->cF, (float)as->cF);
+    const F2 cd = mk2((float)as->cd, (float)as->cd), kp = mk2((float)as->kp, (float)as->kp);
+    const float g0v = (float)(-2.0 * as->bS[0] * M.inv_dx2 * M.inv_sites), g1v = (float)(-2.0 * as->bS[1] * M.inv_dx2 * M.inv_sites);
+    const F2 sg0 = mk2(g0v, g0v), sg1 = mk2(g1v, g1v);
+    const F2 sv2 = mk2((float)(as->bS[2] * M.inv_sites), (float)(as->bS[2] * M.inv_sites));
+    const F2 sv3 = mk2((float)(as->bS[3] * M.inv_sites), (float)(as->bS[3] * M.inv_sites));
+    const F2 two = mk2(2.0f, 2.0f), three = mk2(3.0f, 3.0f);
+    const bool quartic = M.beta == 4;
+    const bool sums = B.fm[0] != nullptr;
+    const float* R[8] = {B.pb[0], B.pb[1], B.fb[0], B.fb[1], B.f[0], B.f[1], B.fm[0], B.fm[1]};
+    const int nraw = sums ? 8 : 6;
+    const uint32_t col = (uint32_t)y * n + x0;
+    const bool hxl = tx == 0, hxr = tx == kPX - 1, hyb = ty == 0, hya = ty == kPY - 1;
+    const uint32_t colx = (uint32_t)y * n + (hxl ? (x0 == 0 ? n - 1 : x0 - 1) : (x0 + 2 == n ? 0 : x0 + 2));
+    const uint32_t coly = (uint32_t)(hyb ? (y == 0 ? n - 1 : y - 1) : (y == n - 1 ? 0 : y + 1)) * n + x0;
+    const int xs = hxl ? 0 : 1, ys = hyb ? 0 : 1;
+    auto plane_of = [&](int z) -> uint32_t { return (uint32_t)(z < 0 ? z + n : (z >= n ? z - n : z)) * nn; };
+    auto st2 = [&](const F2* r, int a) -> F2 { return a < 2 ? fma2(dt, r[a + 2], r[a]) : r[a + 2]; };
+    auto st1 = [&](const float* r, int a) -> float { return a < 2 ? r[a] + dts * r[a + 2] : r[a + 2]; };
+    // copies of plane z into stage slot s: this thread's pair, and its halo values
+    auto stage_plane = [&](int z, int s) {
+        const uint32_t o = plane_of(z);
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (q < nraw) {
+                cp_async_small<8>(&SM.stage[s][q][tid], R[q] + o + col);
+                if (hxl || hxr) cp_async_small<4>(&SM.sx[s][q][ty][xs], R[q] + o + colx);
+                if (hyb || hya) cp_async_small<8>(&SM.sy[s][q][ys][tx], R[q] + o + coly);
+            }
+    };
+    // halos of the plane in slot s into tile t
+    auto halo_to_tile = [&](int s, int t) {
+        if (hxl || hxr) {
+            float r[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (q < nraw) r[q] = SM.sx[s][q][ty][xs];
+#pragma unroll
+            for (int a = 0; a < 6; a++)
+                if (a + 2 < nraw) SM.tile[t][a][ty + 1][hxl ? 1 : 2 * kPX + 2] = st1(r, a);
+        }
+        if (hyb || hya) {
+            F2 r[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (q < nraw) r[q] = SM.sy[s][q][ys][tx];
+#pragma unroll
+            for (int a = 0; a < 6; a++)
+                if (a + 2 < nraw)
+                    *reinterpret_cast<F2*>(&SM.tile[t][a][hyb ? 0 : kPY + 1][2 + 2 * tx]) = st2(r, a);
+        }
+    };
+
+    F2 w[6][3];          // stencil pairs at z-1, z, z+1
+    F2 fbz[2][2];        // raw fb pairs at z, z+1
+    {
+        F2 r0[8], r1[8];
+        const uint32_t pm = plane_of(z0 - 1) + col, pc = plane_of(z0) + col;
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (q < nraw) {
+                r0[q] = *reinterpret_cast<const F2*>(R[q] + pm);
+                r1[q] = *reinterpret_cast<const F2*>(R[q] + pc);
+            }
+#pragma unroll
+        for (int a = 0; a < 6; a++)
+            if (a + 2 < nraw) {
+                w[a][0] = st2(r0, a);
+                w[a][1] = st2(r1, a);
+            }
+        fbz[0][0] = r1[2];
+        fbz[1][0] = r1[3];
+    }
+    // halos of plane z0 straight into tile 0; plane z0+1 staged into slot 1
+    stage_plane(z0, 0);
+    cp_async_commit();
+    if (nz > 0) stage_plane(z0 + 1, 1);
+    cp_async_commit();
+    cp_async_wait(1);
+    halo_to_tile(0, 0);
+    F2 acc[kSums] = {mk2(0.f, 0.f), mk2(0.f, 0.f), mk2(0.f, 0.f), mk2(0.f, 0.f)};
+    // plane k of the run, T_ = k & 1 as a compile-time constant (slot and
+    // tile offsets fold into immediates)
+    auto plane_step = [&](int k, auto T_) {
+        constexpr int t = decltype(T_)::value, sn = 1 - t;
+        const int z = z0 + k;
+        float(*tile)[kPY + 2][kPW] = SM.tile[t];
+        cp_async_wait(0);   // plane z+1 in slot sn
+        F2 raw[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (q < nraw) raw[q] = SM.stage[sn][q][tid];
+        // plane z+2 into the other slot (its plane z was read a plane ago)
+        if (k + 1 < nz) stage_plane(z + 2, t);
+        cp_async_commit();
+#pragma unroll
+        for (int a = 0; a < 6; a++)
+            if (a + 2 < nraw) {
+                w[a][2] = st2(raw, a);
+                *reinterpret_cast<F2*>(&tile[a][ty + 1][2 + 2 * tx]) = w[a][1];
+            }
+        fbz[0][1] = raw[2];
+        fbz[1][1] = raw[3];
+        __syncthreads();
+        // the next plane's halos, into the copy of the tile read before this barrier
+        if (k + 1 < nz) halo_to_tile(sn, 1 - t);
+        F2 lap[6];
+#pragma unroll
+        for (int a = 0; a < 6; a++)
+            if (a + 2 < nraw) {
+                const F2 c = w[a][1];
+                const F2 lft = mk2(tile[a][ty + 1][1 + 2 * tx], lo2(c));
+                const F2 rgt = mk2(hi2(c), tile[a][ty + 1][4 + 2 * tx]);
+                const F2 up = *reinterpret_cast<const F2*>(&tile[a][ty][2 + 2 * tx]);
+                const F2 dn = *reinterpret_cast<const F2*>(&tile[a][ty + 2][2 + 2 * tx]);
+                lap[a] = add2(add2(add2(sub2(lft, c), sub2(rgt, c)), add2(sub2(up, c), sub2(dn, c))),
+                              add2(sub2(w[a][0], c), sub2(w[a][2], c)));
+            }
+        const F2 pt0 = w[0][1], pt1 = w[1][1], f0 = w[2][1], f1 = w[3][1];
+        const F2 f0f0 = mul2(f0, f0), f1f1 = mul2(f1, f1), f0f1 = mul2(f0, f1);
+        const F2 h00 = fma2(kp, f1f1, quartic ? mul2(mul2(three, cd), f0f0) : cd);
+        const F2 h01 = mul2(mul2(two, kp), f0f1);
+        const F2 h11 = mul2(kp, f0f0);
+        // g = cL Lap pt + cF pt - H pt
+        const F2 g0 = sub2(fma2(cLs, lap[0], mul2(cF, pt0)), fma2(h00, pt0, mul2(h01, pt1)));
+        const F2 g1 = sub2(fma2(cLs, lap[1], mul2(cF, pt1)), fma2(h01, pt0, mul2(h11, pt1)));
+        const F2 f0b = quartic ? mul2(f0f0, f0) : f0;
+        const F2 s0 = fma2(sg0, lap[2], fma2(sv2, f0b, mul2(sv3, mul2(f0, f1f1))));
+        const F2 s1 = fma2(sg1, lap[3], mul2(sv3, mul2(f0f0, f1)));
+        const F2 nf0 = add2(fma2(dt, g0, fbz[0][0]), s0);
+        const F2 nf1 = add2(fma2(dt, g1, fbz[1][0]), s1);
+        const uint32_t i = (uint32_t)z * nn + col;
+        *reinterpret_cast<F2*>(B.fbo[0] + i) = nf0;
+        *reinterpret_cast<F2*>(B.fbo[1] + i) = nf1;
+        *reinterpret_cast<F2*>(B.pbo[0] + i) = pt0;
+        *reinterpret_cast<F2*>(B.pbo[1] + i) = pt1;
+        if (sums) {
+            const F2 q0 = fma2(dt, nf0, pt0), q1 = fma2(dt, nf1, pt1);
+            const F2 m0 = w[4][1], m1 = w[5][1];
+            const F2 m0m0 = mul2(m0, m0), m1m1 = mul2(m1, m1);
+            acc[0] = fma2(q0, lap[4], fma2(q1, lap[5], acc[0]));
+            acc[1] = fma2(q0, m0, fma2(q1, m1, acc[1]));
+            acc[2] = fma2(q0, quartic ? mul2(m0m0, m0) : m0, acc[2]);
+            acc[3] = fma2(mul2(q0, m0), m1m1, fma2(mul2(q1, m1), m0m0, acc[3]));
+        }
+#pragma unroll
+        for (int a = 0; a < 6; a++) {
+            w[a][0] = w[a][1];
+            w[a][1] = w[a][2];
+        }
+        fbz[0][0] = fbz[0][1];
+        fbz[1][0] = fbz[1][1];
+    };
+    for (int k = 0; k < nz; k += 2) {
+        plane_step(k, std::integral_constant<int, 0>{});
+        if (k + 1 < nz) plane_step(k + 1, std::integral_constant<int, 1>{});
+    }
+    cp_async_wait(0);
+    if (!sums) return;
+    float v[kSums] = {lo2(acc[0]) + hi2(acc[0]), lo2(acc[1]) + hi2(acc[1]), lo2(acc[2]) + hi2(acc[2]),
+                      lo2(acc[3]) + hi2(acc[3])};
+    adj_finish(v, red, as, hist, partials, M);
+}
+
 // J = <f1^2> (volume mean of chi squared) per block, and its gradient 2 f1 / N^3.
 template <typename T>
 __global__ void __launch_bounds__(kAdjThreads) chi2_kernel(const T* __restrict__ f1, T* __restrict__ grad, long long n3,
@@ -470,14 +669,13 @@ int adj_blocks(long long n3)
     return (int)std::max<long long>(1, std::min<long long>(need, (long long)sms * 8));
 }
 
-// z chunks of the z-march reverse kernel: enough blocks for four per SM, runs
-// of at least 8 planes.
-int adj_march_nzc(int n)
+// z chunks of the z-march reverse kernels for `tiles` (x, y) tiles: enough
+// blocks for four per SM, runs of at least 8 planes.
+int adj_zchunks(int n, int tiles)
 {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int tiles = (n / kMX) * (n / kMY);
     const int want = (4 * sms + tiles - 1) / tiles;
     return std::max(1, std::min(want, std::max(1, n / 8)));
 }
@@ -521,11 +719,20 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
                                      : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)n)));
     const int64_t nck = n > 0 ? (n + K - 1) / K : 0;
     const int nb = adj_blocks((long long)N3);
-    const bool march = M.n % kMX == 0 &&
+    // FP32 lattices with N a multiple of 64 take the two-site kernel, other
+    // multiples of 32 the one-site z-march, the rest one site per thread
+    bool pair = false;
+    if constexpr (sizeof(T) == 4)
+        pair = M.n % (2 * kPX) == 0 &&
+               cudaFuncSetAttribute(adj_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(AdjPairSmem)) == cudaSuccess;
+    const bool march = !pair && M.n % kMX == 0 &&
                        cudaFuncSetAttribute(adj_march_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)adj_march_smem<T>()) == cudaSuccess;
-    const int nzc = march ? adj_march_nzc(M.n) : 0;
-    const dim3 mgrid(march ? M.n / kMX : 1, march ? M.n / kMY : 1, march ? nzc : 1);
+    const int nzc = pair ? adj_zchunks(M.n, (M.n / (2 * kPX)) * (M.n / kPY))
+                         : march ? adj_zchunks(M.n, (M.n / kMX) * (M.n / kMY)) : 0;
+    const dim3 mgrid(pair ? M.n / (2 * kPX) : march ? M.n / kMX : 1, pair ? M.n / kPY : march ? M.n / kMY : 1,
+                     (pair || march) ? nzc : 1);
     const size_t nparts = std::max<size_t>(nb, (size_t)mgrid.x * mgrid.y * mgrid.z);
 
     Scratch S;
@@ -631,6 +838,15 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
         for (int64_t k = e - 1; k >= c; k--) {
             const T* fk = arr(seg, (size_t)(k - c) * 2);
             const T* fm = k > c ? arr(seg, (size_t)(k - c - 1) * 2) : (k > 0 ? cp + 4 * N3 : nullptr);
+            if constexpr (sizeof(T) == 4) {
+                if (pair) {
+                    adj_pair_kernel<<<mgrid, dim3(kPX, kPY), sizeof(AdjPairSmem), st>>>(
+                        adj_bufs(fk, fm), M, as, k > 0 ? hist + (k - 1) : hist, part, nzc);
+                    LAT_CUDA(cudaGetLastError());
+                    cur = 1 - cur;
+                    continue;
+                }
+            }
             if (march)
                 adj_march_kernel<T><<<mgrid, dim3(kMX, kMY), adj_march_smem<T>(), st>>>(
                     adj_bufs(fk, fm), M, as, k > 0 ? hist + (k - 1) : hist, part, nzc);

@@ -204,6 +204,21 @@ def test_adjoint_fp32_matches_oracle(model):
         assert normwise(dp[i], dpo[i]) <= 2e-4, ("dp", i, normwise(dp[i], dpo[i]))
 
 
+@pytest.mark.parametrize("model,n,steps", [("lphi4", 64, 12), ("m2phi2", 64, 12), ("lphi4", 128, 4)])
+def test_adjoint_pair_kernel_fp32(model, n, steps):
+    """FP32 lattices with N a multiple of 64 take the two-site reverse kernel."""
+    p, st, sc = _case(model, n, 32)
+    g = _gpu(p, st, sc)
+    J, df, dp, dg2 = g.adjoint(steps)
+    Jo, dfo, dpo, dg2o = _oracle_grad(dict(p, precision=64), st, sc, steps)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    assert abs(dg2 - dg2o) <= 2e-4 * abs(dg2o)
+    df, dp = df.cpu().numpy(), dp.cpu().numpy()
+    for i in (0, 1):
+        assert normwise(df[i], dfo[i]) <= 2e-4, ("df", i, normwise(df[i], dfo[i]))
+        assert normwise(dp[i], dpo[i]) <= 2e-4, ("dp", i, normwise(dp[i], dpo[i]))
+
+
 def test_autograd_function():
     n, steps = 16, 15
     p, st, sc = _case("lphi4", n, 64)
