@@ -490,44 +490,61 @@ __global__ void __launch_bounds__(kPX * kPY, 2)
     const float* R[8] = {B.pb[0], B.pb[1], B.fb[0], B.fb[1], B.f[0], B.f[1], B.fm[0], B.fm[1]};
     const int nraw = sums ? 8 : 6;
     const uint32_t col = (uint32_t)y * n + x0;
-    const bool hxl = tx == 0, hxr = tx == kPX - 1, hyb = ty == 0, hya = ty == kPY - 1;
-    const uint32_t colx = (uint32_t)y * n + (hxl ? (x0 == 0 ? n - 1 : x0 - 1) : (x0 + 2 == n ? 0 : x0 + 2));
-    const uint32_t coly = (uint32_t)(hyb ? (y == 0 ? n - 1 : y - 1) : (y == n - 1 ? 0 : y + 1)) * n + x0;
-    const int xs = hxl ? 0 : 1, ys = hyb ? 0 : 1;
+    const float* Rc[8];   // this thread's site pair in each array (plane 0)
+#pragma unroll
+    for (int q = 0; q < 8; q++) Rc[q] = q < nraw ? R[q] + col : nullptr;
+    // Halo sites are fetched by warps 0 and kPY-1 only (warp-uniform branches):
+    // every lane of warp 0 the pair below the tile, every lane of warp kPY-1 the
+    // pair above it, and lanes 0..2kPY-1 of warp 0 the single sites left and
+    // right of the tile's rows (row = lane % kPY, side = lane / kPY).
+    const bool wb = ty == 0, wa = ty == kPY - 1;
+    const bool xh = wb && tx < 2 * kPY;
+    const int xrow = tx % kPY, xside = tx / kPY;
+    const int xt = blockIdx.x * (2 * kPX), y0 = blockIdx.y * kPY;
+    const uint32_t colx = (uint32_t)(y0 + xrow) * n +
+                          (xside ? (xt + 2 * kPX == n ? 0 : xt + 2 * kPX) : (xt == 0 ? n - 1 : xt - 1));
+    const uint32_t coly = (uint32_t)(wb ? (y0 == 0 ? n - 1 : y0 - 1) : (y0 + kPY == n ? 0 : y0 + kPY)) * n + x0;
     auto plane_of = [&](int z) -> uint32_t { return (uint32_t)(z < 0 ? z + n : (z >= n ? z - n : z)) * nn; };
     auto st2 = [&](const F2* r, int a) -> F2 { return a < 2 ? fma2(dt, r[a + 2], r[a]) : r[a + 2]; };
     auto st1 = [&](const float* r, int a) -> float { return a < 2 ? r[a] + dts * r[a + 2] : r[a + 2]; };
-    // copies of plane z into stage slot s: this thread's pair, and its halo values
+    // copies of plane z into stage slot s: this thread's pair, and halo sites
     auto stage_plane = [&](int z, int s) {
         const uint32_t o = plane_of(z);
 #pragma unroll
         for (int q = 0; q < 8; q++)
-            if (q < nraw) {
-                cp_async_small<8>(&SM.stage[s][q][tid], R[q] + o + col);
-                if (hxl || hxr) cp_async_small<4>(&SM.sx[s][q][ty][xs], R[q] + o + colx);
-                if (hyb || hya) cp_async_small<8>(&SM.sy[s][q][ys][tx], R[q] + o + coly);
+            if (q < nraw) cp_async_small<8>(&SM.stage[s][q][tid], Rc[q] + o);
+        if (wb || wa) {
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (q < nraw) cp_async_small<8>(&SM.sy[s][q][wa][tx], R[q] + o + coly);
+            if (xh) {
+#pragma unroll
+                for (int q = 0; q < 8; q++)
+                    if (q < nraw) cp_async_small<4>(&SM.sx[s][q][xrow][xside], R[q] + o + colx);
             }
+        }
     };
     // halos of the plane in slot s into tile t
     auto halo_to_tile = [&](int s, int t) {
-        if (hxl || hxr) {
-            float r[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                if (q < nraw) r[q] = SM.sx[s][q][ty][xs];
-#pragma unroll
-            for (int a = 0; a < 6; a++)
-                if (a + 2 < nraw) SM.tile[t][a][ty + 1][hxl ? 1 : 2 * kPX + 2] = st1(r, a);
-        }
-        if (hyb || hya) {
+        if (!(wb || wa)) return;
+        {
             F2 r[8];
 #pragma unroll
             for (int q = 0; q < 8; q++)
-                if (q < nraw) r[q] = SM.sy[s][q][ys][tx];
+                if (q < nraw) r[q] = SM.sy[s][q][wa][tx];
 #pragma unroll
             for (int a = 0; a < 6; a++)
                 if (a + 2 < nraw)
-                    *reinterpret_cast<F2*>(&SM.tile[t][a][hyb ? 0 : kPY + 1][2 + 2 * tx]) = st2(r, a);
+                    *reinterpret_cast<F2*>(&SM.tile[t][a][wb ? 0 : kPY + 1][2 + 2 * tx]) = st2(r, a);
+        }
+        if (xh) {
+            float r[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (q < nraw) r[q] = SM.sx[s][q][xrow][xside];
+#pragma unroll
+            for (int a = 0; a < 6; a++)
+                if (a + 2 < nraw) SM.tile[t][a][xrow + 1][xside ? 2 * kPX + 2 : 1] = st1(r, a);
         }
     };
 
@@ -535,12 +552,12 @@ __global__ void __launch_bounds__(kPX * kPY, 2)
     F2 fbz[2][2];        // raw fb pairs at z, z+1
     {
         F2 r0[8], r1[8];
-        const uint32_t pm = plane_of(z0 - 1) + col, pc = plane_of(z0) + col;
+        const uint32_t pm = plane_of(z0 - 1), pc = plane_of(z0);
 #pragma unroll
         for (int q = 0; q < 8; q++)
             if (q < nraw) {
-                r0[q] = *reinterpret_cast<const F2*>(R[q] + pm);
-                r1[q] = *reinterpret_cast<const F2*>(R[q] + pc);
+                r0[q] = *reinterpret_cast<const F2*>(Rc[q] + pm);
+                r1[q] = *reinterpret_cast<const F2*>(Rc[q] + pc);
             }
 #pragma unroll
         for (int a = 0; a < 6; a++)
