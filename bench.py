@@ -75,13 +75,18 @@ def config_of(name, p, world):
                   if state / 2 > L2_BYTES else "state fits in L2"}
 
 
+STEP_KERNEL_SOURCES = ("lat_step_fast.cu", "lat_step_march.cu", "lat_march.cuh", "lat_common.cuh", "lat_pairs.cuh",
+                       "lat_async.cuh", "lat_kernels.h")
+
+
 def kernel_source_hash():
+    """Hash of the sources the fused step kernels are built from (a recorded
+    DRAM-traffic figure is valid only for these exact sources)."""
     d = os.path.join(ROOT, "paper_0911_5692_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in STEP_KERNEL_SOURCES:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
