@@ -345,3 +345,31 @@ def test_specialised_instances(prec, n, ty, depth, zr):
     compare_states(g, o, steps * TOL[prec], f"fast N={n} ty={ty} depth={depth} zr={zr} fp{prec}")
     gs, os_ = g.scalars(), o.scalars()
     assert abs(gs["a"] / os_["a"] - 1) <= (1e-13 if prec == 64 else 1e-7)
+
+
+@pytest.mark.parametrize("fluct", [1.0, 1e4])
+def test_fp32_run_statistics(fluct):
+    """Statistics over a run (<f>, var f, total energy, a(t)) of the 32^3 lambda phi^4
+    configuration on the FP32 path against the FP64 oracle from the same start, every
+    100 of 1000 steps, within 1e-3 (parametric resonance does not saturate this early).
+    At the vacuum amplitude (fluct = 1) the inflaton's fluctuations (1.6e-7 about 1)
+    are below FP32 resolution, so var phi is compared only with fluctuations scaled
+    up by 1e4, where FP32 resolves them."""
+    p = lphi4(32, precision=32, fluct=fluct)
+    g = Lattice(p)
+    g.init_fields()
+    st = g.get_state()
+    sc = g.scalars()
+    o = Oracle(dict(p, precision=64))
+    o.set_state(*st, t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
+    for _ in range(10):
+        g.evolve(100)
+        o.step(100)
+        eg, eo = g.energies(), o.energies()
+        assert abs(eg["a"] / eo["a"] - 1) <= 1e-3
+        assert abs(eg["rho"] / eo["rho"] - 1) <= 1e-3
+        assert abs(eg["mean0"] - eo["mean0"]) <= 1e-3 * abs(eo["mean0"]) + 1e-3 * math.sqrt(eo["var0"])
+        assert abs(eg["mean1"] - eo["mean1"]) <= 1e-3 * math.sqrt(eo["var1"])
+        assert abs(eg["var1"] / eo["var1"] - 1) <= 1e-3
+        if fluct > 1.0:
+            assert abs(eg["var0"] / eo["var0"] - 1) <= 1e-3
