@@ -35,7 +35,11 @@
  *   gradient average   Sec. II.B, divergence-theorem identity: on a periodic
  *                      lattice <|grad f|^2> = -<f Lap f>; here it is evaluated
  *                      from forward differences, the 7-point stencil's gradient.
- *   Laplacian          Sec. II.C names the 7-point ("naive", LATTICEEASY) stencil.
+ *   Laplacian          Sec. II.C: the 7-point ("naive", LATTICEEASY) stencil, or the
+ *                      paper's 27-point stencil (Patra and Karttunen; second-order
+ *                      accurate, fourth-order isotropic); with the 27-point stencil
+ *                      the gradient average is -<f L f> with the same L, as the
+ *                      paper's kernel forms it from the Laplacian.
  *   initial conditions Sec. II.B, last paragraph: homogeneous values plus Gaussian
  *                      vacuum fluctuations (DEFROST style), converted with
  *                      f = A a^r phi, f' = (A/B) a^(r-s) phidot + r (a'/a) f, then
@@ -66,7 +70,7 @@ typedef struct {
     int32_t n;          /* lattice is n^3 */
     int32_t model;      /* 0: V = lambda/4 phi^4 + g2/2 phi^2 chi^2; 1: V = m^2/2 phi^2 + g2/2 phi^2 chi^2 */
     int32_t expansion;  /* 0: static space, a = 1; 1: FRW */
-    int32_t reserved;
+    int32_t stencil;    /* Laplacian: 7 (or 0) = 7-point, 27 = 27-point (Sec. II.C) */
     double L, dt;       /* box side and time step, program units */
     double lambda, m, g2;
     double phi0[2], dphi0[2]; /* homogeneous values and physical-time derivatives */
@@ -152,6 +156,7 @@ int orc_create(const orc_params *p, orc_lattice **out)
 {
     *out = NULL;
     if (p->n < 2 || p->n > 1024 || p->L <= 0.0 || p->dt <= 0.0) return ORC_EINVAL;
+    if (p->stencil != 0 && p->stencil != 7 && p->stencil != 27) return ORC_EINVAL;
     orc_lattice *L = (orc_lattice *)calloc(1, sizeof(orc_lattice));
     if (!L) return ORC_ENOMEM;
     L->p = *p;
@@ -214,6 +219,60 @@ void orc_laplacian(int n, double dx, const double *f, double *out)
             }
 }
 
+/* 27-point Laplacian over the 3x3x3 cube, periodic. The weights (in units of
+ * 1/dx^2) depend on the neighbour's distance class: face (6 neighbours) 14/30,
+ * edge (12) 3/30, corner (8) 1/30, centre -128/30. With symbol
+ * L(k) = c0 + 2 c1 sum cos k_i + 4 c2 sum_{i<j} cos k_i cos k_j + 8 c3 prod cos k_i,
+ * L(0) = 0, the k^2 coefficient -1 (second-order accuracy) and an isotropic k^4
+ * term (fourth-order isotropy: coefficient of sum_{i<j} k_i^2 k_j^2 twice that of
+ * sum k_i^4) leave a one-parameter family c1 = 2 c2 + 8 c3, c2 = (1 - 12 c3)/6;
+ * c3 = 1/30 is the member the paper takes from Patra and Karttunen (the one
+ * DEFROST uses). */
+static const double ORC_W27[4] = {-128.0 / 30.0, 14.0 / 30.0, 3.0 / 30.0, 1.0 / 30.0};
+
+void orc_laplacian27(int n, double dx, const double *f, double *out)
+{
+    double inv = 1.0 / (dx * dx);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < n; z++)
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                double acc = 0.0;
+                for (int dz = -1; dz <= 1; dz++)
+                    for (int dy = -1; dy <= 1; dy++)
+                        for (int ddx = -1; ddx <= 1; ddx++) {
+                            int cls = abs(dz) + abs(dy) + abs(ddx);
+                            acc += ORC_W27[cls] * f[idx(n, wrap(x + ddx, n), wrap(y + dy, n), wrap(z + dz, n))];
+                        }
+                out[idx(n, x, y, z)] = acc * inv;
+            }
+}
+
+/* the configured Laplacian */
+static int is27(const orc_lattice *L) { return L->p.stencil == 27; }
+static void laplacian_of(const orc_lattice *L, const double *f, double *out)
+{
+    if (is27(L)) orc_laplacian27(L->n, L->dx, f, out);
+    else orc_laplacian(L->n, L->dx, f, out);
+}
+
+/* volume average of -f L27 f, the gradient average of the 27-point stencil */
+double orc_grad2_mean27(int n, double dx, const double *f)
+{
+    size_t N3 = (size_t)n * n * n;
+    double *lf = (double *)malloc(sizeof(double) * N3);
+    orc_laplacian27(n, dx, f, lf);
+    double tot = 0.0;
+    size_t plane = (size_t)n * n;
+    for (int z = 0; z < n; z++) {
+        double acc = 0.0;
+        for (size_t k = 0; k < plane; k++) acc += -f[(size_t)z * plane + k] * lf[(size_t)z * plane + k];
+        tot += acc;
+    }
+    free(lf);
+    return tot / (double)N3;
+}
+
 /* volume average of |grad f|^2 with forward differences */
 double orc_grad2_mean(int n, double dx, const double *f)
 {
@@ -241,8 +300,8 @@ double orc_grad2_mean(int n, double dx, const double *f)
 void orc_sums(orc_lattice *L)
 {
     int n = L->n;
-    L->S[0] = orc_grad2_mean(n, L->dx, L->f[0]);
-    L->S[1] = orc_grad2_mean(n, L->dx, L->f[1]);
+    L->S[0] = is27(L) ? orc_grad2_mean27(n, L->dx, L->f[0]) : orc_grad2_mean(n, L->dx, L->f[0]);
+    L->S[1] = is27(L) ? orc_grad2_mean27(n, L->dx, L->f[1]) : orc_grad2_mean(n, L->dx, L->f[1]);
     double *pd = (double *)calloc((size_t)n, sizeof(double));
     double *pi = (double *)calloc((size_t)n, sizeof(double));
     const double *f0 = L->f[0], *f1 = L->f[1];
@@ -311,8 +370,8 @@ static void field_coefficients(const orc_lattice *L, double a, double ad_half, d
 /* acceleration F_i = cL Lap f_i + cF f_i - dV_pr/df_i at the field time */
 static void accelerations(const orc_lattice *L, double cL, double cF, double *F0, double *F1)
 {
-    orc_laplacian(L->n, L->dx, L->f[0], F0);
-    orc_laplacian(L->n, L->dx, L->f[1], F1);
+    laplacian_of(L, L->f[0], F0);
+    laplacian_of(L, L->f[1], F1);
     const double *f0 = L->f[0], *f1 = L->f[1];
     double a = L->a;
 #pragma omp parallel for schedule(static)
@@ -498,6 +557,22 @@ static double kcut_of(const orc_lattice *L) { return L->p.kcut > 0.0 ? L->p.kcut
  * omega^2 = k_lat^2 + m_eff^2 and k_lat^2 = sum_d (2/dx sin(pi n_d / n))^2. The
  * program-unit amplitude carries the factor A B (f = A phi, x_pr = B x). Modes
  * with |n| = 0 or |n| > kcut, and modes with omega^2 <= 0, are left empty. */
+/* -L(k) of the configured stencil for the integer wave vector (nx, ny, nz): the
+ * lattice k^2 that replaces |k|^2 in the dispersion relation */
+static double klat2(const orc_lattice *L, int nx, int ny, int nz)
+{
+    int n = L->n;
+    if (!is27(L)) {
+        double sx = 2.0 / L->dx * sin(ORC_PI * nx / n), sy = 2.0 / L->dx * sin(ORC_PI * ny / n),
+               sz = 2.0 / L->dx * sin(ORC_PI * nz / n);
+        return sx * sx + sy * sy + sz * sz;
+    }
+    double cx = cos(2.0 * ORC_PI * nx / n), cy = cos(2.0 * ORC_PI * ny / n), cz = cos(2.0 * ORC_PI * nz / n);
+    double sym = ORC_W27[0] + 2.0 * ORC_W27[1] * (cx + cy + cz) + 4.0 * ORC_W27[2] * (cx * cy + cx * cz + cy * cz)
+               + 8.0 * ORC_W27[3] * cx * cy * cz;
+    return -sym / (L->dx * L->dx);
+}
+
 static void fluctuation(const orc_lattice *L, int field, int q, double meff2, double *out)
 {
     int n = L->n;
@@ -512,9 +587,7 @@ static void fluctuation(const orc_lattice *L, int field, int q, double meff2, do
             for (int x = 0; x < n; x++) {
                 int nx = x < n / 2 ? x : x - n, ny = y < n / 2 ? y : y - n, nz = z < n / 2 ? z : z - n;
                 double nmag = sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
-                double sx = 2.0 / L->dx * sin(ORC_PI * nx / n), sy = 2.0 / L->dx * sin(ORC_PI * ny / n),
-                       sz = 2.0 / L->dx * sin(ORC_PI * nz / n);
-                double w2 = sx * sx + sy * sy + sz * sz + meff2;
+                double w2 = klat2(L, nx, ny, nz) + meff2;
                 double scale = 0.0;
                 if (nmag > 0.0 && nmag <= kc && w2 > 0.0) {
                     double w = sqrt(w2);
@@ -620,7 +693,8 @@ int orc_energies(orc_lattice *L, double out[17])
     free(F0); free(F1);
     double cg = pow(a, -2.0 * L->s - 2.0);
     double grad[2];
-    for (int i = 0; i < 2; i++) grad[i] = 0.5 * cg * orc_grad2_mean(L->n, L->dx, L->f[i]);
+    for (int i = 0; i < 2; i++)
+        grad[i] = 0.5 * cg * (is27(L) ? orc_grad2_mean27(L->n, L->dx, L->f[i]) : orc_grad2_mean(L->n, L->dx, L->f[i]));
     double conv = L->B * L->B / (L->A * L->A) * pow(a, 2.0 * L->s - 2.0 * L->r);
     double rho = conv * (kin[0] + kin[1] + grad[0] + grad[1] + pot);
     double pres = conv * (kin[0] + kin[1] - (grad[0] + grad[1]) / 3.0 - pot);
@@ -862,8 +936,8 @@ int orc_adjoint(orc_lattice *L, int64_t nsteps, double *fbar[2], double *pibar[2
         }
         /* kick pi_{k+1} = pi_k + dt (cL Lap f + cF f - dV/df): adjoints of the
          * step coefficients are volume sums */
-        orc_laplacian(n, L->dx, f0, lf0);
-        orc_laplacian(n, L->dx, f1, lf1);
+        laplacian_of(L, f0, lf0);
+        laplacian_of(L, f1, lf1);
         for (size_t i = 0; i < N3; i++) t0[i] = pt0[i] * lf0[i] + pt1[i] * lf1[i];
         double bcL = dt * volume_sum(n, t0);
         for (size_t i = 0; i < N3; i++) t0[i] = pt0[i] * f0[i] + pt1[i] * f1[i];
@@ -875,8 +949,8 @@ int orc_adjoint(orc_lattice *L, int64_t nsteps, double *fbar[2], double *pibar[2
         double bS[4] = {0.0, 0.0, 0.0, 0.0};
         step_coefs_adjoint(L, a, S, &o, bcL, bcF, bcd, bkp, by, &ba, &bad, bS, &bk0);
         /* field adjoints: fbar_k = fbar_{k+1} + dt (dF/df)^T pt + sum_j bS_j dS_j/df */
-        orc_laplacian(n, L->dx, pt0, lp0);
-        orc_laplacian(n, L->dx, pt1, lp1);
+        laplacian_of(L, pt0, lp0);
+        laplacian_of(L, pt1, lp1);
         for (size_t i = 0; i < N3; i++) {
             double p0 = f0[i], p1 = f1[i];
             double h00 = o.cd * (beta - 1.0) * pow(p0, beta - 2.0) + o.kp * p1 * p1;

@@ -30,7 +30,7 @@ ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_ENONFINITE = 0, 1, 3, 5
 
 class OrcParams(C.Structure):
     _fields_ = [
-        ("n", C.c_int32), ("model", C.c_int32), ("expansion", C.c_int32), ("reserved", C.c_int32),
+        ("n", C.c_int32), ("model", C.c_int32), ("expansion", C.c_int32), ("stencil", C.c_int32),
         ("L", C.c_double), ("dt", C.c_double),
         ("lam", C.c_double), ("m", C.c_double), ("g2", C.c_double),
         ("phi0", C.c_double * 2), ("dphi0", C.c_double * 2),
@@ -82,6 +82,9 @@ def lib():
             L.orc_normal.restype = C.c_double
             L.orc_fft1.argtypes = [C.c_int, dp, dp, dp, dp, C.c_int]
             L.orc_fft3.argtypes = [C.c_int, dp, dp, C.c_int]
+            L.orc_laplacian27.argtypes = [C.c_int, C.c_double, dp, dp]
+            L.orc_grad2_mean27.argtypes = [C.c_int, C.c_double, dp]
+            L.orc_grad2_mean27.restype = C.c_double
             L.orc_set_g2.argtypes = [P, C.c_double]
             L.orc_adjoint.argtypes = [P, C.c_int64, C.POINTER(dp), C.POINTER(dp), dp]
             L.orc_step_coefs.argtypes = [P, C.c_double, C.c_double, dp, dp]
@@ -97,6 +100,7 @@ def _dp(a: np.ndarray):
 def make_params(d: dict) -> OrcParams:
     p = OrcParams()
     p.n = int(d["n"]); p.model = int(d.get("model", 0)); p.expansion = int(d.get("expansion", 1))
+    p.stencil = int(d.get("stencil", 7))
     p.L = float(d.get("L", 10.0)); p.dt = float(d["dt"])
     p.lam = float(d.get("lam", 0.0)); p.m = float(d.get("m", 0.0)); p.g2 = float(d.get("g2", 0.0))
     phi0 = d.get("phi0", (1.0, 0.0)); dphi0 = d.get("dphi0", (0.0, 0.0))
@@ -251,6 +255,18 @@ def laplacian(f: np.ndarray, dx: float) -> np.ndarray:
     out = np.empty_like(f)
     lib().orc_laplacian(f.shape[0], float(dx), _dp(f), _dp(out))
     return out
+
+
+def laplacian27(f: np.ndarray, dx: float) -> np.ndarray:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(f)
+    lib().orc_laplacian27(f.shape[0], float(dx), _dp(f), _dp(out))
+    return out
+
+
+def grad2_mean27(f: np.ndarray, dx: float) -> float:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return lib().orc_grad2_mean27(f.shape[0], float(dx), _dp(f))
 
 
 def grad2_mean(f: np.ndarray, dx: float) -> float:
