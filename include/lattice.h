@@ -69,6 +69,11 @@ typedef struct {
                              2 pi / L); 0: N/4 */
     double fluct;         /* multiplier on the vacuum fluctuation amplitude (1 = vacuum) */
     uint64_t seed;        /* seed of the counter-based generator for the initial state */
+    int32_t stencil;      /* Laplacian (Sec. II.C): 0 or 7 = 7-point (LATTICEEASY);
+                             27 = the 27-point stencil of Patra and Karttunen over
+                             the 3x3x3 cube, weights 14/30 (6 faces), 3/30 (12
+                             edges), 1/30 (8 corners), -128/30 (centre), in 1/dx^2 */
+    int32_t reserved;     /* 0 */
 } lat_params;
 
 /* Volume averages at the field time, in physical units (Sec. II.B, eq. rho-pres;
@@ -84,8 +89,11 @@ typedef struct {
  * stream) with library-owned device buffers (8 arrays of N^3 elements: f and
  * f' of both fields, twice for the leapfrog's ping-pong). Validates the
  * parameters and the stability bound of the leapfrog (LAT_ECFL when
- * dt^2 (12 a^(-2s-2)/dx^2 + m_eff^2) > 4 at the initial state). The fields
- * start at zero; call lat_init_fields or lat_set_state. On error *out is NULL. */
+ * dt^2 (k_max^2 + m_eff^2) > 4 at the initial state, with k_max^2 the
+ * stencil's largest lattice frequency squared: 12/dx^2 for 7 points, 92/(15 dx^2)
+ * for 27). The fields start at zero; call lat_init_fields or lat_set_state.
+ * A 27-point lattice runs on the plane-ring step kernel only (variant 2 of
+ * lat_set_kernel). On error *out is NULL. */
 lat_status lat_create(const lat_params* params, void* cuda_stream, lat_handle** out);
 
 /* As lat_create, with caller-owned device buffers (e.g. torch tensors):
@@ -99,14 +107,15 @@ lat_status lat_create_with_buffers(const lat_params* params, void* cuda_stream,
  * values from params plus Gaussian vacuum fluctuations of every field and
  * momentum (white noise from Philox-4x32-10 keyed by the seed, filtered in
  * Fourier space to |f_k|^2 = 1/(2 w_k), |f'_k|^2 = w_k/2, w_k^2 = k_lat^2 +
- * m_eff^2), converted to program units (f = A a^r phi, f' = (A/B) a^(r-s) phidot
+ * m_eff^2, k_lat^2 = -L(k) the symbol of the configured stencil), converted to program units (f = A a^r phi, f' = (A/B) a^(r-s) phidot
  * + r (a'/a) f), then the fields and a advanced by dt/2. Runs on the device with
  * temporary buffers; synchronises the stream. */
 lat_status lat_init_fields(lat_handle* h);
 
 /* Advance n_steps leapfrog steps (Sec. II.B, eq. evo with eq. scalar-evo and
- * eq. scale). Each step is one fused kernel: 7-point Laplacian, potential
- * derivative, kick and drift of both fields, the <|grad f|^2> and <V> sums of
+ * eq. scale). Each step is one fused kernel: the configured Laplacian (7- or
+ * 27-point), potential derivative, kick and drift of both fields, the
+ * <|grad f|^2> and <V> sums of
  * the new fields, and (in its last block) the FP64 scale-factor update that sets
  * the coefficients of the next step. Asynchronous; no host synchronisation.
  * n_steps >= 0. */
@@ -138,7 +147,10 @@ lat_status lat_set_state(lat_handle* h, int field, int what, const void* src, in
 /* Scalars: out[0] = t (time of the momenta), out[1] = a (at t + dt/2),
  * out[2] = a' (at t), out[3] = step count, out[4..7] = the volume averages
  * <|grad f_phi|^2>, <|grad f_chi|^2>, <f_phi^beta/beta>, <f_phi^2 f_chi^2/2> at the
- * field time. Synchronises; returns a sticky device error if one is set. */
+ * field time, where <|grad f|^2> = -<f L f> for the configured Laplacian L (the
+ * forward-difference sum for 7 points; the weighted sum over the 13 neighbour
+ * pairs of each site for 27). Synchronises; returns a sticky device error if one
+ * is set. */
 lat_status lat_get_scalars(lat_handle* h, double out[8]);
 
 /* Set t, a (at t + dt/2), a' (at t) and the step count from in[0..3]; the sums
@@ -165,7 +177,8 @@ lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
  * asynchronous copies (the fast path), 3 = plane ring filled by TMA boxes;
  * ty = owned rows per tile, zr = planes per z-chunk (variant 3: planes per
  * block), depth = planes prefetched ahead (variants 2 and 3), 0 = automatic.
- * LAT_EUNSUPPORTED if the variant cannot run this lattice. */
+ * LAT_EUNSUPPORTED if the variant cannot run this lattice (a 27-point lattice
+ * runs on variant 2 only; ty, zr and depth apply to it as above). */
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth);
 
 /* Launch geometry of the current step kernel: out[0] = variant, out[1] = blocks
@@ -183,8 +196,9 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8]);
  * to out_dev (device, 4 doubles, caller-owned) the averages <|grad f_phi|^2>,
  * <|grad f_chi|^2> (forward differences / dx^2), <f_phi^beta/beta> and
  * <f_phi^2 f_chi^2 / 2>: the same values lat_get_scalars reports in out[4..7]
- * for a handle holding these fields. Asynchronous on cuda_stream (a
- * cudaStream_t; NULL = legacy default stream).
+ * for a handle holding these fields with the 7-point stencil (the gradient
+ * average of the 27-point stencil is not served here). Asynchronous on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream).
  * Scratch: one static device array per GPU (about 33 KB, held by every GPU that
  * loads the library until the process exits); it calls no cudaMalloc, cudaFree
  * or allocating library routine. The first call on a device looks the array up
@@ -223,8 +237,9 @@ lat_status lat_set_g2(lat_handle* h, double g2);
  *     arrays.
  * The handle ends at the state after n_steps (as after lat_evolve). Handles
  * configured for the TMA step kernel take the plane-ring kernel in both passes.
- * Synchronises. LAT_ENOMEM if the checkpoints do not fit; sticky device errors
- * of the forward or reverse pass are returned. */
+ * Synchronises. LAT_ENOMEM if the checkpoints do not fit; LAT_EUNSUPPORTED for
+ * a 27-point lattice; sticky device errors of the forward or reverse pass are
+ * returned. */
 lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fbar_dev, void* pibar_dev,
                    double sbar[4]);
 
@@ -254,7 +269,8 @@ lat_status lat_adjoint(lat_handle* h, int64_t n_steps, int observable, int64_t c
  * lat_slab_advance(advance = 0). lat_get_state / lat_set_state /
  * lat_get_scalars / lat_set_scalars act on the slab's stored arrays; the
  * whole-lattice calls (evolve, init, energies, spectrum, checkpoints,
- * derivative, set_kernel) return LAT_ESTATE on a slab. nzl >= 2. */
+ * derivative, set_kernel) return LAT_ESTATE on a slab. nzl >= 2.
+ * LAT_EUNSUPPORTED for a 27-point lattice. */
 lat_status lat_slab_create(const lat_params* params, int z0, int nzl, void* cuda_stream, void* const dev_bufs[8],
                            lat_handle** out);
 
@@ -284,7 +300,8 @@ typedef struct lat_batch lat_batch;
  * member owns its buffers), bound to cuda_stream. The launch shape comes from
  * the process's autotuner cache for this set of sizes and precision, else a
  * default. LAT_EINVAL for mixed precisions or a bad member (its lat_create
- * status is returned), LAT_EUNSUPPORTED if a member size fits no block shape. */
+ * status is returned), LAT_EUNSUPPORTED if a member size fits no block shape or
+ * a member has the 27-point stencil. */
 lat_status lat_batch_create(const lat_params* params, int count, void* cuda_stream, lat_batch** out);
 
 /* lat_init_fields on every member (each with its own seed). Synchronises. */

@@ -32,6 +32,7 @@ lat_status derive_model(const lat_params& p, Model* M)
     if (p.precision != 32 && p.precision != 64) return LAT_EINVAL;
     if (!(p.L > 0.0) || !(p.dt > 0.0) || !std::isfinite(p.L) || !std::isfinite(p.dt)) return LAT_EINVAL;
     if (p.expansion != 0 && p.expansion != 1) return LAT_EINVAL;
+    if (p.stencil != 0 && p.stencil != 7 && p.stencil != 27) return LAT_EINVAL;
     double cpl, beta;
     if (p.model == LAT_MODEL_LPHI4) { cpl = p.lambda; beta = 4.0; }
     else if (p.model == LAT_MODEL_M2PHI2) { cpl = p.m * p.m; beta = 2.0; }
@@ -55,6 +56,8 @@ lat_status derive_model(const lat_params& p, Model* M)
     M->dx = p.L / p.n;
     M->dt = p.dt;
     M->inv_dx2 = 1.0 / (M->dx * M->dx);
+    M->stencil = p.stencil == 27 ? 27 : 7;
+    M->lap_scale = M->stencil == 27 ? M->inv_dx2 / 30.0 : M->inv_dx2;
     M->A = A; M->B = B; M->r = r; M->s = s;
     M->cdom0 = cpl * std::pow(A, 2.0 - beta) / (B * B);
     M->pdom = 2.0 * r - 2.0 * s - beta * r;
@@ -73,14 +76,18 @@ void meff2_initial(const lat_params& p, const Model& M, double out[2])
     out[1] = M.kappa0 * fh * fh;
 }
 
-// Stability of the leapfrog for the 7-point stencil: the largest lattice
-// frequency must satisfy w dt < 2, w^2 = 12/dx^2 + m_eff^2 (a = 1).
+// Stability of the leapfrog: the largest lattice frequency must satisfy
+// w dt < 2, w^2 = k_max^2 + m_eff^2 (a = 1), k_max^2 = max over k of -L(k). For
+// the 7-point stencil -L = 4 sum_i s_i / dx^2 with s_i = sin^2(k_i dx / 2); for
+// the 27-point one -L = (4 sum s_i - 8/3 sum_{i<j} s_i s_j + 32/15 s_1 s_2 s_3) / dx^2,
+// multilinear in s in [0, 1]^3 and largest at s = (1, 1, 1): 12/dx^2 and
+// 92/(15 dx^2).
 lat_status check_cfl(const lat_params& p, const Model& M)
 {
     double m2[2];
     meff2_initial(p, M, m2);
     const double mmax = std::max(0.0, std::max(m2[0], m2[1]));
-    const double w2 = 12.0 * M.inv_dx2 + mmax;
+    const double w2 = (M.stencil == 27 ? 92.0 / 15.0 : 12.0) * M.inv_dx2 + mmax;
     if (!(p.dt * p.dt * w2 <= 4.0)) return LAT_ECFL;
     return LAT_OK;
 }
@@ -161,6 +168,20 @@ lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int dept
 {
     const int n = h->p.n;
     if (variant < 0 || variant > 3) return LAT_EINVAL;
+    if (h->M.stencil == 27) {   // the 27-point Laplacian runs on its plane-ring kernel only
+        if (variant != 0 && variant != 2) return LAT_EUNSUPPORTED;
+        MarchConfig cfg;
+        if (!march27_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr,
+                            variant == 0 ? 0 : depth, &cfg) ||
+            (size_t)cfg.blocks * kSums > h->partials_cap)
+            return LAT_EUNSUPPORTED;
+        h->mcfg = cfg;
+        h->ty = cfg.ty;
+        h->zr = cfg.zr;
+        h->variant = 2;
+        drop_graph(h);
+        return LAT_OK;
+    }
     int chosen = 0;
     if (variant == 0 || variant == 2) {
         MarchConfig cfg;
@@ -493,7 +514,7 @@ lat_status lat_init_fields(lat_handle* h)
                 double* outq = q == 0 ? df : dp;
                 if (launch_white_noise(re, n, p.seed, (uint32_t)field, (uint32_t)q, h->stream) != cudaSuccess) st = LAT_ECUDA;
                 else if (cufftExecD2Z(fwd, re, (cufftDoubleComplex*)spec) != CUFFT_SUCCESS) st = LAT_ECUDA;
-                else if (launch_spectral_scale(spec, n, M.dx, m2[field], amp, kcut, q, h->stream) != cudaSuccess) st = LAT_ECUDA;
+                else if (launch_spectral_scale(spec, n, M.dx, m2[field], amp, kcut, q, M.stencil, h->stream) != cudaSuccess) st = LAT_ECUDA;
                 else if (cufftExecZ2D(inv, (cufftDoubleComplex*)spec, outq) != CUFFT_SUCCESS) st = LAT_ECUDA;
             }
         }
@@ -559,7 +580,7 @@ lat_status lat_energies(lat_handle* h, lat_energy_report* out)
     const double cg = std::pow(a, -2.0 * M.s - 2.0);
     const double conv = M.B * M.B / (M.A * M.A) * std::pow(a, 2.0 * M.s - 2.0 * M.r);
     const double kin0 = tot[0], kin1 = tot[1], pot = tot[4];
-    const double gr0 = 0.5 * cg * tot[2] * M.inv_dx2, gr1 = 0.5 * cg * tot[3] * M.inv_dx2;
+    const double gr0 = 0.5 * cg * tot[2] * M.lap_scale, gr1 = 0.5 * cg * tot[3] * M.lap_scale;
     out->t = s.t + 0.5 * M.dt;
     out->a = a;
     out->ad = M.expansion ? s.ad_half : 0.0;
@@ -639,7 +660,7 @@ lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, doub
 namespace {
 
 struct CkptHeader {
-    char magic[8];       // "LATCKPT2"
+    char magic[8];       // "LATCKPT3"
     uint64_t bytes;      // whole blob
     uint32_t scalars_bytes;
     uint32_t esize;
@@ -672,7 +693,7 @@ lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes)
     if (s.status != LAT_OK) return (lat_status)s.status;
     CkptHeader hd;
     std::memset(&hd, 0, sizeof(hd));
-    std::memcpy(hd.magic, "LATCKPT2", 8);
+    std::memcpy(hd.magic, "LATCKPT3", 8);
     hd.bytes = bytes;
     hd.scalars_bytes = sizeof(DevScalars);
     hd.esize = (uint32_t)h->esize;
@@ -695,7 +716,7 @@ lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes)
     if (h->slab) return LAT_ESTATE;
     CkptHeader hd;
     std::memcpy(&hd, src, sizeof(hd));
-    if (std::memcmp(hd.magic, "LATCKPT2", 8) != 0 || hd.bytes != bytes || hd.scalars_bytes != sizeof(DevScalars) ||
+    if (std::memcmp(hd.magic, "LATCKPT3", 8) != 0 || hd.bytes != bytes || hd.scalars_bytes != sizeof(DevScalars) ||
         hd.esize != h->esize || std::memcmp(&hd.params, &h->p, sizeof(lat_params)) != 0)
         return LAT_EINVAL;
     DevScalars s;

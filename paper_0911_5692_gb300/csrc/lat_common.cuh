@@ -16,8 +16,12 @@ struct Model {
     int n;
     int expansion;
     int beta;           // 2 or 4: exponent of the dominant potential term
-    int pad;
+    int stencil;        // Laplacian: 7-point or 27-point (Sec. II.C)
     double dx, dt, inv_dx2;
+    // factor turning the stencil's integer-weight neighbour sums into the
+    // Laplacian and the gradient average: 1/dx^2 (7-point, weights 1) or
+    // 1/(30 dx^2) (27-point, weights 14, 3, 1 for face, edge, corner)
+    double lap_scale;
     double A, B, r, s;
     double cdom0, pdom; // V_pr dominant term: cdom0 a^pdom f^beta / beta
     double kappa0, pint;// V_pr interaction: kappa0 a^pint f^2 chi^2 / 2
@@ -148,7 +152,7 @@ __device__ inline double apow(double a, double p)
 // The per-step coefficients of eq. scalar-evo as the step kernels use them.
 __device__ inline void step_coefficients(const Model& M, DevScalars* sc)
 {
-    sc->kd[0] = M.dt * sc->cL * M.inv_dx2;
+    sc->kd[0] = M.dt * sc->cL * M.lap_scale;
     sc->kd[1] = M.dt * sc->cF;
     sc->kd[2] = -M.dt * sc->cdom;
     sc->kd[3] = -M.dt * sc->kappa;
@@ -235,8 +239,8 @@ __device__ inline void reduce_partials(const Model& M, const double* partials, i
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if (tid == 0) {
-        out[0] = v[0] * M.inv_dx2 * M.inv_sites;
-        out[1] = v[1] * M.inv_dx2 * M.inv_sites;
+        out[0] = v[0] * M.lap_scale * M.inv_sites;
+        out[1] = v[1] * M.lap_scale * M.inv_sites;
         out[2] = v[2] * M.inv_sites;
         out[3] = v[3] * M.inv_sites;
     }

@@ -4,6 +4,7 @@
 #include <cufft.h>
 
 #include "lat_kernels.h"
+#include "lat_stencil27.cuh"
 
 namespace lat {
 
@@ -15,7 +16,9 @@ __device__ __forceinline__ size_t sidx(int n, int x, int y, int z) { return ((si
 // pass 0: [kin0, kin1, grad0, grad1, pot, sum f0, sum f1], where the momenta at
 // the field time are f' + (dt/2) F(f) (the average of the stored f' and the
 // next kick's), kin_i = (f'_i - r h f_i)^2 / 2 with h = a'/a at the field time,
-// grad_i = sum_d (forward difference)^2 (unscaled), pot = V_pr;
+// grad_i = the stencil's gradient sum before its factor M.lap_scale (7 points:
+// sum_d (forward difference)^2; 27 points: the 13 owned weighted bonds),
+// pot = V_pr;
 // pass 1: [0, 0, 0, 0, 0, sum (f0 - mean0)^2, sum (f1 - mean1)^2].
 template <typename T>
 __global__ void __launch_bounds__(256) energies_kernel(Bufs<T> B, Model M, const DevScalars* sc, double* partials,
@@ -47,14 +50,24 @@ __global__ void __launch_bounds__(256) energies_kernel(Bufs<T> B, Model M, const
                 continue;
             }
             const int zm = z == 0 ? n - 1 : z - 1, zp = z == n - 1 ? 0 : z + 1;
-            const double fx0 = (double)f0[sidx(n, xp, y, z)], fy0 = (double)f0[sidx(n, x, yp, z)],
-                         fz0 = (double)f0[sidx(n, x, y, zp)];
-            const double fx1 = (double)f1[sidx(n, xp, y, z)], fy1 = (double)f1[sidx(n, x, yp, z)],
-                         fz1 = (double)f1[sidx(n, x, y, zp)];
-            const double lap0 = (((fx0 - a0) + ((double)f0[sidx(n, xm, y, z)] - a0)) + ((fy0 - a0) + ((double)f0[sidx(n, x, ym, z)] - a0))
-                                 + ((fz0 - a0) + ((double)f0[sidx(n, x, y, zm)] - a0))) * M.inv_dx2;
-            const double lap1 = (((fx1 - a1) + ((double)f1[sidx(n, xm, y, z)] - a1)) + ((fy1 - a1) + ((double)f1[sidx(n, x, ym, z)] - a1))
-                                 + ((fz1 - a1) + ((double)f1[sidx(n, x, y, zm)] - a1))) * M.inv_dx2;
+            double lap0, lap1, gs0, gs1;
+            if (M.stencil == 27) {
+                lap0 = lap27_sum(f0, n, x, y, z) * M.lap_scale;
+                lap1 = lap27_sum(f1, n, x, y, z) * M.lap_scale;
+                gs0 = bonds27_sum(f0, n, x, y, z);
+                gs1 = bonds27_sum(f1, n, x, y, z);
+            } else {
+                const double fx0 = (double)f0[sidx(n, xp, y, z)], fy0 = (double)f0[sidx(n, x, yp, z)],
+                             fz0 = (double)f0[sidx(n, x, y, zp)];
+                const double fx1 = (double)f1[sidx(n, xp, y, z)], fy1 = (double)f1[sidx(n, x, yp, z)],
+                             fz1 = (double)f1[sidx(n, x, y, zp)];
+                lap0 = (((fx0 - a0) + ((double)f0[sidx(n, xm, y, z)] - a0)) + ((fy0 - a0) + ((double)f0[sidx(n, x, ym, z)] - a0))
+                                     + ((fz0 - a0) + ((double)f0[sidx(n, x, y, zm)] - a0))) * M.inv_dx2;
+                lap1 = (((fx1 - a1) + ((double)f1[sidx(n, xm, y, z)] - a1)) + ((fy1 - a1) + ((double)f1[sidx(n, x, ym, z)] - a1))
+                                     + ((fz1 - a1) + ((double)f1[sidx(n, x, y, zm)] - a1))) * M.inv_dx2;
+                gs0 = (fx0 - a0) * (fx0 - a0) + (fy0 - a0) * (fy0 - a0) + (fz0 - a0) * (fz0 - a0);
+                gs1 = (fx1 - a1) * (fx1 - a1) + (fy1 - a1) * (fy1 - a1) + (fz1 - a1) * (fz1 - a1);
+            }
             const double a0b = M.beta == 4 ? a0 * a0 * a0 : a0;
             const double F0 = cL * lap0 + cF * a0 - (cdom * a0b + kap * a0 * a1 * a1);
             const double F1 = cL * lap1 + cF * a1 - kap * a0 * a0 * a1;
@@ -62,8 +75,8 @@ __global__ void __launch_bounds__(256) energies_kernel(Bufs<T> B, Model M, const
             const double q1 = (double)p1[c] + 0.5 * dt * F1 - M.r * h * a1;
             acc[0] += 0.5 * q0 * q0;
             acc[1] += 0.5 * q1 * q1;
-            acc[2] += (fx0 - a0) * (fx0 - a0) + (fy0 - a0) * (fy0 - a0) + (fz0 - a0) * (fz0 - a0);
-            acc[3] += (fx1 - a1) * (fx1 - a1) + (fy1 - a1) * (fy1 - a1) + (fz1 - a1) * (fz1 - a1);
+            acc[2] += gs0;
+            acc[3] += gs1;
             const double sq = a0 * a0;
             acc[4] += cdom * (M.beta == 4 ? 0.25 * sq * sq : 0.5 * sq) + 0.5 * kap * sq * a1 * a1;
             acc[5] += a0;

@@ -49,7 +49,7 @@ __global__ void white_noise_kernel(double* out, size_t count, uint64_t seed, uin
 // with w^2 = k_lat^2 + m_eff^2, k_lat^2 = sum_d (2/dx sin(pi n_d/N))^2. Empty for
 // |n| = 0, |n| > kcut or w^2 <= 0.
 __global__ void spectral_scale_kernel(cufftDoubleComplex* spec, int n, double dx, double meff2, double amp,
-                                      double kcut, int quantity)
+                                      double kcut, int quantity, int stencil)
 {
     const int nh = n / 2 + 1;
     const size_t count = (size_t)n * n * nh;
@@ -61,9 +61,16 @@ __global__ void spectral_scale_kernel(cufftDoubleComplex* spec, int n, double dx
         const int ny = ky < n / 2 ? ky : ky - n;
         const int nz = kz < n / 2 ? kz : kz - n;
         const double nmag = sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
-        const double sx = 2.0 / dx * sinpi((double)nx / n), sy = 2.0 / dx * sinpi((double)ny / n),
-                     sz = 2.0 / dx * sinpi((double)nz / n);
-        const double w2 = sx * sx + sy * sy + sz * sz + meff2;
+        // k_lat^2 = -L(k) of the stencil in s_i = sin^2(pi n_i / N) (no
+        // cancellation at small k): 7-point 4 sum s_i / dx^2; 27-point
+        // (4 sum s_i - 8/3 sum_{i<j} s_i s_j + 32/15 s_1 s_2 s_3) / dx^2, the weights
+        // 14/30, 3/30, 1/30 of face, edge and corner neighbours written with
+        // cos(k_i dx) = 1 - 2 s_i
+        const double qx = sinpi((double)nx / n), qy = sinpi((double)ny / n), qz = sinpi((double)nz / n);
+        const double s1 = qx * qx, s2 = qy * qy, s3 = qz * qz;
+        double klat = 4.0 * (s1 + s2 + s3);
+        if (stencil == 27) klat += -8.0 / 3.0 * (s1 * s2 + s1 * s3 + s2 * s3) + 32.0 / 15.0 * s1 * s2 * s3;
+        const double w2 = klat / (dx * dx) + meff2;
         double scale = 0.0;
         if (nmag > 0.0 && nmag <= kcut && w2 > 0.0) {
             const double w = sqrt(w2);
@@ -110,11 +117,11 @@ cudaError_t launch_white_noise(double* out, int n, uint64_t seed, uint32_t field
 }
 
 cudaError_t launch_spectral_scale(void* spec, int n, double dx, double meff2, double amp, double kcut,
-                                  int quantity, cudaStream_t st)
+                                  int quantity, int stencil, cudaStream_t st)
 {
     const size_t count = (size_t)n * n * (n / 2 + 1);
     spectral_scale_kernel<<<grid_for(count), 256, 0, st>>>((cufftDoubleComplex*)spec, n, dx, meff2, amp, kcut,
-                                                           quantity);
+                                                           quantity, stencil);
     return cudaGetLastError();
 }
 

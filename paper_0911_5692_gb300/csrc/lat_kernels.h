@@ -42,6 +42,7 @@ struct MarchConfig {
     int fast;      // 1: the instance specialised for this (N, ty, depth)
     int nzl = 0;   // z-slab: owned planes (0: a whole periodic lattice)
     int zbase = 0; // z-slab: stored plane of z = z + zbase
+    int s27 = 0;   // 1: the 27-point Laplacian kernel (lat_step27.cu)
 };
 // kernel specialised for (element bytes, N, ty, depth), or null; *smem gets its
 // dynamic shared memory in bytes
@@ -56,6 +57,11 @@ bool march_slab_config(int n, int elem_bytes, int nzl, MarchConfig* cfg);
 template <typename T>
 cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                               const MarchConfig& cfg, cudaStream_t st, double* sums_out = nullptr);
+// the same ring with the 27-point Laplacian (whole periodic lattices)
+bool march27_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
+template <typename T>
+cudaError_t launch_step27(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
+                          cudaStream_t st);
 
 // TMA plane-ring fused step.
 struct TmaGeom {
@@ -99,7 +105,7 @@ cudaError_t launch_init_combine(const Bufs<T>& b, int field, const double* df, c
 cudaError_t launch_white_noise(double* out, int n, uint64_t seed, uint32_t field, uint32_t quantity,
                                cudaStream_t st);
 cudaError_t launch_spectral_scale(void* spec, int n, double dx, double meff2, double amp, double kcut,
-                                  int quantity, cudaStream_t st);
+                                  int quantity, int stencil, cudaStream_t st);
 
 // Diagnostics (off the timed path).
 constexpr int kEnergySums = 7;

@@ -1,0 +1,505 @@
+// lat_step27.cu -- the fused leapfrog step with the 27-point Laplacian of
+// Sec. II.C (Patra and Karttunen: second-order accurate, fourth-order
+// isotropic) on the shared-memory plane ring, FP32 and FP64.
+//
+// Same step and same ring as the 7-point plane-ring kernel (lat_march.cuh):
+// a block owns full x rows, ty rows in y and a run of z planes; one thread owns
+// one 16-byte vector of one row of the tile or of its halo (one row below, two
+// above); planes arrive by per-thread asynchronous copies `depth` planes ahead.
+//
+// Laplacian. With the weights in units of 1/(30 dx^2) (faces 14, edges 12 x 3,
+// corners 8 x 1) and, for each plane p of the 3x3x3 cube, the in-plane sums of
+// exact differences from that plane's own centre C_p,
+//   e_p = sum of the 4 face neighbours in the plane - 4 C_p,
+//   k_p = sum of the 4 corner neighbours in the plane - 4 C_p,
+// the stencil is
+//   30 dx^2 L f = (14 e_z + 3 k_z) + (3 e_{z-1} + k_{z-1}) + (3 e_{z+1} + k_{z+1})
+//                 + 30 ((C_{z-1} - c) + (C_{z+1} - c)),
+// every term a sum of differences that are exact for f = const + small
+// (Sterbenz), as in the 7-point kernel.
+//
+// Gradient average of the new fields (eq. scale): -<g L g> equals the mean over
+// sites of the weighted squared differences over the 13 neighbour pairs each
+// site owns. The owned offsets all have dy >= 0, so the one look-ahead row in
+// +y that the ring already provides suffices: per site four pairs in its plane
+// P, six to plane P + 1 and, for the site above it in P + 1, three back to P
+// (rows y, y + 1 of planes P and P + 1). The new-field planes are kept in a
+// triple buffer so that the pairs of plane P = k - 2 are summed at plane k
+// without another barrier; the last pair of planes of a run is summed after it.
+#include <algorithm>
+
+#include "lat_kernels.h"
+#include "lat_march.cuh"
+
+namespace lat {
+
+namespace {
+
+template <typename T>
+struct RowV {
+    typename PK<T>::P v[PK<T>::NP];
+    T l, r;   // the row's values left of the vector's first site and right of its last
+};
+
+// One row vector and its x neighbours: from the adjacent lanes where they hold
+// the same row, else from shared memory (dl, dr: offsets of the periodic
+// neighbours). Every lane of the warp calls this (shuffles).
+template <typename T>
+__device__ __forceinline__ void load_row(const T* p, RowV<T>& R, bool nbl, bool nbr, int dl, int dr)
+{
+    constexpr int NP = PK<T>::NP;
+    PK<T>::ld(p, R.v);
+    R.l = __shfl_up_sync(0xffffffffu, hi2(R.v[NP - 1]), 1);
+    R.r = __shfl_down_sync(0xffffffffu, lo2(R.v[0]), 1);
+    if (!nbl) R.l = p[dl];
+    if (!nbr) R.r = p[dr];
+}
+
+// the row shifted by one site: o[i] holds the value at x_i - 1 (shl) or x_i + 1 (shr)
+template <typename T>
+__device__ __forceinline__ void shl(const RowV<T>& R, typename PK<T>::P (&o)[PK<T>::NP])
+{
+    if constexpr (PK<T>::NP == 2) {
+        T c0, c1, c2, c3;
+        un2(R.v[0], c0, c1);
+        un2(R.v[1], c2, c3);
+        o[0] = mk2(R.l, c0);
+        o[1] = mk2(c1, c2);
+    } else {
+        o[0] = mk2(R.l, lo2(R.v[0]));
+    }
+}
+template <typename T>
+__device__ __forceinline__ void shr(const RowV<T>& R, typename PK<T>::P (&o)[PK<T>::NP])
+{
+    if constexpr (PK<T>::NP == 2) {
+        T c0, c1, c2, c3;
+        un2(R.v[0], c0, c1);
+        un2(R.v[1], c2, c3);
+        o[0] = mk2(c1, c2);
+        o[1] = mk2(c3, R.r);
+    } else {
+        o[0] = mk2(hi2(R.v[0]), R.r);
+    }
+}
+
+// e and k of one plane at this thread's sites: C the centre row, Ym and Yp the
+// rows y - 1 and y + 1 of the same plane
+template <typename T>
+__device__ __forceinline__ void plane_ek(const RowV<T>& C, const RowV<T>& Ym, const RowV<T>& Yp,
+                                         typename PK<T>::P (&e)[PK<T>::NP], typename PK<T>::P (&k)[PK<T>::NP])
+{
+    typedef typename PK<T>::P P;
+    constexpr int NP = PK<T>::NP;
+    P cl[NP], cr[NP], ml[NP], mr[NP], pl[NP], pr[NP];
+    shl(C, cl);
+    shr(C, cr);
+    shl(Ym, ml);
+    shr(Ym, mr);
+    shl(Yp, pl);
+    shr(Yp, pr);
+#pragma unroll
+    for (int v = 0; v < NP; v++) {
+        const P c = C.v[v];
+        e[v] = add2(add2(sub2(cl[v], c), sub2(cr[v], c)), add2(sub2(Ym.v[v], c), sub2(Yp.v[v], c)));
+        k[v] = add2(add2(sub2(ml[v], c), sub2(mr[v], c)), add2(sub2(pl[v], c), sub2(pr[v], c)));
+    }
+}
+
+// Per-thread sums of the new fields: the squared differences of each field
+// over its owned pairs by weight class (14, 3, 1), f0^beta and f0^2 f1^2.
+template <typename T>
+struct Sums27 {
+    typename PK<T>::P w14[2], w3[2], w1[2], vd, vi;
+    __device__ void zero()
+    {
+        const typename PK<T>::P z = mk2(T(0), T(0));
+        w14[0] = w14[1] = w3[0] = w3[1] = w1[0] = w1[1] = vd = vi = z;
+    }
+    __device__ void totals(bool quartic, double v[kSums]) const
+    {
+        for (int f = 0; f < 2; f++)
+            v[f] = 14.0 * ((double)lo2(w14[f]) + (double)hi2(w14[f])) + 3.0 * ((double)lo2(w3[f]) + (double)hi2(w3[f]))
+                   + ((double)lo2(w1[f]) + (double)hi2(w1[f]));
+        v[2] = ((double)lo2(vd) + (double)hi2(vd)) * (quartic ? 0.25 : 0.5);
+        v[3] = 0.5 * ((double)lo2(vi) + (double)hi2(vi));
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ typename PK<T>::P sq_acc(typename PK<T>::P a, typename PK<T>::P b, typename PK<T>::P acc)
+{
+    const typename PK<T>::P d = sub2(a, b);
+    return fma2(d, d, acc);
+}
+
+// Pairs of new-field plane P (Gp) with plane P + 1 (Gu) at this thread's own
+// row: rows j, j + 1 (o1 = n for own rows, 0 otherwise so that other threads
+// stay inside the plane). Every lane calls this.
+template <typename T>
+__device__ __forceinline__ void pair_sums(const T* Gp, const T* Gu, uint32_t fieldG, int o1, bool own, bool quartic,
+                                          bool nbl, bool nbr, int dl, int dr, Sums27<T>& A)
+{
+    typedef typename PK<T>::P P;
+    constexpr int NP = PK<T>::NP;
+    P c0[NP];
+#pragma unroll
+    for (int f = 0; f < 2; f++) {
+        const T* gp = Gp + f * fieldG;
+        const T* gu = Gu + f * fieldG;
+        RowV<T> p0, p1, u0, u1;
+        load_row(gp, p0, nbl, nbr, dl, dr);
+        load_row(gp + o1, p1, nbl, nbr, dl, dr);
+        load_row(gu, u0, nbl, nbr, dl, dr);
+        load_row(gu + o1, u1, nbl, nbr, dl, dr);
+        if (own) {
+            P p0r[NP], p1l[NP], p1r[NP], u0l[NP], u0r[NP], u1l[NP], u1r[NP];
+            shr(p0, p0r);
+            shl(p1, p1l);
+            shr(p1, p1r);
+            shl(u0, u0l);
+            shr(u0, u0r);
+            shl(u1, u1l);
+            shr(u1, u1r);
+            P a14 = A.w14[f], a3 = A.w3[f], a1 = A.w1[f];
+#pragma unroll
+            for (int v = 0; v < NP; v++) {
+                const P c = p0.v[v], cu = u0.v[v];
+                // site (x, y, P): in its plane (1,0,0) (0,1,0) (1,1,0) (-1,1,0); to P + 1
+                // (0,0,1) (+-1,0,1) (0,1,1) (+-1,1,1); site (x, y, P + 1): (0,1,-1) (+-1,1,-1)
+                a14 = sq_acc<T>(p0r[v], c, sq_acc<T>(p1.v[v], c, sq_acc<T>(u0.v[v], c, a14)));
+                a3 = sq_acc<T>(p1r[v], c, sq_acc<T>(p1l[v], c, sq_acc<T>(u0r[v], c, sq_acc<T>(u0l[v], c,
+                         sq_acc<T>(u1.v[v], c, sq_acc<T>(p1.v[v], cu, a3))))));
+                a1 = sq_acc<T>(u1r[v], c, sq_acc<T>(u1l[v], c, sq_acc<T>(p1r[v], cu, sq_acc<T>(p1l[v], cu, a1))));
+                if (f == 0) c0[v] = c;
+            }
+            A.w14[f] = a14;
+            A.w3[f] = a3;
+            A.w1[f] = a1;
+            if (f == 1) {
+#pragma unroll
+                for (int v = 0; v < NP; v++) {
+                    const P sq = mul2(c0[v], c0[v]);
+                    A.vd = quartic ? fma2(sq, sq, A.vd) : add2(sq, A.vd);
+                    A.vi = fma2(sq, mul2(p0.v[v], p0.v[v]), A.vi);
+                }
+            }
+        }
+    }
+}
+
+// March planes [z0, z0 + nz) of y tile yt through the ring S (the ring of the
+// 7-point kernel followed by three new-field planes).
+template <typename T>
+__device__ void march_segment27(const MarchLattice<T>& L, int yt, int z0, int nz, T* S, Sums27<T>& A, bool first)
+{
+    typedef typename PK<T>::P P;
+    constexpr int NP = PK<T>::NP;
+    constexpr int VW = 2 * NP;
+    const int n = L.n, ty = L.ty, D = L.depth, Q = n / VW;
+    const int t = threadIdx.x;
+    const int rho_raw = t / Q;
+    const bool live = rho_raw < ty + 3;
+    const int rho = min(rho_raw, ty + 2);
+    const int x = live ? (t - rho_raw * Q) * VW : 0;
+    const bool comp = live && rho >= 1 && rho <= ty + 1;   // owned rows and the look-ahead row
+    const bool own = live && rho >= 1 && rho <= ty;
+    const int dl = x == 0 ? n - 1 : -1;
+    const int dr = x + VW == n ? VW - n : VW;
+    const RingGeom R = ring_geom(n, ty, D);
+    const uint32_t offF = (uint32_t)rho * n + x;
+    const uint32_t offP = (uint32_t)(comp ? rho - 1 : 0) * n + x;
+    const int ry = comp ? n : 0;       // row step to y +- 1 (0 for threads that only stage)
+    const int o1 = own ? n : 0;
+    const uint32_t nn = (uint32_t)n * n;
+    const uint32_t rowg = (uint32_t)wrapn(yt * ty - 1 + rho, n) * n + x;
+
+    auto fetch_f = [&](int zrel, int slot) {
+        const uint32_t gi = L.plane(z0 + zrel) * nn + rowg;
+        T* d = S + (uint32_t)slot * R.slotF + offF;
+        cp_async16(d, L.f0 + gi);
+        cp_async16(d + R.fieldF, L.f1 + gi);
+    };
+    auto fetch_p = [&](int zrel, int slot) {
+        const uint32_t gi = L.plane(z0 + zrel) * nn + rowg;
+        T* d = S + R.p0 + (uint32_t)slot * R.slotP + offP;
+        cp_async16(d, L.p0 + gi);
+        cp_async16(d + R.fieldP, L.p1 + gi);
+    };
+    const int lane = t & 31;
+    const int qv = x / VW;
+    const bool nbl = qv > 0 && lane > 0, nbr = qv < Q - 1 && lane < 31;
+    auto addm = [](int a, int b, int m) { return a + b >= m ? a + b - m : a + b; };
+    T* const G0 = S + R.g0;            // three new-field planes of R.planeG elements
+
+    if (!first) __syncthreads();
+    if (live) {
+        fetch_f(-1, 0);
+        fetch_f(0, 1);
+        fetch_f(1, 2);
+        if (comp) fetch_p(0, 0);
+    }
+    cp_async_commit();
+    for (int j = 1; j < D; j++) {
+        if (live && 1 + j <= nz + 1) fetch_f(1 + j, 2 + j);
+        if (comp && j <= nz) fetch_p(j, j);
+        cp_async_commit();
+    }
+    int sf = 0, sp = 0, sg = 0;        // k mod (D+3), k mod (D+1), k mod 3
+
+    const P dtcl2 = mk2(L.dtcl, L.dtcl), dtcf2 = mk2(L.dtcf, L.dtcf);
+    const P c3 = mk2(T(3), T(3)), c14 = mk2(T(14), T(14)), c30 = mk2(T(30), T(30));
+    for (int k = 0; k <= nz; k++) {
+        const bool ahead = k == nz;
+        const int z = z0 + k;
+        cp_async_wait(D - 1);
+        __syncthreads();
+        if (live && k + 1 + D <= nz + 1) fetch_f(k + 1 + D, addm(sf, D + 2, R.rf));
+        if (comp && k + D <= nz) fetch_p(k + D, addm(sp, D, R.rp));
+        cp_async_commit();
+
+        const T* Fm = S + (uint32_t)sf * R.slotF + offF;
+        const T* Fc = S + (uint32_t)addm(sf, 1, R.rf) * R.slotF + offF;
+        const T* Fp = S + (uint32_t)addm(sf, 2, R.rf) * R.slotF + offF;
+        const T* Pc = S + R.p0 + (uint32_t)sp * R.slotP + offP;
+        sf = addm(sf, 1, R.rf);
+        sp = addm(sp, 1, R.rp);
+        T* Gw = G0 + (uint32_t)sg * R.planeG;
+        const T* Gm1 = G0 + (uint32_t)addm(sg, 2, 3) * R.planeG;   // plane k - 1
+        const T* Gm2 = G0 + (uint32_t)addm(sg, 1, 3) * R.planeG;   // plane k - 2
+        sg = addm(sg, 1, 3);
+
+        // kick and drift of rows 1 .. ty + 1 (owned and look-ahead) of plane z
+        P cen[2][NP], pn[2][NP];
+#pragma unroll
+        for (int f = 0; f < 2; f++) {
+            const uint32_t fo = f * R.fieldF;
+            P lap[NP], dsum[NP];
+            {
+                RowV<T> c, ym, yp;
+                load_row(Fc + fo, c, nbl, nbr, dl, dr);
+                load_row(Fc + fo - ry, ym, nbl, nbr, dl, dr);
+                load_row(Fc + fo + ry, yp, nbl, nbr, dl, dr);
+                P e[NP], kk[NP];
+                plane_ek(c, ym, yp, e, kk);
+#pragma unroll
+                for (int v = 0; v < NP; v++) {
+                    cen[f][v] = c.v[v];
+                    lap[v] = fma2(c14, e[v], mul2(c3, kk[v]));
+                }
+            }
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                const T* Fs = (side == 0 ? Fm : Fp) + fo;
+                RowV<T> c, ym, yp;
+                load_row(Fs, c, nbl, nbr, dl, dr);
+                load_row(Fs - ry, ym, nbl, nbr, dl, dr);
+                load_row(Fs + ry, yp, nbl, nbr, dl, dr);
+                P e[NP], kk[NP];
+                plane_ek(c, ym, yp, e, kk);
+#pragma unroll
+                for (int v = 0; v < NP; v++) {
+                    lap[v] = add2(lap[v], fma2(c3, e[v], kk[v]));
+                    const P d = sub2(c.v[v], cen[f][v]);
+                    dsum[v] = side == 0 ? d : add2(dsum[v], d);
+                }
+            }
+            P pv[NP];
+            PK<T>::ld(Pc + f * R.fieldP, pv);
+#pragma unroll
+            for (int v = 0; v < NP; v++) {
+                lap[v] = fma2(c30, dsum[v], lap[v]);
+                pn[f][v] = fma2(dtcl2, lap[v], fma2(dtcf2, cen[f][v], pv[v]));
+            }
+        }
+        if (comp) {
+            const P mdtcdom2 = mk2(L.mdtcdom, L.mdtcdom), mdtkap2 = mk2(L.mdtkap, L.mdtkap), dt2 = mk2(L.dt, L.dt);
+            P g[2][NP];
+#pragma unroll
+            for (int v = 0; v < NP; v++) {
+                const P a0 = cen[0][v], a1 = cen[1][v];
+                const P a0a1 = mul2(a0, a1);
+                const P dom = L.quartic ? mul2(mul2(a0, a0), a0) : a0;
+                pn[0][v] = fma2(mdtcdom2, dom, fma2(mdtkap2, mul2(a0a1, a1), pn[0][v]));
+                pn[1][v] = fma2(mdtkap2, mul2(a0a1, a0), pn[1][v]);
+                g[0][v] = fma2(dt2, pn[0][v], a0);
+                g[1][v] = fma2(dt2, pn[1][v], a1);
+            }
+            if (own && !ahead) {
+                const uint32_t gi = L.plane(z) * nn + rowg;
+                PK<T>::st(L.op0 + gi, pn[0]);
+                PK<T>::st(L.op1 + gi, pn[1]);
+                PK<T>::st(L.of0 + gi, g[0]);
+                PK<T>::st(L.of1 + gi, g[1]);
+            }
+            PK<T>::st(Gw + offP, g[0]);
+            PK<T>::st(Gw + R.fieldG + offP, g[1]);
+        }
+
+        // pairs of planes k - 2 and k - 1 (both written before the barrier above)
+        if (k >= 2) pair_sums(Gm2 + offP, Gm1 + offP, R.fieldG, o1, own, L.quartic, nbl, nbr, dl, dr, A);
+    }
+    // the last pair: planes nz - 1 and nz (the look-ahead plane)
+    __syncthreads();
+    {
+        const T* Gl = G0 + (uint32_t)addm(sg, 2, 3) * R.planeG;   // plane nz (sg = (nz + 1) mod 3)
+        const T* Gb = G0 + (uint32_t)addm(sg, 1, 3) * R.planeG;   // plane nz - 1
+        pair_sums(Gb + offP, Gl + offP, R.fieldG, o1, own, L.quartic, nbl, nbr, dl, dr, A);
+    }
+}
+
+struct Args27 {
+    int ty, nyt, depth;
+};
+
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) step27_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, Args27 G)
+{
+    __shared__ double red[32 * kSums];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (sc->status != LAT_OK) return;
+    T* const S = reinterpret_cast<T*>(smem_raw);
+    const int n = M.n;
+    const bool par = (sc->step & 1) != 0;
+    MarchLattice<T> L;
+    L.f0 = par ? B.f[1][0] : B.f[0][0];
+    L.f1 = par ? B.f[1][1] : B.f[0][1];
+    L.p0 = par ? B.p[1][0] : B.p[0][0];
+    L.p1 = par ? B.p[1][1] : B.p[0][1];
+    L.of0 = par ? B.f[0][0] : B.f[1][0];
+    L.of1 = par ? B.f[0][1] : B.f[1][1];
+    L.op0 = par ? B.p[0][0] : B.p[1][0];
+    L.op1 = par ? B.p[0][1] : B.p[1][1];
+    L.n = n;
+    L.ty = G.ty;
+    L.depth = G.depth;
+    // dt cL / (30 dx^2) multiplies the integer-weight neighbour sum
+    L.dt = step_coef<T>(sc, 4);
+    L.dtcl = step_coef<T>(sc, 0);
+    L.dtcf = step_coef<T>(sc, 1);
+    L.mdtcdom = step_coef<T>(sc, 2);
+    L.mdtkap = step_coef<T>(sc, 3);
+    L.quartic = M.beta == 4;
+    L.periodic = true;
+    L.zbase = 0;
+    Sums27<T> A;
+    A.zero();
+
+    // the nyt * n (y tile, z plane) units in tile-major order, an equal share per block
+    const long long U = (long long)G.nyt * n;
+    long long u = (long long)blockIdx.x * U / gridDim.x;
+    const long long uend = ((long long)blockIdx.x + 1) * U / gridDim.x;
+    for (bool first = true; u < uend; first = false) {
+        const int yt = (int)(u / n);
+        const int z0 = (int)(u - (long long)yt * n);
+        const int nz = (int)min((long long)(n - z0), uend - u);
+        u += nz;
+        march_segment27(L, yt, z0, nz, S, A, first);
+    }
+    double v[kSums];
+    A.totals(L.quartic, v);
+    finish_block(M, sc, partials, v, red, true);
+}
+
+constexpr int kMaxts27[] = {256, 512, 768, 1024};
+
+int maxt27_for(int threads)
+{
+    for (int m : kMaxts27)
+        if (threads <= m) return m;
+    return 0;
+}
+
+template <typename T>
+const void* step27_fn(int maxt)
+{
+    switch (maxt) {
+    case 256: return (const void*)step27_kernel<T, 256>;
+    case 512: return (const void*)step27_kernel<T, 512>;
+    case 768: return (const void*)step27_kernel<T, 768>;
+    default: return (const void*)step27_kernel<T, 1024>;
+    }
+}
+
+size_t smem27(int n, int esize, int ty, int depth)
+{
+    // the ring of the 7-point kernel with three new-field planes instead of two
+    return (size_t)esize * n * ((depth + 3) * 2 * (ty + 3) + (depth + 1) * 2 * (ty + 1) + 3 * 2 * (ty + 1));
+}
+
+bool geom27(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
+{
+    const int vw = 16 / esize;
+    if (n % 4 != 0 || n < 4 || ty < 1 || ty > n || n % ty != 0) return false;
+    if (depth < 1 || depth > 4) return false;
+    int threads = (ty + 3) * (n / vw);
+    threads = ((threads + 31) / 32) * 32;
+    if (threads > 1024) return false;
+    const size_t smem = smem27(n, esize, ty, depth);
+    if (smem > 227 * 1024 - 2048) return false;
+    const int maxt = maxt27_for(threads);
+    const void* fn = esize == 4 ? step27_fn<float>(maxt) : step27_fn<double>(maxt);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return false;
+    const int nyt = n / ty;
+    const long long units = (long long)nyt * n;
+    long long blocks = 0;
+    if (zr > 0) blocks = (long long)nyt * ((n + std::min(zr, n) - 1) / std::min(zr, n));
+    else blocks = std::min((long long)sms * occ, units);
+    cfg->ty = ty;
+    cfg->zr = (int)((units + blocks - 1) / blocks);
+    cfg->nzc = (int)((blocks + nyt - 1) / nyt);
+    cfg->depth = depth;
+    cfg->threads = threads;
+    cfg->maxt = maxt;
+    cfg->fast = 0;
+    cfg->smem = smem;
+    cfg->nyt = nyt;
+    cfg->blocks = (int)blocks;
+    cfg->nzl = 0;
+    cfg->zbase = 0;
+    cfg->s27 = 1;
+    return true;
+}
+
+} // namespace
+
+bool march27_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg)
+{
+    const int d = depth > 0 ? depth : 1;
+    if (ty > 0) return geom27(n, elem_bytes, ty, zr, d, cfg);
+    // default: the tallest tile whose block stays within 512 threads (registers
+    // for the 27-point arithmetic), else the tallest that fits at all
+    const int tys[] = {16, 8, 4, 2, 1};
+    const int vw = 16 / elem_bytes;
+    for (int t : tys)
+        if ((t + 3) * (n / vw) <= 512 && geom27(n, elem_bytes, t, zr, d, cfg)) return true;
+    for (int t : tys)
+        if (geom27(n, elem_bytes, t, zr, d, cfg)) return true;
+    return false;
+}
+
+template <typename T>
+cudaError_t launch_step27(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
+                          cudaStream_t st)
+{
+    Args27 G{cfg.ty, cfg.nyt, cfg.depth};
+    switch (cfg.maxt) {
+    case 256: step27_kernel<T, 256><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
+    case 512: step27_kernel<T, 512><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
+    case 768: step27_kernel<T, 768><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
+    default: step27_kernel<T, 1024><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step27<float>(const Bufs<float>&, const Model&, DevScalars*, double*, const MarchConfig&,
+                                          cudaStream_t);
+template cudaError_t launch_step27<double>(const Bufs<double>&, const Model&, DevScalars*, double*,
+                                           const MarchConfig&, cudaStream_t);
+
+} // namespace lat

@@ -16,6 +16,7 @@
 // This kernel is the portable path (FP32 and FP64, any N % 4 == 0); the TMA
 // plane-ring kernel in lat_step_tma.cu is the fast FP32/FP64 path on sm_103a.
 #include "lat_kernels.h"
+#include "lat_stencil27.cuh"
 
 namespace lat {
 
@@ -139,9 +140,11 @@ __global__ void __launch_bounds__(TX * TY) step_simple_kernel(Bufs<T> B, Model M
     finish_block(M, sc, partials, v, red, true);
 }
 
-// Sums of the current fields (no step): forward-difference gradients and the
-// potential terms, one thread per (x, y) column, for initialisation and after
-// a state upload; its last block solves the a' update for the first step.
+// Sums of the current fields (no step): the gradient averages of the configured
+// stencil (forward differences for 7 points, the 13 owned weighted bonds of
+// each site for 27) and the potential terms, one thread per (x, y) column, for
+// initialisation and after a state upload; its last block solves the a' update
+// for the first step.
 template <typename T>
 __global__ void __launch_bounds__(256) sums_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials)
 {
@@ -160,15 +163,20 @@ __global__ void __launch_bounds__(256) sums_kernel(Bufs<T> B, Model M, DevScalar
             const int zp = z == n - 1 ? 0 : z + 1;
             const size_t c = sidx(n, x, y, z);
             const double a0 = (double)f0[c], a1 = (double)f1[c];
+            const double sq = a0 * a0;
+            acc[2] += M.beta == 4 ? 0.25 * sq * sq : 0.5 * sq;
+            acc[3] += 0.5 * sq * a1 * a1;
+            if (M.stencil == 27) {
+                acc[0] += bonds27_sum(f0, n, x, y, z);
+                acc[1] += bonds27_sum(f1, n, x, y, z);
+                continue;
+            }
             const double e0 = (double)f0[sidx(n, xp, y, z)] - a0, e1 = (double)f0[sidx(n, x, yp, z)] - a0,
                          e2 = (double)f0[sidx(n, x, y, zp)] - a0;
             const double h0 = (double)f1[sidx(n, xp, y, z)] - a1, h1 = (double)f1[sidx(n, x, yp, z)] - a1,
                          h2 = (double)f1[sidx(n, x, y, zp)] - a1;
             acc[0] += e0 * e0 + e1 * e1 + e2 * e2;
             acc[1] += h0 * h0 + h1 * h1 + h2 * h2;
-            const double sq = a0 * a0;
-            acc[2] += M.beta == 4 ? 0.25 * sq * sq : 0.5 * sq;
-            acc[3] += 0.5 * sq * a1 * a1;
         }
     }
     finish_block(M, sc, partials, acc, red, false);

@@ -39,6 +39,7 @@ class LatParams(C.Structure):
         ("A", C.c_double), ("B", C.c_double), ("r", C.c_double), ("s", C.c_double),
         ("kcut", C.c_double), ("fluct", C.c_double),
         ("seed", C.c_uint64),
+        ("stencil", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -146,6 +147,7 @@ def make_params(d: dict) -> LatParams:
     p.r = float(d.get("r", 0.0)); p.s = float(d.get("s", 0.0))
     p.kcut = float(d.get("kcut", 0.0)); p.fluct = float(d.get("fluct", 1.0))
     p.seed = int(d.get("seed", 0))
+    p.stencil = int(d.get("stencil", 7))
     return p
 
 

@@ -3,6 +3,7 @@ sm_103a, loads, exports every entry point include/lattice.h declares, the
 ctypes structs match the C layout, and parameter validation (which runs before
 any CUDA call) rejects bad inputs with the documented status codes."""
 import ctypes as C
+import math
 import os
 import re
 import subprocess
@@ -36,14 +37,15 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lattice.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(lat_params), '
-                   'offsetof(lat_params, seed), offsetof(lat_params, fluct), sizeof(lat_energy_report), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lat_params), '
+                   'offsetof(lat_params, seed), offsetof(lat_params, fluct), offsetof(lat_params, stencil), '
+                   'sizeof(lat_energy_report), '
                    'offsetof(lat_energy_report, var));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [C.sizeof(lat.LatParams), lat.LatParams.seed.offset, lat.LatParams.fluct.offset,
-                    C.sizeof(lat.LatEnergyReport), lat.LatEnergyReport.var.offset]
+                    lat.LatParams.stencil.offset, C.sizeof(lat.LatEnergyReport), lat.LatEnergyReport.var.offset]
 
 
 def test_status_strings():
@@ -76,6 +78,7 @@ def _create_status(params):
     dict(phi0=(0.0, 0.0)),    # A = 1/phi0 undefined
     dict(A=1.0, B=1.0, r=1.0, s=0.0),   # violates s - 2r + 3 = 0
     dict(expansion=3),
+    dict(stencil=9),          # 7 (or 0) and 27 points only
 ])
 def test_validation_rejects_bad_parameters(bad):
     p = dict(lphi4(16), **bad)
@@ -88,6 +91,34 @@ def test_validation_rejects_unstable_time_step():
     assert _create_status(p) == 2  # LAT_ECFL
     q = m2phi2(64, g2=2.5e-5)     # heavy chi at dt = 2^-10: w dt > 2
     assert _create_status(q) == 2
+
+
+def test_stability_bound_follows_the_stencil():
+    """The leapfrog is stable while dt^2 (k_max^2 + m_eff^2) <= 4, with
+    k_max^2 = max over the Brillouin zone of -L(k): 12/dx^2 for the 7-point
+    stencil, 92/(15 dx^2) for the 27-point one (at k dx = (pi, pi, pi), where the
+    oracle's stencil gives the same value). Between the two bounds the 7-point
+    lattice is refused and the 27-point one passes the check (creation then stops
+    at the missing device on this host, with another status)."""
+    import numpy as np
+    from oracle.oracle import laplacian27
+    n = 16
+    p = lphi4(n)
+    dx = p["L"] / n
+    # k_max^2 of the oracle's stencil: the checkerboard mode at k dx = (pi, pi, pi)
+    z, y, x = np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij")
+    mode = (-1.0) ** (x + y + z)
+    kmax2 = -laplacian27(mode, dx)[0, 0, 0] / mode[0, 0, 0]
+    assert abs(kmax2 * dx * dx - 92 / 15) < 1e-12
+    p["g2"] = 0.0   # no chi mass: m_eff^2 = 3 (cdom0 = 1, A phi0 = 1 in the default rescaling)
+    meff2 = 3.0
+    between = 2.0 / math.sqrt(0.5 * (12.0 / dx ** 2 + 92 / 15 / dx ** 2) + meff2)
+    p7 = dict(p, dt=between, stencil=7)
+    p27 = dict(p, dt=between, stencil=27)
+    assert _create_status(p7) == 2
+    assert _create_status(p27) != 2
+    above = 2.0 / math.sqrt(92 / 15 / dx ** 2 + meff2) * 1.01
+    assert _create_status(dict(p, dt=above, stencil=27)) == 2
 
 
 def test_null_arguments():
