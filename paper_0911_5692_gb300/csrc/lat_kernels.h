@@ -43,6 +43,7 @@ struct MarchConfig {
     int nzl = 0;   // z-slab: owned planes (0: a whole periodic lattice)
     int zbase = 0; // z-slab: stored plane of z = z + zbase
     int s27 = 0;   // 1: the 27-point Laplacian kernel (lat_step27.cu)
+    int nxt = 1;   // 27-point kernel: x tiles per row
 };
 // kernel specialised for (element bytes, N, ty, depth), or null; *smem gets its
 // dynamic shared memory in bytes

@@ -134,24 +134,34 @@ __device__ __forceinline__ typename PK<T>::P sq_acc(typename PK<T>::P a, typenam
 }
 
 // Pairs of new-field plane P (Gp) with plane P + 1 (Gu) at this thread's own
-// row: rows j, j + 1 (o1 = n for own rows, 0 otherwise so that other threads
-// stay inside the plane). Every lane calls this.
+// row: rows j, j + 1 (o1 = the row stride for the owned rows, 0 for the others
+// so that they stay inside the plane). Rows j, j + 1 of plane P are those of the previous
+// call's plane P + 1 when `carried` (kept in c0r, c1r); this call leaves its
+// plane P + 1 rows there. Every lane calls this.
 template <typename T>
 __device__ __forceinline__ void pair_sums(const T* Gp, const T* Gu, uint32_t fieldG, int o1, bool own, bool quartic,
-                                          bool nbl, bool nbr, int dl, int dr, Sums27<T>& A)
+                                          bool nbl, bool nbr, int dl, int dr, bool carried, RowV<T> (&c0r)[2],
+                                          RowV<T> (&c1r)[2], Sums27<T>& A)
 {
     typedef typename PK<T>::P P;
     constexpr int NP = PK<T>::NP;
     P c0[NP];
 #pragma unroll
     for (int f = 0; f < 2; f++) {
-        const T* gp = Gp + f * fieldG;
         const T* gu = Gu + f * fieldG;
         RowV<T> p0, p1, u0, u1;
-        load_row(gp, p0, nbl, nbr, dl, dr);
-        load_row(gp + o1, p1, nbl, nbr, dl, dr);
+        if (carried) {
+            p0 = c0r[f];
+            p1 = c1r[f];
+        } else {
+            const T* gp = Gp + f * fieldG;
+            load_row(gp, p0, nbl, nbr, dl, dr);
+            load_row(gp + o1, p1, nbl, nbr, dl, dr);
+        }
         load_row(gu, u0, nbl, nbr, dl, dr);
         load_row(gu + o1, u1, nbl, nbr, dl, dr);
+        c0r[f] = u0;
+        c1r[f] = u1;
         if (own) {
             P p0r[NP], p1l[NP], p1r[NP], u0l[NP], u0r[NP], u1l[NP], u1r[NP];
             shr(p0, p0r);
@@ -188,31 +198,72 @@ __device__ __forceinline__ void pair_sums(const T* Gp, const T* Gu, uint32_t fie
     }
 }
 
-// March planes [z0, z0 + nz) of y tile yt through the ring S (the ring of the
-// 7-point kernel followed by three new-field planes).
+// Plane aggregates at this thread's sites: centre C, q = 3 e + k (the plane's
+// part when it is the plane below or above) and r = 14 e + 3 k (its part when it
+// is the centre plane). F points at this thread's vector of the plane; ry is
+// the row step (0 for threads that only stage). Every lane calls this.
 template <typename T>
-__device__ void march_segment27(const MarchLattice<T>& L, int yt, int z0, int nz, T* S, Sums27<T>& A, bool first)
+__device__ __forceinline__ void plane_aggr(const T* F, int ry, bool nbl, bool nbr, int dl, int dr,
+                                           typename PK<T>::P (&C)[PK<T>::NP], typename PK<T>::P (&q)[PK<T>::NP],
+                                           typename PK<T>::P (&r)[PK<T>::NP])
+{
+    typedef typename PK<T>::P P;
+    constexpr int NP = PK<T>::NP;
+    RowV<T> c, ym, yp;
+    load_row(F, c, nbl, nbr, dl, dr);
+    load_row(F - ry, ym, nbl, nbr, dl, dr);
+    load_row(F + ry, yp, nbl, nbr, dl, dr);
+    P e[NP], k[NP];
+    plane_ek(c, ym, yp, e, k);
+    const P c3 = mk2(T(3), T(3)), c14 = mk2(T(14), T(14));
+#pragma unroll
+    for (int v = 0; v < NP; v++) {
+        C[v] = c.v[v];
+        q[v] = fma2(c3, e[v], k[v]);
+        r[v] = fma2(c14, e[v], mul2(c3, k[v]));
+    }
+}
+
+// March planes [z0, z0 + nz) of tile (xt, yt) through the ring S (the ring of
+// the 7-point kernel followed by three new-field planes). A tile is W columns
+// (x0 = xt W) by ty rows. Each shared-memory row holds the tile's W columns with
+// one 16-byte vector on either side (the columns just left of x0 and just right
+// of x0 + W, periodic in x): the threads of those halo vectors stage them and
+// also kick and drift them, so that the new fields one column beyond the tile
+// are at hand for the pairs of the sums; only the tile's own sites are stored.
+template <typename T>
+__device__ void march_segment27(const MarchLattice<T>& L, int xt, int W, int yt, int z0, int nz, T* S, Sums27<T>& A,
+                                bool first)
 {
     typedef typename PK<T>::P P;
     constexpr int NP = PK<T>::NP;
     constexpr int VW = 2 * NP;
-    const int n = L.n, ty = L.ty, D = L.depth, Q = n / VW;
+    const int n = L.n, ty = L.ty, D = L.depth;
+    const int Qh = W / VW + 2;                             // vectors per staged row
+    const int RW = W + 2 * VW;                             // elements per staged row
     const int t = threadIdx.x;
-    const int rho_raw = t / Q;
-    const bool live = rho_raw < ty + 3;
+    const int rho_raw = t / Qh;
+    const bool live = rho_raw < ty + 3;                    // threads past the tile only join the barriers
     const int rho = min(rho_raw, ty + 2);
-    const int x = live ? (t - rho_raw * Q) * VW : 0;
-    const bool comp = live && rho >= 1 && rho <= ty + 1;   // owned rows and the look-ahead row
-    const bool own = live && rho >= 1 && rho <= ty;
-    const int dl = x == 0 ? n - 1 : -1;
-    const int dr = x + VW == n ? VW - n : VW;
-    const RingGeom R = ring_geom(n, ty, D);
-    const uint32_t offF = (uint32_t)rho * n + x;
-    const uint32_t offP = (uint32_t)(comp ? rho - 1 : 0) * n + x;
-    const int ry = comp ? n : 0;       // row step to y +- 1 (0 for threads that only stage)
-    const int o1 = own ? n : 0;
+    const int xi = live ? t - rho_raw * Qh : 0;            // vector within the staged row
+    const int xs = xi * VW;
+    const bool comp = live && rho >= 1 && rho <= ty + 1;   // owned rows and the look-ahead row, halo vectors included
+    const bool ownrow = comp && rho <= ty;
+    const bool own = ownrow && xi >= 1 && xi <= Qh - 2;
+    // x neighbours: adjacent vectors of the staged row (contiguous); the outer
+    // neighbours of the halo vectors are not staged and not needed (read in place)
+    const int dl = xi > 0 ? -1 : 0;
+    const int dr = xi < Qh - 1 ? VW : 0;
+    const RingGeom R = ring_geom(RW, ty, D);
+    const uint32_t offF = (uint32_t)rho * RW + xs;
+    const uint32_t offP = (uint32_t)(comp ? rho - 1 : 0) * RW + xs;
+    const int ry = comp ? RW : 0;      // row step to y +- 1 (0 for threads that only stage)
+    // row step to j + 1 in the sums: the same for every vector of a row (the halo
+    // vectors of an owned row feed their neighbours' shuffles)
+    const int o1 = ownrow ? RW : 0;
     const uint32_t nn = (uint32_t)n * n;
-    const uint32_t rowg = (uint32_t)wrapn(yt * ty - 1 + rho, n) * n + x;
+    const int gx = wrapn(xt * W - VW + xs, n);
+    const uint32_t rowg = (uint32_t)wrapn(yt * ty - 1 + rho, n) * n + gx;
 
     auto fetch_f = [&](int zrel, int slot) {
         const uint32_t gi = L.plane(z0 + zrel) * nn + rowg;
@@ -227,8 +278,7 @@ __device__ void march_segment27(const MarchLattice<T>& L, int yt, int z0, int nz
         cp_async16(d + R.fieldP, L.p1 + gi);
     };
     const int lane = t & 31;
-    const int qv = x / VW;
-    const bool nbl = qv > 0 && lane > 0, nbr = qv < Q - 1 && lane < 31;
+    const bool nbl = xi > 0 && lane > 0, nbr = xi < Qh - 1 && lane < 31;
     auto addm = [](int a, int b, int m) { return a + b >= m ? a + b - m : a + b; };
     T* const G0 = S + R.g0;            // three new-field planes of R.planeG elements
 
@@ -248,7 +298,9 @@ __device__ void march_segment27(const MarchLattice<T>& L, int yt, int z0, int nz
     int sf = 0, sp = 0, sg = 0;        // k mod (D+3), k mod (D+1), k mod 3
 
     const P dtcl2 = mk2(L.dtcl, L.dtcl), dtcf2 = mk2(L.dtcf, L.dtcf);
-    const P c3 = mk2(T(3), T(3)), c14 = mk2(T(14), T(14)), c30 = mk2(T(30), T(30));
+    const P c30 = mk2(T(30), T(30));
+    P Cm[2][NP], qm[2][NP], Cc[2][NP], qc[2][NP], rc[2][NP];   // aggregates of planes z - 1 and z
+    RowV<T> gr0[2], gr1[2];   // rows j, j + 1 of the newest new-field plane summed so far
     for (int k = 0; k <= nz; k++) {
         const bool ahead = k == nz;
         const int z = z0 + k;
@@ -269,47 +321,33 @@ __device__ void march_segment27(const MarchLattice<T>& L, int yt, int z0, int nz
         const T* Gm2 = G0 + (uint32_t)addm(sg, 1, 3) * R.planeG;   // plane k - 2
         sg = addm(sg, 1, 3);
 
-        // kick and drift of rows 1 .. ty + 1 (owned and look-ahead) of plane z
-        P cen[2][NP], pn[2][NP];
+        // kick and drift of rows 1 .. ty + 1 (owned and look-ahead) of plane z:
+        // the aggregates of planes z - 1 and z come from the two previous planes
+        // (computed here for the first plane of the run), those of z + 1 are new
+        P pn[2][NP];
+        if (k == 0) {
+#pragma unroll
+            for (int f = 0; f < 2; f++) {
+                P rdummy[NP];
+                plane_aggr<T>(Fm + f * R.fieldF, ry, nbl, nbr, dl, dr, Cm[f], qm[f], rdummy);
+                plane_aggr<T>(Fc + f * R.fieldF, ry, nbl, nbr, dl, dr, Cc[f], qc[f], rc[f]);
+            }
+        }
 #pragma unroll
         for (int f = 0; f < 2; f++) {
-            const uint32_t fo = f * R.fieldF;
-            P lap[NP], dsum[NP];
-            {
-                RowV<T> c, ym, yp;
-                load_row(Fc + fo, c, nbl, nbr, dl, dr);
-                load_row(Fc + fo - ry, ym, nbl, nbr, dl, dr);
-                load_row(Fc + fo + ry, yp, nbl, nbr, dl, dr);
-                P e[NP], kk[NP];
-                plane_ek(c, ym, yp, e, kk);
-#pragma unroll
-                for (int v = 0; v < NP; v++) {
-                    cen[f][v] = c.v[v];
-                    lap[v] = fma2(c14, e[v], mul2(c3, kk[v]));
-                }
-            }
-#pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const T* Fs = (side == 0 ? Fm : Fp) + fo;
-                RowV<T> c, ym, yp;
-                load_row(Fs, c, nbl, nbr, dl, dr);
-                load_row(Fs - ry, ym, nbl, nbr, dl, dr);
-                load_row(Fs + ry, yp, nbl, nbr, dl, dr);
-                P e[NP], kk[NP];
-                plane_ek(c, ym, yp, e, kk);
-#pragma unroll
-                for (int v = 0; v < NP; v++) {
-                    lap[v] = add2(lap[v], fma2(c3, e[v], kk[v]));
-                    const P d = sub2(c.v[v], cen[f][v]);
-                    dsum[v] = side == 0 ? d : add2(dsum[v], d);
-                }
-            }
-            P pv[NP];
+            P Cp[NP], qp[NP], rp[NP], pv[NP];
+            plane_aggr<T>(Fp + f * R.fieldF, ry, nbl, nbr, dl, dr, Cp, qp, rp);
             PK<T>::ld(Pc + f * R.fieldP, pv);
 #pragma unroll
             for (int v = 0; v < NP; v++) {
-                lap[v] = fma2(c30, dsum[v], lap[v]);
-                pn[f][v] = fma2(dtcl2, lap[v], fma2(dtcf2, cen[f][v], pv[v]));
+                const P c = Cc[f][v];
+                const P lap = fma2(c30, add2(sub2(Cm[f][v], c), sub2(Cp[v], c)), add2(rc[f][v], add2(qm[f][v], qp[v])));
+                pn[f][v] = fma2(dtcl2, lap, fma2(dtcf2, c, pv[v]));
+                Cm[f][v] = c;
+                qm[f][v] = qc[f][v];
+                Cc[f][v] = Cp[v];
+                qc[f][v] = qp[v];
+                rc[f][v] = rp[v];
             }
         }
         if (comp) {
@@ -317,7 +355,7 @@ __device__ void march_segment27(const MarchLattice<T>& L, int yt, int z0, int nz
             P g[2][NP];
 #pragma unroll
             for (int v = 0; v < NP; v++) {
-                const P a0 = cen[0][v], a1 = cen[1][v];
+                const P a0 = Cm[0][v], a1 = Cm[1][v];   // plane z (shifted down above)
                 const P a0a1 = mul2(a0, a1);
                 const P dom = L.quartic ? mul2(mul2(a0, a0), a0) : a0;
                 pn[0][v] = fma2(mdtcdom2, dom, fma2(mdtkap2, mul2(a0a1, a1), pn[0][v]));
@@ -337,19 +375,21 @@ __device__ void march_segment27(const MarchLattice<T>& L, int yt, int z0, int nz
         }
 
         // pairs of planes k - 2 and k - 1 (both written before the barrier above)
-        if (k >= 2) pair_sums(Gm2 + offP, Gm1 + offP, R.fieldG, o1, own, L.quartic, nbl, nbr, dl, dr, A);
+        if (k >= 2)
+            pair_sums(Gm2 + offP, Gm1 + offP, R.fieldG, o1, own, L.quartic, nbl, nbr, dl, dr, false, gr0, gr1, A);
     }
     // the last pair: planes nz - 1 and nz (the look-ahead plane)
     __syncthreads();
     {
         const T* Gl = G0 + (uint32_t)addm(sg, 2, 3) * R.planeG;   // plane nz (sg = (nz + 1) mod 3)
         const T* Gb = G0 + (uint32_t)addm(sg, 1, 3) * R.planeG;   // plane nz - 1
-        pair_sums(Gb + offP, Gl + offP, R.fieldG, o1, own, L.quartic, nbl, nbr, dl, dr, A);
+        pair_sums(Gb + offP, Gl + offP, R.fieldG, o1, own, L.quartic, nbl, nbr, dl, dr, false, gr0, gr1, A);
     }
 }
 
 struct Args27 {
     int ty, nyt, depth;
+    int nxt, W;     // x tiles per row and their width
 };
 
 template <typename T, int MAXT>
@@ -385,16 +425,17 @@ __global__ void __launch_bounds__(MAXT, 1) step27_kernel(Bufs<T> B, Model M, Dev
     Sums27<T> A;
     A.zero();
 
-    // the nyt * n (y tile, z plane) units in tile-major order, an equal share per block
-    const long long U = (long long)G.nyt * n;
+    // the nyt * nxt * n (tile, z plane) units in tile-major order (x tiles of a
+    // y tile adjacent), an equal share per block
+    const long long U = (long long)G.nyt * G.nxt * n;
     long long u = (long long)blockIdx.x * U / gridDim.x;
     const long long uend = ((long long)blockIdx.x + 1) * U / gridDim.x;
     for (bool first = true; u < uend; first = false) {
-        const int yt = (int)(u / n);
-        const int z0 = (int)(u - (long long)yt * n);
+        const int tile = (int)(u / n);
+        const int z0 = (int)(u - (long long)tile * n);
         const int nz = (int)min((long long)(n - z0), uend - u);
         u += nz;
-        march_segment27(L, yt, z0, nz, S, A, first);
+        march_segment27(L, tile % G.nxt, G.W, tile / G.nxt, z0, nz, S, A, first);
     }
     double v[kSums];
     A.totals(L.quartic, v);
@@ -421,10 +462,21 @@ const void* step27_fn(int maxt)
     }
 }
 
-size_t smem27(int n, int esize, int ty, int depth)
+size_t smem27(int rw, int esize, int ty, int depth)
 {
-    // the ring of the 7-point kernel with three new-field planes instead of two
-    return (size_t)esize * n * ((depth + 3) * 2 * (ty + 3) + (depth + 1) * 2 * (ty + 1) + 3 * 2 * (ty + 1));
+    // the ring of the 7-point kernel over rows of rw elements, with three
+    // new-field planes instead of two
+    return (size_t)esize * rw * ((depth + 3) * 2 * (ty + 3) + (depth + 1) * 2 * (ty + 1) + 3 * 2 * (ty + 1));
+}
+
+// x tiles per row: the fewest that keep a tile at most 64 vectors wide, among
+// those that divide the row into whole vectors
+int nxt_for(int n, int vw)
+{
+    const int q = n / vw;
+    for (int nxt = (q + 63) / 64; nxt <= q; nxt++)
+        if (q % nxt == 0) return nxt;
+    return q;
 }
 
 bool geom27(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
@@ -432,10 +484,12 @@ bool geom27(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     const int vw = 16 / esize;
     if (n % 4 != 0 || n < 4 || ty < 1 || ty > n || n % ty != 0) return false;
     if (depth < 1 || depth > 4) return false;
-    int threads = (ty + 3) * (n / vw);
+    const int nxt = nxt_for(n, vw);
+    const int W = n / nxt;
+    int threads = (ty + 3) * (W / vw + 2);
     threads = ((threads + 31) / 32) * 32;
     if (threads > 1024) return false;
-    const size_t smem = smem27(n, esize, ty, depth);
+    const size_t smem = smem27(W + 2 * vw, esize, ty, depth);
     if (smem > 227 * 1024 - 2048) return false;
     const int maxt = maxt27_for(threads);
     const void* fn = esize == 4 ? step27_fn<float>(maxt) : step27_fn<double>(maxt);
@@ -446,13 +500,14 @@ bool geom27(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return false;
     const int nyt = n / ty;
-    const long long units = (long long)nyt * n;
+    const long long tiles = (long long)nyt * nxt;
+    const long long units = tiles * n;
     long long blocks = 0;
-    if (zr > 0) blocks = (long long)nyt * ((n + std::min(zr, n) - 1) / std::min(zr, n));
+    if (zr > 0) blocks = tiles * ((n + std::min(zr, n) - 1) / std::min(zr, n));
     else blocks = std::min((long long)sms * occ, units);
     cfg->ty = ty;
     cfg->zr = (int)((units + blocks - 1) / blocks);
-    cfg->nzc = (int)((blocks + nyt - 1) / nyt);
+    cfg->nzc = (int)((blocks + tiles - 1) / tiles);
     cfg->depth = depth;
     cfg->threads = threads;
     cfg->maxt = maxt;
@@ -463,6 +518,7 @@ bool geom27(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     cfg->nzl = 0;
     cfg->zbase = 0;
     cfg->s27 = 1;
+    cfg->nxt = nxt;
     return true;
 }
 
@@ -476,8 +532,9 @@ bool march27_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfi
     // for the 27-point arithmetic), else the tallest that fits at all
     const int tys[] = {16, 8, 4, 2, 1};
     const int vw = 16 / elem_bytes;
+    const int qh = n / nxt_for(n, vw) / vw + 2;
     for (int t : tys)
-        if ((t + 3) * (n / vw) <= 512 && geom27(n, elem_bytes, t, zr, d, cfg)) return true;
+        if ((t + 3) * qh <= 512 && geom27(n, elem_bytes, t, zr, d, cfg)) return true;
     for (int t : tys)
         if (geom27(n, elem_bytes, t, zr, d, cfg)) return true;
     return false;
@@ -487,7 +544,7 @@ template <typename T>
 cudaError_t launch_step27(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
                           cudaStream_t st)
 {
-    Args27 G{cfg.ty, cfg.nyt, cfg.depth};
+    Args27 G{cfg.ty, cfg.nyt, cfg.depth, cfg.nxt, M.n / cfg.nxt};
     switch (cfg.maxt) {
     case 256: step27_kernel<T, 256><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;
     case 512: step27_kernel<T, 512><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G); break;

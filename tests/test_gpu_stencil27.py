@@ -108,6 +108,20 @@ def test_geometries_27(prec, ty, zr, depth):
     _check_scalars(g, o, prec, 10)
 
 
+@pytest.mark.parametrize("prec,n", [(64, 136), (64, 200), (32, 260), (32, 264)])
+def test_x_tiles_27(prec, n):
+    """Rows wider than 64 vectors are split into x tiles with a halo vector on
+    either side (2 tiles of 68 and 100 columns in FP64, 5 of 52 and 2 of 132 in
+    FP32): three steps against the oracle."""
+    p = _params("lphi4", n, prec)
+    st = _state("lphi4", n, prec, seed=n)
+    g, o = paired(p, st, (0.0, 1.1, 0.45, 0))
+    g.evolve(3)
+    o.step(3)
+    compare_states(g, o, 3 * TOL[prec], f"27-point x tiles N={n} fp{prec}")
+    _check_scalars(g, o, prec, 3)
+
+
 def test_fp64_run_from_init_27():
     """Both sides initialise from seed 7 with their own Philox / FFT pipelines and
     the 27-point dispersion, then evolve 300 steps (FP64)."""
