@@ -45,6 +45,11 @@
  *                      f = A a^r phi, f' = (A/B) a^(r-s) phidot + r (a'/a) f, then
  *                      fields advanced by dt/2.
  *   energy, pressure   Sec. II.B, eq. rho-pres; residual curvature and w of Sec. III.
+ *                      Per site (the paper's second kernel, Sec. II.C): the same
+ *                      terms at each site, the gradient energy of a site being half
+ *                      the weighted squared differences to all its stencil
+ *                      neighbours (each neighbour pair shared evenly by its two
+ *                      sites), so that the volume means are the averages above.
  *   spectrum           Sec. IV (named as future work): shell-binned |f_k|^2.
  *
  * Counter-based random numbers: Philox-4x32-10 (J. Salmon, M. Moraes, R. Dror,
@@ -660,6 +665,66 @@ int orc_init_fields(orc_lattice *L)
  *   p   = conv [ sum_i (1/2 (f_i' - r h f_i)^2 - 1/6 a^(-2s-2) |grad f_i|^2) - V_pr ]
  * with conv = (B^2/A^2) a^(2s-2r). H = B a^s h; K/(a^2H^2) = 8piG<rho>/(3H^2) - 1.
  * out: t, a, a', H, rho, p, w, curv, kin0, kin1, grad0, grad1, pot, mean0, mean1, var0, var1 */
+/* Gradient energy density of one site: half of sum over the stencil's
+ * neighbours b of w_b (f(x+b) - f(x))^2 / dx^2 (7-point: the six face
+ * neighbours with weight 1; 27-point: the 26 neighbours with the weights of
+ * ORC_W27). Its volume mean is -<f L f>. */
+static double site_grad2(const orc_lattice *L, const double *f, int x, int y, int z)
+{
+    int n = L->n;
+    double c = f[idx(n, x, y, z)], acc = 0.0;
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int ddx = -1; ddx <= 1; ddx++) {
+                int cls = abs(dz) + abs(dy) + abs(ddx);
+                if (cls == 0 || (!is27(L) && cls != 1)) continue;
+                double w = is27(L) ? ORC_W27[cls] : 1.0;
+                double d = f[idx(n, wrap(x + ddx, n), wrap(y + dy, n), wrap(z + dz, n))] - c;
+                acc += w * d * d;
+            }
+    return 0.5 * acc / (L->dx * L->dx);
+}
+
+/* Energy density and pressure at every site (eq. rho-pres per site, physical
+ * units as in orc_energies): rho = conv (sum_i [kin_i + grad_i] + V),
+ * p = conv (sum_i [kin_i - grad_i / 3] - V), with kin_i = (pibar_i - r h f_i)^2 / 2
+ * (pibar the momentum at the field time), grad_i = a^(-2s-2) site_grad2 / 2 and
+ * V = V_pr. */
+int orc_energy_field(orc_lattice *L, double *rho_out, double *p_out)
+{
+    double cL = 1.0, cF = 0.0, ad_next = 0.0, ad_half = 0.0, add = 0.0;
+    if (L->p.expansion) {
+        int st = orc_scale_update(L, &ad_next, &ad_half, &add);
+        if (st != ORC_OK) return st;
+        field_coefficients(L, L->a, ad_half, add, &cL, &cF);
+    }
+    double *F0 = (double *)malloc(L->nsites * sizeof(double)), *F1 = (double *)malloc(L->nsites * sizeof(double));
+    if (!F0 || !F1) { free(F0); free(F1); return ORC_ENOMEM; }
+    accelerations(L, cL, cF, F0, F1);
+    int n = L->n;
+    double a = L->a, h = L->p.expansion ? ad_half / a : 0.0, dt = L->p.dt;
+    double cg = pow(a, -2.0 * L->s - 2.0);
+    double conv = L->B * L->B / (L->A * L->A) * pow(a, 2.0 * L->s - 2.0 * L->r);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < n; z++)
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                size_t k = idx(n, x, y, z);
+                double kin = 0.0, grad = 0.0;
+                for (int i = 0; i < 2; i++) {
+                    const double *F = i == 0 ? F0 : F1;
+                    double v = L->pi[i][k] + 0.5 * dt * F[k] - L->r * h * L->f[i][k];
+                    kin += 0.5 * v * v;
+                    grad += 0.5 * cg * site_grad2(L, L->f[i], x, y, z);
+                }
+                double V = Vpr(L, a, L->f[0][k], L->f[1][k]);
+                rho_out[k] = conv * (kin + grad + V);
+                p_out[k] = conv * (kin - grad / 3.0 - V);
+            }
+    free(F0); free(F1);
+    return ORC_OK;
+}
+
 int orc_energies(orc_lattice *L, double out[17])
 {
     double cL = 1.0, cF = 0.0, ad_next = 0.0, ad_half = 0.0, add = 0.0;

@@ -76,6 +76,7 @@ def lib():
             L.orc_step.argtypes = [P, C.c_int64]
             L.orc_init_fields.argtypes = [P]
             L.orc_energies.argtypes = [P, dp]
+            L.orc_energy_field.argtypes = [P, dp, dp]
             L.orc_spectrum.argtypes = [P, C.c_int, C.c_int, dp, dp, C.POINTER(C.c_int64)]
             L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
             L.orc_normal.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
@@ -192,6 +193,16 @@ class Oracle:
         out = (C.c_double * 17)()
         _check(self._L.orc_energies(self._h, out), "orc_energies")
         return dict(zip(self.ENERGY_KEYS, list(out)))
+
+    def energy_field(self):
+        """Energy density and pressure at every site (eq. rho-pres per site), as
+        two (n, n, n) arrays [z][y][x] in the units of energies()."""
+        n3 = self.n ** 3
+        rho = np.zeros(n3)
+        pres = np.zeros(n3)
+        _check(self._L.orc_energy_field(self._h, _dp(rho), _dp(pres)), "orc_energy_field")
+        shp = (self.n,) * 3
+        return rho.reshape(shp), pres.reshape(shp)
 
     def set_g2(self, g2: float):
         """Change the coupling g^2 (kappa0 follows); the state is kept."""
