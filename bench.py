@@ -41,7 +41,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="m2phi2_256_fp32")
-    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 plain loads, 2 TMA")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="step kernel: 0 auto, 1 plain loads, 2 plane ring (cp.async), 3 plane ring (TMA)")
+    ap.add_argument("--stencil", type=int, choices=[7, 27], default=7,
+                    help="Laplacian: 7-point, or the paper's 27-point stencil (Sec. II.C)")
     ap.add_argument("--ty", type=int, default=0)
     ap.add_argument("--zr", type=int, default=0)
     ap.add_argument("--depth", type=int, default=0)
@@ -68,23 +71,27 @@ def config_of(name, p, world):
     n = p["n"]
     esize = 4 if p["precision"] == 32 else 8
     state = 8 * n ** 3 * esize
-    return {"workload": name, "model": model_name(p), "n": n, "sites": n ** 3, "precision": p["precision"],
+    return {"workload": name, "model": model_name(p), "stencil": int(p.get("stencil", 7)), "n": n, "sites": n ** 3,
+            "precision": p["precision"],
             "expansion": bool(p["expansion"]), "global_batch": world, "lattices_per_gpu": 1,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": f"inputs larger than L2: {state / 2 / 1e6:.0f} MB read + {state / 2 / 1e6:.0f} MB written per step"
                   if state / 2 > L2_BYTES else "state fits in L2"}
 
 
-STEP_KERNEL_SOURCES = ("lat_step_fast.cu", "lat_step_march.cu", "lat_march.cuh", "lat_common.cuh", "lat_pairs.cuh",
-                       "lat_async.cuh", "lat_kernels.h")
+STEP_KERNEL_SOURCES = {
+    7: ("lat_step_fast.cu", "lat_step_march.cu", "lat_march.cuh", "lat_common.cuh", "lat_pairs.cuh", "lat_async.cuh",
+        "lat_kernels.h"),
+    27: ("lat_step27.cu", "lat_march.cuh", "lat_common.cuh", "lat_pairs.cuh", "lat_async.cuh", "lat_kernels.h"),
+}
 
 
-def kernel_source_hash():
-    """Hash of the sources the fused step kernels are built from (a recorded
-    DRAM-traffic figure is valid only for these exact sources)."""
+def kernel_source_hash(stencil=7):
+    """Hash of the sources the fused step kernels of a stencil are built from (a
+    recorded DRAM-traffic figure is valid only for these exact sources)."""
     d = os.path.join(ROOT, "paper_0911_5692_gb300", "csrc")
     h = hashlib.sha256()
-    for f in STEP_KERNEL_SOURCES:
+    for f in STEP_KERNEL_SOURCES[stencil]:
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
@@ -97,7 +104,7 @@ def measured_peaks():
         return None
 
 
-def traffic_record(name, variant):
+def traffic_record(name, variant, stencil=7):
     """DRAM bytes per launch of the step kernel from a committed ncu summary, if it
     was taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "step_traffic.json")
@@ -105,9 +112,10 @@ def traffic_record(name, variant):
         recs = json.load(open(path))
     except Exception:
         return None
-    hsh = kernel_source_hash()
+    hsh = kernel_source_hash(stencil)
     for r in recs.get("records", []):
-        if r.get("kernel_hash") == hsh and r.get("workload") == name and r.get("variant") == variant:
+        if (r.get("kernel_hash") == hsh and r.get("workload") == name and r.get("variant") == variant
+                and r.get("stencil", 7) == stencil):
             return r.get("dram_bytes_per_launch")
     return None
 
@@ -256,6 +264,96 @@ def measure_ensemble(local, steps=200):
                        "launches_per_evolve": info["launches"]}}
 
 
+def measure_stencil27(local, names=("m2phi2_256_fp32", "lphi4_512_fp32"), steps=100):
+    """The step with the paper's 27-point Laplacian (Sec. II.C) on the same
+    workloads; m2phi2 at 256^3 in FP32 is the configuration of the paper's own
+    timing (0.022 s per step on a GTX 260)."""
+    import torch
+    from paper_0911_5692_gb300 import Lattice
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and peaks.get("hbm_gbs") else FALLBACK_HBM_GBS
+    out = []
+    for name in names:
+        p = dict(workload(name), stencil=27)
+        n = p["n"]
+        lat = Lattice(p, device=local)
+        lat.init_fields()
+        lat.evolve(10)
+        lat.sync()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(lat.stream)
+        lat.evolve(steps)
+        e.record(lat.stream)
+        lat.sync()
+        ms = s.elapsed_time(e) / steps
+        info = lat.kernel_info()
+        su = n ** 3 / (ms / 1e3)
+        rec = {"workload": name, "stencil": 27, "steps": steps, "ms_per_step": ms, "value": su, "unit": UNIT,
+               "hbm_frac": su * 32 / 1e9 / peak,
+               "launch": {"blocks": info["blocks"], "threads": info["threads"], "ty": info["ty"],
+                          "smem": info["smem"]}}
+        if name == "m2phi2_256_fp32":
+            rec["paper_s_per_step"] = 0.022
+            rec["vs_paper"] = 0.022 / (ms / 1e3)
+        out.append(rec)
+        lat.close()
+    return out
+
+
+def measure_diagnostics(local, name, every=512, steps=2048):
+    """Cost of the periodic diagnostics on the benchmark workload: 2048 steps with
+    the per-site energy density and pressure (lat_energy_field) taken every 512
+    steps, the interval of the paper's runs, against 2048 plain steps (CUDA
+    events on the lattice's stream); and one call each of the field, the volume
+    averages (lat_energies) and the binned spectrum (lat_spectrum)."""
+    import time
+    import torch
+    from paper_0911_5692_gb300 import Lattice
+    p = workload(name)
+    n = p["n"]
+    lat = Lattice(p, device=local)
+    lat.init_fields()
+    rho = torch.empty((n, n, n), dtype=lat.dtype, device=lat.device)
+    pres = torch.empty_like(rho)
+    lat.evolve(64)
+    lat.energy_field(rho, pres)
+    lat.sync()
+
+    def timed(with_field):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(lat.stream)
+        for _ in range(steps // every):
+            lat.evolve(every)
+            if with_field:
+                lat.energy_field(rho, pres)
+        e.record(lat.stream)
+        lat.sync()
+        return s.elapsed_time(e)
+
+    plain = min(timed(False) for _ in range(2))
+    withf = min(timed(True) for _ in range(2))
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(lat.stream)
+    for _ in range(5):
+        lat.energy_field(rho, pres)
+    e.record(lat.stream)
+    lat.sync()
+    field_ms = s.elapsed_time(e) / 5
+    t0 = time.perf_counter()
+    lat.energies()
+    energies_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    lat.spectrum(0, n // 2)
+    spectrum_ms = (time.perf_counter() - t0) * 1e3
+    lat.close()
+    return {"workload": name, "every": every, "steps": steps, "ms_plain": plain, "ms_with_energy_field": withf,
+            "overhead": withf / plain - 1.0, "energy_field_ms": field_ms,
+            "energies_ms_wall": energies_ms, "spectrum_ms_wall": spectrum_ms}
+
+
 def measure_fp32_error(local, name, steps=200):
     """FP32 against FP64 on the GPU for the benchmark workload: both precisions
     from the same initial state (FP64 initialisation rounded to FP32), `steps`
@@ -296,7 +394,7 @@ def run_reference(args):
     import numpy as np
     from oracle.oracle import Oracle
     from paper_0911_5692_gb300.workloads import random_state
-    p = workload(args.workload)
+    p = dict(workload(args.workload), stencil=args.stencil)
     n_full = p["n"]
     # per-site cost from a short calibration, then the sample lattice that keeps
     # the whole (warmup + steps) run near 90 s
@@ -345,7 +443,7 @@ def run_ours(args):
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    p = workload(args.workload)
+    p = dict(workload(args.workload), stencil=args.stencil)
     p["seed"] = p.get("seed", 0) + rank          # independent replica per rank
     n = p["n"]
     esize = 4 if p["precision"] == 32 else 8
@@ -425,7 +523,7 @@ def run_ours(args):
         peak, peak_src = FALLBACK_HBM_GBS, "fallback"
     bytes_per_launch = 32 * n ** 3 if esize == 4 else 64 * n ** 3
     achieved = bytes_per_launch / (ms_per_step / 1e3) / 1e9
-    traffic = traffic_record(args.workload, info["variant"])
+    traffic = traffic_record(args.workload, info["variant"], args.stencil)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -434,20 +532,24 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "kernel": f"fused step variant {info['variant']} ({info['blocks']} blocks x "
+                     "kernel": f"fused step variant {info['variant']}"
+                               f"{', 27-point Laplacian' if args.stencil == 27 else ''} ({info['blocks']} blocks x "
                                f"{info['threads']} threads, ty={info['ty']}, zr={info['zr']}, depth={info['depth']})"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3 * esize,
                 "d2h_bytes_per_step": 8 * 8, "steps": E},
         "gpu_launches": args.steps * info["launches_per_step"],
         "clocks": clocks.summary(),
         "context": {"paper_gtx260_256cubed_su_per_s": 7.6e8,
-                    "note": "paper: GTX 260, 27-point stencil, 0.022 s/step at 256^3 (not this workload)"},
+                    "note": "paper: GTX 260, 27-point stencil, 0.022 s/step at 256^3; the same configuration "
+                            "with the 27-point stencil is timed under stencil27"},
     }
     if not args.no_extras and world == 1:
         lat.close()
         line["fp32_vs_fp64"] = measure_fp32_error(local, args.workload)
         line["adjoint"] = measure_adjoint(local)
         line["ensemble"] = measure_ensemble(local)
+        line["stencil27"] = measure_stencil27(local)
+        line["diagnostics"] = measure_diagnostics(local, args.workload)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -127,6 +127,21 @@ lat_status lat_evolve(lat_handle* h, int64_t n_steps);
  * at t and t + dt. Synchronises; returns a sticky device error if one is set. */
 lat_status lat_energies(lat_handle* h, lat_energy_report* out);
 
+/* Energy density and pressure at every site: eq. rho-pres of Sec. II.B evaluated
+ * per site, the quantities of the paper's second kernel (Sec. II.C), which it
+ * writes out every few hundred steps for visualisation.
+ *   rho_dev, p_dev: device arrays of N^3 elements of the handle's precision,
+ *     layout of lat_get_state, caller-owned; written with rho(x) and p(x) in the
+ *     units of lat_energies (physical), at the field time.
+ * Per site: the kinetic terms with the momenta at the field time, the potential,
+ * and a gradient energy equal to half the weighted squared differences to all
+ * the site's stencil neighbours (each neighbour pair shared evenly by its two
+ * sites), so that the volume means of rho_dev and p_dev are lat_energies' rho
+ * and p. Arithmetic in the handle's precision. Asynchronous on the handle's
+ * stream (no host synchronisation). LAT_EINVAL for null or misaligned pointers,
+ * LAT_ESTATE on a slab. */
+lat_status lat_energy_field(lat_handle* h, void* rho_dev, void* p_dev);
+
 /* Shell-binned power spectrum of field `field` (0 = phi, 1 = chi), the
  * diagnostic Sec. IV names as future work: bin b = round(|n|), n the integer
  * wave vector; p_out[b] = shell mean of |F_k|^2 / N^3 (F the forward DFT),

@@ -596,6 +596,20 @@ lat_status lat_energies(lat_handle* h, lat_energy_report* out)
     return (lat_status)s.status;
 }
 
+lat_status lat_energy_field(lat_handle* h, void* rho_dev, void* p_dev)
+{
+    if (!h || !rho_dev || !p_dev) return LAT_EINVAL;
+    if (((uintptr_t)rho_dev | (uintptr_t)p_dev) % h->esize != 0) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
+    LAT_TRY(ensure_prepared(h));
+    cudaError_t e = h->prec == 32
+                        ? launch_energy_field<float>(bufs_of<float>(h), h->M, h->sc, (float*)rho_dev, (float*)p_dev,
+                                                     h->stream)
+                        : launch_energy_field<double>(bufs_of<double>(h), h->M, h->sc, (double*)rho_dev,
+                                                      (double*)p_dev, h->stream);
+    return cuda_status(e);
+}
+
 lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, double* p_out, int64_t* count_out)
 {
     if (!h || field < 0 || field > 1 || nbins < 1 || nbins > 4096 || !k_out || !p_out || !count_out)

@@ -137,7 +137,112 @@ __global__ void spectrum_bins_kernel(const cufftDoubleComplex* spec, int n, doub
     for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) partials[(size_t)blockIdx.x * 3 * nbins + i] = sb[i];
 }
 
+// Integer-weight sums over the site's stencil neighbours of the differences
+// (30 dx^2 L f for 27 points, dx^2 L f for 7) and of their squares.
+template <typename T>
+__device__ __forceinline__ void neighbour_sums(const T* __restrict__ f, int n, int x, int y, int z, bool s27, T& lap,
+                                               T& sq)
+{
+    const T c = __ldg(f + sidx(n, x, y, z));
+    T l = T(0), g = T(0);
+    if (s27) {
+#pragma unroll
+        for (int dz = -1; dz <= 1; dz++) {
+            const int zz = wrap27(z + dz, n);
+#pragma unroll
+            for (int dy = -1; dy <= 1; dy++) {
+                const int yy = wrap27(y + dy, n);
+#pragma unroll
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int cls = (dx != 0) + (dy != 0) + (dz != 0);
+                    if (cls == 0) continue;
+                    const T d = __ldg(f + sidx(n, wrap27(x + dx, n), yy, zz)) - c;
+                    const T w = T(w27(cls));
+                    l += w * d;
+                    g += w * d * d;
+                }
+            }
+        }
+    } else {
+        const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? n - 1 : z - 1, zp = z == n - 1 ? 0 : z + 1;
+        const T d[6] = {__ldg(f + sidx(n, xm, y, z)) - c, __ldg(f + sidx(n, xp, y, z)) - c,
+                        __ldg(f + sidx(n, x, ym, z)) - c, __ldg(f + sidx(n, x, yp, z)) - c,
+                        __ldg(f + sidx(n, x, y, zm)) - c, __ldg(f + sidx(n, x, y, zp)) - c};
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            l += d[k];
+            g += d[k] * d[k];
+        }
+    }
+    lap = l;
+    sq = g;
+}
+
+// Energy density and pressure at every site (eq. rho-pres per site), in the
+// units of lat_energies: rho = conv (sum_i [kin_i + grad_i] + V_pr),
+// p = conv (sum_i [kin_i - grad_i / 3] - V_pr), kin_i = (f'_i + (dt/2) F_i - r h f_i)^2 / 2
+// (the momentum at the field time), grad_i = a^(-2s-2) / 2 times half the
+// weighted squared differences to all the site's stencil neighbours (each
+// neighbour pair shared evenly by its two sites). One thread per (x, y) column;
+// arithmetic in the lattice precision on exact neighbour differences, the
+// coefficients in FP64 rounded once.
+template <typename T>
+__global__ void __launch_bounds__(256) energy_field_kernel(Bufs<T> B, Model M, const DevScalars* sc, T* rho, T* pres)
+{
+    const int n = M.n;
+    const int par = (int)(sc->step & 1);
+    const T* f0 = B.f[par][0];
+    const T* f1 = B.f[par][1];
+    const T* p0 = B.p[par][0];
+    const T* p1 = B.p[par][1];
+    const double a = sc->a;
+    const double h = M.expansion ? sc->ad_half / a : 0.0;
+    const double conv = M.B * M.B / (M.A * M.A) * pow(a, 2.0 * M.s - 2.0 * M.r);
+    const T cL = (T)(sc->cL * M.lap_scale), cF = (T)sc->cF, cdom = (T)sc->cdom, kap = (T)sc->kappa;
+    const T hdt = (T)(0.5 * M.dt), rh = (T)(M.r * h);
+    const T gq = (T)(0.25 * pow(a, -2.0 * M.s - 2.0) * M.lap_scale);   // grad_i = gq * sum w d^2
+    const T cv = (T)conv;
+    const bool s27 = M.stencil == 27, quartic = M.beta == 4;
+    const long long cols = (long long)n * n;
+    for (long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
+         col += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(col % n), y = (int)(col / n);
+        for (int z = 0; z < n; z++) {
+            const size_t c = sidx(n, x, y, z);
+            const T a0 = __ldg(f0 + c), a1 = __ldg(f1 + c);
+            T l0, g0, l1, g1;
+            neighbour_sums(f0, n, x, y, z, s27, l0, g0);
+            neighbour_sums(f1, n, x, y, z, s27, l1, g1);
+            const T a0b = quartic ? a0 * a0 * a0 : a0;
+            const T F0 = cL * l0 + cF * a0 - (cdom * a0b + kap * a0 * a1 * a1);
+            const T F1 = cL * l1 + cF * a1 - kap * a0 * a0 * a1;
+            const T q0 = __ldg(p0 + c) + hdt * F0 - rh * a0;
+            const T q1 = __ldg(p1 + c) + hdt * F1 - rh * a1;
+            const T kin = T(0.5) * (q0 * q0 + q1 * q1);
+            const T grad = gq * (g0 + g1);
+            const T sq = a0 * a0;
+            const T V = cdom * (quartic ? T(0.25) * sq * sq : T(0.5) * sq) + T(0.5) * kap * sq * a1 * a1;
+            rho[c] = cv * (kin + grad + V);
+            pres[c] = cv * (kin - grad / T(3) - V);
+        }
+    }
+}
+
 } // namespace
+
+template <typename T>
+cudaError_t launch_energy_field(const Bufs<T>& b, const Model& M, const DevScalars* sc, T* rho, T* pres,
+                                cudaStream_t st)
+{
+    energy_field_kernel<T><<<energies_grid_blocks(M.n), 256, 0, st>>>(b, M, sc, rho, pres);
+    return cudaGetLastError();
+}
+template cudaError_t launch_energy_field<float>(const Bufs<float>&, const Model&, const DevScalars*, float*, float*,
+                                                cudaStream_t);
+template cudaError_t launch_energy_field<double>(const Bufs<double>&, const Model&, const DevScalars*, double*,
+                                                 double*, cudaStream_t);
 
 int energies_grid_blocks(int n)
 {

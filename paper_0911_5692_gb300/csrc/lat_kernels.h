@@ -116,6 +116,10 @@ cudaError_t launch_energies(const Bufs<T>& b, const Model& M, const DevScalars* 
                             const double* means, int pass, cudaStream_t st);
 template <typename T>
 cudaError_t launch_to_double(const T* src, double* dst, size_t count, cudaStream_t st);
+// energy density and pressure at every site (eq. rho-pres per site)
+template <typename T>
+cudaError_t launch_energy_field(const Bufs<T>& b, const Model& M, const DevScalars* sc, T* rho, T* pres,
+                                cudaStream_t st);
 int spectrum_grid_blocks(int n);
 cudaError_t launch_spectrum_bins(const void* spec, int n, double L, int nbins, double* partials,
                                  cudaStream_t st);

@@ -26,7 +26,7 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_set_g2", "lat_vjp", "lat_adjoint", "lat_batch_create", "lat_batch_init_fields",
             "lat_batch_evolve", "lat_batch_sync", "lat_batch_tune", "lat_batch_member", "lat_batch_info",
             "lat_batch_destroy", "lat_batch_check_barrier", "lat_slab_create", "lat_slab_sums", "lat_slab_step",
-            "lat_slab_advance")
+            "lat_slab_advance", "lat_energy_field")
 
 
 class LatParams(C.Structure):
@@ -79,6 +79,7 @@ def load_library(build_if_missing: bool = True):
             L.lat_init_fields.argtypes = [P]
             L.lat_evolve.argtypes = [P, C.c_int64]
             L.lat_energies.argtypes = [P, C.POINTER(LatEnergyReport)]
+            L.lat_energy_field.argtypes = [P, P, P]
             L.lat_spectrum.argtypes = [P, C.c_int, C.c_int, dp, dp, i64p]
             L.lat_get_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
             L.lat_set_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
@@ -321,6 +322,24 @@ class Lattice:
         vals = [r.t, r.a, r.ad, r.H, r.rho, r.p, r.w, r.curv_resid, r.kin[0], r.kin[1], r.grad[0], r.grad[1],
                 r.pot, r.mean[0], r.mean[1], r.var[0], r.var[1]]
         return dict(zip(self.ENERGY_KEYS, vals))
+
+    def energy_field(self, rho=None, p=None):
+        """Energy density and pressure at every site (lat_energy_field) as (N, N, N)
+        CUDA tensors [z][y][x] of the lattice dtype, written on the lattice's
+        stream without a host synchronisation. ``rho``/``p``: optional
+        preallocated contiguous tensors to fill."""
+        torch = self._torch
+        n = self.n
+        if rho is None:
+            rho = torch.empty((n, n, n), dtype=self.dtype, device=self.device)
+        if p is None:
+            p = torch.empty((n, n, n), dtype=self.dtype, device=self.device)
+        for t in (rho, p):
+            if t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != n ** 3:
+                raise ValueError("energy_field buffers must be contiguous CUDA tensors of N^3 lattice-dtype elements")
+        _check(self._L.lat_energy_field(self._h, C.c_void_p(rho.data_ptr()), C.c_void_p(p.data_ptr())),
+               "lat_energy_field")
+        return rho, p
 
     def spectrum(self, field: int, nbins: int):
         k = np.zeros(nbins); p = np.zeros(nbins); c = np.zeros(nbins, dtype=np.int64)

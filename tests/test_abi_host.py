@@ -126,4 +126,5 @@ def test_null_arguments():
     assert L.lat_create(None, None, None) == 1
     assert L.lat_evolve(None, 1) == 1
     assert L.lat_sync(None) == 1
+    assert L.lat_energy_field(None, None, None) == 1
     L.lat_destroy(None)
