@@ -199,17 +199,23 @@ def cpu_baseline(p, seconds):
                       f"synthetic state ({el:.1f} s, OpenMP over {cores} host cores)"}
 
 
-def measure_adjoint(local, name="lphi4_128_fp32"):
+def measure_adjoint(local, name="lphi4_128_fp32", n=None, steps=None):
     """Cost of the reverse-mode derivative on the 128^3 lambda phi^4 workload:
     J = <chi^2> after its 2000 steps and dJ/d(f, pi, g^2) by lat_adjoint
     (sqrt(n) checkpointing), against the plain forward evolution of the same
     steps. ratio_total = adjoint call / forward; ratio_backward = (adjoint call -
-    forward) / forward, the recomputation plus reverse sweep per forward step."""
+    forward) / forward, the recomputation plus reverse sweep per forward step.
+    n, steps: the same model on another lattice side (dt = dx / 20) and step
+    count (at 128^3 part of the state stays in L2)."""
     import torch
     from paper_0911_5692_gb300 import Lattice
     from paper_0911_5692_gb300.workloads import WORKLOADS
     w = WORKLOADS[name]
-    p, steps = dict(w["params"]), int(w["steps"])
+    p, steps = dict(w["params"]), int(steps or w["steps"])
+    if n:
+        p["n"] = int(n)
+        p["dt"] = p["L"] / n / 20
+        name = f"{name.split('_')[0]}_{n}_fp{p['precision']}"
     g = Lattice(p, device=local)
     g.init_fields()
     g.sync()
@@ -547,6 +553,7 @@ def run_ours(args):
         lat.close()
         line["fp32_vs_fp64"] = measure_fp32_error(local, args.workload)
         line["adjoint"] = measure_adjoint(local)
+        line["adjoint_256"] = measure_adjoint(local, n=256, steps=400)
         line["ensemble"] = measure_ensemble(local)
         line["stencil27"] = measure_stencil27(local)
         line["diagnostics"] = measure_diagnostics(local, args.workload)

@@ -688,13 +688,34 @@ int adj_blocks(long long n3)
 
 // z chunks of the z-march reverse kernels for `tiles` (x, y) tiles: enough
 // blocks for four per SM, runs of at least 8 planes.
-int adj_zchunks(int n, int tiles)
+// z chunks per tile column of the reverse kernels: the launch runs in
+// ceil(tiles * nzc / slots) waves of blocks that each march n / nzc planes and
+// stage two halo planes more, so pick the nzc (at least 8 planes per chunk) that
+// minimises waves x (planes per block + 2), the fewest chunks among equals.
+// `slots` = resident blocks on the device.
+int adj_zchunks(int n, int tiles, int slots)
 {
-    int dev = 0, sms = 148;
+    slots = std::max(1, slots);
+    int best = 1;
+    double best_t = 1e300;
+    for (int nzc = 1; nzc <= std::max(1, n / 8); nzc++) {
+        const long long waves = ((long long)tiles * nzc + slots - 1) / slots;
+        const double t = (double)waves * ((n + nzc - 1) / nzc + 2);
+        if (t < best_t - 1e-9) {
+            best_t = t;
+            best = nzc;
+        }
+    }
+    return best;
+}
+
+int resident_slots(const void* fn, int threads, size_t smem)
+{
+    int dev = 0, sms = 148, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int want = (4 * sms + tiles - 1) / tiles;
-    return std::max(1, std::min(want, std::max(1, n / 8)));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) occ = 1;
+    return sms * occ;
 }
 
 // Device allocations of one reverse-mode call, freed together.
@@ -746,8 +767,12 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
     const bool march = !pair && M.n % kMX == 0 &&
                        cudaFuncSetAttribute(adj_march_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)adj_march_smem<T>()) == cudaSuccess;
-    const int nzc = pair ? adj_zchunks(M.n, (M.n / (2 * kPX)) * (M.n / kPY))
-                         : march ? adj_zchunks(M.n, (M.n / kMX) * (M.n / kMY)) : 0;
+    const int nzc =
+        pair ? adj_zchunks(M.n, (M.n / (2 * kPX)) * (M.n / kPY),
+                           resident_slots((const void*)adj_pair_kernel, kPX * kPY, sizeof(AdjPairSmem)))
+        : march ? adj_zchunks(M.n, (M.n / kMX) * (M.n / kMY),
+                              resident_slots((const void*)adj_march_kernel<T>, kMX * kMY, adj_march_smem<T>()))
+                : 0;
     const dim3 mgrid(pair ? M.n / (2 * kPX) : march ? M.n / kMX : 1, pair ? M.n / kPY : march ? M.n / kMY : 1,
                      (pair || march) ? nzc : 1);
     const size_t nparts = std::max<size_t>(nb, (size_t)mgrid.x * mgrid.y * mgrid.z);
