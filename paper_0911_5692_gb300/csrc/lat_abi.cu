@@ -713,6 +713,8 @@ lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes)
     hd.esize = (uint32_t)h->esize;
     hd.params = h->p;
     unsigned char* out = (unsigned char*)dst;
+    s.log = nullptr;
+    s.log_base = 0;
     std::memcpy(out, &hd, sizeof(hd));
     std::memcpy(out + sizeof(hd), &s, sizeof(s));
     unsigned char* arr = out + sizeof(hd) + sizeof(s);
@@ -737,6 +739,8 @@ lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes)
     std::memcpy(&s, (const unsigned char*)src + sizeof(hd), sizeof(s));
     s.ticket = 0;
     s.ticket2 = 0;
+    s.log = nullptr;   // a device pointer is never taken from a blob
+    s.log_base = 0;
     const unsigned char* arr = (const unsigned char*)src + sizeof(hd) + sizeof(s);
     const int par = (int)(s.step & 1);
     LAT_CUDA(cudaStreamSynchronize(h->stream));

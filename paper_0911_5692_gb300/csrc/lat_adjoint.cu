@@ -20,6 +20,7 @@
 // f_{k-1} and the incoming adjoints, write the outgoing adjoints.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -686,8 +687,6 @@ int adj_blocks(long long n3)
     return (int)std::max<long long>(1, std::min<long long>(need, (long long)sms * 8));
 }
 
-// z chunks of the z-march reverse kernels for `tiles` (x, y) tiles: enough
-// blocks for four per SM, runs of at least 8 planes.
 // z chunks per tile column of the reverse kernels: the launch runs in
 // ceil(tiles * nzc / slots) waves of blocks that each march n / nzc planes and
 // stage two halo planes more, so pick the nzc (at least 8 planes per chunk) that
@@ -717,6 +716,38 @@ int resident_slots(const void* fn, int threads, size_t smem)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) occ = 1;
     return sms * occ;
 }
+
+// The history pointer of a scalar block (DevScalars::log, log_base).
+struct LogField {
+    DevScalars* log;
+    long long log_base;
+};
+static_assert(offsetof(DevScalars, log_base) == offsetof(DevScalars, log) + sizeof(DevScalars*),
+              "log and log_base are adjacent");
+
+// Clears the history pointer of the handle's scalar block when armed: the
+// pointer refers to scratch that the call frees, so no later step may see it.
+// Declared after the call's Scratch, so it runs (and waits for the clear)
+// before the scratch is freed.
+struct LogGuard {
+    DevScalars* sc;
+    cudaStream_t st;
+    bool armed = false;
+    lat_status clear()
+    {
+        if (!armed) return LAT_OK;
+        static const LogField zero{nullptr, 0};
+        if (cudaMemcpyAsync((unsigned char*)sc + offsetof(DevScalars, log), &zero, sizeof(zero),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return LAT_ECUDA;
+        armed = false;
+        return LAT_OK;
+    }
+    ~LogGuard()
+    {
+        if (armed && clear() == LAT_OK) cudaStreamSynchronize(st);
+    }
+};
 
 // Device allocations of one reverse-mode call, freed together.
 struct Scratch {
@@ -783,7 +814,7 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
     AdjScalars* as = nullptr;
     double* part = nullptr;
     if (!S.alloc(&ck, (size_t)nck * 6 * ab) || !S.alloc(&ck_sc, (size_t)nck * sizeof(DevScalars)) ||
-        !S.alloc(&hist, (size_t)std::max<int64_t>(n, 1) * sizeof(DevScalars)) || !S.alloc(&seg, (size_t)K * 2 * ab) ||
+        !S.alloc(&hist, (size_t)(n + 1) * sizeof(DevScalars)) || !S.alloc(&seg, (size_t)K * 2 * ab) ||
         !S.alloc(&adj1, 4 * ab) || !S.alloc(&fin, 4 * ab) || !S.alloc(&fin_sc, sizeof(DevScalars)) ||
         !S.alloc(&as, sizeof(AdjScalars)) || !S.alloc(&part, nparts * kSums * sizeof(double)))
         return LAT_ENOMEM;
@@ -791,7 +822,17 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
     auto arr = [&](T* base, size_t i) { return base + i * N3; };
 
     // forward pass: checkpoints (f_c, pi_c, f_{c-1}, scalars) every K steps and
-    // the scalars every step started from
+    // the scalars every step started from: hist[0] copied here, hist[k + 1]
+    // stored by step k's last block while the handle's scalar block carries the
+    // history pointer (cleared below, and by the guard on every early return)
+    LogGuard guard{h->sc, st};
+    {
+        const LogField lf{hist, (long long)s0.step};
+        LAT_CUDA(cudaMemcpyAsync((unsigned char*)h->sc + offsetof(DevScalars, log), &lf, sizeof(lf),
+                                 cudaMemcpyHostToDevice, st));
+        guard.armed = true;
+    }
+    LAT_CUDA(cudaMemcpyAsync(hist, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
     for (int64_t k = 0; k < n; k++) {
         const int par = (int)((s0.step + k) & 1);
         if (k % K == 0) {
@@ -803,9 +844,9 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
             }
             LAT_CUDA(cudaMemcpyAsync(ck_sc + k / K, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
         }
-        LAT_CUDA(cudaMemcpyAsync(hist + k, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
         LAT_CUDA(launch_step_with<T>(h, hb, false));
     }
+    LAT_TRY(guard.clear());
     const int parN = (int)((s0.step + n) & 1);
     for (int f = 0; f < 2; f++) {
         LAT_CUDA(cudaMemcpyAsync(fin + f * N3, hb.f[parN][f], ab, cudaMemcpyDeviceToDevice, st));
@@ -867,6 +908,8 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
             LAT_CUDA(cudaMemcpyAsync(hb.p[parc][f], cp + (2 + f) * N3, ab, cudaMemcpyDeviceToDevice, st));
         }
         LAT_CUDA(cudaMemcpyAsync(h->sc, ck_sc + sgi, sizeof(DevScalars), cudaMemcpyDeviceToDevice, st));
+        guard.armed = true;   // the checkpoint's block carries the history pointer
+        LAT_TRY(guard.clear());
         for (int64_t k = c; k + 1 < e; k++) {
             const int par = (int)((s0.step + k) & 1);
             Bufs<T> b = hb;

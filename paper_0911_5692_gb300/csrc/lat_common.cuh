@@ -50,6 +50,11 @@ struct DevScalars {
     double kd[5];    // step coefficients dt cL/dx^2, dt cF, -dt cdom, -dt kappa, dt
     float kf[5];     // the same rounded once to FP32 for the FP32 kernels
     int pad2;
+    // History of the scalar blocks (the reverse-mode derivative's forward pass):
+    // when set, the last block of each step also stores the block it produces,
+    // the one the next step starts from, at log[step - log_base]. Null otherwise.
+    DevScalars* log;
+    long long log_base;
 };
 
 // Step coefficient i for element type T (kd / kf above).
@@ -278,6 +283,7 @@ __device__ inline void finish_block(const Model& M, DevScalars* sc, double* part
         s.ticket = 0u;
         advance_scalars(M, s, S, advance);
         *sc = s;
+        if (advance && s.log) s.log[s.step - s.log_base] = s;
         __threadfence();
     }
 }
