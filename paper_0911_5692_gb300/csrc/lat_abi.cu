@@ -64,6 +64,7 @@ lat_status derive_model(const lat_params& p, Model* M)
     M->kappa0 = p.g2 / (A * A * B * B);
     M->pint = -2.0 * r - 2.0 * s;
     M->eight_pi_G = p.eight_pi_G;
+    M->g8A2 = p.eight_pi_G / (A * A);
     M->inv_sites = 1.0 / ((double)p.n * p.n * p.n);
     return LAT_OK;
 }

@@ -63,10 +63,10 @@ struct ScaleFwd {
 // (same formulas as scale_solve, with the intermediates kept).
 __device__ void scale_forward(const Model& M, const DevScalars& s, ScaleFwd& o)
 {
-    const double a = s.a;
+    const double a = s.a, ia = 1.0 / a;
     o.vpr = s.cdom * s.S[2] + s.kappa * s.S[3];
-    o.ea = apow(a, -2.0 * M.s - 2.0 * M.r - 1.0);
-    o.eb = apow(a, 2.0 * M.s + 2.0);
+    o.ea = apow(a, ia, -2.0 * M.s - 2.0 * M.r - 1.0);
+    o.eb = apow(a, ia, 2.0 * M.s + 2.0);
     o.c = M.eight_pi_G / (M.A * M.A) * o.ea * ((s.S[0] + s.S[1]) / 3.0 + o.eb * o.vpr);
     o.q = -(M.s + 2.0) / a;
     o.alpha = M.dt * o.q * 0.25;
@@ -81,7 +81,7 @@ __device__ void scale_forward(const Model& M, const DevScalars& s, ScaleFwd& o)
 __device__ void scale_reverse(const Model& M, const DevScalars& s, double bcL, double bcF, double bcd, double bkp,
                               double by, AdjScalars* as, double bS[4])
 {
-    const double a = s.a;
+    const double a = s.a, ia = 1.0 / a;
     double ba = 0.0, bad = 0.0;
     for (int k = 0; k < 4; k++) bS[k] = 0.0;
     if (M.expansion) {
@@ -108,7 +108,7 @@ __device__ void scale_reverse(const Model& M, const DevScalars& s, double bcL, d
         bc += M.dt * bgamma;
         ba += bq * (sx + 2.0) / (a * a);
         // cL = a^(-2s-2)
-        ba += bcL * (-2.0 * sx - 2.0) * apow(a, -2.0 * sx - 3.0);
+        ba += bcL * (-2.0 * sx - 2.0) * apow(a, ia, -2.0 * sx - 3.0);
         // c = K ea (T + eb vpr)
         const double K = M.eight_pi_G / (M.A * M.A);
         const double T = (s.S[0] + s.S[1]) / 3.0;
@@ -116,8 +116,8 @@ __device__ void scale_reverse(const Model& M, const DevScalars& s, double bcL, d
         const double bT = bc * K * o.ea;
         const double beb = bc * K * o.ea * o.vpr;
         const double bvpr = bc * K * o.ea * o.eb;
-        ba += bea * (-2.0 * sx - 2.0 * r - 1.0) * apow(a, -2.0 * sx - 2.0 * r - 2.0);
-        ba += beb * (2.0 * sx + 2.0) * apow(a, 2.0 * sx + 1.0);
+        ba += bea * (-2.0 * sx - 2.0 * r - 1.0) * apow(a, ia, -2.0 * sx - 2.0 * r - 2.0);
+        ba += beb * (2.0 * sx + 2.0) * apow(a, ia, 2.0 * sx + 1.0);
         bS[0] = bT / 3.0;
         bS[1] = bT / 3.0;
         bcd += bvpr * s.S[2];
@@ -126,8 +126,8 @@ __device__ void scale_reverse(const Model& M, const DevScalars& s, double bcL, d
         bS[3] = bvpr * s.kappa;
     }
     // cdom = cdom0 a^pdom, kappa = kappa0 a^pint
-    ba += bcd * M.cdom0 * M.pdom * apow(a, M.pdom - 1.0) + bkp * M.kappa0 * M.pint * apow(a, M.pint - 1.0);
-    as->bk0 += bkp * apow(a, M.pint);
+    ba += bcd * M.cdom0 * M.pdom * apow(a, ia, M.pdom - 1.0) + bkp * M.kappa0 * M.pint * apow(a, ia, M.pint - 1.0);
+    as->bk0 += bkp * apow(a, ia, M.pint);
     as->ba += ba;
     as->bad += bad;
 }

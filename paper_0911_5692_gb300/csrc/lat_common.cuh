@@ -26,6 +26,7 @@ struct Model {
     double cdom0, pdom; // V_pr dominant term: cdom0 a^pdom f^beta / beta
     double kappa0, pint;// V_pr interaction: kappa0 a^pint f^2 chi^2 / 2
     double eight_pi_G;
+    double g8A2;        // eight_pi_G / A^2 (eq. scale)
     double inv_sites;   // 1 / N^3
 };
 
@@ -137,19 +138,20 @@ __device__ __forceinline__ void block_reduce(double v[kSums], double* red, doubl
 }
 
 // a^p. The exponents of the two models' rescalings (Sec. II.B) are integers
-// for which repeated multiplication is exact to a few ulp and costs a handful
-// of FP64 multiplies instead of a general pow on the slow FP64 pipe.
-__device__ inline double apow(double a, double p)
+// for which repeated multiplication of a (or of inv_a = 1/a for negative p) is
+// exact to a few ulp and costs a handful of FP64 multiplies instead of a
+// general pow, or a division, on the slow FP64 pipe.
+__device__ inline double apow(double a, double inv_a, double p)
 {
     if (p == rint(p) && fabs(p) <= 16.0) {
         int e = (int)fabs(p);
-        double r = 1.0, b = a;
+        double r = 1.0, b = p < 0.0 ? inv_a : a;
         while (e) {
             if (e & 1) r *= b;
             b *= b;
             e >>= 1;
         }
-        return p < 0.0 ? 1.0 / r : r;
+        return r;
     }
     return pow(a, p);
 }
@@ -175,9 +177,10 @@ __device__ inline void step_coefficients(const Model& M, DevScalars* sc)
 // r(s-r+2) h^2 + r a''/a that follows from eq. fe under the rescaling).
 __device__ inline void scale_solve(const Model& M, DevScalars* sc)
 {
-    const double a = sc->a;
-    sc->cdom = M.cdom0 * apow(a, M.pdom);
-    sc->kappa = M.kappa0 * apow(a, M.pint);
+    // one FP64 division (1/a) serves every negative power and quotient below
+    const double a = sc->a, ia = 1.0 / a;
+    sc->cdom = M.cdom0 * apow(a, ia, M.pdom);
+    sc->kappa = M.kappa0 * apow(a, ia, M.pint);
     if (!M.expansion) {
         sc->ad_next = 0.0; sc->ad_half = 0.0; sc->add = 0.0;
         sc->cL = 1.0; sc->cF = 0.0;
@@ -185,9 +188,9 @@ __device__ inline void scale_solve(const Model& M, DevScalars* sc)
         return;
     }
     const double vpr = sc->cdom * sc->S[2] + sc->kappa * sc->S[3];
-    const double c = M.eight_pi_G / (M.A * M.A) * apow(a, -2.0 * M.s - 2.0 * M.r - 1.0)
-                   * ((sc->S[0] + sc->S[1]) / 3.0 + apow(a, 2.0 * M.s + 2.0) * vpr);
-    const double q = -(M.s + 2.0) / a;
+    const double c = M.g8A2 * apow(a, ia, -2.0 * M.s - 2.0 * M.r - 1.0)
+                   * ((sc->S[0] + sc->S[1]) * (1.0 / 3.0) + apow(a, ia, 2.0 * M.s + 2.0) * vpr);
+    const double q = -(M.s + 2.0) * ia;
     const double alpha = M.dt * q * 0.25;
     const double gamma = 2.0 * sc->ad + M.dt * c;
     const double disc = 1.0 - 4.0 * alpha * gamma;
@@ -199,9 +202,9 @@ __device__ inline void scale_solve(const Model& M, DevScalars* sc)
     sc->ad_half = 0.5 * y;
     sc->ad_next = y - sc->ad;
     sc->add = q * sc->ad_half * sc->ad_half + c;
-    sc->cL = apow(a, -2.0 * M.s - 2.0);
-    const double h = sc->ad_half / a;
-    sc->cF = M.r * (M.s - M.r + 2.0) * h * h + M.r * sc->add / a;
+    sc->cL = apow(a, ia, -2.0 * M.s - 2.0);
+    const double h = sc->ad_half * ia;
+    sc->cF = M.r * (M.s - M.r + 2.0) * h * h + M.r * sc->add * ia;
     step_coefficients(M, sc);
 }
 
@@ -236,9 +239,32 @@ __device__ inline void reduce_partials(const Model& M, const double* partials, i
     const int tid = linear_tid();
     if (tid >= 32) return;
     double v[kSums] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = tid; b < nblocks; b += 32)
+    // blocks tid, tid + 32, ... in order; four of them per pass so that their
+    // L2 loads are in flight together
+    const double2* p2 = reinterpret_cast<const double2*>(partials);   // kSums = 4 doubles per block
+    int b = tid;
+    for (; b + 96 < nblocks; b += 128) {
+        double2 x[4][2];
 #pragma unroll
-        for (int k = 0; k < kSums; k++) v[k] += __ldcg(partials + (size_t)b * kSums + k);
+        for (int j = 0; j < 4; j++) {
+            x[j][0] = __ldcg(p2 + (size_t)(b + 32 * j) * 2);
+            x[j][1] = __ldcg(p2 + (size_t)(b + 32 * j) * 2 + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            v[0] += x[j][0].x;
+            v[1] += x[j][0].y;
+            v[2] += x[j][1].x;
+            v[3] += x[j][1].y;
+        }
+    }
+    for (; b < nblocks; b += 32) {
+        const double2 x0 = __ldcg(p2 + (size_t)b * 2), x1 = __ldcg(p2 + (size_t)b * 2 + 1);
+        v[0] += x0.x;
+        v[1] += x0.y;
+        v[2] += x1.x;
+        v[3] += x1.y;
+    }
 #pragma unroll
     for (int k = 0; k < kSums; k++)
 #pragma unroll
