@@ -490,7 +490,8 @@ def run_ours(args):
     ms_per_step = ms_max / args.steps
 
     # end to end through the C ABI with host buffers: every step uploads the
-    # state (4 arrays) from pinned host memory, advances one step and reads the
+    # state (4 arrays) from pinned host memory (lat_upload_state), advances one
+    # step (the sums of the uploaded fields, then the fused step) and reads the
     # scalars (t, a, a', step, sums) back.
     E = max(1, args.e2e_steps)
     host = []
@@ -506,9 +507,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
+    srcs = (C.c_void_p * 4)(*[hbuf.data_ptr() for f, w, hbuf in host])   # f0, f1, pi0, pi1
     for _ in range(E):
-        for f, w, hbuf in host:
-            assert lib.lat_set_state(h, f, w, C.c_void_p(hbuf.data_ptr()), 0) == 0
+        assert lib.lat_upload_state(h, srcs, 0) == 0
         assert lib.lat_evolve(h, 1) == 0
         assert lib.lat_get_scalars(h, out8) == 0
     e2e_sec = time.perf_counter() - t0

@@ -159,6 +159,17 @@ lat_status lat_get_state(lat_handle* h, int field, int what, void* dst, int dst_
  * coefficients are recomputed before the next step or diagnostic. */
 lat_status lat_set_state(lat_handle* h, int field, int what, const void* src, int src_is_device);
 
+/* Upload the whole state in one call: src[0..3] = f_phi, f_chi, pi_phi, pi_chi
+ * (layout of lat_get_state; device memory if src_is_device, else host memory).
+ * The step parity is read from the device first (one small synchronous read);
+ * then the four copies are queued on the handle's stream after the work already
+ * there, and the call returns without waiting for them. Host sources should be
+ * page-locked for the copies to run asynchronously and must stay unchanged until
+ * the stream has passed them (the next synchronising call or lat_sync). The sums
+ * and coefficients are recomputed before the next step or diagnostic.
+ * LAT_EINVAL for a null pointer. */
+lat_status lat_upload_state(lat_handle* h, const void* const src[4], int src_is_device);
+
 /* Scalars: out[0] = t (time of the momenta), out[1] = a (at t + dt/2),
  * out[2] = a' (at t), out[3] = step count, out[4..7] = the volume averages
  * <|grad f_phi|^2>, <|grad f_chi|^2>, <f_phi^beta/beta>, <f_phi^2 f_chi^2/2> at the
@@ -210,10 +221,12 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8]);
  * for 64), layout as in lat_get_state; model: LAT_MODEL_*; L: box side. Writes
  * to out_dev (device, 4 doubles, caller-owned) the averages <|grad f_phi|^2>,
  * <|grad f_chi|^2> (forward differences / dx^2), <f_phi^beta/beta> and
- * <f_phi^2 f_chi^2 / 2>: the same values lat_get_scalars reports in out[4..7]
- * for a handle holding these fields with the 7-point stencil (the gradient
- * average of the 27-point stencil is not served here). Asynchronous on
- * cuda_stream (a cudaStream_t; NULL = legacy default stream).
+ * <f_phi^2 f_chi^2 / 2> in FP64 arithmetic: the averages lat_get_scalars
+ * reports in out[4..7] for a handle holding these fields with the 7-point
+ * stencil (equal to FP64 rounding for FP64 fields; a handle with FP32 fields
+ * forms them in FP32 with compensated per-thread sums, within about 1e-7
+ * relative). The gradient average of the 27-point stencil is not served here.
+ * Asynchronous on cuda_stream (a cudaStream_t; NULL = legacy default stream).
  * Scratch: one static device array per GPU (about 33 KB, held by every GPU that
  * loads the library until the process exits); it calls no cudaMalloc, cudaFree
  * or allocating library routine. The first call on a device looks the array up

@@ -458,6 +458,21 @@ lat_status lat_set_state(lat_handle* h, int field, int what, const void* src, in
     return LAT_OK;
 }
 
+lat_status lat_upload_state(lat_handle* h, const void* const src[4], int src_is_device)
+{
+    if (!h || !src) return LAT_EINVAL;
+    for (int k = 0; k < 4; k++)
+        if (!src[k]) return LAT_EINVAL;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    const int par = (int)(s.step & 1);
+    for (int k = 0; k < 4; k++)   // f_phi, f_chi, pi_phi, pi_chi of the current set
+        LAT_CUDA(cudaMemcpyAsync(h->buf[4 * par + k], src[k], h->nsites * h->esize,
+                                 src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    h->dirty = true;
+    return LAT_OK;
+}
+
 lat_status lat_init_fields(lat_handle* h)
 {
     if (!h) return LAT_EINVAL;

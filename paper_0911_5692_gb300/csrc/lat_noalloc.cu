@@ -28,11 +28,11 @@ constexpr int kMaxDevices = 64;
 // on a device; see the entry point for the rules that follow from that.
 __device__ __align__(256) unsigned char g_sums_scratch[kScratchBytes];
 
-// Same reduction as the sums pass of a handle: forward-difference |grad f|^2 of
-// both fields (unscaled), f0^beta/beta and f0^2 f1^2/2, accumulated in FP64
-// per thread over (x, y) columns marched in z, then a fixed-order block and
-// last-block reduction. The last block writes the volume averages and clears
-// the counter.
+// The sums of a handle's sums pass, in FP64 arithmetic: forward-difference
+// |grad f|^2 of both fields (unscaled), f0^beta/beta and f0^2 f1^2/2,
+// accumulated in FP64 per thread over (x, y) columns marched in z, then a
+// fixed-order block and last-block reduction. The last block writes the volume
+// averages and clears the counter.
 template <typename T>
 __global__ void __launch_bounds__(kStaticThreads) field_sums_static_kernel(const T* __restrict__ f0,
                                                                           const T* __restrict__ f1, int n,

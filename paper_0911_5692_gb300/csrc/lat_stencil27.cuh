@@ -36,22 +36,23 @@ __device__ inline double lap27_sum(const T* f, int n, int x, int y, int z)
 // f(x))^2; the gradient average is -<f L f> = < that sum > / (30 dx^2). A site
 // owns one offset of each +-b pair, all with dy >= 0, so that a tile of rows
 // needs the new fields of one row beyond it (in +y) only: four in its plane,
-// six to the plane above, three to the plane below ({dx, dy, dz}).
-template <typename T>
-__device__ inline double bonds27_sum(const T* f, int n, int x, int y, int z)
+// six to the plane above, three to the plane below ({dx, dy, dz}). Arithmetic
+// in R (the differences are exact in the lattice precision for f = const + small).
+template <typename R = double, typename T>
+__device__ inline R bonds27_sum(const T* f, int n, int x, int y, int z)
 {
     constexpr signed char B[13][3] = {{1, 0, 0},  {0, 1, 0},  {1, 1, 0},  {-1, 1, 0},
                                       {0, 0, 1},  {1, 0, 1},  {-1, 0, 1}, {0, 1, 1}, {1, 1, 1}, {-1, 1, 1},
                                       {0, 1, -1}, {1, 1, -1}, {-1, 1, -1}};
-    const double c = (double)f[((size_t)z * n + y) * n + x];
-    double acc = 0.0;
+    const R c = (R)__ldg(f + ((size_t)z * n + y) * n + x);
+    R acc = R(0);
 #pragma unroll
     for (int b = 0; b < 13; b++) {
         const int dx = B[b][0], dy = B[b][1], dz = B[b][2];
         const int cls = (dx != 0) + (dy != 0) + (dz != 0);
         const size_t j = ((size_t)wrap27(z + dz, n) * n + wrap27(y + dy, n)) * n + wrap27(x + dx, n);
-        const double d = (double)f[j] - c;
-        acc += w27(cls) * d * d;
+        const R d = (R)__ldg(f + j) - c;
+        acc += R(w27(cls)) * d * d;
     }
     return acc;
 }

@@ -15,6 +15,8 @@
 //
 // This kernel is the portable path (FP32 and FP64, any N % 4 == 0); the TMA
 // plane-ring kernel in lat_step_tma.cu is the fast FP32/FP64 path on sm_103a.
+#include <algorithm>
+
 #include "lat_kernels.h"
 #include "lat_stencil27.cuh"
 
@@ -142,44 +144,65 @@ __global__ void __launch_bounds__(TX * TY) step_simple_kernel(Bufs<T> B, Model M
 
 // Sums of the current fields (no step): the gradient averages of the configured
 // stencil (forward differences for 7 points, the 13 owned weighted bonds of
-// each site for 27) and the potential terms, one thread per (x, y) column, for
-// initialisation and after a state upload; its last block solves the a' update
-// for the first step.
+// each site for 27) and the potential terms, one thread per (x, y) column
+// marching z, for initialisation and after a state upload; its last block
+// solves the a' update for the first step. Arithmetic in the lattice precision
+// on exact neighbour differences; each thread keeps compensated (Kahan) sums,
+// which the block folds in FP64 as the step kernels do.
 template <typename T>
-__global__ void __launch_bounds__(256) sums_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials)
+struct KSum {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T v)
+    {
+        const T y = v - c;
+        const T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) sums_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, int nzc)
 {
     __shared__ double red[32 * kSums];
     const int n = M.n;
     const int par = (int)(sc->step & 1);
     const T* __restrict__ f0 = B.f[par][0];
     const T* __restrict__ f1 = B.f[par][1];
-    double acc[kSums] = {0.0, 0.0, 0.0, 0.0};
-    const long long cols = (long long)n * n;
-    for (long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
-         col += (long long)gridDim.x * blockDim.x) {
+    const bool s27 = M.stencil == 27, quartic = M.beta == 4;
+    KSum<T> acc[kSums];
+    // work items: (x, y) columns cut into nzc z runs, so that small lattices
+    // still give every SM enough threads
+    const long long cols = (long long)n * n, items = cols * nzc;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const long long col = it % cols;
+        const int zc = (int)(it / cols);
         const int x = (int)(col % n), y = (int)(col / n);
         const int xp = x == n - 1 ? 0 : x + 1, yp = y == n - 1 ? 0 : y + 1;
-        for (int z = 0; z < n; z++) {
+        const int zb = (int)((long long)zc * n / nzc), ze = (int)((long long)(zc + 1) * n / nzc);
+        T a0 = __ldg(f0 + sidx(n, x, y, zb)), a1 = __ldg(f1 + sidx(n, x, y, zb));
+        for (int z = zb; z < ze; z++) {
             const int zp = z == n - 1 ? 0 : z + 1;
-            const size_t c = sidx(n, x, y, z);
-            const double a0 = (double)f0[c], a1 = (double)f1[c];
-            const double sq = a0 * a0;
-            acc[2] += M.beta == 4 ? 0.25 * sq * sq : 0.5 * sq;
-            acc[3] += 0.5 * sq * a1 * a1;
-            if (M.stencil == 27) {
-                acc[0] += bonds27_sum(f0, n, x, y, z);
-                acc[1] += bonds27_sum(f1, n, x, y, z);
-                continue;
+            const T u0 = __ldg(f0 + sidx(n, x, y, zp)), u1 = __ldg(f1 + sidx(n, x, y, zp));   // the next centre
+            const T sq = a0 * a0;
+            acc[2].add(quartic ? T(0.25) * sq * sq : T(0.5) * sq);
+            acc[3].add(T(0.5) * sq * a1 * a1);
+            if (s27) {
+                acc[0].add(bonds27_sum<T>(f0, n, x, y, z));
+                acc[1].add(bonds27_sum<T>(f1, n, x, y, z));
+            } else {
+                const T e0 = __ldg(f0 + sidx(n, xp, y, z)) - a0, e1 = __ldg(f0 + sidx(n, x, yp, z)) - a0, e2 = u0 - a0;
+                const T h0 = __ldg(f1 + sidx(n, xp, y, z)) - a1, h1 = __ldg(f1 + sidx(n, x, yp, z)) - a1, h2 = u1 - a1;
+                acc[0].add(e0 * e0 + e1 * e1 + e2 * e2);
+                acc[1].add(h0 * h0 + h1 * h1 + h2 * h2);
             }
-            const double e0 = (double)f0[sidx(n, xp, y, z)] - a0, e1 = (double)f0[sidx(n, x, yp, z)] - a0,
-                         e2 = (double)f0[sidx(n, x, y, zp)] - a0;
-            const double h0 = (double)f1[sidx(n, xp, y, z)] - a1, h1 = (double)f1[sidx(n, x, yp, z)] - a1,
-                         h2 = (double)f1[sidx(n, x, y, zp)] - a1;
-            acc[0] += e0 * e0 + e1 * e1 + e2 * e2;
-            acc[1] += h0 * h0 + h1 * h1 + h2 * h2;
+            a0 = u0;
+            a1 = u1;
         }
     }
-    finish_block(M, sc, partials, acc, red, false);
+    T v[kSums] = {acc[0].s, acc[1].s, acc[2].s, acc[3].s};
+    finish_block(M, sc, partials, v, red, false);
 }
 
 } // namespace
@@ -199,17 +222,25 @@ cudaError_t launch_step_simple(const Bufs<T>& b, const Model& M, DevScalars* sc,
     return cudaGetLastError();
 }
 
-int sums_grid_blocks(int n)
+// z runs per (x, y) column of the sums pass: about 4 x 152 x 256 threads'
+// worth of (column, run) items, runs of at least 4 planes
+int sums_zruns(int n)
 {
     const long long cols = (long long)n * n;
-    long long blocks = (cols + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(n / 4, (155648 + cols - 1) / cols));
+}
+
+int sums_grid_blocks(int n)
+{
+    const long long items = (long long)n * n * sums_zruns(n);
+    long long blocks = (items + 255) / 256;
     return (int)(blocks < 1024 ? blocks : 1024);
 }
 
 template <typename T>
 cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, cudaStream_t st)
 {
-    sums_kernel<T><<<sums_grid_blocks(M.n), 256, 0, st>>>(b, M, sc, partials);
+    sums_kernel<T><<<sums_grid_blocks(M.n), 256, 0, st>>>(b, M, sc, partials, sums_zruns(M.n));
     return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_set_g2", "lat_vjp", "lat_adjoint", "lat_batch_create", "lat_batch_init_fields",
             "lat_batch_evolve", "lat_batch_sync", "lat_batch_tune", "lat_batch_member", "lat_batch_info",
             "lat_batch_destroy", "lat_batch_check_barrier", "lat_slab_create", "lat_slab_sums", "lat_slab_step",
-            "lat_slab_advance", "lat_energy_field")
+            "lat_slab_advance", "lat_energy_field", "lat_upload_state")
 
 
 class LatParams(C.Structure):
@@ -80,6 +80,7 @@ def load_library(build_if_missing: bool = True):
             L.lat_evolve.argtypes = [P, C.c_int64]
             L.lat_energies.argtypes = [P, C.POINTER(LatEnergyReport)]
             L.lat_energy_field.argtypes = [P, P, P]
+            L.lat_upload_state.argtypes = [P, C.POINTER(C.c_void_p), C.c_int]
             L.lat_spectrum.argtypes = [P, C.c_int, C.c_int, dp, dp, i64p]
             L.lat_get_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
             L.lat_set_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
@@ -277,6 +278,22 @@ class Lattice:
             self.set_state_host(i, 0, arr)
         for i, arr in enumerate((pi0, pi1)):
             self.set_state_host(i, 1, arr)
+
+    def upload_state(self, f0, f1, pi0, pi1):
+        """Queue the upload of the whole state (lat_upload_state) from four
+        contiguous tensors of N^3 lattice-dtype elements: CUDA tensors, or host
+        tensors (page-locked for asynchronous copies). Returns without waiting for
+        the copies; the sources must stay unchanged until the lattice's stream has
+        passed them (e.g. sync())."""
+        ts = (f0, f1, pi0, pi1)
+        dev = all(t.is_cuda for t in ts)
+        if not dev and any(t.is_cuda for t in ts):
+            raise ValueError("upload_state takes four CUDA tensors or four host tensors")
+        for t in ts:
+            if t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.n ** 3:
+                raise ValueError("upload_state arrays must be contiguous with N^3 lattice-dtype elements")
+        ptrs = (C.c_void_p * 4)(*[t.data_ptr() for t in ts])
+        _check(self._L.lat_upload_state(self._h, ptrs, 1 if dev else 0), "lat_upload_state")
 
     def set_state_device(self, field: int, what: int, tensor):
         t = tensor.contiguous()

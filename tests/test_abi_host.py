@@ -127,4 +127,5 @@ def test_null_arguments():
     assert L.lat_evolve(None, 1) == 1
     assert L.lat_sync(None) == 1
     assert L.lat_energy_field(None, None, None) == 1
+    assert L.lat_upload_state(None, None, 0) == 1
     L.lat_destroy(None)

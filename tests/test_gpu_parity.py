@@ -62,8 +62,12 @@ def test_one_step_parity(n, model, expansion, prec, variant):
     compare_states(g, o, TOL[prec], f"N={n} {model} exp={expansion} fp{prec} v{variant}")
     gs, os_ = g.scalars(), o.scalars()
     assert gs["step"] == os_["step"] == 1
-    assert abs(gs["a"] - os_["a"]) <= 1e-14 * os_["a"]
-    assert abs(gs["ad"] - os_["ad"]) <= 1e-13 * max(abs(os_["ad"]), 1.0)
+    # a and a' are FP64 on both sides; an FP32 lattice forms the sums that set a''
+    # in FP32 (compensated per thread, relative error ~1e-7), which moves a' by
+    # about dt dc and a by about dt^2 dc (dt <= 0.125 here)
+    ta, tad = (1e-14, 1e-13) if prec == 64 else (1e-8, 1e-7)
+    assert abs(gs["a"] - os_["a"]) <= ta * os_["a"]
+    assert abs(gs["ad"] - os_["ad"]) <= tad * max(abs(os_["ad"]), 1.0)
     # sums of the new fields: FP64 exact to rounding; FP32 gradient sums carry the
     # FP32 rounding of f (~6e-8 on differences of ~1e-3)
     stol = [1e-11, 1e-11, 1e-13, 1e-11] if prec == 64 else [3e-3, 3e-3, 1e-6, 1e-5]
@@ -373,3 +377,30 @@ def test_fp32_run_statistics(fluct):
         assert abs(eg["var1"] / eo["var1"] - 1) <= 1e-3
         if fluct > 1.0:
             assert abs(eg["var0"] / eo["var0"] - 1) <= 1e-3
+
+
+@pytest.mark.parametrize("src", ["host", "device"])
+def test_upload_state_is_set_state(src):
+    """lat_upload_state (all four arrays queued on the stream at once, from pinned
+    host or device memory) leaves the lattice exactly as four lat_set_state calls
+    do: same arrays, same scalars, and bit-identical steps after it."""
+    import torch
+    n = 32
+    p = lphi4(n, precision=32)
+    st = _state("lphi4", n, 32, seed=41)
+    a = Lattice(p)
+    a.set_state(*st, t=0.0, a=1.1, ad=0.4)
+    b = Lattice(p)
+    b.set_scalars(0.0, 1.1, 0.4, 0)
+    ts = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32).reshape(-1)) for x in st]
+    ts = [t.pin_memory() for t in ts] if src == "host" else [t.cuda() for t in ts]
+    b.upload_state(*ts)
+    b.sync()
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    assert a.scalars() == b.scalars()
+    a.evolve(3)
+    b.evolve(3)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    assert a.scalars() == b.scalars()

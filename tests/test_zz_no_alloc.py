@@ -4,7 +4,8 @@ It exists for callers that cannot call cudaMalloc (memory already reserved by
 another allocator, a fixed budget, or no room for cudaMalloc's implicit
 synchronisation). Its scratch is a static device array shared by all calls, so
 this test checks two calls in a row against the sums the handle path reports
-(lat_get_scalars out[4..7]) for the same fields. This file is collected last so
+(lat_get_scalars out[4..7]) for the same fields: to FP64 rounding for FP64
+fields, to the FP32 rounding of the handle's sums (1e-6) for FP32 fields. This file is collected last so
 that a run stopping at the first failure has already run every other test; it
 passes alone in a fresh process and after the others.
 """
@@ -37,7 +38,9 @@ def test_static_sums_match_handle_sums(n, model, prec):
         field_sums_static(f_phi, f_chi, n, prec, p["model"], p["L"], out, stream=g.stream)
         g.stream.synchronize()
         got = out.cpu().numpy()
-        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0, err_msg=f"call {call}")
+        # FP64 on both sides for FP64 fields; a handle with FP32 fields forms
+        # the sums in FP32 (exact differences, compensated per-thread sums)
+        np.testing.assert_allclose(got, ref, rtol=1e-12 if prec == 64 else 1e-6, atol=0, err_msg=f"call {call}")
 
 
 def test_static_sums_reject_bad_sizes():
