@@ -84,3 +84,24 @@ def test_energy_field_rejects_bad_buffers():
     g = Lattice(dict(lphi4(n, precision=32)))
     with pytest.raises(ValueError):
         g.energy_field(torch.empty((n, n, n), dtype=torch.float64, device="cuda"))
+
+
+def test_energy_field_and_upload_on_a_slab():
+    """The per-site fields are a whole-lattice diagnostic: a slab handle refuses
+    them (LAT_ESTATE); its state can still be uploaded in one call."""
+    from paper_0911_5692_gb300.slab import SlabGPU
+    n = 16
+    p = lphi4(n, precision=32)
+    s = SlabGPU(p, 0, 8)
+    rho = torch.empty((s.nzl + 3) * n * n, dtype=torch.float32, device="cuda")
+    pres = torch.empty_like(rho)
+    import ctypes as C
+    st = s._L.lat_energy_field(s._h, C.c_void_p(rho.data_ptr()), C.c_void_p(pres.data_ptr()))
+    assert st == 8
+    src = [torch.full(((s.nzl + 3) * n * n,), float(k + 1), dtype=torch.float32, device="cuda") for k in range(4)]
+    ptrs = (C.c_void_p * 4)(*[t.data_ptr() for t in src])
+    assert s._L.lat_upload_state(s._h, ptrs, 1) == 0
+    s.sync()
+    for k in range(4):
+        assert torch.equal(s.buffers[k], src[k].view_as(s.buffers[k]))
+    s.close()

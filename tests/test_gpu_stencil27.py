@@ -243,3 +243,43 @@ def test_paths_without_27_point_form_refuse():
     from paper_0911_5692_gb300.slab import SlabGPU
     with pytest.raises(LatticeError, match="UNSUPPORTED"):
         SlabGPU(p, 0, n)
+
+
+def test_checkpoint_resume_bit_identical_27():
+    """n steps == k steps, checkpoint, load into a new lattice, n - k steps:
+    bit-identical with the 27-point kernel (the stencil is part of the
+    parameters the blob must match)."""
+    n = 32
+    p = _params("lphi4", n, 32)
+    a = Lattice(p)
+    a.init_fields()
+    a.evolve(70)
+    b = Lattice(p)
+    b.init_fields()
+    b.evolve(33)
+    blob = b.save_checkpoint()
+    c = Lattice(p)
+    c.load_checkpoint(blob)
+    c.evolve(37)
+    for x, y in zip(a.get_state(), c.get_state()):
+        assert np.array_equal(x, y)
+    assert a.scalars() == c.scalars()
+    d = Lattice(dict(p, stencil=7))
+    with pytest.raises(LatticeError):
+        d.load_checkpoint(blob)
+
+
+def test_nonfinite_is_sticky_27():
+    """A NaN in the uploaded fields makes the 27-point sums non-finite; the device
+    raises LAT_ENONFINITE and the next synchronising call returns it."""
+    n = 16
+    p = _params("lphi4", n, 32)
+    st = list(_state("lphi4", n, 32, seed=1))
+    st[0] = st[0].copy()
+    st[0][2, 3, 4] = np.nan
+    g = Lattice(p)
+    g.set_state(*st, t=0.0, a=1.0, ad=0.4)
+    with pytest.raises(LatticeError) as ei:
+        g.evolve(3)
+        g.sync()
+    assert ei.value.status == 5
