@@ -198,11 +198,14 @@ lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes);
 lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
 
 /* Choose the step kernel (all compute the same step): variant 0 = automatic
- * (2 where it fits, else 1), 1 = one site per thread with cached loads,
+ * (4 for FP32 lattices with N >= 512, else 2 where it fits, else 1), 1 = one
+ * site per thread with cached loads,
  * 2 = z-march through a shared-memory plane ring filled by per-thread
- * asynchronous copies (the fast path), 3 = plane ring filled by TMA boxes;
+ * asynchronous copies (the fast path), 3 = plane ring filled by TMA boxes,
+ * 4 = the plane ring of 2 over x tiles of at most 32 (or 16) 16-byte vectors
+ * with taller y tiles (7-point only);
  * ty = owned rows per tile, zr = planes per z-chunk (variant 3: planes per
- * block), depth = planes prefetched ahead (variants 2 and 3), 0 = automatic.
+ * block), depth = planes prefetched ahead (variants 2, 3 and 4), 0 = automatic.
  * LAT_EUNSUPPORTED if the variant cannot run this lattice (a 27-point lattice
  * runs on variant 2 only; ty, zr and depth apply to it as above). */
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth);

@@ -116,7 +116,7 @@ lat_status launch_prepare(lat_handle* h)
 template <typename T>
 cudaError_t launch_step_with(lat_handle* h, const Bufs<T>& b, bool own_buffers)
 {
-    if (h->variant == 2) return launch_step_march<T>(b, h->M, h->sc, h->partials, h->mcfg, h->stream);
+    if (h->variant == 2 || h->variant == 4) return launch_step_march<T>(b, h->M, h->sc, h->partials, h->mcfg, h->stream);
     if (h->variant == 3) {
         if (own_buffers) return launch_step_tma<T>(b, h->M, h->sc, h->partials, h->tcfg, h->tmaps, h->stream);
         if (!h->alt_ok) {
@@ -168,7 +168,19 @@ lat_status read_scalars(lat_handle* h, DevScalars* out)
 lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
 {
     const int n = h->p.n;
-    if (variant < 0 || variant > 3) return LAT_EINVAL;
+    if (variant < 0 || variant > 4) return LAT_EINVAL;
+    if (variant == 4) {   // the x-tiled plane ring (7-point)
+        if (h->M.stencil == 27) return LAT_EUNSUPPORTED;
+        MarchConfig cfg;
+        if (!xt_config(n, (int)h->esize, ty, zr, depth, &cfg) || (size_t)cfg.blocks * kSums > h->partials_cap)
+            return LAT_EUNSUPPORTED;
+        h->mcfg = cfg;
+        h->ty = cfg.ty;
+        h->zr = cfg.zr;
+        h->variant = 4;
+        drop_graph(h);
+        return LAT_OK;
+    }
     if (h->M.stencil == 27) {   // the 27-point Laplacian runs on its plane-ring kernel only
         if (variant != 0 && variant != 2) return LAT_EUNSUPPORTED;
         MarchConfig cfg;
@@ -184,6 +196,20 @@ lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int dept
         return LAT_OK;
     }
     int chosen = 0;
+    if (variant == 0 && h->esize == 4 && n / 4 >= 128) {
+        // FP32 rows of 128 vectors or more: full-row tiles leave room for 4
+        // owned rows per 7 staged; x tiles of 32 vectors take 16 rows with two
+        // planes in flight (512^3: 0.89 ms per step against 0.98 ms)
+        MarchConfig cfg;
+        if (xt_config(n, 4, 16, 0, 2, &cfg) && (size_t)cfg.blocks * kSums <= h->partials_cap) {
+            h->mcfg = cfg;
+            h->ty = cfg.ty;
+            h->zr = cfg.zr;
+            h->variant = 4;
+            drop_graph(h);
+            return LAT_OK;
+        }
+    }
     if (variant == 0 || variant == 2) {
         MarchConfig cfg;
         if (march_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr, variant == 0 ? 0 : depth,
@@ -346,7 +372,7 @@ lat_status lat_set_g2(lat_handle* h, double g2)
 
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
 {
-    if (!h || variant < 0 || variant > 3 || ty < 0 || zr < 0 || depth < 0) return LAT_EINVAL;
+    if (!h || variant < 0 || variant > 4 || ty < 0 || zr < 0 || depth < 0) return LAT_EINVAL;
     if (h->slab) return LAT_ESTATE;
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     return configure_kernel(h, variant, ty, zr, depth);
@@ -356,7 +382,7 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8])
 {
     if (!h || !out) return LAT_EINVAL;
     out[0] = h->variant;
-    if (h->variant == 2) {
+    if (h->variant == 2 || h->variant == 4) {
         out[1] = h->mcfg.blocks; out[2] = h->mcfg.threads; out[3] = (int64_t)h->mcfg.smem;
     } else if (h->variant == 3) {
         out[1] = h->tcfg.blocks; out[2] = h->tcfg.threads; out[3] = (int64_t)h->tcfg.smem;
@@ -366,7 +392,7 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8])
     out[4] = 1;
     out[5] = h->ty;
     out[6] = h->zr;
-    out[7] = h->variant == 2 ? h->mcfg.depth : h->variant == 3 ? h->tcfg.depth : 0;
+    out[7] = (h->variant == 2 || h->variant == 4) ? h->mcfg.depth : h->variant == 3 ? h->tcfg.depth : 0;
     return LAT_OK;
 }
 

@@ -60,15 +60,15 @@ struct ScaleFwd {
 };
 
 // Recompute the forward scalar update from the scalars the step started from
-// (same formulas as scale_solve, with the intermediates kept).
-__device__ void scale_forward(const Model& M, const DevScalars& s, ScaleFwd& o)
+// (same formulas as scale_solve, with the intermediates kept). ia = 1/a.
+__device__ void scale_forward(const Model& M, const DevScalars& s, double ia, ScaleFwd& o)
 {
-    const double a = s.a, ia = 1.0 / a;
+    const double a = s.a;
     o.vpr = s.cdom * s.S[2] + s.kappa * s.S[3];
     o.ea = apow(a, ia, -2.0 * M.s - 2.0 * M.r - 1.0);
     o.eb = apow(a, ia, 2.0 * M.s + 2.0);
-    o.c = M.eight_pi_G / (M.A * M.A) * o.ea * ((s.S[0] + s.S[1]) / 3.0 + o.eb * o.vpr);
-    o.q = -(M.s + 2.0) / a;
+    o.c = M.g8A2 * o.ea * ((s.S[0] + s.S[1]) * (1.0 / 3.0) + o.eb * o.vpr);
+    o.q = -(M.s + 2.0) * ia;
     o.alpha = M.dt * o.q * 0.25;
     o.y = 2.0 * s.ad_half;
     o.ah = s.ad_half;
@@ -77,49 +77,52 @@ __device__ void scale_forward(const Model& M, const DevScalars& s, ScaleFwd& o)
 
 // Reverse of the scalar update of one step: given the adjoints of the
 // coefficients the kick used (bcL, bcF, bcd, bkp) and of y (from the a, a'
-// update), add to the adjoints of a, a', kappa0 and produce those of S.
+// update), add to the adjoints of a, a' and kappa0 (ba, bad, bk0, kept in
+// registers by the caller) and produce those of S. One reciprocal of a and one
+// of the solve's denominator serve every quotient (the FP64 pipe is narrow and
+// this runs in one thread).
 __device__ void scale_reverse(const Model& M, const DevScalars& s, double bcL, double bcF, double bcd, double bkp,
-                              double by, AdjScalars* as, double bS[4])
+                              double by, double& ba_io, double& bad_io, double& bk0_io, double bS[4])
 {
-    const double a = s.a, ia = 1.0 / a;
+    const double a = s.a, ia = 1.0 / a, ia2 = ia * ia;
     double ba = 0.0, bad = 0.0;
     for (int k = 0; k < 4; k++) bS[k] = 0.0;
     if (M.expansion) {
         ScaleFwd o;
-        scale_forward(M, s, o);
+        scale_forward(M, s, ia, o);
         const double r = M.r, sx = M.s;
-        const double hh = o.ah / a;
+        const double hh = o.ah * ia;
         // cF = r(s-r+2) h^2 + r a''/a, h = a'_half / a
         const double bh = bcF * 2.0 * r * (sx - r + 2.0) * hh;
-        const double badd = bcF * r / a;
-        ba -= bcF * r * o.add / (a * a);
-        double bah = bh / a;
-        ba -= bh * o.ah / (a * a);
+        const double badd = bcF * r * ia;
+        ba -= bcF * r * o.add * ia2;
+        double bah = bh * ia;
+        ba -= bh * o.ah * ia2;
         // a'' = q a'_half^2 + c
         double bq = badd * o.ah * o.ah;
         bah += badd * 2.0 * o.q * o.ah;
         double bc = badd;
         // a'_half = y / 2; y solves alpha y^2 - y + gamma = 0 with gamma = 2a' + dt c
         by += 0.5 * bah;
-        const double den = 1.0 - 2.0 * o.alpha * o.y;
-        const double bgamma = by / den, balpha = by * o.y * o.y / den;
+        const double iden = 1.0 / (1.0 - 2.0 * o.alpha * o.y);
+        const double bgamma = by * iden, balpha = by * o.y * o.y * iden;
         bq += balpha * M.dt * 0.25;
         bad += 2.0 * bgamma;
         bc += M.dt * bgamma;
-        ba += bq * (sx + 2.0) / (a * a);
+        ba += bq * (sx + 2.0) * ia2;
         // cL = a^(-2s-2)
         ba += bcL * (-2.0 * sx - 2.0) * apow(a, ia, -2.0 * sx - 3.0);
         // c = K ea (T + eb vpr)
-        const double K = M.eight_pi_G / (M.A * M.A);
-        const double T = (s.S[0] + s.S[1]) / 3.0;
+        const double K = M.g8A2;
+        const double T = (s.S[0] + s.S[1]) * (1.0 / 3.0);
         const double bea = bc * K * (T + o.eb * o.vpr);
         const double bT = bc * K * o.ea;
         const double beb = bc * K * o.ea * o.vpr;
         const double bvpr = bc * K * o.ea * o.eb;
         ba += bea * (-2.0 * sx - 2.0 * r - 1.0) * apow(a, ia, -2.0 * sx - 2.0 * r - 2.0);
         ba += beb * (2.0 * sx + 2.0) * apow(a, ia, 2.0 * sx + 1.0);
-        bS[0] = bT / 3.0;
-        bS[1] = bT / 3.0;
+        bS[0] = bT * (1.0 / 3.0);
+        bS[1] = bT * (1.0 / 3.0);
         bcd += bvpr * s.S[2];
         bkp += bvpr * s.S[3];
         bS[2] = bvpr * s.cdom;
@@ -127,9 +130,9 @@ __device__ void scale_reverse(const Model& M, const DevScalars& s, double bcL, d
     }
     // cdom = cdom0 a^pdom, kappa = kappa0 a^pint
     ba += bcd * M.cdom0 * M.pdom * apow(a, ia, M.pdom - 1.0) + bkp * M.kappa0 * M.pint * apow(a, ia, M.pint - 1.0);
-    as->bk0 += bkp * apow(a, ia, M.pint);
-    as->ba += ba;
-    as->bad += bad;
+    bk0_io += bkp * apow(a, ia, M.pint);
+    ba_io += ba;
+    bad_io += bad;
 }
 
 template <typename T>
@@ -162,30 +165,58 @@ __device__ void adj_finish(T acc[kSums], double* red, AdjScalars* as, const DevS
     __threadfence();
     if (tid >= 32) return;
     double v[kSums] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = tid; b < nblocks; b += 32)
+    // blocks tid, tid + 32, ... in order, four per pass so that their L2 loads
+    // are in flight together
+    const double2* p2 = reinterpret_cast<const double2*>(partials);   // kSums = 4 doubles per block
+    int b = tid;
+    for (; b + 96 < nblocks; b += 128) {
+        double2 x[4][2];
 #pragma unroll
-        for (int k = 0; k < kSums; k++) v[k] += __ldcg(partials + (size_t)b * kSums + k);
+        for (int j = 0; j < 4; j++) {
+            x[j][0] = __ldcg(p2 + (size_t)(b + 32 * j) * 2);
+            x[j][1] = __ldcg(p2 + (size_t)(b + 32 * j) * 2 + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            v[0] += x[j][0].x;
+            v[1] += x[j][0].y;
+            v[2] += x[j][1].x;
+            v[3] += x[j][1].y;
+        }
+    }
+    for (; b < nblocks; b += 32) {
+        const double2 x0 = __ldcg(p2 + (size_t)b * 2), x1 = __ldcg(p2 + (size_t)b * 2 + 1);
+        v[0] += x0.x;
+        v[1] += x0.y;
+        v[2] += x1.x;
+        v[3] += x1.y;
+    }
 #pragma unroll
     for (int k = 0; k < kSums; k++)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if (tid != 0) return;
+    // the scalar adjoints live in registers for the serial FP64 part
+    double ba = as->ba, bad = as->bad, bk0 = as->bk0;
     as->ticket = 0u;
     const DevScalars s = *hist;
     // reverse of a_{k} = a_{k-1} + dt a'_{k}, a'_{k} = y - a'_{k-1}
     double by = 0.0;
     if (M.expansion) {
-        by = as->bad + M.dt * as->ba;
-        as->bad = -by;
+        by = bad + M.dt * ba;
+        bad = -by;
     }
     const double bcL = M.dt * v[0] * M.inv_dx2, bcF = M.dt * v[1], bcd = -M.dt * v[2], bkp = -M.dt * v[3];
     double bS[4];
-    scale_reverse(M, s, bcL, bcF, bcd, bkp, by, as, bS);
-    bool finite = isfinite(as->ba) && isfinite(as->bad) && isfinite(as->bk0);
+    scale_reverse(M, s, bcL, bcF, bcd, bkp, by, ba, bad, bk0, bS);
+    bool finite = isfinite(ba) && isfinite(bad) && isfinite(bk0);
     for (int k = 0; k < 4; k++) {
         as->bS[k] = bS[k];
         finite = finite && isfinite(bS[k]);
     }
+    as->ba = ba;
+    as->bad = bad;
+    as->bk0 = bk0;
     as->cL = s.cL;
     as->cF = s.cF;
     as->cd = s.cdom;

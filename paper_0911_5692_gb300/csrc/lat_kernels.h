@@ -43,7 +43,8 @@ struct MarchConfig {
     int nzl = 0;   // z-slab: owned planes (0: a whole periodic lattice)
     int zbase = 0; // z-slab: stored plane of z = z + zbase
     int s27 = 0;   // 1: the 27-point Laplacian kernel (lat_step27.cu)
-    int nxt = 1;   // 27-point kernel: x tiles per row
+    int nxt = 1;   // 27-point and x-tiled kernels: x tiles per row
+    int xt = 0;    // 1: the x-tiled 7-point kernel (lat_step_xt.cu)
 };
 // kernel specialised for (element bytes, N, ty, depth), or null; *smem gets its
 // dynamic shared memory in bytes
@@ -58,6 +59,12 @@ bool march_slab_config(int n, int elem_bytes, int nzl, MarchConfig* cfg);
 template <typename T>
 cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                               const MarchConfig& cfg, cudaStream_t st, double* sums_out = nullptr);
+// the same ring with x tiles of at most 32 (or 16) vectors and taller y tiles
+// (whole periodic lattices)
+bool xt_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
+template <typename T>
+cudaError_t launch_step_xt(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
+                           cudaStream_t st);
 // the same ring with the 27-point Laplacian (whole periodic lattices)
 bool march27_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
 template <typename T>

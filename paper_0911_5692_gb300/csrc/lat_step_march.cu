@@ -209,6 +209,10 @@ template <typename T>
 cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                               const MarchConfig& cfg, cudaStream_t st, double* sums_out)
 {
+    if (cfg.xt) {
+        if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
+        return launch_step_xt<T>(b, M, sc, partials, cfg, st);
+    }
     if (cfg.s27) {
         if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
         return launch_step27<T>(b, M, sc, partials, cfg, st);

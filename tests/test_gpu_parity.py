@@ -18,7 +18,7 @@ from paper_0911_5692_gb300.workloads import lphi4, m2phi2, random_state
 pytestmark = pytest.mark.gpu
 
 TOL = {32: 2e-6, 64: 1e-12}
-VARIANTS = [1, 2, 3]
+VARIANTS = [1, 2, 3, 4]
 
 
 def _params(model, n, prec, expansion):
@@ -404,3 +404,45 @@ def test_upload_state_is_set_state(src):
     for x, y in zip(a.get_state(), b.get_state()):
         assert np.array_equal(x, y)
     assert a.scalars() == b.scalars()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("n,ty", [(4, 0), (16, 0), (36, 4), (64, 8), (64, 16), (128, 32), (136, 8), (264, 8),
+                                  (200, 8)])
+def test_xtile_kernel_geometries(n, ty, prec):
+    """Variant 4 (x tiles of at most 32 or 16 vectors, taller y tiles) over tile
+    heights and sides whose rows split into ragged x tiles, against the oracle:
+    five FP64 steps (an indexing mistake shows far above 1e-12), one FP32 step
+    (the per-step FP32 bound; FP32 rounding of the degenerate N = 4 lattice,
+    dt = 0.125, grows past five times it over five steps)."""
+    p = lphi4(n, precision=prec)
+    st = _state("lphi4", n, prec, seed=n + ty)
+    g, o = paired(p, st, (0.0, 1.1, 0.45, 0))
+    try:
+        g.set_kernel(4, ty, 0, 0)
+    except LatticeError:
+        pytest.skip("geometry does not fit")
+    info = g.kernel_info()
+    assert info["variant"] == 4 and (ty == 0 or info["ty"] == ty)
+    g.set_state(*st, t=0.0, a=1.1, ad=0.45, step=0)
+    steps = 5 if prec == 64 else 1
+    g.evolve(steps)
+    o.step(steps)
+    compare_states(g, o, steps * TOL[prec], f"x tiles N={n} ty={ty} fp{prec}")
+
+
+def test_xtile_kernel_full_size_512():
+    """Variant 4 on the 512^3 lambda phi^4 lattice (FP32): one step against the
+    oracle's full-lattice step."""
+    n = 512
+    p = _params("lphi4", n, 32, 1)
+    st = _state("lphi4", n, 32, seed=79)
+    g = Lattice(p)
+    g.set_kernel(4)
+    g.set_state(*st, t=0.0, a=1.02, ad=0.5)
+    o = Oracle(p)
+    o.set_state(*st, t=0.0, a=1.02, ad=0.5)
+    del st
+    g.evolve(1)
+    o.step(1)
+    compare_states(g, o, TOL[32], "x tiles full size 512")
