@@ -87,12 +87,14 @@ STEP_KERNEL_SOURCES = {
 }
 
 
-def kernel_source_hash(stencil=7):
-    """Hash of the sources the fused step kernels of a stencil are built from (a
-    recorded DRAM-traffic figure is valid only for these exact sources)."""
+def kernel_source_hash(stencil=7, variant=2):
+    """Hash of the sources the fused step kernels of a stencil (and, for the
+    x-tiled variant 4, its own file) are built from: a recorded DRAM-traffic
+    figure is valid only for these exact sources."""
     d = os.path.join(ROOT, "paper_0911_5692_gb300", "csrc")
     h = hashlib.sha256()
-    for f in STEP_KERNEL_SOURCES[stencil]:
+    files = STEP_KERNEL_SOURCES[stencil] + (("lat_step_xt.cu",) if variant == 4 else ())
+    for f in files:
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
@@ -113,7 +115,7 @@ def traffic_record(name, variant, stencil=7):
         recs = json.load(open(path))
     except Exception:
         return None
-    hsh = kernel_source_hash(stencil)
+    hsh = kernel_source_hash(stencil, variant)
     for r in recs.get("records", []):
         if (r.get("kernel_hash") == hsh and r.get("workload") == name and r.get("variant") == variant
                 and r.get("stencil", 7) == stencil):
