@@ -198,7 +198,8 @@ lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes);
 lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
 
 /* Choose the step kernel (all compute the same step): variant 0 = automatic
- * (4 for FP32 lattices with N >= 512, else 2 where it fits, else 1), 1 = one
+ * (4 where a row is 128 or more 16-byte vectors: FP32 N >= 512, FP64 N >= 256;
+ * else 2 where it fits, else 1), 1 = one
  * site per thread with cached loads,
  * 2 = z-march through a shared-memory plane ring filled by per-thread
  * asynchronous copies (the fast path), 3 = plane ring filled by TMA boxes,

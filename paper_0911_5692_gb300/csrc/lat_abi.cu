@@ -196,12 +196,13 @@ lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int dept
         return LAT_OK;
     }
     int chosen = 0;
-    if (variant == 0 && h->esize == 4 && n / 4 >= 128) {
-        // FP32 rows of 128 vectors or more: full-row tiles leave room for 4
-        // owned rows per 7 staged; x tiles of 32 vectors take 16 rows with two
-        // planes in flight (512^3: 0.89 ms per step against 0.98 ms)
+    if (variant == 0 && n / (16 / (int)h->esize) >= 128) {
+        // rows of 128 16-byte vectors or more: full-row tiles leave room for at
+        // most 4 owned rows per 7 staged; x tiles of 32 vectors take 16 rows with
+        // two planes in flight (FP32 512^3: 0.89 ms per step against 0.98 ms;
+        // FP64 512^3: 16 ms against 24 ms, 256^3: 2.04 against 2.10 ms)
         MarchConfig cfg;
-        if (xt_config(n, 4, 16, 0, 2, &cfg) && (size_t)cfg.blocks * kSums <= h->partials_cap) {
+        if (xt_config(n, (int)h->esize, 16, 0, 2, &cfg) && (size_t)cfg.blocks * kSums <= h->partials_cap) {
             h->mcfg = cfg;
             h->ty = cfg.ty;
             h->zr = cfg.zr;

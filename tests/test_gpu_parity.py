@@ -446,3 +446,20 @@ def test_xtile_kernel_full_size_512():
     g.evolve(1)
     o.step(1)
     compare_states(g, o, TOL[32], "x tiles full size 512")
+
+
+def test_fp64_full_size_default_kernel():
+    """FP64 rows of 128 vectors take the x-tiled kernel by default: one 256^3
+    FP64 step against the oracle at the FP64 bound."""
+    n = 256
+    p = _params("m2phi2", n, 64, 1)
+    st = _state("m2phi2", n, 64, seed=80)
+    g = Lattice(p)
+    assert g.kernel_info()["variant"] == 4
+    g.set_state(*st, t=0.0, a=1.02, ad=0.5)
+    o = Oracle(p)
+    o.set_state(*st, t=0.0, a=1.02, ad=0.5)
+    del st
+    g.evolve(1)
+    o.step(1)
+    compare_states(g, o, TOL[64], "FP64 full size 256, default kernel")
