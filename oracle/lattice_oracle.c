@@ -51,6 +51,17 @@
  *                      neighbours (each neighbour pair shared evenly by its two
  *                      sites), so that the volume means are the averages above.
  *   spectrum           Sec. IV (named as future work): shell-binned |f_k|^2.
+ *   L = 1/H form       Sec. II.B mentions that DEFROST evolves L = 1/H first and a
+ *                      from L, which removes the gradient terms; the paper prints no
+ *                      equation for it. Here (expansion = 2), from the acceleration
+ *                      equation a-double-dot/a = -(4piG/3)(rho + 3p), rho + 3p =
+ *                      2 sum phidot^2 - 2V, in program time with h = a'/a, l = 1/h:
+ *                        l' = (s + 1) + Gamma l^2,  a' = a / l,  a''/a = -s h^2 - Gamma,
+ *                        Gamma = (8piG/(3A^2)) a^(-2r) (sum_i <(f_i' - r h f_i)^2> - <V_pr>),
+ *                      so the f coefficient of eq. scalar-evo is r(2-r) h^2 - r Gamma.
+ *                      Staggering: l at the momentum times (with a'), a at the field
+ *                      times; the step is the implicit midpoint rule for l (solved
+ *                      by fixed-point iteration) and a_{n+3/2} = a_{n+1/2} exp(dt/l_{n+1}).
  *
  * Counter-based random numbers: Philox-4x32-10 (J. Salmon, M. Moraes, R. Dror,
  * D. Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11), normals by the
@@ -74,7 +85,7 @@
 typedef struct {
     int32_t n;          /* lattice is n^3 */
     int32_t model;      /* 0: V = lambda/4 phi^4 + g2/2 phi^2 chi^2; 1: V = m^2/2 phi^2 + g2/2 phi^2 chi^2 */
-    int32_t expansion;  /* 0: static space, a = 1; 1: FRW */
+    int32_t expansion;  /* 0: static space, a = 1; 1: FRW, eq. scale; 2: FRW, L = 1/H form */
     int32_t stencil;    /* Laplacian: 7 (or 0) = 7-point, 27 = 27-point (Sec. II.C) */
     double L, dt;       /* box side and time step, program units */
     double lambda, m, g2;
@@ -99,6 +110,7 @@ typedef struct {
     double ad;     /* a' at t */
     double S[4];   /* <|grad f0|^2>, <|grad f1|^2>, <f0^beta/beta>, <f0^2 f1^2/2> at field time */
     int64_t step;
+    double ell;    /* L = 1/H form: l = a/a' (program time) at t */
 } orc_lattice;
 
 static size_t idx(int n, int x, int y, int z) { return ((size_t)z * n + y) * n + x; }
@@ -162,6 +174,7 @@ int orc_create(const orc_params *p, orc_lattice **out)
     *out = NULL;
     if (p->n < 2 || p->n > 1024 || p->L <= 0.0 || p->dt <= 0.0) return ORC_EINVAL;
     if (p->stencil != 0 && p->stencil != 7 && p->stencil != 27) return ORC_EINVAL;
+    if (p->expansion < 0 || p->expansion > 2) return ORC_EINVAL;
     orc_lattice *L = (orc_lattice *)calloc(1, sizeof(orc_lattice));
     if (!L) return ORC_ENOMEM;
     L->p = *p;
@@ -370,6 +383,69 @@ static void field_coefficients(const orc_lattice *L, double a, double ad_half, d
     *cF = L->r * (L->s - L->r + 2.0) * h * h + L->r * add / a;
 }
 
+/* ---------------------------------------------------------------- L = 1/H form */
+
+/* l at the momentum time t from a at the field time t + dt/2 and a' at t:
+ * l = a_t / a'_t with a_t = a - (dt/2) a' (the state stores no a at t). */
+static double ell_of(double a, double ad, double dt) { return (a - 0.5 * dt * ad) / ad; }
+
+typedef struct {
+    double cL, cF;      /* coefficients of eq. scalar-evo at the field time */
+    double ad_half;     /* a' at the field time: a h */
+    double add;         /* a'' at the field time: a (-s h^2 - Gamma) */
+    double ad_next;     /* (a_{n+3/2} - a_{n+1/2}) / dt */
+    double ell_next;    /* l_{n+1} */
+} orc_lform;
+
+/* The implicit step of the L form at the current field time. Ft_i = cL Lap f_i -
+ * dV_pr/df_i (the acceleration without the cF f term). Unknowns l_{n+1} and cF,
+ * with Lambda = (l_n + l_{n+1})/2, h = 1/Lambda and the momenta at the field time
+ * pi_n + (dt/2)(Ft + cF f):
+ *   Gamma    = (8piG/(3A^2)) a^(-2r) (sum_i <(pi_i + (dt/2)(Ft_i + cF f_i) - r h f_i)^2> - <V_pr>)
+ *   cF       = r(2-r) h^2 - r Gamma
+ *   l_{n+1}  = l_n + dt ((s + 1) + Gamma Lambda^2).
+ * Fixed-point iteration from cF = 0, l_{n+1} = l_n, each pass taking the volume
+ * average afresh, until neither unknown changes by more than 1e-15 relative. */
+static int lform_solve(const orc_lattice *L, const double *Ft0, const double *Ft1, orc_lform *o)
+{
+    const double a = L->a, dt = L->p.dt, r = L->r, s = L->s;
+    const double g = L->p.eight_pi_G / (3.0 * L->A * L->A) * pow(a, -2.0 * r);
+    const double *f0 = L->f[0], *f1 = L->f[1], *p0 = L->pi[0], *p1 = L->pi[1];
+    if (!isfinite(L->ell) || L->ell == 0.0) return ORC_EINVAL;
+    double W = 0.0;
+    for (size_t k = 0; k < L->nsites; k++) W += Vpr(L, a, f0[k], f1[k]);
+    W /= (double)L->nsites;
+    double ell_next = L->ell, cF = 0.0, Gam = 0.0;
+    int converged = 0;
+    for (int it = 0; it < 200 && !converged; it++) {
+        double Lam = 0.5 * (L->ell + ell_next), h = 1.0 / Lam;
+        double P = 0.0;
+        for (size_t k = 0; k < L->nsites; k++) {
+            double v0 = p0[k] + 0.5 * dt * (Ft0[k] + cF * f0[k]) - r * h * f0[k];
+            double v1 = p1[k] + 0.5 * dt * (Ft1[k] + cF * f1[k]) - r * h * f1[k];
+            P += v0 * v0 + v1 * v1;
+        }
+        P /= (double)L->nsites;
+        Gam = g * (P - W);
+        double cF_new = r * (2.0 - r) * h * h - r * Gam;
+        double ell_new = L->ell + dt * ((s + 1.0) + Gam * Lam * Lam);
+        if (!isfinite(cF_new) || !isfinite(ell_new)) return ORC_ENONFINITE;
+        converged = fabs(ell_new - ell_next) <= 1e-15 * fabs(ell_new)
+                 && fabs(cF_new - cF) <= 1e-15 * (fabs(cF_new) + h * h);
+        cF = cF_new;
+        ell_next = ell_new;
+    }
+    if (!converged) return ORC_ENONFINITE;
+    double h = 2.0 / (L->ell + ell_next);
+    o->cL = pow(a, -2.0 * s - 2.0);
+    o->cF = cF;
+    o->ad_half = a * h;
+    o->add = a * (-s * h * h - Gam);
+    o->ad_next = (a * exp(dt / ell_next) - a) / dt;
+    o->ell_next = ell_next;
+    return ORC_OK;
+}
+
 /* ---------------------------------------------------------------- leapfrog */
 
 /* acceleration F_i = cL Lap f_i + cF f_i - dV_pr/df_i at the field time */
@@ -387,21 +463,47 @@ static void accelerations(const orc_lattice *L, double cL, double cF, double *F0
     }
 }
 
+/* The coefficients of the next step at the current field time, from eq. scale
+ * (expansion 1) or the L form (expansion 2), and the accelerations
+ * F_i = cL Lap f_i + cF f_i - dV_pr/df_i they give. */
+static int step_setup(const orc_lattice *L, double *F0, double *F1, double *cL, double *cF, double *ad_next,
+                      double *ad_half, double *add, double *ell_next)
+{
+    *cL = 1.0; *cF = 0.0; *ad_next = 0.0; *ad_half = 0.0; *add = 0.0; *ell_next = L->ell;
+    if (L->p.expansion == 1) {
+        int st = orc_scale_update(L, ad_next, ad_half, add);
+        if (st != ORC_OK) return st;
+        field_coefficients(L, L->a, *ad_half, *add, cL, cF);
+    }
+    if (L->p.expansion == 2) {
+        *cL = pow(L->a, -2.0 * L->s - 2.0);
+        accelerations(L, *cL, 0.0, F0, F1);
+        orc_lform o;
+        int st = lform_solve(L, F0, F1, &o);
+        if (st != ORC_OK) return st;
+        *cF = o.cF; *ad_next = o.ad_next; *ad_half = o.ad_half; *add = o.add; *ell_next = o.ell_next;
+        for (size_t k = 0; k < L->nsites; k++) {
+            F0[k] += o.cF * L->f[0][k];
+            F1[k] += o.cF * L->f[1][k];
+        }
+        return ORC_OK;
+    }
+    accelerations(L, *cL, *cF, F0, F1);
+    return ORC_OK;
+}
+
 /* one step of eq. evo for both fields and for a:
  *   pi_{n+1}    = pi_n + dt F(f_{n+1/2})           (kick, both fields from the same f)
  *   f_{n+3/2}   = f_{n+1/2} + dt pi_{n+1}           (drift)
  *   a_{n+3/2}   = a_{n+1/2} + dt a'_{n+1}
- * then the sums are recomputed at the new field time. */
+ * (in the L form a'_{n+1} is (a_{n+3/2} - a_{n+1/2})/dt with a_{n+3/2} from l_{n+1},
+ * and l advances to l_{n+1}); then the sums are recomputed at the new field time. */
 static int one_step(orc_lattice *L, double *F0, double *F1)
 {
-    double cL = 1.0, cF = 0.0, ad_next = 0.0, ad_half = 0.0, add = 0.0;
-    if (L->p.expansion) {
-        int st = orc_scale_update(L, &ad_next, &ad_half, &add);
-        if (st != ORC_OK) return st;
-        field_coefficients(L, L->a, ad_half, add, &cL, &cF);
-    }
+    double cL, cF, ad_next, ad_half, add, ell_next;
+    int st = step_setup(L, F0, F1, &cL, &cF, &ad_next, &ad_half, &add, &ell_next);
+    if (st != ORC_OK) return st;
     double dt = L->p.dt;
-    accelerations(L, cL, cF, F0, F1);
     double *f0 = L->f[0], *f1 = L->f[1], *p0 = L->pi[0], *p1 = L->pi[1];
 #pragma omp parallel for schedule(static)
     for (long long i = 0; i < (long long)L->nsites; i++) {
@@ -416,6 +518,7 @@ static int one_step(orc_lattice *L, double *F0, double *F1)
     if (L->p.expansion) {
         L->a += dt * ad_next;
         L->ad = ad_next;
+        L->ell = ell_next;
     }
     L->t += dt;
     L->step += 1;
@@ -441,8 +544,13 @@ int orc_step(orc_lattice *L, int64_t nsteps)
 void orc_set_scalars(orc_lattice *L, double t, double a, double ad, int64_t step)
 {
     L->t = t; L->a = a; L->ad = ad; L->step = step;
+    L->ell = ell_of(a, ad, L->p.dt);
     orc_sums(L);
 }
+
+/* The L form's l = 1/h at the momentum time (set_scalars derives it from a and a'). */
+double orc_get_ell(const orc_lattice *L) { return L->ell; }
+void orc_set_ell(orc_lattice *L, double ell) { L->ell = ell; }
 
 /* ---------------------------------------------------------------- random numbers */
 
@@ -650,6 +758,7 @@ int orc_init_fields(orc_lattice *L)
     for (int i = 0; i < 2; i++)
         for (size_t k = 0; k < L->nsites; k++) L->f[i][k] += 0.5 * dt * L->pi[i][k];
     if (p->expansion) L->a += 0.5 * dt * L->ad;
+    L->ell = ell_of(L->a, L->ad, dt);
     orc_sums(L);
     return ORC_OK;
 }
@@ -692,15 +801,11 @@ static double site_grad2(const orc_lattice *L, const double *f, int x, int y, in
  * V = V_pr. */
 int orc_energy_field(orc_lattice *L, double *rho_out, double *p_out)
 {
-    double cL = 1.0, cF = 0.0, ad_next = 0.0, ad_half = 0.0, add = 0.0;
-    if (L->p.expansion) {
-        int st = orc_scale_update(L, &ad_next, &ad_half, &add);
-        if (st != ORC_OK) return st;
-        field_coefficients(L, L->a, ad_half, add, &cL, &cF);
-    }
+    double cL, cF, ad_next, ad_half, add, ell_next;
     double *F0 = (double *)malloc(L->nsites * sizeof(double)), *F1 = (double *)malloc(L->nsites * sizeof(double));
     if (!F0 || !F1) { free(F0); free(F1); return ORC_ENOMEM; }
-    accelerations(L, cL, cF, F0, F1);
+    int st = step_setup(L, F0, F1, &cL, &cF, &ad_next, &ad_half, &add, &ell_next);
+    if (st != ORC_OK) { free(F0); free(F1); return st; }
     int n = L->n;
     double a = L->a, h = L->p.expansion ? ad_half / a : 0.0, dt = L->p.dt;
     double cg = pow(a, -2.0 * L->s - 2.0);
@@ -727,15 +832,11 @@ int orc_energy_field(orc_lattice *L, double *rho_out, double *p_out)
 
 int orc_energies(orc_lattice *L, double out[17])
 {
-    double cL = 1.0, cF = 0.0, ad_next = 0.0, ad_half = 0.0, add = 0.0;
-    if (L->p.expansion) {
-        int st = orc_scale_update(L, &ad_next, &ad_half, &add);
-        if (st != ORC_OK) return st;
-        field_coefficients(L, L->a, ad_half, add, &cL, &cF);
-    }
+    double cL, cF, ad_next, ad_half, add, ell_next;
     double *F0 = (double *)malloc(L->nsites * sizeof(double)), *F1 = (double *)malloc(L->nsites * sizeof(double));
     if (!F0 || !F1) { free(F0); free(F1); return ORC_ENOMEM; }
-    accelerations(L, cL, cF, F0, F1);
+    int st = step_setup(L, F0, F1, &cL, &cF, &ad_next, &ad_half, &add, &ell_next);
+    if (st != ORC_OK) { free(F0); free(F1); return st; }
     double a = L->a, h = L->p.expansion ? ad_half / a : 0.0, dt = L->p.dt;
     double kin[2] = {0, 0}, mean[2] = {0, 0}, var[2] = {0, 0}, pot = 0.0;
     for (int i = 0; i < 2; i++) {
@@ -960,6 +1061,7 @@ static double volume_sum(int n, const double *v)
 
 int orc_adjoint(orc_lattice *L, int64_t nsteps, double *fbar[2], double *pibar[2], double sbar[4])
 {
+    if (L->p.expansion == 2) return ORC_EINVAL;   /* the reverse pass follows eq. scale only */
     const size_t N3 = L->nsites;
     const int n = L->n;
     const double dt = L->p.dt, beta = L->beta;
@@ -1045,6 +1147,7 @@ int orc_adjoint(orc_lattice *L, int64_t nsteps, double *fbar[2], double *pibar[2
  * averages themselves (domain-decomposed runs in the tests). */
 int orc_step_coefs(const orc_lattice *L, double a, double ad, const double S[4], double out[5])
 {
+    if (L->p.expansion == 2) return ORC_EINVAL;
     orc_coefs o;
     int st = step_coefs(L, a, ad, S, &o);
     out[0] = o.cL; out[1] = o.cF; out[2] = o.cd; out[3] = o.kp; out[4] = o.y;

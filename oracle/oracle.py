@@ -68,6 +68,9 @@ def lib():
             L.orc_array.restype = dp
             L.orc_get_scalars.argtypes = [P, dp]
             L.orc_set_scalars.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int64]
+            L.orc_get_ell.argtypes = [P]
+            L.orc_get_ell.restype = C.c_double
+            L.orc_set_ell.argtypes = [P, C.c_double]
             L.orc_laplacian.argtypes = [C.c_int, C.c_double, dp, dp]
             L.orc_grad2_mean.argtypes = [C.c_int, C.c_double, dp]
             L.orc_grad2_mean.restype = C.c_double
@@ -174,6 +177,13 @@ class Oracle:
         out = (C.c_double * 8)()
         self._L.orc_get_scalars(self._h, out)
         return {"t": out[0], "a": out[1], "ad": out[2], "step": int(out[3]), "S": list(out[4:8])}
+
+    def ell(self) -> float:
+        """The L = 1/H form's l = a/a' (program time) at the momentum time."""
+        return self._L.orc_get_ell(self._h)
+
+    def set_ell(self, ell: float):
+        self._L.orc_set_ell(self._h, float(ell))
 
     def init_fields(self):
         _check(self._L.orc_init_fields(self._h), "orc_init_fields")
