@@ -405,7 +405,9 @@ typedef struct {
  *   cF       = r(2-r) h^2 - r Gamma
  *   l_{n+1}  = l_n + dt ((s + 1) + Gamma Lambda^2).
  * Fixed-point iteration from cF = 0, l_{n+1} = l_n, each pass taking the volume
- * average afresh, until neither unknown changes by more than 1e-15 relative. */
+ * average afresh, until neither unknown changes by more than 1e-13 relative to
+ * the size of its terms (the iteration contracts by about dt h per pass; below
+ * that it cycles through a few rounding levels). */
 static int lform_solve(const orc_lattice *L, const double *Ft0, const double *Ft1, orc_lform *o)
 {
     const double a = L->a, dt = L->p.dt, r = L->r, s = L->s;
@@ -430,8 +432,9 @@ static int lform_solve(const orc_lattice *L, const double *Ft0, const double *Ft
         double cF_new = r * (2.0 - r) * h * h - r * Gam;
         double ell_new = L->ell + dt * ((s + 1.0) + Gam * Lam * Lam);
         if (!isfinite(cF_new) || !isfinite(ell_new)) return ORC_ENONFINITE;
-        converged = fabs(ell_new - ell_next) <= 1e-15 * fabs(ell_new)
-                 && fabs(cF_new - cF) <= 1e-15 * (fabs(cF_new) + h * h);
+        /* rounding leaves a cycle of a few ulps of the terms of cF and l */
+        converged = fabs(ell_new - ell_next) <= 1e-13 * fabs(ell_new)
+                 && fabs(cF_new - cF) <= 1e-13 * fabs(r) * (fabs(2.0 - r) * h * h + fabs(Gam));
         cF = cF_new;
         ell_next = ell_new;
     }
@@ -441,7 +444,7 @@ static int lform_solve(const orc_lattice *L, const double *Ft0, const double *Ft
     o->cF = cF;
     o->ad_half = a * h;
     o->add = a * (-s * h * h - Gam);
-    o->ad_next = (a * exp(dt / ell_next) - a) / dt;
+    o->ad_next = a * expm1(dt / ell_next) / dt;   /* a_{n+3/2} - a_{n+1/2} = a (exp(dt/l) - 1) */
     o->ell_next = ell_next;
     return ORC_OK;
 }
