@@ -46,6 +46,8 @@ def parse():
                          "4 plane ring over x tiles")
     ap.add_argument("--stencil", type=int, choices=[7, 27], default=7,
                     help="Laplacian: 7-point, or the paper's 27-point stencil (Sec. II.C)")
+    ap.add_argument("--expansion", type=int, choices=[1, 2], default=1,
+                    help="scale-factor update: 1 eq. scale, 2 the L = 1/H form (one more pass per step)")
     ap.add_argument("--ty", type=int, default=0)
     ap.add_argument("--zr", type=int, default=0)
     ap.add_argument("--depth", type=int, default=0)
@@ -74,7 +76,9 @@ def config_of(name, p, world):
     state = 8 * n ** 3 * esize
     return {"workload": name, "model": model_name(p), "stencil": int(p.get("stencil", 7)), "n": n, "sites": n ** 3,
             "precision": p["precision"],
-            "expansion": bool(p["expansion"]), "global_batch": world, "lattices_per_gpu": 1,
+            "expansion": bool(p["expansion"]),
+            "scale_factor": {0: "static", 1: "eq. scale", 2: "L = 1/H form"}[int(p["expansion"])],
+            "global_batch": world, "lattices_per_gpu": 1,
             "parallelism": "replicas" if world > 1 else "single",
             "l2": f"inputs larger than L2: {state / 2 / 1e6:.0f} MB read + {state / 2 / 1e6:.0f} MB written per step"
                   if state / 2 > L2_BYTES else "state fits in L2"}
@@ -395,6 +399,50 @@ def measure_step(local, name="lphi4_512_fp32", steps=300):
                        "ty": info["ty"], "depth": info["depth"]}}
 
 
+def measure_lform(local, name, steps=320):
+    """The L = 1/H form of the scale-factor update (DEFROST's choice, Sec. II.B)
+    against eq. scale on the benchmark workload: per-step time of each (CUDA
+    events over graph replays, the two runs alternated twice, best of each), the
+    extra read-only pass's cost as their difference and its bandwidth against
+    its 16 B (FP32) of algorithmic reads per site."""
+    import torch
+    from paper_0911_5692_gb300 import Lattice
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and peaks.get("hbm_gbs") else FALLBACK_HBM_GBS
+    base = workload(name)
+    n = base["n"]
+    esize = 4 if base["precision"] == 32 else 8
+    lats = {}
+    for e in (1, 2):
+        lat = Lattice(dict(base, expansion=e), device=local)
+        lat.init_fields()
+        lat.evolve(64)
+        lat.sync()
+        lats[e] = lat
+    best = {1: float("inf"), 2: float("inf")}
+    for _ in range(2):
+        for e in (1, 2):
+            lat = lats[e]
+            s = torch.cuda.Event(enable_timing=True)
+            t = torch.cuda.Event(enable_timing=True)
+            s.record(lat.stream)
+            lat.evolve(steps)
+            t.record(lat.stream)
+            lat.sync()
+            best[e] = min(best[e], s.elapsed_time(t) / steps)
+    a1, a2 = lats[1].scalars()["a"], lats[2].scalars()["a"]
+    info = lats[2].kernel_info()
+    for lat in lats.values():
+        lat.close()
+    pass_ms = best[2] - best[1]
+    gbs = 4 * esize * n ** 3 / (pass_ms / 1e3) / 1e9 if pass_ms > 0 else None
+    return {"workload": name, "steps": steps, "ms_per_step_eq_scale": best[1], "ms_per_step_lform": best[2],
+            "value": n ** 3 / (best[2] / 1e3), "unit": UNIT, "lform_pass_ms": pass_ms,
+            "lform_pass_GBs": gbs, "lform_pass_hbm_frac": gbs / peak if gbs else None,
+            "launches_per_step": info["launches_per_step"],
+            "a_rel_gap_after_run": a2 / a1 - 1.0}
+
+
 def measure_fp32_error(local, name, steps=200):
     """FP32 against FP64 on the GPU for the benchmark workload: both precisions
     from the same initial state (FP64 initialisation rounded to FP32), `steps`
@@ -435,7 +483,7 @@ def run_reference(args):
     import numpy as np
     from oracle.oracle import Oracle
     from paper_0911_5692_gb300.workloads import random_state
-    p = dict(workload(args.workload), stencil=args.stencil)
+    p = dict(workload(args.workload), stencil=args.stencil, expansion=args.expansion)
     n_full = p["n"]
     # per-site cost from a short calibration, then the sample lattice that keeps
     # the whole (warmup + steps) run near 90 s
@@ -484,7 +532,7 @@ def run_ours(args):
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    p = dict(workload(args.workload), stencil=args.stencil)
+    p = dict(workload(args.workload), stencil=args.stencil, expansion=args.expansion)
     p["seed"] = p.get("seed", 0) + rank          # independent replica per rank
     n = p["n"]
     esize = 4 if p["precision"] == 32 else 8
@@ -594,6 +642,7 @@ def run_ours(args):
         line["ensemble"] = measure_ensemble(local)
         line["stencil27"] = measure_stencil27(local)
         line["diagnostics"] = measure_diagnostics(local, args.workload)
+        line["lform"] = measure_lform(local, args.workload)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     print(json.dumps(line), flush=True)

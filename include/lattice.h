@@ -55,7 +55,8 @@ typedef struct {
     int32_t n;            /* lattice side N (N^3 sites); 4 <= N <= 1024, N % 4 == 0 */
     int32_t precision;    /* 32 or 64: storage and arithmetic of fields and momenta */
     int32_t model;        /* LAT_MODEL_* */
-    int32_t expansion;    /* 0: static space (a = 1, a' = 0); 1: FRW, eq. scale */
+    int32_t expansion;    /* 0: static space (a = 1, a' = 0); 1: FRW, eq. scale;
+                             2: FRW through L = 1/H (lat_get_hubble_length) */
     double L;             /* box side, program units; dx = L / N */
     double dt;            /* time step, program units */
     double lambda, m, g2; /* physical couplings (Planck units fixed by eight_pi_G) */
@@ -180,8 +181,35 @@ lat_status lat_upload_state(lat_handle* h, const void* const src[4], int src_is_
 lat_status lat_get_scalars(lat_handle* h, double out[8]);
 
 /* Set t, a (at t + dt/2), a' (at t) and the step count from in[0..3]; the sums
- * and coefficients are recomputed before the next step. */
+ * and coefficients are recomputed before the next step. With expansion = 2 the
+ * Hubble length l at t is set to a_t / a' with a_t = a - (dt/2) a'; LAT_EINVAL
+ * there for a' = 0. */
 lat_status lat_set_scalars(lat_handle* h, const double in[4]);
+
+/* The L = 1/H form of the scale-factor update (expansion = 2; Sec. II.B notes
+ * that DEFROST evolves L = 1/H first and a from it, so that no gradient average
+ * enters, and prints no equation for it). In program time, with h = a'/a and
+ * the Hubble length l = 1/h (physical L = a^(-s) l / B), the acceleration
+ * equation a-double-dot/a = -(4 pi G/3)(rho + 3p), rho + 3p = 2 sum phidot^2 - 2V,
+ * gives
+ *   l' = (s + 1) + Gamma l^2,   a' = a / l,   a''/a = -s h^2 - Gamma,
+ *   Gamma = (8 pi G / (3 A^2)) a^(-2r) (sum_i <(f_i' - r h f_i)^2> - <V_pr>),
+ * and the f coefficient of eq. scalar-evo becomes r(2 - r) h^2 - r Gamma. l is
+ * stored at the momentum time t (with a'), a at the field time. A step solves
+ * the implicit midpoint equations for l_{n+1} and that coefficient, with the
+ * momenta at the field time taken as the mean of the kick's two ends, then sets
+ * a_{n+3/2} = a_{n+1/2} exp(dt / l_{n+1}); the a' reported after it is
+ * (a_{n+3/2} - a_{n+1/2}) / dt. The L form does not impose the Friedmann
+ * constraint: an initial mismatch is carried as spatial curvature
+ * K = a^2 (H^2 - 8 pi G rho / 3), which it conserves. It cannot pass a = const
+ * (H = 0, l infinite): a recollapsing lattice raises LAT_ENONFINITE there. Each
+ * step takes one extra read-only pass over the four state arrays (its sums
+ * need the Laplacian of the fields at the field time).
+ * lat_get_hubble_length writes l at t (Synchronises); lat_set_hubble_length
+ * sets it (after lat_set_scalars, which derives it from a and a'). Both return
+ * LAT_ESTATE unless expansion = 2; set: LAT_EINVAL for l = 0 or not finite. */
+lat_status lat_get_hubble_length(lat_handle* h, double* ell);
+lat_status lat_set_hubble_length(lat_handle* h, double ell);
 
 /* Wait for the handle's stream; return a sticky device error if one is set. */
 lat_status lat_sync(lat_handle* h);
@@ -270,8 +298,8 @@ lat_status lat_set_g2(lat_handle* h, double g2);
  * The handle ends at the state after n_steps (as after lat_evolve). Handles
  * configured for the TMA step kernel take the plane-ring kernel in both passes.
  * Synchronises. LAT_ENOMEM if the checkpoints do not fit; LAT_EUNSUPPORTED for
- * a 27-point lattice; sticky device errors of the forward or reverse pass are
- * returned. */
+ * a 27-point lattice or expansion = 2; sticky device errors of the forward or
+ * reverse pass are returned. */
 lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fbar_dev, void* pibar_dev,
                    double sbar[4]);
 
@@ -302,7 +330,7 @@ lat_status lat_adjoint(lat_handle* h, int64_t n_steps, int observable, int64_t c
  * lat_get_scalars / lat_set_scalars act on the slab's stored arrays; the
  * whole-lattice calls (evolve, init, energies, spectrum, checkpoints,
  * derivative, set_kernel) return LAT_ESTATE on a slab. nzl >= 2.
- * LAT_EUNSUPPORTED for a 27-point lattice. */
+ * LAT_EUNSUPPORTED for a 27-point lattice or expansion = 2. */
 lat_status lat_slab_create(const lat_params* params, int z0, int nzl, void* cuda_stream, void* const dev_bufs[8],
                            lat_handle** out);
 
@@ -333,7 +361,7 @@ typedef struct lat_batch lat_batch;
  * the process's autotuner cache for this set of sizes and precision, else a
  * default. LAT_EINVAL for mixed precisions or a bad member (its lat_create
  * status is returned), LAT_EUNSUPPORTED if a member size fits no block shape or
- * a member has the 27-point stencil. */
+ * a member has the 27-point stencil or expansion = 2. */
 lat_status lat_batch_create(const lat_params* params, int count, void* cuda_stream, lat_batch** out);
 
 /* lat_init_fields on every member (each with its own seed). Synchronises. */

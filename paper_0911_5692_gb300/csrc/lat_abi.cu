@@ -31,7 +31,7 @@ lat_status derive_model(const lat_params& p, Model* M)
     if (p.n < 4 || p.n > 1024 || (p.n % 4) != 0) return LAT_EINVAL;
     if (p.precision != 32 && p.precision != 64) return LAT_EINVAL;
     if (!(p.L > 0.0) || !(p.dt > 0.0) || !std::isfinite(p.L) || !std::isfinite(p.dt)) return LAT_EINVAL;
-    if (p.expansion != 0 && p.expansion != 1) return LAT_EINVAL;
+    if (p.expansion < 0 || p.expansion > 2) return LAT_EINVAL;
     if (p.stencil != 0 && p.stencil != 7 && p.stencil != 27) return LAT_EINVAL;
     double cpl, beta;
     if (p.model == LAT_MODEL_LPHI4) { cpl = p.lambda; beta = 4.0; }
@@ -102,11 +102,22 @@ size_t partials_needed(int n)
     return need;
 }
 
+// The L = 1/H form (expansion 2) solves the next step's coefficients in a pass
+// of its own after the sums (and after every step).
+lat_status launch_lform_pass(lat_handle* h)
+{
+    if (h->M.expansion != 2) return LAT_OK;
+    cudaError_t e = h->prec == 32 ? launch_lform<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->stream)
+                                  : launch_lform<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->stream);
+    return cuda_status(e);
+}
+
 lat_status launch_prepare(lat_handle* h)
 {
     cudaError_t e = h->prec == 32 ? launch_sums<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->stream)
                                   : launch_sums<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->stream);
-    return cuda_status(e);
+    LAT_TRY(cuda_status(e));
+    return launch_lform_pass(h);
 }
 
 // One step of the configured kernel on the given buffers (the handle's own for
@@ -136,7 +147,8 @@ lat_status launch_one_step(lat_handle* h)
 {
     cudaError_t e = h->prec == 32 ? launch_step_with<float>(h, bufs_of<float>(h), true)
                                   : launch_step_with<double>(h, bufs_of<double>(h), true);
-    return cuda_status(e);
+    LAT_TRY(cuda_status(e));
+    return launch_lform_pass(h);
 }
 
 void drop_graph(lat_handle* h)
@@ -157,6 +169,10 @@ lat_status ensure_prepared(lat_handle* h)
     h->dirty = false;
     return LAT_OK;
 }
+
+// The L form's Hubble length l = a_t / a'_t at the momentum time t, with a_t
+// taken half a step back from the stored a at the field time: a - (dt/2) a'.
+double ell_at_momentum_time(double a, double ad, double dt) { return (a - 0.5 * dt * ad) / ad; }
 
 lat_status read_scalars(lat_handle* h, DevScalars* out)
 {
@@ -390,7 +406,7 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8])
     } else {
         out[1] = simple_grid_blocks(h->p.n, h->zr); out[2] = kSimpleTX * kSimpleTY; out[3] = 0;
     }
-    out[4] = 1;
+    out[4] = h->M.expansion == 2 ? 2 : 1;   // the L form adds its own pass
     out[5] = h->ty;
     out[6] = h->zr;
     out[7] = (h->variant == 2 || h->variant == 4) ? h->mcfg.depth : h->variant == 3 ? h->tcfg.depth : 0;
@@ -446,15 +462,43 @@ lat_status lat_set_scalars(lat_handle* h, const double in[4])
     if (!std::isfinite(in[0]) || !(in[1] > 0.0) || !std::isfinite(in[2]) || !(in[3] >= 0.0)) return LAT_EINVAL;
     DevScalars s;
     LAT_TRY(read_scalars(h, &s));
+    if (h->M.expansion == 2 && in[2] == 0.0) return LAT_EINVAL;   // l = a/a' undefined
     s.t = in[0];
     s.a = h->M.expansion ? in[1] : 1.0;
     s.ad = h->M.expansion ? in[2] : 0.0;
+    s.ell = h->M.expansion == 2 ? ell_at_momentum_time(s.a, s.ad, h->M.dt) : 0.0;
     s.step = (long long)in[3];
     s.ticket = 0;
     s.ticket2 = 0;
     LAT_CUDA(cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     h->dirty = true;
+    return LAT_OK;
+}
+
+lat_status lat_get_hubble_length(lat_handle* h, double* ell)
+{
+    if (!h || !ell) return LAT_EINVAL;
+    if (h->M.expansion != 2) return LAT_ESTATE;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    *ell = s.ell;
+    return (lat_status)s.status;
+}
+
+lat_status lat_set_hubble_length(lat_handle* h, double ell)
+{
+    if (!h) return LAT_EINVAL;
+    if (h->M.expansion != 2) return LAT_ESTATE;
+    if (!std::isfinite(ell) || ell == 0.0) return LAT_EINVAL;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    s.ell = ell;
+    s.ticket = 0;
+    s.ticket2 = 0;
+    LAT_CUDA(cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    h->dirty = true;   // the next step's coefficients follow l
     return LAT_OK;
 }
 
@@ -575,6 +619,7 @@ lat_status lat_init_fields(lat_handle* h)
         s.t = 0.0;
         s.ad = ad;
         s.a = 1.0 + (p.expansion ? 0.5 * p.dt * ad : 0.0);
+        s.ell = p.expansion == 2 ? ell_at_momentum_time(s.a, s.ad, p.dt) : 0.0;
         s.step = 0;
         if (cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) st = LAT_ECUDA;
     }
@@ -717,7 +762,7 @@ lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, doub
 namespace {
 
 struct CkptHeader {
-    char magic[8];       // "LATCKPT3"
+    char magic[8];       // "LATCKPT4"
     uint64_t bytes;      // whole blob
     uint32_t scalars_bytes;
     uint32_t esize;
@@ -750,7 +795,7 @@ lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes)
     if (s.status != LAT_OK) return (lat_status)s.status;
     CkptHeader hd;
     std::memset(&hd, 0, sizeof(hd));
-    std::memcpy(hd.magic, "LATCKPT3", 8);
+    std::memcpy(hd.magic, "LATCKPT4", 8);
     hd.bytes = bytes;
     hd.scalars_bytes = sizeof(DevScalars);
     hd.esize = (uint32_t)h->esize;
@@ -775,7 +820,7 @@ lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes)
     if (h->slab) return LAT_ESTATE;
     CkptHeader hd;
     std::memcpy(&hd, src, sizeof(hd));
-    if (std::memcmp(hd.magic, "LATCKPT3", 8) != 0 || hd.bytes != bytes || hd.scalars_bytes != sizeof(DevScalars) ||
+    if (std::memcmp(hd.magic, "LATCKPT4", 8) != 0 || hd.bytes != bytes || hd.scalars_bytes != sizeof(DevScalars) ||
         hd.esize != h->esize || std::memcmp(&hd.params, &h->p, sizeof(lat_params)) != 0)
         return LAT_EINVAL;
     DevScalars s;

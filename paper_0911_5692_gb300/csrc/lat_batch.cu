@@ -564,8 +564,8 @@ lat_status lat_batch_create(const lat_params* params, int count, void* cuda_stre
     if (!params || count < 1) return LAT_EINVAL;
     for (int i = 1; i < count; i++)
         if (params[i].precision != params[0].precision) return LAT_EINVAL;
-    for (int i = 0; i < count; i++)   // the ensemble kernel is written for the 7-point Laplacian
-        if (params[i].stencil == 27) return LAT_EUNSUPPORTED;
+    for (int i = 0; i < count; i++)   // the ensemble kernel is written for 7 points and eq. scale
+        if (params[i].stencil == 27 || params[i].expansion == 2) return LAT_EUNSUPPORTED;
     lat_batch* b = new (std::nothrow) lat_batch();
     if (!b) return LAT_ENOMEM;
     b->count = count;

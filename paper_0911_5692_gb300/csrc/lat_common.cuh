@@ -14,7 +14,7 @@ namespace lat {
 // Constants of one lattice, fixed at creation (program units, Sec. II.B).
 struct Model {
     int n;
-    int expansion;
+    int expansion;      // 0: static; 1: eq. scale; 2: the L = 1/H form (lat_lform.cu)
     int beta;           // 2 or 4: exponent of the dominant potential term
     int stencil;        // Laplacian: 7-point or 27-point (Sec. II.C)
     double dx, dt, inv_dx2;
@@ -56,6 +56,9 @@ struct DevScalars {
     // the one the next step starts from, at log[step - log_base]. Null otherwise.
     DevScalars* log;
     long long log_base;
+    // The L = 1/H form (expansion 2): the Hubble length l = a/a' of program time
+    // at t, and l at t + dt as solved for the next step (lat_lform.cu).
+    double ell, ell_next;
 };
 
 // Step coefficient i for element type T (kd / kf above).
@@ -211,7 +214,9 @@ __device__ inline void scale_solve(const Model& M, DevScalars* sc)
 // The scalars after one step, from those before it and the volume sums S of the
 // new fields: a_{n+3/2} = a_{n+1/2} + dt a'_{n+1}, a' <- a'_{n+1}, t += dt, then
 // the a' solve and coefficients for the next step (scale_solve). `advance` is
-// false for the sums-only pass after initialisation or a state upload.
+// false for the sums-only pass after initialisation or a state upload. In the
+// L = 1/H form the solve for the next step is a pass of its own (its sums need
+// the Laplacian of the new fields), launched after this one.
 __device__ inline void advance_scalars(const Model& M, DevScalars& s, const double S[kSums], bool advance)
 {
     bool finite = true;
@@ -223,12 +228,13 @@ __device__ inline void advance_scalars(const Model& M, DevScalars& s, const doub
         if (M.expansion) {
             s.a = s.a + M.dt * s.ad_next;
             s.ad = s.ad_next;
+            s.ell = s.ell_next;
         }
         s.t = s.t + M.dt;
         s.step = s.step + 1;
     }
     if (!finite) s.status = LAT_ENONFINITE;
-    else scale_solve(M, &s);
+    else if (M.expansion != 2) scale_solve(M, &s);
 }
 
 // Fixed-order reduction of the per-block partials by warp 0 of the block that

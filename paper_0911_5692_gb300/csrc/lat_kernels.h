@@ -25,6 +25,7 @@ cudaError_t launch_step_simple(const Bufs<T>& b, const Model& M, DevScalars* sc,
 
 // Sums of the current fields (no step) followed by the scale-factor solve.
 int sums_grid_blocks(int n);
+int sums_zruns(int n);
 template <typename T>
 cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, cudaStream_t st);
 
@@ -127,6 +128,11 @@ cudaError_t launch_to_double(const T* src, double* dst, size_t count, cudaStream
 template <typename T>
 cudaError_t launch_energy_field(const Bufs<T>& b, const Model& M, const DevScalars* sc, T* rho, T* pres,
                                 cudaStream_t st);
+
+// The L = 1/H form (expansion 2): the read-only pass over the current state
+// whose last block solves the next step's coefficients (lat_lform.cu).
+template <typename T>
+cudaError_t launch_lform(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, cudaStream_t st);
 int spectrum_grid_blocks(int n);
 cudaError_t launch_spectrum_bins(const void* spec, int n, double L, int nbins, double* partials,
                                  cudaStream_t st);

@@ -95,6 +95,7 @@ lat_status lat_slab_create(const lat_params* params, int z0, int nzl, void* cuda
     if (!params || !dev_bufs) return LAT_EINVAL;
     if (z0 < 0 || z0 >= params->n || nzl < 2 || nzl > params->n) return LAT_EINVAL;
     if (params->stencil == 27) return LAT_EUNSUPPORTED;   // the slab step is written for 7 points
+    if (params->expansion == 2) return LAT_EUNSUPPORTED;  // and for eq. scale
     lat_handle* h = nullptr;
     LAT_TRY(lat_create_with_buffers(params, cuda_stream, dev_bufs, &h));
     h->slab = true;

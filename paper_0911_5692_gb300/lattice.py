@@ -26,7 +26,8 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_set_g2", "lat_vjp", "lat_adjoint", "lat_batch_create", "lat_batch_init_fields",
             "lat_batch_evolve", "lat_batch_sync", "lat_batch_tune", "lat_batch_member", "lat_batch_info",
             "lat_batch_destroy", "lat_batch_check_barrier", "lat_slab_create", "lat_slab_sums", "lat_slab_step",
-            "lat_slab_advance", "lat_energy_field", "lat_upload_state")
+            "lat_slab_advance", "lat_energy_field", "lat_upload_state", "lat_get_hubble_length",
+            "lat_set_hubble_length")
 
 
 class LatParams(C.Structure):
@@ -86,6 +87,8 @@ def load_library(build_if_missing: bool = True):
             L.lat_set_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
             L.lat_get_scalars.argtypes = [P, dp]
             L.lat_set_scalars.argtypes = [P, dp]
+            L.lat_get_hubble_length.argtypes = [P, dp]
+            L.lat_set_hubble_length.argtypes = [P, C.c_double]
             L.lat_sync.argtypes = [P]
             L.lat_set_kernel.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int]
             L.lat_kernel_info.argtypes = [P, i64p]
@@ -315,6 +318,16 @@ class Lattice:
     def set_scalars(self, t=0.0, a=1.0, ad=0.0, step=0):
         v = (C.c_double * 4)(float(t), float(a), float(ad), float(step))
         _check(self._L.lat_set_scalars(self._h, v), "lat_set_scalars")
+
+    def hubble_length(self) -> float:
+        """The L = 1/H form's l = a/a' of program time at the momentum time
+        (lat_get_hubble_length; expansion = 2 only)."""
+        v = C.c_double()
+        _check(self._L.lat_get_hubble_length(self._h, C.byref(v)), "lat_get_hubble_length")
+        return v.value
+
+    def set_hubble_length(self, ell: float):
+        _check(self._L.lat_set_hubble_length(self._h, float(ell)), "lat_set_hubble_length")
 
     # -- checkpoints
     def save_checkpoint(self) -> bytes:
