@@ -96,10 +96,12 @@ __device__ __forceinline__ void site_terms(const SiteCoef<T>& C, T f0, T f1, T p
 
 // The implicit midpoint solve of the L form from the volume averages
 // S = (P0, Q, F2, W) taken with the guess w0; writes the next step's
-// coefficients into s, or sets LAT_ENONFINITE when it does not converge (a
-// recollapse through H = 0, or non-finite sums).
-__device__ inline void lform_solve(const Model& M, DevScalars& s, const double S[kSums], double w0)
+// coefficients into the scalar block in place (every other block of the
+// launch has finished reading it), or sets LAT_ENONFINITE when it does not
+// converge (a recollapse through H = 0, or non-finite sums).
+__device__ inline void lform_solve(const Model& M, DevScalars* sc, const double S[kSums], double w0)
 {
+    DevScalars& s = *sc;
     const double a = s.a, ia = 1.0 / a, dt = M.dt, r = M.r, sg = M.s, ell = s.ell;
     const double g = M.g8A2 * (1.0 / 3.0) * apow(a, ia, -2.0 * r);
     bool ok = isfinite(S[0]) && isfinite(S[1]) && isfinite(S[2]) && isfinite(S[3]) && isfinite(ell) && ell != 0.0;
@@ -155,21 +157,42 @@ __device__ inline void lform_finish(const Model& M, DevScalars* sc, double* part
     if (!is_last) return;
     __threadfence();
     if (tid >= 32) return;
+    // lane l folds blocks l, l + 32, ... in order, the loads of four of them in
+    // flight together (kSums = 4 doubles per block: two double2 loads)
     double acc[kSums] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = tid; b < nblocks; b += 32)
+    const double2* p2 = reinterpret_cast<const double2*>(partials);
+    int b = tid;
+    for (; b + 96 < nblocks; b += 128) {
+        double2 x[4][2];
 #pragma unroll
-        for (int k = 0; k < kSums; k++) acc[k] += __ldcg(partials + (size_t)b * kSums + k);
+        for (int j = 0; j < 4; j++) {
+            x[j][0] = __ldcg(p2 + (size_t)(b + 32 * j) * 2);
+            x[j][1] = __ldcg(p2 + (size_t)(b + 32 * j) * 2 + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            acc[0] += x[j][0].x;
+            acc[1] += x[j][0].y;
+            acc[2] += x[j][1].x;
+            acc[3] += x[j][1].y;
+        }
+    }
+    for (; b < nblocks; b += 32) {
+        const double2 x0 = __ldcg(p2 + (size_t)b * 2), x1 = __ldcg(p2 + (size_t)b * 2 + 1);
+        acc[0] += x0.x;
+        acc[1] += x0.y;
+        acc[2] += x1.x;
+        acc[3] += x1.y;
+    }
 #pragma unroll
     for (int k = 0; k < kSums; k++)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
     if (tid == 0) {
-        DevScalars s = *sc;
-        s.ticket = 0u;
+        sc->ticket = 0u;
         double S[kSums];
         for (int k = 0; k < kSums; k++) S[k] = acc[k] * M.inv_sites;
-        lform_solve(M, s, S, w0);
-        *sc = s;
+        lform_solve(M, sc, S, w0);
         __threadfence();
     }
 }
@@ -201,8 +224,9 @@ __device__ inline SiteCoef<T> block_coefs(const Model& M, const DevScalars* sc, 
 // marching a z run with the vectors of the planes below and above in
 // registers; the y neighbours as vectors, the x neighbours beyond the vector as
 // two scalars. Items: (n/V vectors x n rows) columns cut into nzc z runs.
+// FP32: at most 80 registers, for 3 blocks (24 warps) per SM.
 template <typename T>
-__global__ void __launch_bounds__(256) lform7_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, int nzc)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) lform7_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, int nzc)
 {
     constexpr int V = 16 / sizeof(T);
     using Raw = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
