@@ -32,6 +32,8 @@ METRIC = "lattice site-updates/s (2 fields, FP32) and % HBM roofline; adjoint/fo
 UNIT = "site-updates/s"
 L2_BYTES = 129e6
 FALLBACK_HBM_GBS = 6800.0
+# GB300's nominal HBM3e bandwidth (8 TB/s class), reported beside the measured copy rate
+NOMINAL_HBM_GBS = 8000.0
 
 
 def parse():
@@ -178,12 +180,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(p, seconds):
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def cpu_baseline(p, seconds, one_thread_seconds=6.0):
     """The FP64 oracle as it stands, on this host's cores, on a bounded sample of
     the workload: steps of the full lattice from a seeded synthetic state until
-    `seconds` have passed."""
+    `seconds` have passed, with OpenMP over all cores; then the same on one
+    thread for `one_thread_seconds`."""
     import numpy as np
-    from oracle.oracle import Oracle
+    from oracle.oracle import Oracle, set_threads
     from paper_0911_5692_gb300.workloads import random_state
     n = p["n"]
     st = random_state(n, 1, precision=p["precision"], f_mean=(1.0, 0.0), f_amp=(1e-3, 1e-4), pi_mean=(0.3, 0.0),
@@ -191,19 +208,30 @@ def cpu_baseline(p, seconds):
     o = Oracle(p)
     o.set_state(*st, t=0.0, a=1.0, ad=0.5)
     del st
-    o.step(1)
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
+
+    def timed(limit):
         o.step(1)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
+        steps = 0
+        t0 = time.perf_counter()
+        while True:
+            o.step(1)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= limit:
+                return steps, el
+
     cores = os.cpu_count()
-    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+    all_threads = set_threads(cores)
+    steps, el = timed(seconds)
+    set_threads(1)
+    steps1, el1 = timed(one_thread_seconds)
+    set_threads(all_threads)
+    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": all_threads, "kind": "oracle",
             "sample": f"{steps} FP64 oracle steps of the full {n}^3 {model_name(p)} lattice from a seeded "
-                      f"synthetic state ({el:.1f} s, OpenMP over {cores} host cores)"}
+                      f"synthetic state ({el:.1f} s, OpenMP over {all_threads} host threads)",
+            "cpu_model": cpu_model(),
+            "one_thread": {"value": n ** 3 * steps1 / el1, "unit": UNIT, "cores": 1,
+                           "sample": f"{steps1} steps of the same lattice on one thread ({el1:.1f} s)"}}
 
 
 def measure_adjoint(local, name="lphi4_128_fp32", n=None, steps=None):
@@ -394,7 +422,7 @@ def measure_step(local, name="lphi4_512_fp32", steps=300):
     gbs = 8 * esize * n ** 3 / (ms / 1e3) / 1e9
     lat.close()
     return {"workload": name, "steps": steps, "ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": UNIT,
-            "achieved_GBs": gbs, "hbm_frac": gbs / peak,
+            "achieved_GBs": gbs, "hbm_frac": gbs / peak, "hbm_frac_of_nominal": gbs / NOMINAL_HBM_GBS,
             "kernel": {"variant": info["variant"], "blocks": info["blocks"], "threads": info["threads"],
                        "ty": info["ty"], "depth": info["depth"]}}
 
@@ -621,6 +649,7 @@ def run_ours(args):
         "config": config_of(args.workload, p, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "kernel": f"fused step variant {info['variant']}"
                                f"{', 27-point Laplacian' if args.stencil == 27 else ''} ({info['blocks']} blocks x "

@@ -73,6 +73,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -549,6 +552,19 @@ void orc_set_scalars(orc_lattice *L, double t, double a, double ad, int64_t step
     L->t = t; L->a = a; L->ad = ad; L->step = step;
     L->ell = ell_of(a, ad, L->p.dt);
     orc_sums(L);
+}
+
+/* Threads of the OpenMP loops from here on (timing only; every sum is taken in
+ * the same order whatever the count). Returns the count in effect. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* The L form's l = 1/h at the momentum time (set_scalars derives it from a and a'). */

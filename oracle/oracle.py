@@ -68,6 +68,8 @@ def lib():
             L.orc_array.restype = dp
             L.orc_get_scalars.argtypes = [P, dp]
             L.orc_set_scalars.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int64]
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = C.c_int
             L.orc_get_ell.argtypes = [P]
             L.orc_get_ell.restype = C.c_double
             L.orc_set_ell.argtypes = [P, C.c_double]
@@ -320,3 +322,9 @@ def fft3(x: np.ndarray, sign: int = -1) -> np.ndarray:
     re = np.ascontiguousarray(x.real); im = np.ascontiguousarray(x.imag)
     lib().orc_fft3(x.shape[0], _dp(re), _dp(im), int(sign))
     return re + 1j * im
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (timing only; results do not depend
+    on it). n <= 0 leaves the count; returns the count in effect."""
+    return int(lib().orc_set_threads(int(n)))
