@@ -666,6 +666,7 @@ def run_ours(args):
         lat.close()
         line["step_512"] = measure_step(local)
         line["fp32_vs_fp64"] = measure_fp32_error(local, args.workload)
+        line["fp32_vs_fp64_512"] = measure_fp32_error(local, "lphi4_512_fp32")
         line["adjoint"] = measure_adjoint(local)
         line["adjoint_256"] = measure_adjoint(local, n=256, steps=400)
         line["ensemble"] = measure_ensemble(local)

@@ -463,3 +463,23 @@ def test_fp64_full_size_default_kernel():
     g.evolve(1)
     o.step(1)
     compare_states(g, o, TOL[64], "FP64 full size 256, default kernel")
+
+
+def test_fp64_full_size_512_two_steps():
+    """The FP64 variant that the 512^3 FP32 run's error is measured against (the
+    bench's fp32_vs_fp64_512, every 16th site per axis): two 512^3 FP64 steps of
+    the lambda phi^4 model against the oracle's full-lattice steps at the FP64
+    bound."""
+    n = 512
+    p = _params("lphi4", n, 64, 1)
+    st = _state("lphi4", n, 64, seed=81)
+    g = Lattice(p)
+    g.set_state(*st, t=0.0, a=1.05, ad=0.45)
+    o = Oracle(p)
+    o.set_state(*st, t=0.0, a=1.05, ad=0.45)
+    del st
+    g.evolve(2)
+    o.step(2)
+    compare_states(g, o, 2 * TOL[64], "FP64 full size 512, two steps")
+    assert abs(g.scalars()["a"] / o.scalars()["a"] - 1) < 1e-13
+
