@@ -224,9 +224,10 @@ __device__ inline SiteCoef<T> block_coefs(const Model& M, const DevScalars* sc, 
 // marching a z run with the vectors of the planes below and above in
 // registers; the y neighbours as vectors, the x neighbours beyond the vector as
 // two scalars. Items: (n/V vectors x n rows) columns cut into nzc z runs.
-// FP32: at most 80 registers, for 3 blocks (24 warps) per SM.
+// FP32: at most 128 registers, for 2 blocks (16 warps) per SM, each with the
+// loads of two planes in flight.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) lform7_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, int nzc)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) lform7_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, int nzc)
 {
     constexpr int V = 16 / sizeof(T);
     using Raw = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
@@ -257,35 +258,53 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) lform7_kernel(Buf
         const int xl = x == 0 ? n - 1 : x - 1, xr = x + V == n ? 0 : x + V;
         const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
         const int zb = (int)((long long)zc * n / nzc), ze = (int)((long long)(zc + 1) * n / nzc);
+        // what plane z needs beyond the centre vectors: the centre above (z + 1),
+        // the y neighbours, the momenta and the two x neighbours past the vector
+        struct Plane {
+            Vec cp, a, b, pv;
+            T l, r;
+        };
+        auto load_plane = [&](int i, int z, Plane& o) {
+            const int zp = z == n - 1 ? 0 : z + 1;
+            o.cp = vec(f[i], x, y, zp);
+            o.a = vec(f[i], x, ym, z);
+            o.b = vec(f[i], x, yp, z);
+            o.pv = vec(p[i], x, y, z);
+            o.l = __ldg(f[i] + lidx(n, xl, y, z));
+            o.r = __ldg(f[i] + lidx(n, xr, y, z));
+        };
         Vec cm[2], c[2];
+        Plane nx[2];
 #pragma unroll
         for (int i = 0; i < 2; i++) {
             cm[i] = vec(f[i], x, y, zb == 0 ? n - 1 : zb - 1);
             c[i] = vec(f[i], x, y, zb);
+            load_plane(i, zb, nx[i]);
         }
         for (int z = zb; z < ze; z++) {
-            const int zp = z == n - 1 ? 0 : z + 1;
-            Vec cp[2], lap[2], pv[2];
+            // the loads of plane z + 1 go out before plane z is computed
+            const Plane cu[2] = {nx[0], nx[1]};
+            if (z + 1 < ze) {
+#pragma unroll
+                for (int i = 0; i < 2; i++) load_plane(i, z + 1, nx[i]);
+            }
+            Vec lap[2];
 #pragma unroll
             for (int i = 0; i < 2; i++) {
-                cp[i] = vec(f[i], x, y, zp);
-                const Vec a = vec(f[i], x, ym, z), b = vec(f[i], x, yp, z);
-                pv[i] = vec(p[i], x, y, z);
-                const T l = __ldg(f[i] + lidx(n, xl, y, z)), r = __ldg(f[i] + lidx(n, xr, y, z));
 #pragma unroll
                 for (int j = 0; j < V; j++) {
                     const T cc = c[i].v[j];
-                    const T left = j == 0 ? l : c[i].v[j - 1], right = j == V - 1 ? r : c[i].v[j + 1];
-                    lap[i].v[j] = ((left - cc) + (right - cc)) + ((a.v[j] - cc) + (b.v[j] - cc)) +
-                                  ((cm[i].v[j] - cc) + (cp[i].v[j] - cc));
+                    const T left = j == 0 ? cu[i].l : c[i].v[j - 1], right = j == V - 1 ? cu[i].r : c[i].v[j + 1];
+                    lap[i].v[j] = ((left - cc) + (right - cc)) + ((cu[i].a.v[j] - cc) + (cu[i].b.v[j] - cc)) +
+                                  ((cm[i].v[j] - cc) + (cu[i].cp.v[j] - cc));
                 }
             }
             T s[kSums] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
             for (int j = 0; j < V; j++) {
                 T t[kSums];
-                site_terms(C, c[0].v[j], c[1].v[j], pv[0].v[j], pv[1].v[j], lap[0].v[j], lap[1].v[j], t[0], t[1],
-                           t[2], t[3]);
+                site_terms(C, c[0].v[j], c[1].v[j], cu[0].pv.v[j], cu[1].pv.v[j], lap[0].v[j], lap[1].v[j], t[0],
+                           t[1], t[2], t[3]);
 #pragma unroll
                 for (int k = 0; k < kSums; k++) s[k] += t[k];
             }
@@ -294,7 +313,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) lform7_kernel(Buf
 #pragma unroll
             for (int i = 0; i < 2; i++) {
                 cm[i] = c[i];
-                c[i] = cp[i];
+                c[i] = cu[i].cp;
             }
         }
     }
