@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(256) sums_kernel(Bufs<T> B, Model M, DevScalar
 // The 7-point sums of an FP32 lattice with one 16-byte vector (four x sites)
 // per thread: per plane, the vector, the one above it in y and in z, and the
 // site right of its last one. Same terms and accuracy as sums_kernel; the
-// vector loads keep each warp on 512 contiguous bytes of a row.
+// vector loads keep each warp on 512 contiguous bytes of a row, and the loads of
+// plane z + 1 go out before plane z is summed.
 __global__ void __launch_bounds__(256) sums7_vec_kernel(Bufs<float> B, Model M, DevScalars* sc, double* partials,
                                                         int nzc)
 {
@@ -230,12 +231,28 @@ __global__ void __launch_bounds__(256) sums7_vec_kernel(Bufs<float> B, Model M, 
         auto vec = [&](const float* f, int yy, int zz) {
             return __ldg(reinterpret_cast<const float4*>(f + sidx(n, x, yy, zz)));
         };
-        float4 c0 = vec(f0, y, zb), c1 = vec(f1, y, zb);
-        for (int z = zb; z < ze; z++) {
+        // per plane z: the vectors above in z and in y, the site right of the vector
+        struct Plane {
+            float4 u0, u1, y0, y1;
+            float r0, r1;
+        };
+        auto load_plane = [&](int z, Plane& o) {
             const int zp = z == n - 1 ? 0 : z + 1;
-            const float4 u0 = vec(f0, y, zp), u1 = vec(f1, y, zp);   // the next plane's vector
-            const float4 y0 = vec(f0, yp, z), y1 = vec(f1, yp, z);
-            const float r0 = __ldg(f0 + sidx(n, xr, y, z)), r1 = __ldg(f1 + sidx(n, xr, y, z));
+            o.u0 = vec(f0, y, zp);
+            o.u1 = vec(f1, y, zp);
+            o.y0 = vec(f0, yp, z);
+            o.y1 = vec(f1, yp, z);
+            o.r0 = __ldg(f0 + sidx(n, xr, y, z));
+            o.r1 = __ldg(f1 + sidx(n, xr, y, z));
+        };
+        float4 c0 = vec(f0, y, zb), c1 = vec(f1, y, zb);
+        Plane nx;
+        load_plane(zb, nx);
+        for (int z = zb; z < ze; z++) {
+            const Plane cu = nx;
+            if (z + 1 < ze) load_plane(z + 1, nx);
+            const float4 u0 = cu.u0, u1 = cu.u1, y0 = cu.y0, y1 = cu.y1;
+            const float r0 = cu.r0, r1 = cu.r1;
             auto grad = [](float4 c, float4 yn, float4 zn, float r) {
                 const float ex0 = c.y - c.x, ex1 = c.z - c.y, ex2 = c.w - c.z, ex3 = r - c.w;
                 const float ey0 = yn.x - c.x, ey1 = yn.y - c.y, ey2 = yn.z - c.z, ey3 = yn.w - c.w;
@@ -293,12 +310,32 @@ cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double
 {
     if constexpr (sizeof(T) == 4) {
         if (M.stencil != 27) {
-            // vector items: (n/4 vectors x n rows) columns cut into z runs, sized
-            // like sums_kernel's so the same partials buffer serves
-            const long long vcols = (long long)(M.n / 4) * M.n;
-            const int nzc = (int)std::max<long long>(1, std::min<long long>(M.n / 4, (155648 + vcols - 1) / vcols));
+            // vector items: (n/4 vectors x n rows) columns cut into z runs. One
+            // resident wave of blocks (no more than sums_grid_blocks, which sizes the
+            // partials buffer); each thread marches whole runs, so its time goes as
+            // (runs it takes) x (planes per run + 1): the run count minimises that.
+            static int occ = 0;
+            if (occ == 0) {
+                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sums7_vec_kernel, 256, 0);
+                if (e != cudaSuccess || occ < 1) occ = 1;
+            }
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return cudaErrorInvalidDevice;
+            const int n = M.n;
+            const long long vcols = (long long)(n / 4) * n;
+            const int blocks_max = std::max(1, std::min(sums_grid_blocks(n), occ * sms));
+            const long long threads = (long long)blocks_max * 256;
+            int nzc = 1;
+            double best = 0.0;
+            for (int c = 1; c <= n / 4; c++) {
+                const long long per_thread = (vcols * c + threads - 1) / threads;
+                const double cost = (double)per_thread * ((double)n / c + 1.0);
+                if (c == 1 || cost < best) { best = cost; nzc = c; }
+            }
             const long long items = vcols * nzc;
-            const int blocks = (int)std::min<long long>(sums_grid_blocks(M.n), (items + 255) / 256);
+            const int blocks = (int)std::min<long long>(blocks_max, (items + 255) / 256);
             sums7_vec_kernel<<<blocks, 256, 0, st>>>(b, M, sc, partials, nzc);
             return cudaGetLastError();
         }
