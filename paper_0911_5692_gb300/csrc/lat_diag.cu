@@ -3,6 +3,10 @@
 // Sec. IV names as future work.
 #include <cufft.h>
 
+#include <algorithm>
+#include <type_traits>
+
+#include "lat_grid.h"
 #include "lat_kernels.h"
 #include "lat_stencil27.cuh"
 
@@ -189,6 +193,49 @@ __device__ __forceinline__ void neighbour_sums(const T* __restrict__ f, int n, i
 // arithmetic in the lattice precision on exact neighbour differences, the
 // coefficients in FP64 rounded once.
 template <typename T>
+struct FieldCoef {
+    T cL, cF, cdom, kap, hdt, rh, gq, cv;
+    bool quartic;
+};
+
+template <typename T>
+__device__ inline FieldCoef<T> field_coefs(const Model& M, const DevScalars* sc)
+{
+    const double a = sc->a;
+    const double h = M.expansion ? sc->ad_half / a : 0.0;
+    FieldCoef<T> k;
+    k.cL = (T)(sc->cL * M.lap_scale);
+    k.cF = (T)sc->cF;
+    k.cdom = (T)sc->cdom;
+    k.kap = (T)sc->kappa;
+    k.hdt = (T)(0.5 * M.dt);
+    k.rh = (T)(M.r * h);
+    k.gq = (T)(0.25 * pow(a, -2.0 * M.s - 2.0) * M.lap_scale);   // grad_i = gq * sum w d^2
+    k.cv = (T)(M.B * M.B / (M.A * M.A) * pow(a, 2.0 * M.s - 2.0 * M.r));
+    k.quartic = M.beta == 4;
+    return k;
+}
+
+// rho and p at one site from its fields a0, a1, momenta m0, m1 and the
+// neighbour sums (l: of the differences, g: of their squares) of each field.
+template <typename T>
+__device__ __forceinline__ void site_energy(const FieldCoef<T>& K, T a0, T a1, T m0, T m1, T l0, T g0, T l1, T g1,
+                                            T& rho, T& pres)
+{
+    const T a0b = K.quartic ? a0 * a0 * a0 : a0;
+    const T F0 = K.cL * l0 + K.cF * a0 - (K.cdom * a0b + K.kap * a0 * a1 * a1);
+    const T F1 = K.cL * l1 + K.cF * a1 - K.kap * a0 * a0 * a1;
+    const T q0 = m0 + K.hdt * F0 - K.rh * a0;
+    const T q1 = m1 + K.hdt * F1 - K.rh * a1;
+    const T kin = T(0.5) * (q0 * q0 + q1 * q1);
+    const T grad = K.gq * (g0 + g1);
+    const T sq = a0 * a0;
+    const T V = K.cdom * (K.quartic ? T(0.25) * sq * sq : T(0.5) * sq) + T(0.5) * K.kap * sq * a1 * a1;
+    rho = K.cv * (kin + grad + V);
+    pres = K.cv * (kin - grad / T(3) - V);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) energy_field_kernel(Bufs<T> B, Model M, const DevScalars* sc, T* rho, T* pres)
 {
     const int n = M.n;
@@ -197,14 +244,8 @@ __global__ void __launch_bounds__(256) energy_field_kernel(Bufs<T> B, Model M, c
     const T* f1 = B.f[par][1];
     const T* p0 = B.p[par][0];
     const T* p1 = B.p[par][1];
-    const double a = sc->a;
-    const double h = M.expansion ? sc->ad_half / a : 0.0;
-    const double conv = M.B * M.B / (M.A * M.A) * pow(a, 2.0 * M.s - 2.0 * M.r);
-    const T cL = (T)(sc->cL * M.lap_scale), cF = (T)sc->cF, cdom = (T)sc->cdom, kap = (T)sc->kappa;
-    const T hdt = (T)(0.5 * M.dt), rh = (T)(M.r * h);
-    const T gq = (T)(0.25 * pow(a, -2.0 * M.s - 2.0) * M.lap_scale);   // grad_i = gq * sum w d^2
-    const T cv = (T)conv;
-    const bool s27 = M.stencil == 27, quartic = M.beta == 4;
+    const FieldCoef<T> K = field_coefs<T>(M, sc);
+    const bool s27 = M.stencil == 27;
     const long long cols = (long long)n * n;
     for (long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
          col += (long long)gridDim.x * blockDim.x) {
@@ -215,17 +256,102 @@ __global__ void __launch_bounds__(256) energy_field_kernel(Bufs<T> B, Model M, c
             T l0, g0, l1, g1;
             neighbour_sums(f0, n, x, y, z, s27, l0, g0);
             neighbour_sums(f1, n, x, y, z, s27, l1, g1);
-            const T a0b = quartic ? a0 * a0 * a0 : a0;
-            const T F0 = cL * l0 + cF * a0 - (cdom * a0b + kap * a0 * a1 * a1);
-            const T F1 = cL * l1 + cF * a1 - kap * a0 * a0 * a1;
-            const T q0 = __ldg(p0 + c) + hdt * F0 - rh * a0;
-            const T q1 = __ldg(p1 + c) + hdt * F1 - rh * a1;
-            const T kin = T(0.5) * (q0 * q0 + q1 * q1);
-            const T grad = gq * (g0 + g1);
-            const T sq = a0 * a0;
-            const T V = cdom * (quartic ? T(0.25) * sq * sq : T(0.5) * sq) + T(0.5) * kap * sq * a1 * a1;
-            rho[c] = cv * (kin + grad + V);
-            pres[c] = cv * (kin - grad / T(3) - V);
+            site_energy(K, a0, a1, __ldg(p0 + c), __ldg(p1 + c), l0, g0, l1, g1, rho[c], pres[c]);
+        }
+    }
+}
+
+// The 7-point energy field with one 16-byte vector of x sites per thread,
+// marching whole z runs, the loads of plane z + 1 issued before plane z is
+// computed; the same per-site terms as energy_field_kernel, the six neighbour
+// differences taken in the same order (-x, +x, -y, +y, -z, +z).
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    energy_field7_kernel(Bufs<T> B, Model M, const DevScalars* sc, T* rho, T* pres, int nzc)
+{
+    constexpr int V = 16 / sizeof(T);
+    using Raw = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    struct Vec {
+        T v[V];
+    };
+    const int n = M.n, q = n / V;
+    const int par = (int)(sc->step & 1);
+    const T* __restrict__ f[2] = {B.f[par][0], B.f[par][1]};
+    const T* __restrict__ p[2] = {B.p[par][0], B.p[par][1]};
+    const FieldCoef<T> K = field_coefs<T>(M, sc);
+    auto vec = [&](const T* a, int x, int y, int z) {
+        const Raw r = __ldg(reinterpret_cast<const Raw*>(a + sidx(n, x, y, z)));
+        Vec o;
+        *reinterpret_cast<Raw*>(o.v) = r;
+        return o;
+    };
+    const long long vcols = (long long)q * n, items = vcols * nzc;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const long long vc = it % vcols;
+        const int zc = (int)(it / vcols);
+        const int x = V * (int)(vc % q), y = (int)(vc / q);
+        const int xl = x == 0 ? n - 1 : x - 1, xr = x + V == n ? 0 : x + V;
+        const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+        const int zb = (int)((long long)zc * n / nzc), ze = (int)((long long)(zc + 1) * n / nzc);
+        struct Plane {
+            Vec cp, a, b, pv;
+            T l, r;
+        };
+        auto load_plane = [&](int i, int z, Plane& o) {
+            const int zp = z == n - 1 ? 0 : z + 1;
+            o.cp = vec(f[i], x, y, zp);
+            o.a = vec(f[i], x, ym, z);
+            o.b = vec(f[i], x, yp, z);
+            o.pv = vec(p[i], x, y, z);
+            o.l = __ldg(f[i] + sidx(n, xl, y, z));
+            o.r = __ldg(f[i] + sidx(n, xr, y, z));
+        };
+        Vec cm[2], c[2];
+        Plane nx[2];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            cm[i] = vec(f[i], x, y, zb == 0 ? n - 1 : zb - 1);
+            c[i] = vec(f[i], x, y, zb);
+            load_plane(i, zb, nx[i]);
+        }
+        for (int z = zb; z < ze; z++) {
+            const Plane cu[2] = {nx[0], nx[1]};
+            if (z + 1 < ze) {
+#pragma unroll
+                for (int i = 0; i < 2; i++) load_plane(i, z + 1, nx[i]);
+            }
+            Vec lsum[2], gsum[2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+#pragma unroll
+                for (int j = 0; j < V; j++) {
+                    const T cc = c[i].v[j];
+                    const T d[6] = {(j == 0 ? cu[i].l : c[i].v[j - 1]) - cc, (j == V - 1 ? cu[i].r : c[i].v[j + 1]) - cc,
+                                    cu[i].a.v[j] - cc, cu[i].b.v[j] - cc, cm[i].v[j] - cc, cu[i].cp.v[j] - cc};
+                    T l = T(0), g = T(0);
+#pragma unroll
+                    for (int k = 0; k < 6; k++) {
+                        l += d[k];
+                        g += d[k] * d[k];
+                    }
+                    lsum[i].v[j] = l;
+                    gsum[i].v[j] = g;
+                }
+            }
+            Vec ro, pr;
+#pragma unroll
+            for (int j = 0; j < V; j++)
+                site_energy(K, c[0].v[j], c[1].v[j], cu[0].pv.v[j], cu[1].pv.v[j], lsum[0].v[j], gsum[0].v[j],
+                            lsum[1].v[j], gsum[1].v[j], ro.v[j], pr.v[j]);
+            const size_t o = sidx(n, x, y, z);
+            *reinterpret_cast<Raw*>(rho + o) = *reinterpret_cast<const Raw*>(ro.v);
+            *reinterpret_cast<Raw*>(pres + o) = *reinterpret_cast<const Raw*>(pr.v);
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                cm[i] = c[i];
+                c[i] = cu[i].cp;
+            }
         }
     }
 }
@@ -236,7 +362,21 @@ template <typename T>
 cudaError_t launch_energy_field(const Bufs<T>& b, const Model& M, const DevScalars* sc, T* rho, T* pres,
                                 cudaStream_t st)
 {
-    energy_field_kernel<T><<<energies_grid_blocks(M.n), 256, 0, st>>>(b, M, sc, rho, pres);
+    const int n = M.n;
+    constexpr int V = 16 / sizeof(T);
+    if (M.stencil != 27 && ((uintptr_t)rho % 16) == 0 && ((uintptr_t)pres % 16) == 0) {
+        // one resident wave; runs of whole planes per thread, two planes loaded
+        // before a run's first
+        static int occ = 0;
+        const int wave = resident_wave((const void*)energy_field7_kernel<T>, 256, &occ);
+        if (wave == 0) return cudaErrorInvalidDevice;
+        const long long vcols = (long long)(n / V) * n;
+        const int nzc = balanced_zruns(vcols, n, (long long)wave * 256, 2.0);
+        const int blocks = (int)std::min<long long>(wave, (vcols * nzc + 255) / 256);
+        energy_field7_kernel<T><<<blocks, 256, 0, st>>>(b, M, sc, rho, pres, nzc);
+        return cudaGetLastError();
+    }
+    energy_field_kernel<T><<<energies_grid_blocks(n), 256, 0, st>>>(b, M, sc, rho, pres);
     return cudaGetLastError();
 }
 template cudaError_t launch_energy_field<float>(const Bufs<float>&, const Model&, const DevScalars*, float*, float*,

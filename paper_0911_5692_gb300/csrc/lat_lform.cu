@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "lat_grid.h"
 #include "lat_kernels.h"
 #include "lat_stencil27.cuh"
 
@@ -380,29 +381,15 @@ cudaError_t launch_lform(const Bufs<T>& b, const Model& M, DevScalars* sc, doubl
         return cudaGetLastError();
     }
     // One resident wave of blocks (no more than the sums pass, whose partials
-    // buffer this pass shares). Each thread marches whole z runs, so its time
-    // goes as (runs it takes) x (planes per run + the two it loads to start): the
-    // number of runs per column is the one that minimises that over the wave.
-    static int occ[2] = {0, 0};   // resident blocks per SM, per element size
-    int& o = occ[sizeof(T) == 4 ? 0 : 1];
-    if (o == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lform7_kernel<T>, 256, 0);
-        if (e != cudaSuccess || o < 1) o = 1;
-    }
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return cudaErrorInvalidDevice;
+    // buffer this pass shares); each thread marches whole z runs, two planes
+    // loaded before a run's first.
+    static int occ = 0;
+    const int wave = resident_wave((const void*)lform7_kernel<T>, 256, &occ);
+    if (wave == 0) return cudaErrorInvalidDevice;
     constexpr int V = 16 / sizeof(T);
     const long long vcols = (long long)(n / V) * n;
-    const int blocks_max = std::max(1, std::min(sums_grid_blocks(n), o * sms));
-    const long long threads = (long long)blocks_max * 256;
-    int nzc = 1;
-    double best = 0.0;
-    for (int c = 1; c <= n / 4; c++) {
-        const long long per_thread = (vcols * c + threads - 1) / threads;
-        const double cost = (double)per_thread * ((double)n / c + 2.0);
-        if (c == 1 || cost < best) { best = cost; nzc = c; }
-    }
+    const int blocks_max = std::max(1, std::min(sums_grid_blocks(n), wave));
+    const int nzc = balanced_zruns(vcols, n, (long long)blocks_max * 256, 2.0);
     const long long items = vcols * nzc;
     const int blocks = (int)std::min<long long>(blocks_max, (items + 255) / 256);
     lform7_kernel<T><<<blocks, 256, 0, st>>>(b, M, sc, partials, nzc);

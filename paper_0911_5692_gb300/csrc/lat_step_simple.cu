@@ -17,6 +17,7 @@
 // plane-ring kernel in lat_step_tma.cu is the fast FP32/FP64 path on sm_103a.
 #include <algorithm>
 
+#include "lat_grid.h"
 #include "lat_kernels.h"
 #include "lat_stencil27.cuh"
 
@@ -312,28 +313,15 @@ cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double
         if (M.stencil != 27) {
             // vector items: (n/4 vectors x n rows) columns cut into z runs. One
             // resident wave of blocks (no more than sums_grid_blocks, which sizes the
-            // partials buffer); each thread marches whole runs, so its time goes as
-            // (runs it takes) x (planes per run + 1): the run count minimises that.
+            // partials buffer); each thread marches whole runs, one plane loaded
+            // before a run's first.
             static int occ = 0;
-            if (occ == 0) {
-                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sums7_vec_kernel, 256, 0);
-                if (e != cudaSuccess || occ < 1) occ = 1;
-            }
-            int dev = 0, sms = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-                return cudaErrorInvalidDevice;
+            const int wave = resident_wave((const void*)sums7_vec_kernel, 256, &occ);
+            if (wave == 0) return cudaErrorInvalidDevice;
             const int n = M.n;
             const long long vcols = (long long)(n / 4) * n;
-            const int blocks_max = std::max(1, std::min(sums_grid_blocks(n), occ * sms));
-            const long long threads = (long long)blocks_max * 256;
-            int nzc = 1;
-            double best = 0.0;
-            for (int c = 1; c <= n / 4; c++) {
-                const long long per_thread = (vcols * c + threads - 1) / threads;
-                const double cost = (double)per_thread * ((double)n / c + 1.0);
-                if (c == 1 || cost < best) { best = cost; nzc = c; }
-            }
+            const int blocks_max = std::max(1, std::min(sums_grid_blocks(n), wave));
+            const int nzc = balanced_zruns(vcols, n, (long long)blocks_max * 256, 1.0);
             const long long items = vcols * nzc;
             const int blocks = (int)std::min<long long>(blocks_max, (items + 255) / 256);
             sums7_vec_kernel<<<blocks, 256, 0, st>>>(b, M, sc, partials, nzc);
