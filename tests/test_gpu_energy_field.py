@@ -105,3 +105,25 @@ def test_energy_field_and_upload_on_a_slab():
     for k in range(4):
         assert torch.equal(s.buffers[k], src[k].view_as(s.buffers[k]))
     s.close()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_energy_field_into_buffers_not_16_byte_aligned(prec):
+    """Buffers aligned to their element but not to 16 bytes take the per-site
+    kernel instead of the vector one; same results against the oracle."""
+    n = 20
+    p, st = _case("lphi4", n, prec, 7, 1, False)
+    g, o = paired(p, st, (0.0, 1.1, 0.4, 0))
+    dt = torch.float32 if prec == 32 else torch.float64
+    base = torch.empty(2 * n ** 3 + 2, dtype=dt, device="cuda")
+    rho, pres = base[1:1 + n ** 3], base[2 + n ** 3 - 1:2 * n ** 3 + 1]
+    assert rho.data_ptr() % 16 != 0 and pres.data_ptr() % 16 != 0
+    g.energy_field(rho, pres)
+    torch.cuda.synchronize()
+    ro, po = o.energy_field()
+    assert normwise(rho.double().cpu().numpy().reshape(n, n, n), ro) <= TOL[prec]
+    assert normwise(pres.double().cpu().numpy().reshape(n, n, n), po) <= TOL[prec]
+    # the vector kernel gives the same fields
+    r2, p2 = g.energy_field()
+    torch.cuda.synchronize()
+    assert normwise(r2.double().cpu().numpy(), ro) <= TOL[prec]
