@@ -935,6 +935,85 @@ int orc_spectrum(orc_lattice *L, int field, int nbins, double *k_out, double *p_
 
 /* Change g^2 (and with it kappa0 = g^2 / (A^2 B^2)) of an existing lattice; the
  * state and the sums (which do not involve g^2) are kept. */
+/* Observable 1 of the derivative: the fraction of the energy density in chi,
+ * at the momentum time t of the stored state (fields taken back half a step,
+ * f_t = f - (dt/2) pi; a_t = a - (dt/2) a'; h = a'/a_t):
+ *   K_i = <(pi_i - r h f_t,i)^2> / 2,   G_i = a_t^(-2s-2) <|grad+ f_t,i|^2> / 2,
+ *   W = <V_pr(f_t; a_t)>,   J = (K_1 + G_1) / (K_0 + K_1 + G_0 + G_1 + W),
+ * the terms of eq. rho-pres, whose physical factor (B/A)^2 a^(2s-2r) cancels in
+ * the ratio; the interaction energy counts in the total only. 7-point gradient.
+ * Writes J and, when fbar is not NULL, its gradient with respect to the stored
+ * f and pi (fbar, pibar, n^3 each), to a and a' (sb[0], sb[1]) and its direct
+ * derivative with respect to g^2 (sb[2]: through kappa0 = g^2/(A^2 B^2) in W,
+ * at a fixed state). */
+int orc_chi_fraction(const orc_lattice *L, double *J_out, double *fbar[2], double *pibar[2], double sb[3])
+{
+    const int n = L->n;
+    const size_t N3 = L->nsites;
+    const double dt = L->p.dt, r = L->r, s = L->s;
+    if (L->p.expansion == 2 || is27(L)) return ORC_EINVAL;
+    const double at = L->a - 0.5 * dt * L->ad;
+    const double h = L->p.expansion ? L->ad / at : 0.0;
+    const double cg = pow(at, -2.0 * s - 2.0), cd = cdom_at(L, at), kp = kappa_at(L, at);
+    double *ft[2], *lap[2];
+    for (int i = 0; i < 2; i++) {
+        ft[i] = (double *)malloc(N3 * sizeof(double));
+        lap[i] = (double *)malloc(N3 * sizeof(double));
+    }
+    if (!ft[0] || !ft[1] || !lap[0] || !lap[1]) {
+        for (int i = 0; i < 2; i++) { free(ft[i]); free(lap[i]); }
+        return ORC_ENOMEM;
+    }
+    for (int i = 0; i < 2; i++)
+        for (size_t k = 0; k < N3; k++) ft[i][k] = L->f[i][k] - 0.5 * dt * L->pi[i][k];
+    double K[2], G[2], UF[2], Wd = 0.0, Wi = 0.0;
+    for (int i = 0; i < 2; i++) {
+        double kk = 0.0, uf = 0.0;
+        for (size_t k = 0; k < N3; k++) {
+            double u = L->pi[i][k] - r * h * ft[i][k];
+            kk += 0.5 * u * u;
+            uf += u * ft[i][k];
+        }
+        K[i] = kk / (double)N3;
+        UF[i] = uf / (double)N3;
+        G[i] = 0.5 * cg * orc_grad2_mean(n, L->dx, ft[i]);
+    }
+    for (size_t k = 0; k < N3; k++) {
+        Wd += pow(ft[0][k], L->beta) / L->beta;
+        Wi += 0.5 * ft[0][k] * ft[0][k] * ft[1][k] * ft[1][k];
+    }
+    Wd /= (double)N3;
+    Wi /= (double)N3;
+    const double W = cd * Wd + kp * Wi;
+    const double D = K[0] + K[1] + G[0] + G[1] + W, J = (K[1] + G[1]) / D;
+    *J_out = J;
+    if (fbar) {
+        /* dJ = (dN - J dD) / D: weight (1 - J)/D on chi's own terms, -J/D on the rest */
+        const double w[2] = {-J / D, (1.0 - J) / D}, wW = -J / D;
+        for (int i = 0; i < 2; i++) orc_laplacian(n, L->dx, ft[i], lap[i]);
+        for (size_t k = 0; k < N3; k++) {
+            const double a0 = ft[0][k], a1 = ft[1][k];
+            const double dW[2] = {cd * pow(a0, L->beta - 1.0) + kp * a0 * a1 * a1, kp * a0 * a0 * a1};
+            for (int i = 0; i < 2; i++) {
+                const double u = L->pi[i][k] - r * h * ft[i][k];
+                const double gf = (w[i] * (-r * h * u - cg * lap[i][k]) + wW * dW[i]) / (double)N3;
+                fbar[i][k] = gf;
+                pibar[i][k] = w[i] * u / (double)N3 - 0.5 * dt * gf;
+            }
+        }
+        const double dJ_dh = w[0] * (-r * UF[0]) + w[1] * (-r * UF[1]);
+        const double dJ_dat = (w[0] * G[0] + w[1] * G[1]) * (-2.0 * s - 2.0) / at
+                            + wW * (L->pdom * cd * Wd + L->pint * kp * Wi) / at;
+        const double dh_da = L->p.expansion ? -L->ad / (at * at) : 0.0;
+        const double dh_dad = L->p.expansion ? 1.0 / at + 0.5 * dt * L->ad / (at * at) : 0.0;
+        sb[0] = L->p.expansion ? dJ_dat + dJ_dh * dh_da : 0.0;
+        sb[1] = L->p.expansion ? -0.5 * dt * dJ_dat + dJ_dh * dh_dad : 0.0;
+        sb[2] = wW * Wi * pow(at, L->pint) / (L->A * L->A * L->B * L->B);
+    }
+    for (int i = 0; i < 2; i++) { free(ft[i]); free(lap[i]); }
+    return ORC_OK;
+}
+
 int orc_set_g2(orc_lattice *L, double g2)
 {
     L->p.g2 = g2;

@@ -68,6 +68,7 @@ def lib():
             L.orc_array.restype = dp
             L.orc_get_scalars.argtypes = [P, dp]
             L.orc_set_scalars.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int64]
+            L.orc_chi_fraction.argtypes = [P, dp, C.POINTER(dp), C.POINTER(dp), dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_set_threads.restype = C.c_int
             L.orc_get_ell.argtypes = [P]
@@ -263,6 +264,36 @@ class Oracle:
         zeros = np.zeros((n, n, n))
         fb, pb, _, _, _, dg2 = self.vjp(nsteps, [zeros, 2.0 * f1 / n ** 3], [zeros, zeros])
         return J, fb, pb, dg2
+
+    def chi_fraction(self, with_gradient: bool = False):
+        """Observable 1: the fraction of the energy density in chi at the momentum
+        time of the stored state (orc_chi_fraction). With with_gradient, also its
+        gradient with respect to the stored f, pi (two arrays each), a, a' and
+        its direct derivative with respect to g^2 (at a fixed state)."""
+        n, n3 = self.n, self.n ** 3
+        J = C.c_double()
+        if not with_gradient:
+            _check(self._L.orc_chi_fraction(self._h, C.byref(J), None, None, None), "orc_chi_fraction")
+            return J.value
+        fb = [np.zeros(n3) for _ in range(2)]
+        pb = [np.zeros(n3) for _ in range(2)]
+        sb = np.zeros(3)
+        fps = (C.POINTER(C.c_double) * 2)(_dp(fb[0]), _dp(fb[1]))
+        pps = (C.POINTER(C.c_double) * 2)(_dp(pb[0]), _dp(pb[1]))
+        _check(self._L.orc_chi_fraction(self._h, C.byref(J), fps, pps, _dp(sb)), "orc_chi_fraction")
+        shp = (n,) * 3
+        return J.value, [f.reshape(shp) for f in fb], [q.reshape(shp) for q in pb], sb[0], sb[1], sb[2]
+
+    def chi_fraction_gradient(self, nsteps: int):
+        """Observable 1 after nsteps steps from the current state and its gradient
+        with respect to the current (f, pi) and g^2, as chi2_gradient."""
+        st = self.get_state()
+        sc = self.scalars()
+        self.step(nsteps)
+        J, fb, pb, ab, adb, dg2_direct = self.chi_fraction(with_gradient=True)
+        self.set_state(*st, t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
+        fb0, pb0, _, _, _, dg2 = self.vjp(nsteps, fb, pb, ab, adb)
+        return J, fb0, pb0, dg2 + dg2_direct
 
     def spectrum(self, field: int, nbins: int):
         k = np.zeros(nbins); p = np.zeros(nbins); c = np.zeros(nbins, dtype=np.int64)
