@@ -305,7 +305,14 @@ lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fba
 
 /* Value and gradient of an observable of the state after n_steps with respect
  * to the starting f, pi and g^2, by lat_vjp. observable 0: J = <chi^2>, the
- * volume mean of the squared program-unit chi (f_1). J_out (host, may be NULL)
+ * volume mean of the squared program-unit chi (f_1). observable 1: the fraction
+ * of the energy density in chi, eq. rho-pres's terms at the momentum time t of
+ * the final state (fields and a taken back half a step: f_t = f - (dt/2) pi,
+ * a_t = a - (dt/2) a', h = a'/a_t): J = (K_chi + G_chi) / (K_phi + K_chi + G_phi +
+ * G_chi + <V_pr>) with K_i = <(pi_i - r h f_t,i)^2>/2 and G_i = a_t^(-2s-2)
+ * <|grad+ f_t,i|^2>/2 (the physical factor cancels; the interaction energy counts
+ * in the total only, so J also depends on g^2 directly, which dJ/dg^2 includes).
+ * J_out (host, may be NULL)
  * gets J; dJ_dg2 (host, may be NULL) gets dJ/dg^2; dJ_df_dev and dJ_dpi_dev
  * (device, 2 n^3 elements each, as in lat_vjp) get dJ/df and dJ/dpi of the
  * starting state. n_steps = 0 gives J and its gradient at the current state.

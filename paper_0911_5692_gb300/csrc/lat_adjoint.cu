@@ -709,6 +709,111 @@ __global__ void __launch_bounds__(kAdjThreads) chi2_kernel(const T* __restrict__
     if (threadIdx.x == 0) partials[blockIdx.x] = bs[0];
 }
 
+// Observable 1: the fraction of the energy density in chi at the momentum time
+// of the final state, fields and a taken back half a step (f_t = f - (dt/2) pi,
+// a_t = a - (dt/2) a', h = a'/a_t): K_i = <(pi_i - r h f_t,i)^2>/2,
+// G_i = a_t^(-2s-2) <|grad+ f_t,i|^2>/2, W = <V_pr(f_t; a_t)>,
+// J = (K_1 + G_1) / (K_0 + K_1 + G_0 + G_1 + W) (eq. rho-pres; the physical
+// factor cancels in the ratio). FP64 arithmetic from the stored elements.
+struct FracConst {
+    double dt2, rh, cg, cd, kp, inv_dx2;
+    int beta;
+};
+constexpr int kFracSums = 8;   // sum u0^2, u1^2, |d+ f_t0|^2, |d+ f_t1|^2, f_t0^beta/beta, f_t0^2 f_t1^2/2, u0 f_t0, u1 f_t1
+
+template <typename T>
+__device__ __forceinline__ double ft_at(const T* f, const T* p, size_t i, double dt2)
+{
+    return (double)f[i] - dt2 * (double)p[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads) frac_sums_kernel(const T* __restrict__ f0, const T* __restrict__ f1,
+                                                                const T* __restrict__ p0, const T* __restrict__ p1,
+                                                                int n, FracConst c, double* partials)
+{
+    __shared__ double red[kAdjThreads / 32][kFracSums];
+    double acc[kFracSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const long long n3 = (long long)n * n * n;
+    const T* f[2] = {f0, f1};
+    const T* p[2] = {p0, p1};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long long)n * n));
+        const size_t nb[3] = {((size_t)z * n + y) * n + (x == n - 1 ? 0 : x + 1),
+                              ((size_t)z * n + (y == n - 1 ? 0 : y + 1)) * n + x,
+                              ((size_t)(z == n - 1 ? 0 : z + 1) * n + y) * n + x};
+        double t[2];
+        for (int k = 0; k < 2; k++) {
+            t[k] = ft_at(f[k], p[k], (size_t)i, c.dt2);
+            const double u = (double)p[k][i] - c.rh * t[k];
+            acc[k] += u * u;
+            acc[6 + k] += u * t[k];
+            double g = 0.0;
+            for (int d = 0; d < 3; d++) {
+                const double e = ft_at(f[k], p[k], nb[d], c.dt2) - t[k];
+                g += e * e;
+            }
+            acc[2 + k] += g;
+        }
+        const double sq = t[0] * t[0];
+        acc[4] += c.beta == 4 ? 0.25 * sq * sq : 0.5 * sq;
+        acc[5] += 0.5 * sq * t[1] * t[1];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < kFracSums; k++) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kFracSums) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * kFracSums + threadIdx.x] = v;
+    }
+}
+
+// dJ/df and dJ/dpi of the stored final state: with dJ = (dN - J dD)/D, weights
+// w_i on field i's own kinetic and gradient terms ((1 - J)/D for chi, -J/D for
+// phi) and wW = -J/D on W,
+//   g_i = (w_i (-r h u_i - a_t^(-2s-2) L f_t,i) + wW dV_pr/df_t,i) / N^3,
+//   dJ/df_i = g_i, dJ/dpi_i = w_i u_i / N^3 - (dt/2) g_i  (u_i = pi_i - r h f_t,i).
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads) frac_seed_kernel(const T* __restrict__ f0, const T* __restrict__ f1,
+                                                                const T* __restrict__ p0, const T* __restrict__ p1,
+                                                                int n, FracConst c, double w0, double w1, double wW,
+                                                                double inv_sites, T* __restrict__ fb, T* __restrict__ pb)
+{
+    const long long n3 = (long long)n * n * n;
+    const T* f[2] = {f0, f1};
+    const T* p[2] = {p0, p1};
+    const double w[2] = {w0, w1};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((long long)n * n));
+        const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? n - 1 : z - 1, zp = z == n - 1 ? 0 : z + 1;
+        const size_t nb[6] = {((size_t)z * n + y) * n + xm,  ((size_t)z * n + y) * n + xp,
+                              ((size_t)z * n + ym) * n + x,  ((size_t)z * n + yp) * n + x,
+                              ((size_t)zm * n + y) * n + x,  ((size_t)zp * n + y) * n + x};
+        double t[2], lap[2];
+        for (int k = 0; k < 2; k++) {
+            t[k] = ft_at(f[k], p[k], (size_t)i, c.dt2);
+            double l = 0.0;
+            for (int d = 0; d < 6; d++) l += ft_at(f[k], p[k], nb[d], c.dt2) - t[k];
+            lap[k] = l * c.inv_dx2;
+        }
+        const double dW[2] = {c.cd * (c.beta == 4 ? t[0] * t[0] * t[0] : t[0]) + c.kp * t[0] * t[1] * t[1],
+                              c.kp * t[0] * t[0] * t[1]};
+        for (int k = 0; k < 2; k++) {
+            const double u = (double)p[k][i] - c.rh * t[k];
+            const double g = (w[k] * (-c.rh * u - c.cg * lap[k]) + wW * dW[k]) * inv_sites;
+            fb[(size_t)k * n3 + i] = (T)g;
+            pb[(size_t)k * n3 + i] = (T)(w[k] * u * inv_sites - c.dt2 * g);
+        }
+    }
+}
+
 int adj_blocks(long long n3)
 {
     int dev = 0, sms = 148;
@@ -799,7 +904,9 @@ struct Scratch {
 };
 
 // Reverse-mode product of n steps. If observable >= 0 the adjoint of the final
-// state is that of the observable (0: <chi^2>), written into fb/pb after the
+// state is that of the observable (0: <chi^2>; 1: the fraction of the energy
+// density in chi), written into fb/pb (and, for 1, into the adjoints of a, a'
+// and kappa0) after the
 // forward pass, and *J_out receives its value; otherwise fb, pb and sbar[0..1]
 // carry the adjoint of the final state in.
 template <typename T>
@@ -847,7 +954,8 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
     if (!S.alloc(&ck, (size_t)nck * 6 * ab) || !S.alloc(&ck_sc, (size_t)nck * sizeof(DevScalars)) ||
         !S.alloc(&hist, (size_t)(n + 1) * sizeof(DevScalars)) || !S.alloc(&seg, (size_t)K * 2 * ab) ||
         !S.alloc(&adj1, 4 * ab) || !S.alloc(&fin, 4 * ab) || !S.alloc(&fin_sc, sizeof(DevScalars)) ||
-        !S.alloc(&as, sizeof(AdjScalars)) || !S.alloc(&part, nparts * kSums * sizeof(double)))
+        !S.alloc(&as, sizeof(AdjScalars)) ||
+        !S.alloc(&part, std::max(nparts * kSums, (size_t)nb * kFracSums) * sizeof(double)))
         return LAT_ENOMEM;
     Bufs<T> hb = bufs_of<T>(h);
     auto arr = [&](T* base, size_t i) { return base + i * N3; };
@@ -899,6 +1007,46 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
         double J = 0.0;
         for (int b = 0; b < nb; b++) J += hp[b];
         if (J_out) *J_out = J * M.inv_sites;
+    } else if (observable == 1) {
+        DevScalars sF;
+        LAT_CUDA(cudaMemcpyAsync(&sF, fin_sc, sizeof(sF), cudaMemcpyDeviceToHost, st));
+        LAT_CUDA(cudaStreamSynchronize(st));
+        const double at = sF.a - 0.5 * M.dt * sF.ad;
+        const double h = M.expansion ? sF.ad / at : 0.0;
+        FracConst c;
+        c.dt2 = 0.5 * M.dt;
+        c.rh = M.r * h;
+        c.cg = std::pow(at, -2.0 * M.s - 2.0);
+        c.cd = M.cdom0 * std::pow(at, M.pdom);
+        c.kp = M.kappa0 * std::pow(at, M.pint);
+        c.inv_dx2 = M.inv_dx2;
+        c.beta = M.beta;
+        const T *F0 = hb.f[parN][0], *F1 = hb.f[parN][1], *P0 = hb.p[parN][0], *P1 = hb.p[parN][1];
+        frac_sums_kernel<T><<<nb, kAdjThreads, 0, st>>>(F0, F1, P0, P1, M.n, c, part);
+        LAT_CUDA(cudaGetLastError());
+        std::vector<double> hp((size_t)nb * kFracSums);
+        LAT_CUDA(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LAT_CUDA(cudaStreamSynchronize(st));
+        double S[kFracSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int b = 0; b < nb; b++)
+            for (int k = 0; k < kFracSums; k++) S[k] += hp[(size_t)b * kFracSums + k];
+        const double is = M.inv_sites;
+        const double K0 = 0.5 * S[0] * is, K1 = 0.5 * S[1] * is;
+        const double G0 = 0.5 * c.cg * S[2] * M.inv_dx2 * is, G1 = 0.5 * c.cg * S[3] * M.inv_dx2 * is;
+        const double Wd = S[4] * is, Wi = S[5] * is, UF0 = S[6] * is, UF1 = S[7] * is;
+        const double W = c.cd * Wd + c.kp * Wi, D = K0 + K1 + G0 + G1 + W, J = (K1 + G1) / D;
+        if (!std::isfinite(J) || !(D != 0.0)) return LAT_ENONFINITE;
+        if (J_out) *J_out = J;
+        const double w0 = -J / D, w1 = (1.0 - J) / D, wW = -J / D;
+        frac_seed_kernel<T><<<nb, kAdjThreads, 0, st>>>(F0, F1, P0, P1, M.n, c, w0, w1, wW, is, fb_user, pb_user);
+        LAT_CUDA(cudaGetLastError());
+        const double dJ_dh = w0 * (-M.r * UF0) + w1 * (-M.r * UF1);
+        const double dJ_dat = (w0 * G0 + w1 * G1) * (-2.0 * M.s - 2.0) / at + wW * (M.pdom * c.cd * Wd + M.pint * c.kp * Wi) / at;
+        if (M.expansion) {
+            a0.ba = dJ_dat + dJ_dh * (-sF.ad / (at * at));
+            a0.bad = -0.5 * M.dt * dJ_dat + dJ_dh * (1.0 / at + 0.5 * M.dt * sF.ad / (at * at));
+        }
+        a0.bk0 = wW * Wi * std::pow(at, M.pint);   // J's own dependence on kappa0 (the interaction energy)
     } else {
         a0.ba = sbar[0];
         a0.bad = sbar[1];
@@ -1024,7 +1172,7 @@ lat_status lat_adjoint(lat_handle* h, int64_t n_steps, int observable, int64_t c
     if (!h || n_steps < 0 || ckpt_every < 0 || !dJ_df_dev || !dJ_dpi_dev) return LAT_EINVAL;
     if (h->slab) return LAT_ESTATE;
     if (h->M.stencil == 27 || h->M.expansion == 2) return LAT_EUNSUPPORTED;
-    if (observable != 0) return LAT_EUNSUPPORTED;
+    if (observable != 0 && observable != 1) return LAT_EUNSUPPORTED;
     if (((uintptr_t)dJ_df_dev | (uintptr_t)dJ_dpi_dev) % h->esize != 0) return LAT_EINVAL;
     double sbar[4] = {0.0, 0.0, 0.0, 0.0};
     const lat_status st =

@@ -399,10 +399,11 @@ class Lattice:
         return sb[0], sb[1], sb[2], sb[3]
 
     def adjoint(self, n_steps: int, observable: int = 0, ckpt_every: int = 0):
-        """J = <chi^2> after n_steps and its gradient with respect to the current
-        state and g^2 (lat_adjoint). Returns (J, dJ/df, dJ/dpi, dJ/dg2) with the
-        gradients as CUDA tensors of shape (2, n, n, n). The lattice ends advanced
-        by n_steps."""
+        """An observable of the state after n_steps and its gradient with respect
+        to the current state and g^2 (lat_adjoint): observable 0, J = <chi^2>;
+        1, the fraction of the energy density in chi. Returns (J, dJ/df, dJ/dpi,
+        dJ/dg2) with the gradients as CUDA tensors of shape (2, n, n, n). The
+        lattice ends advanced by n_steps."""
         torch = self._torch
         n3 = self.n ** 3
         df = torch.empty(2 * n3, dtype=self.dtype, device=self.device)

@@ -252,3 +252,91 @@ def test_set_g2_matches_fresh_handle():
         assert np.array_equal(x, y)
     with pytest.raises(LatticeError):
         a.set_g2(-1.0)
+
+
+# ------------------------------------------------------------------ observable 1: energy fraction in chi
+
+def _oracle_frac(p, st, sc, nsteps):
+    o = Oracle(p)
+    o.set_state(*st, **sc)
+    return o.chi_fraction_gradient(nsteps)
+
+
+@pytest.mark.parametrize("model,expansion", [("lphi4", 1), ("lphi4", 0), ("m2phi2", 1)])
+def test_energy_fraction_fp64_matches_oracle(model, expansion):
+    n, steps = 16, 40
+    p, st, sc = _case(model, n, 64, expansion)
+    g = _gpu(p, st, sc)
+    J, df, dp, dg2 = g.adjoint(steps, observable=1)
+    Jo, dfo, dpo, dg2o = _oracle_frac(p, st, sc, steps)
+    assert abs(J - Jo) <= 1e-12 * abs(Jo)
+    assert abs(dg2 - dg2o) <= 1e-10 * abs(dg2o)
+    df, dp = df.cpu().numpy(), dp.cpu().numpy()
+    for i in (0, 1):
+        assert normwise(df[i], dfo[i]) <= 1e-10, ("df", i)
+        assert normwise(dp[i], dpo[i]) <= 1e-10, ("dp", i)
+
+
+def test_energy_fraction_zero_steps_is_the_oracle_seed():
+    n = 16
+    p, st, sc = _case("lphi4", n, 64)
+    g = _gpu(p, st, sc)
+    J, df, dp, dg2 = g.adjoint(0, observable=1)
+    o = Oracle(p)
+    o.set_state(*st, **sc)
+    Jo, fbo, pbo, _, _, dg2o = o.chi_fraction(with_gradient=True)
+    assert J == pytest.approx(Jo, rel=1e-13)
+    assert dg2 == pytest.approx(dg2o, rel=1e-12)
+    df, dp = df.cpu().numpy(), dp.cpu().numpy()
+    for i in (0, 1):
+        assert normwise(df[i], fbo[i]) <= 1e-12
+        assert normwise(dp[i], pbo[i]) <= 1e-12
+
+
+def test_energy_fraction_central_difference_on_gpu_fp64():
+    """dJ/dg2 of the GPU's own forward map by central differences (16^3 FP64)."""
+    n, steps = 16, 30
+    p, st, sc = _case("lphi4", n, 64)
+
+    def final(g2):
+        g = Lattice(dict(p, g2=g2))
+        g.set_state(*st, **sc)
+        return g.adjoint(steps, observable=1)[0]
+
+    g = _gpu(p, st, sc)
+    _, _, _, dg2 = g.adjoint(steps, observable=1)
+    e = 1e-6 * p["g2"]
+    fd = (final(p["g2"] + e) - final(p["g2"] - e)) / (2 * e)
+    assert abs(dg2 - fd) <= 1e-7 * abs(fd)
+
+
+@pytest.mark.parametrize("n,steps", [(32, 50), (64, 12)])
+def test_energy_fraction_fp32_matches_oracle(n, steps):
+    p, st, sc = _case("lphi4", n, 32)
+    g = _gpu(p, st, sc)
+    J, df, dp, dg2 = g.adjoint(steps, observable=1)
+    Jo, dfo, dpo, dg2o = _oracle_frac(dict(p, precision=64), st, sc, steps)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    assert abs(dg2 - dg2o) <= 2e-4 * abs(dg2o)
+    df, dp = df.cpu().numpy(), dp.cpu().numpy()
+    for i in (0, 1):
+        assert normwise(df[i], dfo[i]) <= 2e-4, ("df", i, normwise(df[i], dfo[i]))
+        assert normwise(dp[i], dpo[i]) <= 2e-4, ("dp", i, normwise(dp[i], dpo[i]))
+
+
+def test_autograd_energy_fraction():
+    n, steps = 16, 15
+    p, st, sc = _case("lphi4", n, 64)
+    g = Lattice(p)
+    f = torch.tensor(np.stack(st[0:2]), device="cuda", requires_grad=True)
+    pi = torch.tensor(np.stack(st[2:4]), device="cuda", requires_grad=True)
+    g2 = torch.tensor(p["g2"], dtype=torch.float64, requires_grad=True)
+    J = LatticeEvolve.apply(f, pi, g2, g, steps, sc, 0, 1)
+    J.backward()
+    Jo, dfo, dpo, dg2o = _oracle_frac(p, st, sc, steps)
+    assert float(J) == pytest.approx(Jo, rel=1e-12)
+    assert abs(float(g2.grad) - dg2o) <= 1e-10 * abs(dg2o)
+    for i in (0, 1):
+        assert normwise(f.grad[i].cpu().numpy(), dfo[i]) <= 1e-10
+        assert normwise(pi.grad[i].cpu().numpy(), dpo[i]) <= 1e-10
+
