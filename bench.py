@@ -659,8 +659,15 @@ def run_ours(args):
         "gpu_launches": args.steps * info["launches_per_step"],
         "clocks": clocks.summary(),
         "context": {"paper_gtx260_256cubed_su_per_s": 7.6e8,
-                    "note": "paper: GTX 260, 27-point stencil, 0.022 s/step at 256^3; the same configuration "
-                            "with the 27-point stencil is timed under stencil27"},
+                    "paper_gtx260_128cubed_su_per_s": 6.2e8,
+                    "paper_speedup_vs_defrost_xeon_256cubed": 14.5,
+                    "paper_speedup_vs_latticeeasy_256cubed": 58.0,
+                    "ours_over_paper_gpu": value / world / 7.6e8,
+                    "note": "paper (Sec. III, context only, other hardware): GTX 260 SP216, 27-point stencil, "
+                            "0.022 s/step at 256^3 (< 900 s for 2^18 steps at 128^3); 14.5x DEFROST's 0.32 s/step "
+                            "on a Xeon, a further 4x over LATTICEEASY. ours_over_paper_gpu compares this 7-point "
+                            "line per GPU; the same configuration with the 27-point stencil is timed under "
+                            "stencil27 (vs_paper)"},
     }
     if not args.no_extras and world == 1:
         lat.close()
