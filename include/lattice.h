@@ -41,7 +41,7 @@ typedef enum {
     LAT_ECUDA = 4,        /* a CUDA runtime or library call failed */
     LAT_ENONFINITE = 5,   /* non-finite sums or no real root for a' (sticky) */
     LAT_ETIMEOUT = 6,     /* a bounded device wait ran out (sticky) */
-    LAT_EUNSUPPORTED = 7, /* valid request this build cannot serve */
+    LAT_EUNSUPPORTED = 7, /* valid request the library does not serve */
     LAT_ESTATE = 8        /* call not valid in the handle's current state */
 } lat_status;
 
