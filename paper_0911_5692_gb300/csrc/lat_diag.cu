@@ -327,8 +327,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
                 for (int j = 0; j < V; j++) {
                     const T cc = c[i].v[j];
-                    const T d[6] = {(j == 0 ? cu[i].l : c[i].v[j - 1]) - cc, (j == V - 1 ? cu[i].r : c[i].v[j + 1]) - cc,
-                                    cu[i].a.v[j] - cc, cu[i].b.v[j] - cc, cm[i].v[j] - cc, cu[i].cp.v[j] - cc};
+                    const T left = j == 0 ? cu[i].l : c[i].v[j - 1], right = j == V - 1 ? cu[i].r : c[i].v[j + 1];
+                    const T d[6] = {left - cc, right - cc, cu[i].a.v[j] - cc, cu[i].b.v[j] - cc, cm[i].v[j] - cc,
+                                    cu[i].cp.v[j] - cc};
                     T l = T(0), g = T(0);
 #pragma unroll
                     for (int k = 0; k < 6; k++) {

@@ -201,7 +201,7 @@ __device__ inline void lform_finish(const Model& M, DevScalars* sc, double* part
 template <typename T>
 __device__ inline SiteCoef<T> block_coefs(const Model& M, const DevScalars* sc, double* w0_used)
 {
-    __shared__ double kc[5];
+    __shared__ double kc[4];
     if (threadIdx.x == 0) {
         const LfConst k = lf_const(M, sc);
         kc[0] = k.cL * M.lap_scale;
@@ -228,7 +228,8 @@ __device__ inline SiteCoef<T> block_coefs(const Model& M, const DevScalars* sc, 
 // FP32: at most 128 registers, for 2 blocks (16 warps) per SM, each with the
 // loads of two planes in flight.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) lform7_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, int nzc)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    lform7_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, int nzc)
 {
     constexpr int V = 16 / sizeof(T);
     using Raw = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
