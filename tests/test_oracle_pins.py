@@ -435,3 +435,29 @@ def test_initial_state_is_desynchronised():
     d = b.derived()
     H0 = math.sqrt(p["eight_pi_G"] * p["lam"] / 4 * p["phi0"][0] ** 4 / 3)
     assert abs(b.scalars()["ad"] - H0 / d["B"]) < 1e-12 * H0 / d["B"]
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """Every oracle sum is taken per z-plane and the planes are added in index
+    order, so one thread and all threads give bit-identical steps, sums and
+    energies (the CPU baseline is timed both ways)."""
+    from oracle.oracle import set_threads
+    n = 12
+    p = lphi4(n, precision=64)
+    st = random_state(n, 21, 64, f_mean=(1.0, 0.0), f_amp=(1e-3, 1e-3), pi_mean=(0.5, 0.0), pi_amp=(1e-3, 1e-3))
+    out = []
+    before = set_threads(0)
+    try:
+        for threads in (1, max(2, os.cpu_count() or 2)):
+            set_threads(threads)
+            o = Oracle(p)
+            o.set_state(*st, t=0.0, a=1.1, ad=0.45)
+            o.step(7)
+            out.append((o.get_state(), o.scalars(), o.energies()))
+    finally:
+        set_threads(before)
+    (s1, c1, e1), (s2, c2, e2) = out
+    for x, y in zip(s1, s2):
+        assert np.array_equal(x, y)
+    assert c1 == c2
+    assert e1 == e2
