@@ -128,4 +128,6 @@ def test_null_arguments():
     assert L.lat_sync(None) == 1
     assert L.lat_energy_field(None, None, None) == 1
     assert L.lat_upload_state(None, None, 0) == 1
+    assert L.lat_get_hubble_length(None, None) == 1
+    assert L.lat_set_hubble_length(None, 1.0) == 1
     L.lat_destroy(None)
