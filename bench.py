@@ -42,10 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="m2phi2_256_fp32")
+    ap.add_argument("--workload", default="lphi4_512_fp32")
     ap.add_argument("--variant", type=int, default=0,
-                    help="step kernel: 0 auto, 1 plain loads, 2 plane ring (cp.async), 3 plane ring (TMA), "
-                         "4 plane ring over x tiles")
+                    help="step kernel: 0 auto, 2 plane ring over full rows, 4 plane ring over x tiles")
     ap.add_argument("--stencil", type=int, choices=[7, 27], default=7,
                     help="Laplacian: 7-point, or the paper's 27-point stencil (Sec. II.C)")
     ap.add_argument("--expansion", type=int, choices=[1, 2], default=1,
@@ -78,6 +77,7 @@ def config_of(name, p, world):
     state = 8 * n ** 3 * esize
     return {"workload": name, "model": model_name(p), "stencil": int(p.get("stencil", 7)), "n": n, "sites": n ** 3,
             "precision": p["precision"],
+            "storage": "phi as an FP64 homogeneous mode + fluctuation arrays" if p.get("split") else "fields whole",
             "expansion": bool(p["expansion"]),
             "scale_factor": {0: "static", 1: "eq. scale", 2: "L = 1/H form"}[int(p["expansion"])],
             "global_batch": world, "lattices_per_gpu": 1,
@@ -395,11 +395,11 @@ def measure_diagnostics(local, name, every=512, steps=2048):
             "energies_ms_wall": energies_ms, "spectrum_ms_wall": spectrum_ms}
 
 
-def measure_step(local, name="lphi4_512_fp32", steps=300):
+def measure_step(local, name="m2phi2_256_fp32", steps=300):
     """The fused 7-point step of another workload with the automatic kernel
-    choice: lambda phi^4 at 512^3 FP32 is the lattice the >= 70 % roofline target
-    is set on. CUDA events over graph replays after warm-up; the state (4.3 GB)
-    exceeds L2."""
+    choice (m^2 phi^2 at 256^3 FP32 is the configuration of the paper's own
+    timing). CUDA events over graph replays after warm-up; the state (537 MB at
+    256^3) exceeds L2."""
     import torch
     from paper_0911_5692_gb300 import Lattice
     p = workload(name)
@@ -472,34 +472,35 @@ def measure_lform(local, name, steps=320):
 
 
 def measure_fp32_error(local, name, steps=200):
-    """FP32 against FP64 on the GPU for the benchmark workload: both precisions
-    from the same initial state (FP64 initialisation rounded to FP32), `steps`
-    steps, normwise error on the strided subset of 32^3 sites."""
+    """FP32 against FP64 on the GPU for a workload: the FP32 lattice as the
+    workload stores it (phi split into an FP64 homogeneous mode and FP32
+    fluctuations) and an FP64 lattice with phi whole, both initialised from the
+    same seed by their own pipelines, `steps` steps, normwise error on the strided
+    subset of 32^3 sites, against the whole field and against its fluctuation
+    part."""
     import numpy as np
     from paper_0911_5692_gb300 import Lattice
     p = workload(name)
     n = p["n"]
-    g64 = Lattice(dict(p, precision=64), device=local)
+    g64 = Lattice(dict(p, precision=64, split=0), device=local)
     g64.init_fields()
-    st = g64.get_state()
-    sc = g64.scalars()
     g32 = Lattice(dict(p, precision=32), device=local)
-    g32.set_state(*[a.astype(np.float32) for a in st], t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
-    g64.set_state(*[a.astype(np.float32).astype(np.float64) for a in st], t=sc["t"], a=sc["a"], ad=sc["ad"],
-                  step=sc["step"])
+    g32.init_fields()
     g32.evolve(steps)
     g64.evolve(steps)
     stride = max(1, n // 32)
     names = ("f_phi", "f_chi", "pi_phi", "pi_chi")
     err = {}
-    for k, (a, b) in enumerate(zip(g32.get_state(), g64.get_state())):
+    for k, (a, b) in enumerate(zip(g32.get_state_exact(), g64.get_state())):
         a, b = a[::stride, ::stride, ::stride], b[::stride, ::stride, ::stride]
         d = b - b.mean() if k in (0, 2) else b
         err[names[k]] = float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
         err[names[k] + "_fluct"] = float(np.max(np.abs(a - b)) / max(np.max(np.abs(d)), 1e-300))
     s32, s64 = g32.scalars(), g64.scalars()
-    return {"steps": steps, "subset": f"every {stride}th site per axis", "normwise": err,
-            "a_rel": abs(s32["a"] / s64["a"] - 1)}
+    g32.close()
+    g64.close()
+    return {"steps": steps, "subset": f"every {stride}th site per axis", "fp32_storage":
+            "phi split" if p.get("split") else "fields whole", "normwise": err, "a_rel": abs(s32["a"] / s64["a"] - 1)}
 
 
 def run_reference(args):
@@ -601,33 +602,36 @@ def run_ours(args):
     ms_per_step = ms_max / args.steps
 
     # end to end through the C ABI with host buffers: every step uploads the
-    # state (4 arrays) from pinned host memory (lat_upload_state), advances one
-    # step (the sums of the uploaded fields, then the fused step) and reads the
-    # scalars (t, a, a', step, sums) back.
+    # stored state (4 arrays) from pinned host memory (lat_upload_state), advances
+    # one step (the sums of the uploaded fields, then the fused step), and copies
+    # the evolved state back into the same host arrays (lat_download_state) and
+    # the scalars (t, a, a', step, sums; lat_get_scalars).
     E = max(1, args.e2e_steps)
     host = []
-    for w in (0, 1):
+    for w in (2, 3):
         for f in (0, 1):
             d = lat.get_state_device(f, w)
             hbuf = torch.empty_like(d, device="cpu").pin_memory()
             hbuf.copy_(d)
-            host.append((f, w, hbuf))
+            host.append(hbuf)
     lib, h = lat._L, lat._h
     out8 = (C.c_double * 8)()
+    bufs = (C.c_void_p * 4)(*[hbuf.data_ptr() for hbuf in host])   # f0, f1, pi0, pi1 as stored
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    srcs = (C.c_void_p * 4)(*[hbuf.data_ptr() for f, w, hbuf in host])   # f0, f1, pi0, pi1
     for _ in range(E):
-        assert lib.lat_upload_state(h, srcs, 0) == 0
+        assert lib.lat_upload_state(h, bufs, 0) == 0
         assert lib.lat_evolve(h, 1) == 0
+        assert lib.lat_download_state(h, bufs, 0) == 0
         assert lib.lat_get_scalars(h, out8) == 0
     e2e_sec = time.perf_counter() - t0
     te = torch.tensor([e2e_sec], dtype=torch.float64, device=f"cuda:{local}")
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * n ** 3 * E / float(te.item())
+    del host
 
     if rank != 0:
         if world > 1:
@@ -655,7 +659,9 @@ def run_ours(args):
                                f"{', 27-point Laplacian' if args.stencil == 27 else ''} ({info['blocks']} blocks x "
                                f"{info['threads']} threads, ty={info['ty']}, zr={info['zr']}, depth={info['depth']})"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3 * esize,
-                "d2h_bytes_per_step": 8 * 8, "steps": E},
+                "d2h_bytes_per_step": 4 * n ** 3 * esize + 8 * 8, "steps": E,
+                "per_step": "upload of the stored state from pinned host memory, one step, download of the "
+                            "evolved state and the scalars"},
         "gpu_launches": args.steps * info["launches_per_step"],
         "clocks": clocks.summary(),
         "context": {"paper_gtx260_256cubed_su_per_s": 7.6e8,
@@ -671,9 +677,9 @@ def run_ours(args):
     }
     if not args.no_extras and world == 1:
         lat.close()
-        line["step_512"] = measure_step(local)
+        line["step_256"] = measure_step(local, "m2phi2_256_fp32", steps=1000)
         line["fp32_vs_fp64"] = measure_fp32_error(local, args.workload)
-        line["fp32_vs_fp64_512"] = measure_fp32_error(local, "lphi4_512_fp32")
+        line["fp32_vs_fp64_256"] = measure_fp32_error(local, "m2phi2_256_fp32")
         line["adjoint"] = measure_adjoint(local)
         line["adjoint_256"] = measure_adjoint(local, n=256, steps=400)
         line["ensemble"] = measure_ensemble(local)

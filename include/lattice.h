@@ -74,7 +74,17 @@ typedef struct {
                              27 = the 27-point stencil of Patra and Karttunen over
                              the 3x3x3 cube, weights 14/30 (6 faces), 3/30 (12
                              edges), 1/30 (8 corners), -128/30 (centre), in 1/dx^2 */
-    int32_t reserved;     /* 0 */
+    int32_t split;        /* 0: every array holds its field whole. 1: the inflaton phi
+                             (field 0) is stored as an FP64 homogeneous mode (its value
+                             at the field time and momentum at the momentum time,
+                             lat_get_background) plus arrays of the fluctuation about
+                             it, the homogeneous initial values of Sec. II.B's initial
+                             conditions evolved in FP64 and the vacuum fluctuations in
+                             the arrays, so that FP32 arrays resolve fluctuations far
+                             below FP32 precision of phi itself. The leapfrog is the
+                             same step in exact arithmetic. chi is always stored whole.
+                             The derivative (lat_vjp, lat_adjoint) returns
+                             LAT_EUNSUPPORTED on a split lattice. */
 } lat_params;
 
 /* Volume averages at the field time, in physical units (Sec. II.B, eq. rho-pres;
@@ -151,25 +161,57 @@ lat_status lat_energy_field(lat_handle* h, void* rho_dev, void* p_dev);
 lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, double* p_out,
                         int64_t* count_out);
 
-/* Copy one array out: field 0/1, what 0 = f (at t + dt/2), 1 = f' (at t).
- * dst holds N^3 elements of the handle's precision, on the device if
- * dst_is_device, else host memory (pinned or pageable). Synchronises. */
+/* Copy one array out: field 0/1, what 0 = f (at t + dt/2), 1 = f' (at t), each
+ * whole (for phi of a split lattice: the homogeneous mode plus the stored
+ * fluctuation, rounded to the handle's precision); what 2 = f, 3 = f' as stored
+ * (for phi of a split lattice the fluctuation about lat_get_background's values,
+ * else the same as 0 and 1). dst holds N^3 elements of the handle's precision, on
+ * the device if dst_is_device, else host memory (pinned or pageable).
+ * Synchronises. */
 lat_status lat_get_state(lat_handle* h, int field, int what, void* dst, int dst_is_device);
 
-/* Copy one array in (same layout as lat_get_state). The sums and scale-factor
- * coefficients are recomputed before the next step or diagnostic. */
+/* Copy one array in (layout and `what` as lat_get_state: 0, 1 whole, from which
+ * the current homogeneous mode is subtracted on a split lattice; 2, 3 as stored).
+ * The sums and scale-factor coefficients are recomputed before the next step or
+ * diagnostic. */
 lat_status lat_set_state(lat_handle* h, int field, int what, const void* src, int src_is_device);
 
 /* Upload the whole state in one call: src[0..3] = f_phi, f_chi, pi_phi, pi_chi
- * (layout of lat_get_state; device memory if src_is_device, else host memory).
- * The step parity is read from the device first (one small synchronous read);
- * then the four copies are queued on the handle's stream after the work already
- * there, and the call returns without waiting for them. Host sources should be
- * page-locked for the copies to run asynchronously and must stay unchanged until
- * the stream has passed them (the next synchronising call or lat_sync). The sums
- * and coefficients are recomputed before the next step or diagnostic.
- * LAT_EINVAL for a null pointer. */
+ * as stored (lat_get_state's what 2 and 3: on a split lattice phi and its
+ * momentum are the fluctuations about lat_get_background's values; device memory
+ * if src_is_device, else host memory). The step parity is read from the device
+ * first (one small synchronous read); then the four copies are queued on the
+ * handle's stream after the work already there, and the call returns without
+ * waiting for them. Host sources should be page-locked for the copies to run
+ * asynchronously and must stay unchanged until the stream has passed them (the
+ * next synchronising call or lat_sync). The sums and coefficients are recomputed
+ * before the next step or diagnostic. LAT_EINVAL for a null pointer. */
 lat_status lat_upload_state(lat_handle* h, const void* const src[4], int src_is_device);
+
+/* The counterpart of lat_upload_state: the four stored arrays of the current
+ * state into dst[0..3] (f_phi, f_chi, pi_phi, pi_chi as stored; device memory if
+ * dst_is_device, else host memory, page-locked for the copies to overlap),
+ * queued on the handle's stream after the work already there; then waits for
+ * them. Returns a sticky device error if one is set. LAT_EINVAL for a null
+ * pointer. */
+lat_status lat_download_state(lat_handle* h, void* const dst[4], int dst_is_device);
+
+/* The homogeneous inflaton mode of split storage (lat_params.split = 1), in
+ * program units: out[0] = its value P at the field time t + dt/2, out[1] = its
+ * momentum at t. Zero on a lattice that stores phi whole. Synchronises. */
+lat_status lat_get_background(lat_handle* h, double out[2]);
+
+/* Move the homogeneous mode of a split lattice to in[0] (field time) and in[1]
+ * (momentum time) without changing the state: the stored fluctuation arrays of
+ * phi and its momentum are shifted by the differences (in FP64, rounded once).
+ * LAT_ESTATE unless split = 1; LAT_EINVAL for non-finite values. */
+lat_status lat_set_background(lat_handle* h, const double in[2]);
+
+/* Move the homogeneous mode of a split lattice to the volume means of phi and of
+ * its momentum (FP64 reductions on the device), so that the stored fluctuations
+ * have zero mean; used after loading whole fields with lat_set_state.
+ * Synchronises. LAT_ESTATE unless split = 1. */
+lat_status lat_recenter(lat_handle* h);
 
 /* Scalars: out[0] = t (time of the momenta), out[1] = a (at t + dt/2),
  * out[2] = a' (at t), out[3] = step count, out[4..7] = the volume averages
@@ -227,14 +269,11 @@ lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
 
 /* Choose the step kernel (all compute the same step): variant 0 = automatic
  * (4 where a row is 128 or more 16-byte vectors: FP32 N >= 512, FP64 N >= 256;
- * else 2 where it fits, else 1), 1 = one
- * site per thread with cached loads,
- * 2 = z-march through a shared-memory plane ring filled by per-thread
- * asynchronous copies (the fast path), 3 = plane ring filled by TMA boxes,
- * 4 = the plane ring of 2 over x tiles of at most 32 (or 16) 16-byte vectors
- * with taller y tiles (7-point only);
- * ty = owned rows per tile, zr = planes per z-chunk (variant 3: planes per
- * block), depth = planes prefetched ahead (variants 2, 3 and 4), 0 = automatic.
+ * else 2 where it fits, else 4), 2 = z-march through a shared-memory plane ring
+ * over full x rows, filled by per-thread asynchronous copies, 4 = the same ring
+ * over x tiles of at most 32 (or 16) 16-byte vectors with taller y tiles
+ * (7-point only); ty = owned rows per tile, zr = planes per z-chunk, depth =
+ * planes prefetched ahead, 0 = automatic. LAT_EINVAL for another variant;
  * LAT_EUNSUPPORTED if the variant cannot run this lattice (a 27-point lattice
  * runs on variant 2 only; ty, zr and depth apply to it as above). */
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth);
@@ -295,11 +334,10 @@ lat_status lat_set_g2(lat_handle* h, double g2);
  *     steps, the reverse pass recomputes each segment into ckpt_every field
  *     pairs; device memory grows as (3 n_steps / ckpt_every + 2 ckpt_every + 8)
  *     arrays.
- * The handle ends at the state after n_steps (as after lat_evolve). Handles
- * configured for the TMA step kernel take the plane-ring kernel in both passes.
+ * The handle ends at the state after n_steps (as after lat_evolve).
  * Synchronises. LAT_ENOMEM if the checkpoints do not fit; LAT_EUNSUPPORTED for
- * a 27-point lattice or expansion = 2; sticky device errors of the forward or
- * reverse pass are returned. */
+ * a 27-point lattice, expansion = 2 or split storage; sticky device errors of the
+ * forward or reverse pass are returned. */
 lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fbar_dev, void* pibar_dev,
                    double sbar[4]);
 

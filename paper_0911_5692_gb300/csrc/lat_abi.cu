@@ -33,6 +33,7 @@ lat_status derive_model(const lat_params& p, Model* M)
     if (!(p.L > 0.0) || !(p.dt > 0.0) || !std::isfinite(p.L) || !std::isfinite(p.dt)) return LAT_EINVAL;
     if (p.expansion < 0 || p.expansion > 2) return LAT_EINVAL;
     if (p.stencil != 0 && p.stencil != 7 && p.stencil != 27) return LAT_EINVAL;
+    if (p.split != 0 && p.split != 1) return LAT_EINVAL;
     double cpl, beta;
     if (p.model == LAT_MODEL_LPHI4) { cpl = p.lambda; beta = 4.0; }
     else if (p.model == LAT_MODEL_M2PHI2) { cpl = p.m * p.m; beta = 2.0; }
@@ -57,6 +58,7 @@ lat_status derive_model(const lat_params& p, Model* M)
     M->dt = p.dt;
     M->inv_dx2 = 1.0 / (M->dx * M->dx);
     M->stencil = p.stencil == 27 ? 27 : 7;
+    M->split = p.split;
     M->lap_scale = M->stencil == 27 ? M->inv_dx2 / 30.0 : M->inv_dx2;
     M->A = A; M->B = B; M->r = r; M->s = s;
     M->cdom0 = cpl * std::pow(A, 2.0 - beta) / (B * B);
@@ -95,10 +97,11 @@ lat_status check_cfl(const lat_params& p, const Model& M)
 
 size_t partials_needed(int n)
 {
-    size_t need = (size_t)std::max(simple_grid_blocks(n, std::min(n, 32)), sums_grid_blocks(n)) * kSums;
+    size_t need = (size_t)sums_grid_blocks(n) * kSums;
     need = std::max(need, (size_t)energies_grid_blocks(n) * kEnergySums);
-    // TMA grids are bounded by (N/ty) * (N/zr) <= N * N / 4 blocks
-    need = std::max(need, (size_t)n * n / 4 * kSums + 1024);
+    // the step kernels: one resident wave, or with an explicit z length at most
+    // (y tiles) x (z chunks) <= N^2 blocks (x-tiled: a few more)
+    need = std::max(need, ((size_t)n * n + 4096) * kSums);
     return need;
 }
 
@@ -121,24 +124,11 @@ lat_status launch_prepare(lat_handle* h)
 }
 
 // One step of the configured kernel on the given buffers (the handle's own for
-// lat_evolve; per-step storage for the recomputation of the reverse pass). The
-// TMA ring is bound to the handle's buffers by its tensor maps, so other buffers
-// take the plane-ring kernel instead.
+// lat_evolve; per-step storage for the recomputation of the reverse pass).
 template <typename T>
-cudaError_t launch_step_with(lat_handle* h, const Bufs<T>& b, bool own_buffers)
+cudaError_t launch_step_with(lat_handle* h, const Bufs<T>& b, bool)
 {
-    if (h->variant == 2 || h->variant == 4) return launch_step_march<T>(b, h->M, h->sc, h->partials, h->mcfg, h->stream);
-    if (h->variant == 3) {
-        if (own_buffers) return launch_step_tma<T>(b, h->M, h->sc, h->partials, h->tcfg, h->tmaps, h->stream);
-        if (!h->alt_ok) {
-            if (!march_config(h->p.n, (int)h->esize, 0, 0, 0, &h->alt_mcfg) ||
-                (size_t)h->alt_mcfg.blocks * kSums > h->partials_cap)
-                return cudaErrorInvalidConfiguration;
-            h->alt_ok = true;
-        }
-        return launch_step_march<T>(b, h->M, h->sc, h->partials, h->alt_mcfg, h->stream);
-    }
-    return launch_step_simple<T>(b, h->M, h->sc, h->partials, h->zr, h->stream);
+    return launch_step_march<T>(b, h->M, h->sc, h->partials, h->mcfg, h->stream);
 }
 template cudaError_t launch_step_with<float>(lat_handle*, const Bufs<float>&, bool);
 template cudaError_t launch_step_with<double>(lat_handle*, const Bufs<double>&, bool);
@@ -184,84 +174,45 @@ lat_status read_scalars(lat_handle* h, DevScalars* out)
 lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
 {
     const int n = h->p.n;
-    if (variant < 0 || variant > 4) return LAT_EINVAL;
-    if (variant == 4) {   // the x-tiled plane ring (7-point)
-        if (h->M.stencil == 27) return LAT_EUNSUPPORTED;
-        MarchConfig cfg;
-        if (!xt_config(n, (int)h->esize, ty, zr, depth, &cfg) || (size_t)cfg.blocks * kSums > h->partials_cap)
-            return LAT_EUNSUPPORTED;
+    if (variant != 0 && variant != 2 && variant != 4) return LAT_EINVAL;
+    auto take = [&](const MarchConfig& cfg, int v) {
         h->mcfg = cfg;
         h->ty = cfg.ty;
         h->zr = cfg.zr;
-        h->variant = 4;
+        h->variant = v;
         drop_graph(h);
         return LAT_OK;
-    }
+    };
+    auto fits = [&](const MarchConfig& cfg) { return (size_t)cfg.blocks * kSums <= h->partials_cap; };
     if (h->M.stencil == 27) {   // the 27-point Laplacian runs on its plane-ring kernel only
-        if (variant != 0 && variant != 2) return LAT_EUNSUPPORTED;
+        if (variant == 4) return LAT_EUNSUPPORTED;
         MarchConfig cfg;
         if (!march27_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr,
-                            variant == 0 ? 0 : depth, &cfg) ||
-            (size_t)cfg.blocks * kSums > h->partials_cap)
+                            variant == 0 ? 0 : depth, &cfg) || !fits(cfg))
             return LAT_EUNSUPPORTED;
-        h->mcfg = cfg;
-        h->ty = cfg.ty;
-        h->zr = cfg.zr;
-        h->variant = 2;
-        drop_graph(h);
-        return LAT_OK;
+        return take(cfg, 2);
     }
-    int chosen = 0;
+    if (variant == 4) {   // the x-tiled plane ring (7-point)
+        MarchConfig cfg;
+        if (!xt_config(n, (int)h->esize, ty, zr, depth, &cfg) || !fits(cfg)) return LAT_EUNSUPPORTED;
+        return take(cfg, 4);
+    }
     if (variant == 0 && n / (16 / (int)h->esize) >= 128) {
         // rows of 128 16-byte vectors or more: full-row tiles leave room for at
         // most 4 owned rows per 7 staged; x tiles of 32 vectors take 16 rows with
         // two planes in flight (FP32 512^3: 0.89 ms per step against 0.98 ms;
         // FP64 512^3: 16 ms against 24 ms, 256^3: 2.04 against 2.10 ms)
         MarchConfig cfg;
-        if (xt_config(n, (int)h->esize, 16, 0, 2, &cfg) && (size_t)cfg.blocks * kSums <= h->partials_cap) {
-            h->mcfg = cfg;
-            h->ty = cfg.ty;
-            h->zr = cfg.zr;
-            h->variant = 4;
-            drop_graph(h);
-            return LAT_OK;
-        }
+        if (xt_config(n, (int)h->esize, 16, 0, 2, &cfg) && fits(cfg)) return take(cfg, 4);
     }
-    if (variant == 0 || variant == 2) {
-        MarchConfig cfg;
-        if (march_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr, variant == 0 ? 0 : depth,
-                         &cfg) &&
-            (size_t)cfg.blocks * kSums <= h->partials_cap) {
-            h->mcfg = cfg;
-            h->ty = cfg.ty;
-            h->zr = cfg.zr;
-            chosen = 2;
-        } else if (variant == 2) {
-            return LAT_EUNSUPPORTED;
-        }
-    }
-    if (variant == 3) {
-        TmaConfig cfg;
-        if (!tma_config(n, (int)h->esize, ty, zr, &cfg) || (size_t)cfg.blocks * kSums > h->partials_cap)
-            return LAT_EUNSUPPORTED;
-        const void* ptrs[8];
-        for (int i = 0; i < 8; i++) ptrs[i] = h->buf[i];
-        LAT_CUDA(tma_encode_maps(ptrs, n, (int)h->esize, cfg.ty, h->tmaps));
-        h->tcfg = cfg;
-        h->ty = cfg.ty;
-        h->zr = cfg.zr;
-        chosen = 3;
-    }
-    if (chosen == 0) {
-        const int zrr = (variant == 1 && zr > 0) ? std::min(zr, n) : std::min(n, 32);
-        if ((size_t)simple_grid_blocks(n, zrr) * kSums > h->partials_cap) return LAT_EUNSUPPORTED;
-        h->ty = kSimpleTY;
-        h->zr = zrr;
-        chosen = 1;
-    }
-    h->variant = chosen;
-    drop_graph(h);
-    return LAT_OK;
+    MarchConfig cfg;
+    if (march_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr, variant == 0 ? 0 : depth, &cfg) &&
+        fits(cfg))
+        return take(cfg, 2);
+    if (variant == 2) return LAT_EUNSUPPORTED;
+    // rows too wide for a block of full-row tiles: the x-tiled ring serves any N
+    if (xt_config(n, (int)h->esize, 0, 0, 0, &cfg) && fits(cfg)) return take(cfg, 4);
+    return LAT_EUNSUPPORTED;
 }
 
 lat_status create_common(const lat_params* params, void* stream, void* const bufs[8], lat_handle** out)
@@ -399,17 +350,11 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8])
 {
     if (!h || !out) return LAT_EINVAL;
     out[0] = h->variant;
-    if (h->variant == 2 || h->variant == 4) {
-        out[1] = h->mcfg.blocks; out[2] = h->mcfg.threads; out[3] = (int64_t)h->mcfg.smem;
-    } else if (h->variant == 3) {
-        out[1] = h->tcfg.blocks; out[2] = h->tcfg.threads; out[3] = (int64_t)h->tcfg.smem;
-    } else {
-        out[1] = simple_grid_blocks(h->p.n, h->zr); out[2] = kSimpleTX * kSimpleTY; out[3] = 0;
-    }
+    out[1] = h->mcfg.blocks; out[2] = h->mcfg.threads; out[3] = (int64_t)h->mcfg.smem;
     out[4] = h->M.expansion == 2 ? 2 : 1;   // the L form adds its own pass
     out[5] = h->ty;
     out[6] = h->zr;
-    out[7] = (h->variant == 2 || h->variant == 4) ? h->mcfg.depth : h->variant == 3 ? h->tcfg.depth : 0;
+    out[7] = h->mcfg.depth;
     return LAT_OK;
 }
 
@@ -502,28 +447,57 @@ lat_status lat_set_hubble_length(lat_handle* h, double ell)
     return LAT_OK;
 }
 
+// The homogeneous mode that whole-field array `what` (0 = f, 1 = f') of `field`
+// differs from its stored array by: P or Pi for phi of a split lattice, else 0.
+double whole_offset(const lat_handle* h, const DevScalars& s, int field, int what)
+{
+    if (!h->M.split || field != 0) return 0.0;
+    return what == 0 ? s.bgf : s.bgp;
+}
+
 lat_status lat_get_state(lat_handle* h, int field, int what, void* dst, int dst_is_device)
 {
-    if (!h || !dst || field < 0 || field > 1 || what < 0 || what > 1) return LAT_EINVAL;
+    if (!h || !dst || field < 0 || field > 1 || what < 0 || what > 3) return LAT_EINVAL;
     DevScalars s;
     LAT_TRY(read_scalars(h, &s));
     const int par = (int)(s.step & 1);
-    const void* src = h->buf[4 * par + 2 * what + field];
+    const void* src = h->buf[4 * par + 2 * (what & 1) + field];
     LAT_CUDA(cudaMemcpyAsync(dst, src, h->nsites * h->esize,
                              dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    const double off = what < 2 ? whole_offset(h, s, field, what) : 0.0;
+    if (off != 0.0 && dst_is_device) {
+        cudaError_t e = h->prec == 32 ? launch_shift<float>((float*)dst, h->nsites, off, h->stream)
+                                      : launch_shift<double>((double*)dst, h->nsites, off, h->stream);
+        LAT_CUDA(e);
+    }
     LAT_CUDA(cudaStreamSynchronize(h->stream));
+    if (off != 0.0 && !dst_is_device) {   // whole values on the host: stored + P in FP64, rounded once
+        if (h->prec == 32) {
+            float* d = (float*)dst;
+            for (size_t i = 0; i < h->nsites; i++) d[i] = (float)((double)d[i] + off);
+        } else {
+            double* d = (double*)dst;
+            for (size_t i = 0; i < h->nsites; i++) d[i] += off;
+        }
+    }
     return (lat_status)s.status;
 }
 
 lat_status lat_set_state(lat_handle* h, int field, int what, const void* src, int src_is_device)
 {
-    if (!h || !src || field < 0 || field > 1 || what < 0 || what > 1) return LAT_EINVAL;
+    if (!h || !src || field < 0 || field > 1 || what < 0 || what > 3) return LAT_EINVAL;
     DevScalars s;
     LAT_TRY(read_scalars(h, &s));
     const int par = (int)(s.step & 1);
-    void* dst = h->buf[4 * par + 2 * what + field];
+    void* dst = h->buf[4 * par + 2 * (what & 1) + field];
     LAT_CUDA(cudaMemcpyAsync(dst, src, h->nsites * h->esize,
                              src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    const double off = what < 2 ? whole_offset(h, s, field, what) : 0.0;
+    if (off != 0.0) {   // whole values in: the stored array is measured from the homogeneous mode
+        cudaError_t e = h->prec == 32 ? launch_shift<float>((float*)dst, h->nsites, -off, h->stream)
+                                      : launch_shift<double>((double*)dst, h->nsites, -off, h->stream);
+        LAT_CUDA(e);
+    }
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     h->dirty = true;
     return LAT_OK;
@@ -542,6 +516,90 @@ lat_status lat_upload_state(lat_handle* h, const void* const src[4], int src_is_
                                  src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     h->dirty = true;
     return LAT_OK;
+}
+
+lat_status lat_download_state(lat_handle* h, void* const dst[4], int dst_is_device)
+{
+    if (!h || !dst) return LAT_EINVAL;
+    for (int k = 0; k < 4; k++)
+        if (!dst[k]) return LAT_EINVAL;
+    LAT_TRY(ensure_prepared(h));
+    // the parity of the state the queued work leaves: read after that work
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    if (s.status != LAT_OK) return (lat_status)s.status;
+    const int par = (int)(s.step & 1);
+    for (int k = 0; k < 4; k++)
+        LAT_CUDA(cudaMemcpyAsync(dst[k], h->buf[4 * par + k], h->nsites * h->esize,
+                                 dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    return LAT_OK;
+}
+
+lat_status lat_get_background(lat_handle* h, double out[2])
+{
+    if (!h || !out) return LAT_EINVAL;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    out[0] = s.bgf;
+    out[1] = s.bgp;
+    return (lat_status)s.status;
+}
+
+lat_status lat_set_background(lat_handle* h, const double in[2])
+{
+    if (!h || !in) return LAT_EINVAL;
+    if (!h->M.split) return LAT_ESTATE;
+    if (!std::isfinite(in[0]) || !std::isfinite(in[1])) return LAT_EINVAL;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    const int par = (int)(s.step & 1);
+    // phi = P + d unchanged: d += P_old - P_new, and the same for the momentum
+    const double df = s.bgf - in[0], dp = s.bgp - in[1];
+    void* f = h->buf[4 * par + 0];
+    void* p = h->buf[4 * par + 2];
+    cudaError_t e = h->prec == 32 ? launch_shift<float>((float*)f, h->nsites, df, h->stream)
+                                  : launch_shift<double>((double*)f, h->nsites, df, h->stream);
+    LAT_CUDA(e);
+    e = h->prec == 32 ? launch_shift<float>((float*)p, h->nsites, dp, h->stream)
+                      : launch_shift<double>((double*)p, h->nsites, dp, h->stream);
+    LAT_CUDA(e);
+    s.bgf = in[0];
+    s.bgp = in[1];
+    s.ticket = 0;
+    s.ticket2 = 0;
+    LAT_CUDA(cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    h->dirty = true;
+    return LAT_OK;
+}
+
+lat_status lat_recenter(lat_handle* h)
+{
+    if (!h) return LAT_EINVAL;
+    if (!h->M.split || h->slab) return LAT_ESTATE;   // a slab holds part of the volume only
+    if ((size_t)2 * kSum2Blocks > h->partials_cap) return LAT_EUNSUPPORTED;
+    DevScalars s;
+    LAT_TRY(read_scalars(h, &s));
+    const int par = (int)(s.step & 1);
+    int nb = 0;
+    cudaError_t e = h->prec == 32
+                        ? launch_sum2<float>((const float*)h->buf[4 * par + 0], (const float*)h->buf[4 * par + 2],
+                                             h->nsites, h->partials, &nb, h->stream)
+                        : launch_sum2<double>((const double*)h->buf[4 * par + 0], (const double*)h->buf[4 * par + 2],
+                                              h->nsites, h->partials, &nb, h->stream);
+    LAT_CUDA(e);
+    std::vector<double> part(2 * (size_t)nb);
+    LAT_CUDA(cudaMemcpyAsync(part.data(), h->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    double mf = 0.0, mp = 0.0;
+    for (int b = 0; b < nb; b++) {
+        mf += part[2 * (size_t)b];
+        mp += part[2 * (size_t)b + 1];
+    }
+    const double in[2] = {s.bgf + mf / (double)h->nsites, s.bgp + mp / (double)h->nsites};
+    return lat_set_background(h, in);
 }
 
 lat_status lat_init_fields(lat_handle* h)
@@ -606,11 +664,15 @@ lat_status lat_init_fields(lat_handle* h)
             }
         }
         if (st != LAT_OK) break;
+        // split storage: the homogeneous part of phi goes to the scalar block and
+        // the arrays hold the fluctuations alone
+        const bool bg = M.split && field == 0;
+        const double fhs = bg ? 0.0 : fh[field], phs = bg ? 0.0 : ph[field];
         cudaError_t e = h->prec == 32
-                            ? launch_init_combine<float>(bufs_of<float>(h), field, df, dp, fh[field], ph[field],
-                                                         M.r * h0, 0.5 * p.dt, n, h->stream)
-                            : launch_init_combine<double>(bufs_of<double>(h), field, df, dp, fh[field], ph[field],
-                                                          M.r * h0, 0.5 * p.dt, n, h->stream);
+                            ? launch_init_combine<float>(bufs_of<float>(h), field, df, dp, fhs, phs, M.r * h0,
+                                                         0.5 * p.dt, n, h->stream)
+                            : launch_init_combine<double>(bufs_of<double>(h), field, df, dp, fhs, phs, M.r * h0,
+                                                          0.5 * p.dt, n, h->stream);
         if (e != cudaSuccess) st = LAT_ECUDA;
     }
     if (st == LAT_OK) {
@@ -621,6 +683,10 @@ lat_status lat_init_fields(lat_handle* h)
         s.a = 1.0 + (p.expansion ? 0.5 * p.dt * ad : 0.0);
         s.ell = p.expansion == 2 ? ell_at_momentum_time(s.a, s.ad, p.dt) : 0.0;
         s.step = 0;
+        if (M.split) {   // the homogeneous mode, advanced by dt/2 like the fields
+            s.bgp = ph[0];
+            s.bgf = fh[0] + 0.5 * p.dt * ph[0];
+        }
         if (cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) st = LAT_ECUDA;
     }
     if (st == LAT_OK) {
@@ -723,6 +789,7 @@ lat_status lat_spectrum(lat_handle* h, int field, int nbins, double* k_out, doub
         const void* src = h->buf[4 * par + field];
         cudaError_t e = h->prec == 32 ? launch_to_double<float>((const float*)src, re, h->nsites, h->stream)
                                       : launch_to_double<double>((const double*)src, re, h->nsites, h->stream);
+        if (e == cudaSuccess) e = launch_shift<double>(re, h->nsites, whole_offset(h, s, field, 0), h->stream);
         if (e != cudaSuccess) st = LAT_ECUDA;
     }
     if (st == LAT_OK) {

@@ -1160,6 +1160,7 @@ lat_status lat_vjp(lat_handle* h, int64_t n_steps, int64_t ckpt_every, void* fba
     if (h->slab) return LAT_ESTATE;
     if (h->M.stencil == 27) return LAT_EUNSUPPORTED;   // the reverse step is written for 7 points
     if (h->M.expansion == 2) return LAT_EUNSUPPORTED;  // and for eq. scale
+    if (h->M.split) return LAT_EUNSUPPORTED;           // and for phi stored whole
     if (((uintptr_t)fbar_dev | (uintptr_t)pibar_dev) % h->esize != 0) return LAT_EINVAL;
     return h->prec == 32 ? vjp_impl<float>(h, n_steps, ckpt_every, (float*)fbar_dev, (float*)pibar_dev, sbar, -1, nullptr)
                          : vjp_impl<double>(h, n_steps, ckpt_every, (double*)fbar_dev, (double*)pibar_dev, sbar, -1,
@@ -1171,7 +1172,7 @@ lat_status lat_adjoint(lat_handle* h, int64_t n_steps, int observable, int64_t c
 {
     if (!h || n_steps < 0 || ckpt_every < 0 || !dJ_df_dev || !dJ_dpi_dev) return LAT_EINVAL;
     if (h->slab) return LAT_ESTATE;
-    if (h->M.stencil == 27 || h->M.expansion == 2) return LAT_EUNSUPPORTED;
+    if (h->M.stencil == 27 || h->M.expansion == 2 || h->M.split) return LAT_EUNSUPPORTED;
     if (observable != 0 && observable != 1) return LAT_EUNSUPPORTED;
     if (((uintptr_t)dJ_df_dev | (uintptr_t)dJ_dpi_dev) % h->esize != 0) return LAT_EINVAL;
     double sbar[4] = {0.0, 0.0, 0.0, 0.0};

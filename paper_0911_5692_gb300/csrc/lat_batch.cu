@@ -193,19 +193,14 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 3 : (MAXT <= 512 ? 2 : 1))
                 L.n = BL.M.n;
                 L.ty = BL.ty;
                 L.depth = BL.depth;
-                L.dtcl = step_coef<T>(&cur, 0);
-                L.dtcf = step_coef<T>(&cur, 1);
-                L.mdtcdom = step_coef<T>(&cur, 2);
-                L.mdtkap = step_coef<T>(&cur, 3);
-                L.dt = step_coef<T>(&cur, 4);
-                L.quartic = BL.M.beta == 4;
+                L.K = site_coefs<T>(&cur, BL.M.beta);
                 L.periodic = true;
                 L.zbase = 0;
                 MarchSums<T> A;
                 A.zero();
                 march_segment(L, g.yt, g.z0, g.nz, S, A, s == sb);
                 T v[kSums];
-                A.totals(L.quartic, v);
+                A.totals(L.K.quartic, v);
                 block_reduce(v, red, bs);
             }
             if (threadIdx.x == 0)

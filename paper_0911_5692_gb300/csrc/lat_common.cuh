@@ -17,6 +17,7 @@ struct Model {
     int expansion;      // 0: static; 1: eq. scale; 2: the L = 1/H form (lat_lform.cu)
     int beta;           // 2 or 4: exponent of the dominant potential term
     int stencil;        // Laplacian: 7-point or 27-point (Sec. II.C)
+    int split;          // 1: phi stored as FP64 homogeneous mode + fluctuation arrays
     double dx, dt, inv_dx2;
     // factor turning the stencil's integer-weight neighbour sums into the
     // Laplacian and the gradient average: 1/dx^2 (7-point, weights 1) or
@@ -30,9 +31,39 @@ struct Model {
     double inv_sites;   // 1 / N^3
 };
 
+// Step coefficients (DevScalars::kd, kf): the kick and drift of eq. scalar-evo
+// and eq. evo, and the homogeneous inflaton mode the stored phi arrays are
+// measured from (zero unless the lattice stores phi split, see below).
+enum {
+    kDtCl = 0,   // dt cL / dx^2 (times the stencil's 1/30 for 27 points)
+    kDtCf,       // dt cF
+    kMDtCdom,    // -dt cdom
+    kMDtKap,     // -dt kappa
+    kDt,         // dt
+    kBg,         // P: homogeneous phi at the field time of the step
+    kBg2,        // P^2
+    kBgNew,      // P': homogeneous phi at the field time after the step
+    kBgNew2,     // P'^2
+    kCoefs = 10
+};
+
 // FP64 scalars that live on the device between steps. The step kernel reads the
 // coefficients at its start and its last block writes those of the next step,
 // so a captured CUDA graph of any number of steps needs no host round trip.
+//
+// Split storage of the inflaton (lat_params.split). phi = P + d with the
+// homogeneous mode P (field time) and its momentum Pi (momentum time) kept here
+// in FP64, and the arrays of field 0 holding the fluctuation d and its momentum.
+// The homogeneous mode follows the same leapfrog with the homogeneous force,
+// Pi_{n+1} = Pi_n + dt (cF P - cdom P^(beta-1)), P_{n+3/2} = P + dt Pi_{n+1}, and
+// the kernels apply to d the rest of the force exactly:
+//   cL Lap d + cF d - [cdom ((P+d)^(beta-1) - P^(beta-1)) + kappa (P+d) chi^2]
+// for phi and -kappa (P+d)^2 chi for chi (the homogeneous value of chi stays
+// zero: chi is stored whole), written without differences of nearby numbers
+// (u = P + d; (u^3 - P^3) = d (u (u + P) + P^2)). The sum of the two parts is
+// the same leapfrog step as for phi stored whole, so the scheme is unchanged;
+// FP32 arrays then resolve the fluctuations of phi to FP32 precision of their
+// own size rather than of phi. P = Pi = 0 is phi stored whole.
 struct DevScalars {
     double t;        // program time of the momenta
     double a;        // scale factor at the field time t + dt/2
@@ -48,9 +79,8 @@ struct DevScalars {
     unsigned int ticket; // last-block counter of the step kernel
     unsigned int ticket2;
     int pad;
-    double kd[5];    // step coefficients dt cL/dx^2, dt cF, -dt cdom, -dt kappa, dt
-    float kf[5];     // the same rounded once to FP32 for the FP32 kernels
-    int pad2;
+    double kd[kCoefs]; // step coefficients (enum above)
+    float kf[kCoefs];  // the same rounded once to FP32 for the FP32 kernels
     // History of the scalar blocks (the reverse-mode derivative's forward pass):
     // when set, the last block of each step also stores the block it produces,
     // the one the next step starts from, at log[step - log_base]. Null otherwise.
@@ -59,6 +89,10 @@ struct DevScalars {
     // The L = 1/H form (expansion 2): the Hubble length l = a/a' of program time
     // at t, and l at t + dt as solved for the next step (lat_lform.cu).
     double ell, ell_next;
+    // Homogeneous inflaton mode of split storage: P at the field time, Pi at the
+    // momentum time, and both after the step being taken (zero when phi is
+    // stored whole).
+    double bgf, bgp, bgf_next, bgp_next;
 };
 
 // Step coefficient i for element type T (kd / kf above).
@@ -159,15 +193,33 @@ __device__ inline double apow(double a, double inv_a, double p)
     return pow(a, p);
 }
 
-// The per-step coefficients of eq. scalar-evo as the step kernels use them.
+// <f0^beta>/beta of the homogeneous mode alone: the potential sums of split
+// storage hold the rest, sum over sites of ((P+d)^beta - P^beta)/beta.
+__host__ __device__ inline double bg_potential(int beta, double P)
+{
+    const double q = P * P;
+    return beta == 4 ? 0.25 * q * q : 0.5 * q;
+}
+
+// The per-step coefficients of eq. scalar-evo as the step kernels use them, and
+// one leapfrog step of the homogeneous inflaton mode under the same cL, cF,
+// cdom (its force is that of the potential at (P, chi = 0)).
 __device__ inline void step_coefficients(const Model& M, DevScalars* sc)
 {
-    sc->kd[0] = M.dt * sc->cL * M.lap_scale;
-    sc->kd[1] = M.dt * sc->cF;
-    sc->kd[2] = -M.dt * sc->cdom;
-    sc->kd[3] = -M.dt * sc->kappa;
-    sc->kd[4] = M.dt;
-    for (int i = 0; i < 5; i++) sc->kf[i] = (float)sc->kd[i];
+    const double P = sc->bgf;
+    const double force = sc->cdom * (M.beta == 4 ? P * P * P : P);
+    sc->bgp_next = sc->bgp + M.dt * (sc->cF * P - force);
+    sc->bgf_next = P + M.dt * sc->bgp_next;
+    sc->kd[kDtCl] = M.dt * sc->cL * M.lap_scale;
+    sc->kd[kDtCf] = M.dt * sc->cF;
+    sc->kd[kMDtCdom] = -M.dt * sc->cdom;
+    sc->kd[kMDtKap] = -M.dt * sc->kappa;
+    sc->kd[kDt] = M.dt;
+    sc->kd[kBg] = P;
+    sc->kd[kBg2] = P * P;
+    sc->kd[kBgNew] = sc->bgf_next;
+    sc->kd[kBgNew2] = sc->bgf_next * sc->bgf_next;
+    for (int i = 0; i < kCoefs; i++) sc->kf[i] = (float)sc->kd[i];
 }
 
 // Scale-factor update of Sec. II.B, eq. scale, with the staggered a':
@@ -220,19 +272,23 @@ __device__ inline void scale_solve(const Model& M, DevScalars* sc)
 __device__ inline void advance_scalars(const Model& M, DevScalars& s, const double S[kSums], bool advance)
 {
     bool finite = true;
-    for (int k = 0; k < kSums; k++) {
-        finite = finite && isfinite(S[k]);
-        s.S[k] = S[k];
-    }
     if (advance) {
         if (M.expansion) {
             s.a = s.a + M.dt * s.ad_next;
             s.ad = s.ad_next;
             s.ell = s.ell_next;
         }
+        s.bgf = s.bgf_next;
+        s.bgp = s.bgp_next;
         s.t = s.t + M.dt;
         s.step = s.step + 1;
     }
+    for (int k = 0; k < kSums; k++) {
+        finite = finite && isfinite(S[k]);
+        s.S[k] = S[k];
+    }
+    // the potential sums of the kernels are taken about the homogeneous mode
+    s.S[2] += bg_potential(M.beta, s.bgf);
     if (!finite) s.status = LAT_ENONFINITE;
     else if (M.expansion != 2) scale_solve(M, &s);
 }

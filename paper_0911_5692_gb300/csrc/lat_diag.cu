@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(256) energies_kernel(Bufs<T> B, Model M, const
     const T* p1 = B.p[par][1];
     const double cL = sc->cL, cF = sc->cF, cdom = sc->cdom, kap = sc->kappa, dt = M.dt;
     const double h = M.expansion ? sc->ad_half / sc->a : 0.0;
+    // split storage: phi = P + stored, its momentum = Pi + stored (P = Pi = 0 otherwise)
+    const double bgf = sc->bgf, bgp = sc->bgp;
     double acc[kEnergySums] = {0, 0, 0, 0, 0, 0, 0};
     const long long cols = (long long)n * n;
     for (long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
@@ -46,7 +48,8 @@ __global__ void __launch_bounds__(256) energies_kernel(Bufs<T> B, Model M, const
         const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
         for (int z = 0; z < n; z++) {
             const size_t c = sidx(n, x, y, z);
-            const double a0 = (double)f0[c], a1 = (double)f1[c];
+            const double s0 = (double)f0[c], a1 = (double)f1[c];
+            const double a0 = s0 + bgf;
             if (pass == 1) {
                 const double d0 = a0 - means[0], d1 = a1 - means[1];
                 acc[5] += d0 * d0;
@@ -65,17 +68,17 @@ __global__ void __launch_bounds__(256) energies_kernel(Bufs<T> B, Model M, const
                              fz0 = (double)f0[sidx(n, x, y, zp)];
                 const double fx1 = (double)f1[sidx(n, xp, y, z)], fy1 = (double)f1[sidx(n, x, yp, z)],
                              fz1 = (double)f1[sidx(n, x, y, zp)];
-                lap0 = (((fx0 - a0) + ((double)f0[sidx(n, xm, y, z)] - a0)) + ((fy0 - a0) + ((double)f0[sidx(n, x, ym, z)] - a0))
-                                     + ((fz0 - a0) + ((double)f0[sidx(n, x, y, zm)] - a0))) * M.inv_dx2;
+                lap0 = (((fx0 - s0) + ((double)f0[sidx(n, xm, y, z)] - s0)) + ((fy0 - s0) + ((double)f0[sidx(n, x, ym, z)] - s0))
+                                     + ((fz0 - s0) + ((double)f0[sidx(n, x, y, zm)] - s0))) * M.inv_dx2;
                 lap1 = (((fx1 - a1) + ((double)f1[sidx(n, xm, y, z)] - a1)) + ((fy1 - a1) + ((double)f1[sidx(n, x, ym, z)] - a1))
                                      + ((fz1 - a1) + ((double)f1[sidx(n, x, y, zm)] - a1))) * M.inv_dx2;
-                gs0 = (fx0 - a0) * (fx0 - a0) + (fy0 - a0) * (fy0 - a0) + (fz0 - a0) * (fz0 - a0);
+                gs0 = (fx0 - s0) * (fx0 - s0) + (fy0 - s0) * (fy0 - s0) + (fz0 - s0) * (fz0 - s0);
                 gs1 = (fx1 - a1) * (fx1 - a1) + (fy1 - a1) * (fy1 - a1) + (fz1 - a1) * (fz1 - a1);
             }
             const double a0b = M.beta == 4 ? a0 * a0 * a0 : a0;
             const double F0 = cL * lap0 + cF * a0 - (cdom * a0b + kap * a0 * a1 * a1);
             const double F1 = cL * lap1 + cF * a1 - kap * a0 * a0 * a1;
-            const double q0 = (double)p0[c] + 0.5 * dt * F0 - M.r * h * a0;
+            const double q0 = ((double)p0[c] + bgp) + 0.5 * dt * F0 - M.r * h * a0;
             const double q1 = (double)p1[c] + 0.5 * dt * F1 - M.r * h * a1;
             acc[0] += 0.5 * q0 * q0;
             acc[1] += 0.5 * q1 * q1;
@@ -195,6 +198,7 @@ __device__ __forceinline__ void neighbour_sums(const T* __restrict__ f, int n, i
 template <typename T>
 struct FieldCoef {
     T cL, cF, cdom, kap, hdt, rh, gq, cv;
+    T bgf, bgp;   // split storage: phi = bgf + stored, its momentum = bgp + stored
     bool quartic;
 };
 
@@ -212,16 +216,20 @@ __device__ inline FieldCoef<T> field_coefs(const Model& M, const DevScalars* sc)
     k.rh = (T)(M.r * h);
     k.gq = (T)(0.25 * pow(a, -2.0 * M.s - 2.0) * M.lap_scale);   // grad_i = gq * sum w d^2
     k.cv = (T)(M.B * M.B / (M.A * M.A) * pow(a, 2.0 * M.s - 2.0 * M.r));
+    k.bgf = (T)sc->bgf;
+    k.bgp = (T)sc->bgp;
     k.quartic = M.beta == 4;
     return k;
 }
 
-// rho and p at one site from its fields a0, a1, momenta m0, m1 and the
-// neighbour sums (l: of the differences, g: of their squares) of each field.
+// rho and p at one site from its fields a0, a1, momenta m0, m1 as stored and
+// the neighbour sums (l: of the differences, g: of their squares) of each field.
 template <typename T>
 __device__ __forceinline__ void site_energy(const FieldCoef<T>& K, T a0, T a1, T m0, T m1, T l0, T g0, T l1, T g1,
                                             T& rho, T& pres)
 {
+    a0 += K.bgf;   // whole phi and its momentum (unchanged when phi is stored whole)
+    m0 += K.bgp;
     const T a0b = K.quartic ? a0 * a0 * a0 : a0;
     const T F0 = K.cL * l0 + K.cF * a0 - (K.cdom * a0b + K.kap * a0 * a1 * a1);
     const T F1 = K.cL * l1 + K.cF * a1 - K.kap * a0 * a0 * a1;

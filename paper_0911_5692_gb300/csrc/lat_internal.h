@@ -18,15 +18,11 @@ struct lat_handle {
     size_t partials_cap; // doubles
     double* means;       // device, 2 doubles
     bool dirty;          // sums and coefficients must be recomputed
-    int variant;         // 1 = plain per-site loads, 2 = plane-ring z-march, 3 = TMA ring
+    int variant;         // 2 = plane-ring z-march over full rows, 4 = over x tiles
     int ty, zr;
     lat::MarchConfig mcfg;
-    lat::TmaConfig tcfg;
-    alignas(64) unsigned char tmaps[lat::kTmaMaps * 128];
     cudaGraphExec_t graph;
     int graph_steps;
-    lat::MarchConfig alt_mcfg; // plane-ring geometry for buffers other than the handle's (TMA handles)
-    bool alt_ok;
     bool slab;           // a z-slab of a larger lattice (lat_slab_create)
     int slab_z0, slab_nzl;
 };

@@ -16,20 +16,15 @@ struct Bufs {
     T* p[2][2];
 };
 
-// Plain-load fused step (both precisions, any N % 4 == 0).
-constexpr int kSimpleTX = 32, kSimpleTY = 8;
-int simple_grid_blocks(int n, int zr);
-template <typename T>
-cudaError_t launch_step_simple(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, int zr,
-                               cudaStream_t st);
-
-// Sums of the current fields (no step) followed by the scale-factor solve.
+// Sums of the current fields (no step) followed by the scale-factor solve
+// (lat_sums.cu).
 int sums_grid_blocks(int n);
 int sums_zruns(int n);
 template <typename T>
 cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, cudaStream_t st);
 
-// Register-prefetch z-march fused step (the default fast path).
+// Plane-ring z-march fused steps (lat_step_march.cu, lat_step_fast.cu,
+// lat_step_xt.cu, lat_step27.cu).
 struct MarchConfig {
     int ty;        // owned rows per tile
     int zr;        // planes per z-chunk (the longest)
@@ -72,35 +67,6 @@ template <typename T>
 cudaError_t launch_step27(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
                           cudaStream_t st);
 
-// TMA plane-ring fused step.
-struct TmaGeom {
-    int n, ty, zr, depth;
-    int bw, nbx;   // TMA box width (elements) and x chunks per row
-    int rs;        // shared-memory row stride in bytes (a multiple of 128)
-    int tall;      // 1: one multi-row box per field and x chunk where y does not wrap
-    int nyt;       // y tiles
-    int rf, rp;    // ring slots for f planes and for momentum planes
-    int items;     // (ty + 1) * n / (16 / element bytes)
-};
-struct TmaConfig {
-    int ty;        // owned rows per tile
-    int zr;        // requested (y tile, z) planes per block; 0 = one resident wave
-    int depth;     // planes prefetched ahead
-    int threads;   // threads per block
-    size_t smem;   // dynamic shared memory bytes
-    int blocks;    // blocks per step (persistent: each marches a contiguous run)
-    TmaGeom geom;
-};
-bool tma_config(int n, int elem_bytes, int ty, int zr, TmaConfig* cfg);
-template <typename T>
-cudaError_t launch_step_tma(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
-                            const TmaConfig& cfg, const void* tmaps, cudaStream_t st);
-// Encode the 16 tensor maps of the TMA kernel into `out` (16 * 128 bytes,
-// 64-byte aligned host memory): one-row boxes for the 8 arrays, then multi-row
-// boxes (ty + 3 rows for fields, ty + 1 for momenta).
-constexpr int kTmaMaps = 16;
-cudaError_t tma_encode_maps(const void* const ptrs[8], int n, int elem_bytes, int ty, void* out);
-
 // Initial conditions (off the timed path).
 struct InitWork {
     double* re;      // N^3 doubles
@@ -115,6 +81,15 @@ cudaError_t launch_white_noise(double* out, int n, uint64_t seed, uint32_t field
                                cudaStream_t st);
 cudaError_t launch_spectral_scale(void* spec, int n, double dx, double meff2, double amp, double kcut,
                                   int quantity, int stencil, cudaStream_t st);
+
+// Split storage (lat_split.cu): a[i] += delta (in FP64, rounded once), and
+// per-block FP64 sums of two arrays into partials[2 b], [2 b + 1] (at most
+// kSum2Blocks blocks; the count is returned in *blocks).
+constexpr int kSum2Blocks = 1024;
+template <typename T>
+cudaError_t launch_shift(T* a, size_t count, double delta, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sum2(const T* a, const T* b, size_t count, double* partials, int* blocks, cudaStream_t st);
 
 // Diagnostics (off the timed path).
 constexpr int kEnergySums = 7;

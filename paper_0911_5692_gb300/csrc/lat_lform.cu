@@ -76,14 +76,18 @@ __device__ inline LfConst lf_const(const Model& M, const DevScalars* sc)
 template <typename T>
 struct SiteCoef {
     T kL, hdt, cdom, kap, w0;
+    T bgf, bgp;   // split storage: phi = bgf + stored, its momentum = bgp + stored
     bool quartic;
 };
 
-// One site's contributions: v_i = pi_i + (dt/2)(cL Lap f_i - dV_pr/df_i) + w0 f_i.
+// One site's contributions: v_i = pi_i + (dt/2)(cL Lap f_i - dV_pr/df_i) + w0 f_i,
+// from the site's values as stored (Lap f_0 is that of the stored array).
 template <typename T>
 __device__ __forceinline__ void site_terms(const SiteCoef<T>& C, T f0, T f1, T p0, T p1, T lap0, T lap1, T& P0, T& Q,
                                            T& F2, T& W)
 {
+    f0 += C.bgf;   // whole phi and its momentum (unchanged when phi is stored whole)
+    p0 += C.bgp;
     const T sq0 = f0 * f0, sq1 = f1 * f1;
     const T dv0 = C.cdom * (C.quartic ? sq0 * f0 : f0) + C.kap * f0 * sq1;
     const T dv1 = C.kap * sq0 * f1;
@@ -201,13 +205,15 @@ __device__ inline void lform_finish(const Model& M, DevScalars* sc, double* part
 template <typename T>
 __device__ inline SiteCoef<T> block_coefs(const Model& M, const DevScalars* sc, double* w0_used)
 {
-    __shared__ double kc[4];
+    __shared__ double kc[6];
     if (threadIdx.x == 0) {
         const LfConst k = lf_const(M, sc);
         kc[0] = k.cL * M.lap_scale;
         kc[1] = k.cdom;
         kc[2] = k.kappa;
         kc[3] = (double)(T)k.w0;   // the guess exactly as the sites use it
+        kc[4] = sc->bgf;
+        kc[5] = sc->bgp;
     }
     __syncthreads();
     SiteCoef<T> C;
@@ -216,6 +222,8 @@ __device__ inline SiteCoef<T> block_coefs(const Model& M, const DevScalars* sc, 
     C.cdom = (T)kc[1];
     C.kap = (T)kc[2];
     C.w0 = (T)kc[3];
+    C.bgf = (T)kc[4];
+    C.bgp = (T)kc[5];
     C.quartic = M.beta == 4;
     *w0_used = kc[3];
     return C;

@@ -16,6 +16,7 @@
 #include "lat_async.cuh"
 #include "lat_common.cuh"
 #include "lat_pairs.cuh"
+#include "lat_site.cuh"
 
 namespace lat {
 
@@ -57,8 +58,7 @@ struct MarchLattice {
     const T *f0, *f1, *p0, *p1;   // fields at the field time and momenta (read)
     T *of0, *of1, *op0, *op1;     // the other ping-pong set (written)
     int n, ty, depth;
-    T dtcl, dtcf, mdtcdom, mdtkap, dt;   // dt cL / dx^2, dt cF, -dt cdom, -dt kappa, dt
-    bool quartic;                        // beta == 4
+    SiteCoefs<T> K;                      // the step's coefficients (lat_site.cuh)
     // z storage: periodic (plane z stored at z mod n) or a z-slab whose arrays
     // hold plane z at z + zbase (halo planes below and above the owned ones)
     bool periodic;
@@ -70,7 +70,8 @@ struct MarchLattice {
 };
 
 // Per-thread sums of the new fields (packed pairs): forward-difference
-// gradients of each field, f0^beta and f0^2 f1^2 (factors applied at the end).
+// gradients of each field and the potential sums of lat_site.cuh (factors
+// applied at the end).
 template <typename T>
 struct MarchSums {
     typename PK<T>::P accg0, accg1, accvd, accvi;
@@ -82,12 +83,12 @@ struct MarchSums {
         accvi = accg0;
     }
     // the four sums of this thread in the element type (1/beta and 1/2 are powers
-    // of two, exact)
+    // of two, exact); the potential sums are taken about the homogeneous mode
     __device__ void totals(bool quartic, T v[kSums]) const
     {
         v[0] = lo2(accg0) + hi2(accg0);
         v[1] = lo2(accg1) + hi2(accg1);
-        v[2] = (lo2(accvd) + hi2(accvd)) * (quartic ? T(0.25) : T(0.5));
+        v[2] = (lo2(accvd) + hi2(accvd)) * site_vsum_factor<T>(quartic);
         v[3] = T(0.5) * (lo2(accvi) + hi2(accvi));
     }
 };
@@ -217,7 +218,7 @@ __device__ void march_segment(const MarchLattice<T>& L, int yt, int z0, int nz, 
                     lft[0] = mk2(left, lo2(cen[f][0]));
                     rgt[0] = mk2(hi2(cen[f][0]), right);
                 }
-                const P dtcl2 = mk2(L.dtcl, L.dtcl), dtcf2 = mk2(L.dtcf, L.dtcf);
+                const P dtcl2 = mk2(L.K.dtcl, L.K.dtcl), dtcf2 = mk2(L.K.dtcf, L.K.dtcf);
 #pragma unroll
                 for (int v = 0; v < NP; v++) {
                     const P c = cen[f][v];
@@ -229,18 +230,9 @@ __device__ void march_segment(const MarchLattice<T>& L, int yt, int z0, int nz, 
                     pn[f][v] = fma2(dtcl2, lapu, fma2(dtcf2, c, pv[v]));
                 }
             }
-            const P mdtcdom2 = mk2(L.mdtcdom, L.mdtcdom), mdtkap2 = mk2(L.mdtkap, L.mdtkap), dt2 = mk2(L.dt, L.dt);
+            // potential part of the kick and the drift (lat_site.cuh)
 #pragma unroll
-            for (int v = 0; v < NP; v++) {
-                // potential: f0 gets -dt (cdom f0^(beta-1) + kappa f0 f1^2), f1 gets -dt kappa f0^2 f1
-                const P a0 = cen[0][v], a1 = cen[1][v];
-                const P a0a1 = mul2(a0, a1);
-                const P dom = L.quartic ? mul2(mul2(a0, a0), a0) : a0;
-                pn[0][v] = fma2(mdtcdom2, dom, fma2(mdtkap2, mul2(a0a1, a1), pn[0][v]));
-                pn[1][v] = fma2(mdtkap2, mul2(a0a1, a0), pn[1][v]);
-                g[0][v] = fma2(dt2, pn[0][v], a0);
-                g[1][v] = fma2(dt2, pn[1][v], a1);
-            }
+            for (int v = 0; v < NP; v++) site_kick_drift<T>(L.K, cen[0][v], cen[1][v], pn[0][v], pn[1][v], g[0][v], g[1][v]);
             if (!ahead) {
                 if (own) {
                     const uint32_t gi = L.plane(z) * nn + rowg;
@@ -292,11 +284,7 @@ __device__ void march_segment(const MarchLattice<T>& L, int yt, int z0, int nz, 
                 else A.accg1 = acc;
             }
 #pragma unroll
-            for (int v = 0; v < NP; v++) {
-                const P sq = mul2(gq[0][v], gq[0][v]);
-                A.accvd = L.quartic ? fma2(sq, sq, A.accvd) : add2(sq, A.accvd);
-                A.accvi = fma2(sq, mul2(gq[1][v], gq[1][v]), A.accvi);
-            }
+            for (int v = 0; v < NP; v++) site_vsum<T>(L.K, gq[0][v], gq[1][v], A.accvd, A.accvi);
             }
         }
     }

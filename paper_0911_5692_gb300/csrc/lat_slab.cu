@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "lat_internal.h"
+#include "lat_site.cuh"
 
 namespace lat {
 
@@ -35,6 +36,8 @@ __global__ void __launch_bounds__(256) slab_sums_kernel(Bufs<T> B, Model M, DevS
     const int par = (int)(sc->step & 1);
     const T* __restrict__ f0 = par ? B.f[1][0] : B.f[0][0];
     const T* __restrict__ f1 = par ? B.f[1][1] : B.f[0][1];
+    const bool quartic = M.beta == 4;
+    const double P = sc->bgf, vfac = site_vsum_factor<double>(quartic);
     double acc[kSums] = {0.0, 0.0, 0.0, 0.0};
     const size_t nn = (size_t)n * n;
     const long long cols = (long long)n * n;
@@ -52,9 +55,9 @@ __global__ void __launch_bounds__(256) slab_sums_kernel(Bufs<T> B, Model M, DevS
                          h2 = (double)f1[pu + (size_t)y * n + x] - a1;
             acc[0] += e0 * e0 + e1 * e1 + e2 * e2;
             acc[1] += h0 * h0 + h1 * h1 + h2 * h2;
-            const double sq = a0 * a0;
-            acc[2] += M.beta == 4 ? 0.25 * sq * sq : 0.5 * sq;
-            acc[3] += 0.5 * sq * a1 * a1;
+            // potential terms about the homogeneous mode (lat_site.cuh)
+            acc[2] += vfac * vdiff_dom(a0, P, P * P, quartic);
+            acc[3] += 0.5 * vint(a0, a1, P);
         }
     }
     finish_block_sums(M, sc, partials, acc, red, sums_out);

@@ -107,7 +107,8 @@ __device__ __forceinline__ void plane_ek(const RowV<T>& C, const RowV<T>& Ym, co
 }
 
 // Per-thread sums of the new fields: the squared differences of each field
-// over its owned pairs by weight class (14, 3, 1), f0^beta and f0^2 f1^2.
+// over its owned pairs by weight class (14, 3, 1) and the potential sums of
+// lat_site.cuh.
 template <typename T>
 struct Sums27 {
     typename PK<T>::P w14[2], w3[2], w1[2], vd, vi;
@@ -139,9 +140,9 @@ __device__ __forceinline__ typename PK<T>::P sq_acc(typename PK<T>::P a, typenam
 // call's plane P + 1 when `carried` (kept in c0r, c1r); this call leaves its
 // plane P + 1 rows there. Every lane calls this.
 template <typename T>
-__device__ __forceinline__ void pair_sums(const T* Gp, const T* Gu, uint32_t fieldG, int o1, bool own, bool quartic,
-                                          bool nbl, bool nbr, int dl, int dr, bool carried, RowV<T> (&c0r)[2],
-                                          RowV<T> (&c1r)[2], Sums27<T>& A)
+__device__ __forceinline__ void pair_sums(const T* Gp, const T* Gu, uint32_t fieldG, int o1, bool own,
+                                          const SiteCoefs<T>& K, bool nbl, bool nbr, int dl, int dr, bool carried,
+                                          RowV<T> (&c0r)[2], RowV<T> (&c1r)[2], Sums27<T>& A)
 {
     typedef typename PK<T>::P P;
     constexpr int NP = PK<T>::NP;
@@ -188,11 +189,7 @@ __device__ __forceinline__ void pair_sums(const T* Gp, const T* Gu, uint32_t fie
             A.w1[f] = a1;
             if (f == 1) {
 #pragma unroll
-                for (int v = 0; v < NP; v++) {
-                    const P sq = mul2(c0[v], c0[v]);
-                    A.vd = quartic ? fma2(sq, sq, A.vd) : add2(sq, A.vd);
-                    A.vi = fma2(sq, mul2(p0.v[v], p0.v[v]), A.vi);
-                }
+                for (int v = 0; v < NP; v++) site_vsum<T>(K, c0[v], p0.v[v], A.vd, A.vi);
             }
         }
     }
@@ -297,7 +294,7 @@ __device__ void march_segment27(const MarchLattice<T>& L, int xt, int W, int yt,
     }
     int sf = 0, sp = 0, sg = 0;        // k mod (D+3), k mod (D+1), k mod 3
 
-    const P dtcl2 = mk2(L.dtcl, L.dtcl), dtcf2 = mk2(L.dtcf, L.dtcf);
+    const P dtcl2 = mk2(L.K.dtcl, L.K.dtcl), dtcf2 = mk2(L.K.dtcf, L.K.dtcf);
     const P c30 = mk2(T(30), T(30));
     P Cm[2][NP], qm[2][NP], Cc[2][NP], qc[2][NP], rc[2][NP];   // aggregates of planes z - 1 and z
     RowV<T> gr0[2], gr1[2];   // rows j, j + 1 of the newest new-field plane summed so far
@@ -351,18 +348,11 @@ __device__ void march_segment27(const MarchLattice<T>& L, int xt, int W, int yt,
             }
         }
         if (comp) {
-            const P mdtcdom2 = mk2(L.mdtcdom, L.mdtcdom), mdtkap2 = mk2(L.mdtkap, L.mdtkap), dt2 = mk2(L.dt, L.dt);
             P g[2][NP];
+            // potential part of the kick and the drift of plane z (shifted down
+            // above) (lat_site.cuh)
 #pragma unroll
-            for (int v = 0; v < NP; v++) {
-                const P a0 = Cm[0][v], a1 = Cm[1][v];   // plane z (shifted down above)
-                const P a0a1 = mul2(a0, a1);
-                const P dom = L.quartic ? mul2(mul2(a0, a0), a0) : a0;
-                pn[0][v] = fma2(mdtcdom2, dom, fma2(mdtkap2, mul2(a0a1, a1), pn[0][v]));
-                pn[1][v] = fma2(mdtkap2, mul2(a0a1, a0), pn[1][v]);
-                g[0][v] = fma2(dt2, pn[0][v], a0);
-                g[1][v] = fma2(dt2, pn[1][v], a1);
-            }
+            for (int v = 0; v < NP; v++) site_kick_drift<T>(L.K, Cm[0][v], Cm[1][v], pn[0][v], pn[1][v], g[0][v], g[1][v]);
             if (own && !ahead) {
                 const uint32_t gi = L.plane(z) * nn + rowg;
                 PK<T>::st(L.op0 + gi, pn[0]);
@@ -376,14 +366,14 @@ __device__ void march_segment27(const MarchLattice<T>& L, int xt, int W, int yt,
 
         // pairs of planes k - 2 and k - 1 (both written before the barrier above)
         if (k >= 2)
-            pair_sums(Gm2 + offP, Gm1 + offP, R.fieldG, o1, own, L.quartic, nbl, nbr, dl, dr, false, gr0, gr1, A);
+            pair_sums(Gm2 + offP, Gm1 + offP, R.fieldG, o1, own, L.K, nbl, nbr, dl, dr, false, gr0, gr1, A);
     }
     // the last pair: planes nz - 1 and nz (the look-ahead plane)
     __syncthreads();
     {
         const T* Gl = G0 + (uint32_t)addm(sg, 2, 3) * R.planeG;   // plane nz (sg = (nz + 1) mod 3)
         const T* Gb = G0 + (uint32_t)addm(sg, 1, 3) * R.planeG;   // plane nz - 1
-        pair_sums(Gb + offP, Gl + offP, R.fieldG, o1, own, L.quartic, nbl, nbr, dl, dr, false, gr0, gr1, A);
+        pair_sums(Gb + offP, Gl + offP, R.fieldG, o1, own, L.K, nbl, nbr, dl, dr, false, gr0, gr1, A);
     }
 }
 
@@ -413,13 +403,7 @@ __global__ void __launch_bounds__(MAXT, 1) step27_kernel(Bufs<T> B, Model M, Dev
     L.n = n;
     L.ty = G.ty;
     L.depth = G.depth;
-    // dt cL / (30 dx^2) multiplies the integer-weight neighbour sum
-    L.dt = step_coef<T>(sc, 4);
-    L.dtcl = step_coef<T>(sc, 0);
-    L.dtcf = step_coef<T>(sc, 1);
-    L.mdtcdom = step_coef<T>(sc, 2);
-    L.mdtkap = step_coef<T>(sc, 3);
-    L.quartic = M.beta == 4;
+    L.K = site_coefs<T>(sc, M.beta);
     L.periodic = true;
     L.zbase = 0;
     Sums27<T> A;
@@ -438,7 +422,7 @@ __global__ void __launch_bounds__(MAXT, 1) step27_kernel(Bufs<T> B, Model M, Dev
         march_segment27(L, tile % G.nxt, G.W, tile / G.nxt, z0, nz, S, A, first);
     }
     double v[kSums];
-    A.totals(L.quartic, v);
+    A.totals(L.K.quartic, v);
     finish_block(M, sc, partials, v, red, true);
 }
 

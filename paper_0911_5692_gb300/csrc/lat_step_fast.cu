@@ -13,6 +13,7 @@
 #include "lat_async.cuh"
 #include "lat_kernels.h"
 #include "lat_pairs.cuh"
+#include "lat_site.cuh"
 
 namespace lat {
 
@@ -48,8 +49,8 @@ struct Fast {
         int rho, lane, z0, nz, dl, dr;
         const T *f0, *f1, *p0, *p1;
         T *of0, *of1, *op0, *op1;
-        P dtcl2, dtcf2, dt2, mdtcdom2, mdtkap2;
-        bool quartic;
+        P dtcl2, dtcf2;
+        SiteCoefs<T> K;
         P accg0, accg1, accvd, accvi;
     };
 
@@ -139,17 +140,9 @@ struct Fast {
                     pn[f][v] = fma2(C.dtcl2, lapu, fma2(C.dtcf2, c, pv[v]));
                 }
             }
+            // potential part of the kick and the drift (lat_site.cuh)
 #pragma unroll
-            for (int v = 0; v < NP; v++) {
-                // potential: f0 gets -dt (cdom f0^(beta-1) + kappa f0 f1^2), f1 gets -dt kappa f0^2 f1
-                const P a0 = cen[0][v], a1 = cen[1][v];
-                const P a0a1 = mul2(a0, a1);
-                const P dom = C.quartic ? mul2(mul2(a0, a0), a0) : a0;
-                pn[0][v] = fma2(C.mdtcdom2, dom, fma2(C.mdtkap2, mul2(a0a1, a1), pn[0][v]));
-                pn[1][v] = fma2(C.mdtkap2, mul2(a0a1, a0), pn[1][v]);
-                g[0][v] = fma2(C.dt2, pn[0][v], a0);
-                g[1][v] = fma2(C.dt2, pn[1][v], a1);
-            }
+            for (int v = 0; v < NP; v++) site_kick_drift<T>(C.K, cen[0][v], cen[1][v], pn[0][v], pn[1][v], g[0][v], g[1][v]);
             if (!ahead) {
                 if (own) {
                     const uint32_t gi = (uint32_t)(C.z0 + k) * NN + C.rowg;
@@ -193,11 +186,7 @@ struct Fast {
                 else C.accg1 = acc;
             }
 #pragma unroll
-            for (int v = 0; v < NP; v++) {
-                const P sq = mul2(gq[0][v], gq[0][v]);
-                C.accvd = C.quartic ? fma2(sq, sq, C.accvd) : add2(sq, C.accvd);
-                C.accvi = fma2(sq, mul2(gq[1][v], gq[1][v]), C.accvi);
-            }
+            for (int v = 0; v < NP; v++) site_vsum<T>(C.K, gq[0][v], gq[1][v], C.accvd, C.accvi);
         }
     }
 
@@ -245,15 +234,9 @@ __global__ void __launch_bounds__(Fast<T, N, TY, D>::THREADS, (Fast<T, N, TY, D>
     C.op0 = par ? B.p[0][0] : B.p[1][0];
     C.op1 = par ? B.p[0][1] : B.p[1][1];
     // f' += dt (cL Lap f + cF f - dV/df), f += dt f', with 1/dx^2 folded into dt cL
-    const T dt_s = step_coef<T>(sc, 4);
-    const T dtcl = step_coef<T>(sc, 0), dtcf = step_coef<T>(sc, 1);
-    const T mdtcdom = step_coef<T>(sc, 2), mdtkap = step_coef<T>(sc, 3);
-    C.dtcl2 = mk2(dtcl, dtcl);
-    C.dtcf2 = mk2(dtcf, dtcf);
-    C.dt2 = mk2(dt_s, dt_s);
-    C.mdtcdom2 = mk2(mdtcdom, mdtcdom);
-    C.mdtkap2 = mk2(mdtkap, mdtkap);
-    C.quartic = M.beta == 4;
+    C.K = site_coefs<T>(sc, M.beta);
+    C.dtcl2 = mk2(C.K.dtcl, C.K.dtcl);
+    C.dtcf2 = mk2(C.K.dtcf, C.K.dtcf);
     C.accg0 = C.accg1 = C.accvd = C.accvi = mk2(T(0), T(0));
 
     // Work: the (N / TY) * N (y tile, z plane) units in tile-major order; block
@@ -292,7 +275,7 @@ __global__ void __launch_bounds__(Fast<T, N, TY, D>::THREADS, (Fast<T, N, TY, D>
     // per-thread sums in the element type (the 1/beta and 1/2 factors are
     // powers of two, exact); the block folds them as finish_block describes
     T v[kSums] = {lo2(C.accg0) + hi2(C.accg0), lo2(C.accg1) + hi2(C.accg1),
-                  (lo2(C.accvd) + hi2(C.accvd)) * (C.quartic ? T(0.25) : T(0.5)),
+                  (lo2(C.accvd) + hi2(C.accvd)) * site_vsum_factor<T>(C.K.quartic),
                   T(0.5) * (lo2(C.accvi) + hi2(C.accvi))};
     finish_block(M, sc, partials, v, red, true);
 }

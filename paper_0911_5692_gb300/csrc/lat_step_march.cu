@@ -51,14 +51,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
     L.n = n;
     L.ty = G.ty;
     L.depth = G.depth;
-    // f' += dt (cL Lap f + cF f - dV/df), f += dt f', with the 1/dx^2 of the
-    // Laplacian folded into dt cL
-    L.dt = step_coef<T>(sc, 4);
-    L.dtcl = step_coef<T>(sc, 0);
-    L.dtcf = step_coef<T>(sc, 1);
-    L.mdtcdom = step_coef<T>(sc, 2);
-    L.mdtkap = step_coef<T>(sc, 3);
-    L.quartic = M.beta == 4;
+    L.K = site_coefs<T>(sc, M.beta);
     L.periodic = G.periodic != 0;
     L.zbase = G.zbase;
     MarchSums<T> A;
@@ -79,7 +72,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
         march_segment(L, yt, z0, nz, S, A, first);
     }
     T v[kSums];
-    A.totals(L.quartic, v);
+    A.totals(L.K.quartic, v);
     if (sums_out) finish_block_sums(M, sc, partials, v, red, sums_out);
     else finish_block(M, sc, partials, v, red, true);
 }

@@ -143,7 +143,7 @@ __device__ void march_segment_xt(const MarchLattice<T>& L, int xt, int W, int yt
                     lft[0] = mk2(left, lo2(cen[f][0]));
                     rgt[0] = mk2(hi2(cen[f][0]), right);
                 }
-                const P dtcl2 = mk2(L.dtcl, L.dtcl), dtcf2 = mk2(L.dtcf, L.dtcf);
+                const P dtcl2 = mk2(L.K.dtcl, L.K.dtcl), dtcf2 = mk2(L.K.dtcf, L.K.dtcf);
 #pragma unroll
                 for (int v = 0; v < NP; v++) {
                     const P c = cen[f][v];
@@ -154,17 +154,9 @@ __device__ void march_segment_xt(const MarchLattice<T>& L, int xt, int W, int yt
                     pn[f][v] = fma2(dtcl2, lapu, fma2(dtcf2, c, pv[v]));
                 }
             }
-            const P mdtcdom2 = mk2(L.mdtcdom, L.mdtcdom), mdtkap2 = mk2(L.mdtkap, L.mdtkap), dt2 = mk2(L.dt, L.dt);
+            // potential part of the kick and the drift (lat_site.cuh)
 #pragma unroll
-            for (int v = 0; v < NP; v++) {
-                const P a0 = cen[0][v], a1 = cen[1][v];
-                const P a0a1 = mul2(a0, a1);
-                const P dom = L.quartic ? mul2(mul2(a0, a0), a0) : a0;
-                pn[0][v] = fma2(mdtcdom2, dom, fma2(mdtkap2, mul2(a0a1, a1), pn[0][v]));
-                pn[1][v] = fma2(mdtkap2, mul2(a0a1, a0), pn[1][v]);
-                g[0][v] = fma2(dt2, pn[0][v], a0);
-                g[1][v] = fma2(dt2, pn[1][v], a1);
-            }
+            for (int v = 0; v < NP; v++) site_kick_drift<T>(L.K, cen[0][v], cen[1][v], pn[0][v], pn[1][v], g[0][v], g[1][v]);
             if (!ahead) {
                 if (own) {
                     const uint32_t gi = L.plane(z) * nn + rowg;
@@ -217,11 +209,7 @@ __device__ void march_segment_xt(const MarchLattice<T>& L, int xt, int W, int yt
                     else A.accg1 = acc;
                 }
 #pragma unroll
-                for (int v = 0; v < NP; v++) {
-                    const P sq = mul2(gq[0][v], gq[0][v]);
-                    A.accvd = L.quartic ? fma2(sq, sq, A.accvd) : add2(sq, A.accvd);
-                    A.accvi = fma2(sq, mul2(gq[1][v], gq[1][v]), A.accvi);
-                }
+                for (int v = 0; v < NP; v++) site_vsum<T>(L.K, gq[0][v], gq[1][v], A.accvd, A.accvi);
             }
         }
     }
@@ -254,12 +242,7 @@ __global__ void __launch_bounds__(MAXT, 1) step_xt_kernel(Bufs<T> B, Model M, De
     L.n = n;
     L.ty = G.ty;
     L.depth = G.depth;
-    L.dt = step_coef<T>(sc, 4);
-    L.dtcl = step_coef<T>(sc, 0);
-    L.dtcf = step_coef<T>(sc, 1);
-    L.mdtcdom = step_coef<T>(sc, 2);
-    L.mdtkap = step_coef<T>(sc, 3);
-    L.quartic = M.beta == 4;
+    L.K = site_coefs<T>(sc, M.beta);
     L.periodic = true;
     L.zbase = 0;
     MarchSums<T> A;
@@ -278,7 +261,7 @@ __global__ void __launch_bounds__(MAXT, 1) step_xt_kernel(Bufs<T> B, Model M, De
         march_segment_xt(L, tile % G.nxt, G.W, tile / G.nxt, z0, nz, S, A, first);
     }
     T v[kSums];
-    A.totals(L.quartic, v);
+    A.totals(L.K.quartic, v);
     finish_block(M, sc, partials, v, red, true);
 }
 

@@ -1,146 +1,22 @@
-// lat_step_simple.cu -- fused leapfrog step with plain (L1-cached) loads.
-//
-// One step of Sec. II.B, eq. evo for both fields at once, with eq. scalar-evo
-// as the acceleration: 7-point Laplacian, potential derivative, kick of f',
-// drift of f; then the volume sums of the NEW fields that eq. scale needs at
-// the next field time: <|grad f|^2> from forward differences (equal to
-// -<f Lap f> on the periodic lattice, the identity of Sec. II.B) and <V_pr>.
-//
-// The forward differences of the new fields need the new values one site
-// beyond the tile in +x, +y and +z. The block therefore also kicks and drifts
-// that one-site rim (reading only the old ping-pong buffers, which nobody
-// writes during the step) without storing it. That keeps the whole step at one
-// pass over memory: the sums the scale factor needs are ready when the kernel
-// ends, and its last block performs the FP64 a(t) update.
-//
-// This kernel is the portable path (FP32 and FP64, any N % 4 == 0); the TMA
-// plane-ring kernel in lat_step_tma.cu is the fast FP32/FP64 path on sm_103a.
+// lat_sums.cu -- the volume averages of the current fields without a step
+// (after initialisation, a state upload or a change of coupling): the gradient
+// averages <|grad f|^2> = -<f L f> of the configured stencil (Sec. II.B, the
+// divergence-theorem identity) and the potential terms, whose last block then
+// solves the a' update of the first step (eq. scale).
 #include <algorithm>
 
 #include "lat_grid.h"
 #include "lat_kernels.h"
+#include "lat_site.cuh"
 #include "lat_stencil27.cuh"
 
 namespace lat {
 
 namespace {
 
-template <typename T>
-struct Coef {
-    T cL, cF, cdom, kap, dt, idx2;
-    int beta;
-};
-
 __device__ __forceinline__ size_t sidx(int n, int x, int y, int z)
 {
     return ((size_t)z * n + y) * n + x;
-}
-
-// Kick and drift of both fields at one site from the old buffers:
-// f'_new = f' + dt (cL Lap f + cF f - dV_pr/df), f_new = f + dt f'_new.
-template <typename T>
-__device__ __forceinline__ void site_update(const T* __restrict__ f0, const T* __restrict__ f1,
-                                            const T* __restrict__ p0, const T* __restrict__ p1, int n, int x,
-                                            int y, int z, const Coef<T>& C, T& np0, T& np1, T& g0, T& g1)
-{
-    const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? n - 1 : z - 1, zp = z == n - 1 ? 0 : z + 1;
-    const size_t c = sidx(n, x, y, z);
-    const T a0 = __ldg(f0 + c), a1 = __ldg(f1 + c);
-    // Laplacian as a sum of neighbour differences: for f = const + small each
-    // difference is exact in floating point (Sterbenz), so the rounding error is
-    // relative to the fluctuation, not to |f|.
-    const T lap0 = (((__ldg(f0 + sidx(n, xm, y, z)) - a0) + (__ldg(f0 + sidx(n, xp, y, z)) - a0))
-                  + ((__ldg(f0 + sidx(n, x, ym, z)) - a0) + (__ldg(f0 + sidx(n, x, yp, z)) - a0))
-                  + ((__ldg(f0 + sidx(n, x, y, zm)) - a0) + (__ldg(f0 + sidx(n, x, y, zp)) - a0))) * C.idx2;
-    const T lap1 = (((__ldg(f1 + sidx(n, xm, y, z)) - a1) + (__ldg(f1 + sidx(n, xp, y, z)) - a1))
-                  + ((__ldg(f1 + sidx(n, x, ym, z)) - a1) + (__ldg(f1 + sidx(n, x, yp, z)) - a1))
-                  + ((__ldg(f1 + sidx(n, x, y, zm)) - a1) + (__ldg(f1 + sidx(n, x, y, zp)) - a1))) * C.idx2;
-    const T a0b = C.beta == 4 ? a0 * a0 * a0 : a0;       // f^(beta-1)
-    const T dv0 = C.cdom * a0b + C.kap * a0 * a1 * a1;
-    const T dv1 = C.kap * a0 * a0 * a1;
-    np0 = __ldg(p0 + c) + C.dt * (C.cL * lap0 + C.cF * a0 - dv0);
-    np1 = __ldg(p1 + c) + C.dt * (C.cL * lap1 + C.cF * a1 - dv1);
-    g0 = a0 + C.dt * np0;
-    g1 = a1 + C.dt * np1;
-}
-
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) step_simple_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials,
-                                                              int zr)
-{
-    __shared__ T g0s[TY + 1][TX + 1];
-    __shared__ T g1s[TY + 1][TX + 1];
-    __shared__ double red[32 * kSums];
-    if (sc->status != LAT_OK) return;
-    const int n = M.n;
-    const int par = (int)(sc->step & 1);
-    const T* __restrict__ f0 = B.f[par][0];
-    const T* __restrict__ f1 = B.f[par][1];
-    const T* __restrict__ p0 = B.p[par][0];
-    const T* __restrict__ p1 = B.p[par][1];
-    T* __restrict__ f0o = B.f[par ^ 1][0];
-    T* __restrict__ f1o = B.f[par ^ 1][1];
-    T* __restrict__ p0o = B.p[par ^ 1][0];
-    T* __restrict__ p1o = B.p[par ^ 1][1];
-    Coef<T> C;
-    C.cL = (T)sc->cL; C.cF = (T)sc->cF; C.cdom = (T)sc->cdom; C.kap = (T)sc->kappa;
-    C.dt = (T)M.dt; C.idx2 = (T)M.inv_dx2; C.beta = M.beta;
-
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zr;
-    const int tw = min(TX, n - x0), th = min(TY, n - y0), z1 = min(z0 + zr, n);
-    const int tid = threadIdx.x, lx = tid % TX, ly = tid / TX;
-    const bool own = lx < tw && ly < th;
-    int hx = -1, hy = -1;                 // the rim site this thread also updates
-    if (tid < tw) { hx = tid; hy = th; }
-    else if (tid < tw + th) { hx = tw; hy = tid - tw; }
-
-    T acc_g0 = 0, acc_g1 = 0, acc_vd = 0, acc_vi = 0;
-    T gp0 = 0, gp1 = 0;
-    for (int z = z0; z <= z1; z++) {
-        const int zz = z == n ? 0 : z;
-        const bool ahead = z == z1;       // look-ahead plane: only the z-pairs need it
-        if (own) {
-            T np0, np1, g0, g1;
-            site_update(f0, f1, p0, p1, n, x0 + lx, y0 + ly, zz, C, np0, np1, g0, g1);
-            g0s[ly][lx] = g0; g1s[ly][lx] = g1;
-            if (!ahead) {
-                const size_t c = sidx(n, x0 + lx, y0 + ly, zz);
-                p0o[c] = np0; p1o[c] = np1; f0o[c] = g0; f1o[c] = g1;
-            }
-        }
-        if (!ahead && hx >= 0) {
-            int x = x0 + hx, y = y0 + hy;
-            if (x >= n) x -= n;
-            if (y >= n) y -= n;
-            T np0, np1, g0, g1;
-            site_update(f0, f1, p0, p1, n, x, y, zz, C, np0, np1, g0, g1);
-            g0s[hy][hx] = g0; g1s[hy][hx] = g1;
-        }
-        __syncthreads();
-        if (own) {
-            const T g0 = g0s[ly][lx], g1 = g1s[ly][lx];
-            if (!ahead) {
-                const T dx0 = g0s[ly][lx + 1] - g0, dy0 = g0s[ly + 1][lx] - g0;
-                const T dx1 = g1s[ly][lx + 1] - g1, dy1 = g1s[ly + 1][lx] - g1;
-                acc_g0 += dx0 * dx0 + dy0 * dy0;
-                acc_g1 += dx1 * dx1 + dy1 * dy1;
-                const T sq = g0 * g0;
-                acc_vd += M.beta == 4 ? T(0.25) * sq * sq : T(0.5) * sq;
-                acc_vi += T(0.5) * sq * g1 * g1;
-            }
-            if (z > z0) {
-                const T dz0 = g0 - gp0, dz1 = g1 - gp1;
-                acc_g0 += dz0 * dz0;
-                acc_g1 += dz1 * dz1;
-            }
-            gp0 = g0; gp1 = g1;
-        }
-        __syncthreads();
-    }
-    double v[kSums] = {(double)acc_g0, (double)acc_g1, (double)acc_vd, (double)acc_vi};
-    finish_block(M, sc, partials, v, red, true);
 }
 
 // Sums of the current fields (no step): the gradient averages of the configured
@@ -171,6 +47,7 @@ __global__ void __launch_bounds__(256) sums_kernel(Bufs<T> B, Model M, DevScalar
     const T* __restrict__ f0 = B.f[par][0];
     const T* __restrict__ f1 = B.f[par][1];
     const bool s27 = M.stencil == 27, quartic = M.beta == 4;
+    const T P = (T)sc->bgf, P2 = (T)(sc->bgf * sc->bgf), vfac = site_vsum_factor<T>(quartic);
     KSum<T> acc[kSums];
     // work items: (x, y) columns cut into nzc z runs, so that small lattices
     // still give every SM enough threads
@@ -186,9 +63,9 @@ __global__ void __launch_bounds__(256) sums_kernel(Bufs<T> B, Model M, DevScalar
         for (int z = zb; z < ze; z++) {
             const int zp = z == n - 1 ? 0 : z + 1;
             const T u0 = __ldg(f0 + sidx(n, x, y, zp)), u1 = __ldg(f1 + sidx(n, x, y, zp));   // the next centre
-            const T sq = a0 * a0;
-            acc[2].add(quartic ? T(0.25) * sq * sq : T(0.5) * sq);
-            acc[3].add(T(0.5) * sq * a1 * a1);
+            // potential terms about the homogeneous mode (lat_site.cuh)
+            acc[2].add(vfac * vdiff_dom(a0, P, P2, quartic));
+            acc[3].add(T(0.5) * vint(a0, a1, P));
             if (s27) {
                 acc[0].add(bonds27_sum<T>(f0, n, x, y, z));
                 acc[1].add(bonds27_sum<T>(f1, n, x, y, z));
@@ -220,6 +97,7 @@ __global__ void __launch_bounds__(256) sums7_vec_kernel(Bufs<float> B, Model M, 
     const float* __restrict__ f0 = B.f[par][0];
     const float* __restrict__ f1 = B.f[par][1];
     const bool quartic = M.beta == 4;
+    const float P = (float)sc->bgf, P2 = (float)(sc->bgf * sc->bgf), vfac = site_vsum_factor<float>(quartic);
     KSum<float> acc[kSums];
     const long long vcols = (long long)q * n, items = vcols * nzc;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
@@ -263,9 +141,10 @@ __global__ void __launch_bounds__(256) sums7_vec_kernel(Bufs<float> B, Model M, 
             };
             acc[0].add(grad(c0, y0, u0, r0));
             acc[1].add(grad(c1, y1, u1, r1));
-            const float s0 = c0.x * c0.x, s1 = c0.y * c0.y, s2 = c0.z * c0.z, s3 = c0.w * c0.w;
-            acc[2].add(quartic ? 0.25f * ((s0 * s0 + s1 * s1) + (s2 * s2 + s3 * s3)) : 0.5f * ((s0 + s1) + (s2 + s3)));
-            acc[3].add(0.5f * ((s0 * c1.x * c1.x + s1 * c1.y * c1.y) + (s2 * c1.z * c1.z + s3 * c1.w * c1.w)));
+            // potential terms about the homogeneous mode (lat_site.cuh)
+            acc[2].add(vfac * ((vdiff_dom(c0.x, P, P2, quartic) + vdiff_dom(c0.y, P, P2, quartic)) +
+                               (vdiff_dom(c0.z, P, P2, quartic) + vdiff_dom(c0.w, P, P2, quartic))));
+            acc[3].add(0.5f * ((vint(c0.x, c1.x, P) + vint(c0.y, c1.y, P)) + (vint(c0.z, c1.z, P) + vint(c0.w, c1.w, P))));
             c0 = u0;
             c1 = u1;
         }
@@ -275,21 +154,6 @@ __global__ void __launch_bounds__(256) sums7_vec_kernel(Bufs<float> B, Model M, 
 }
 
 } // namespace
-
-int simple_grid_blocks(int n, int zr)
-{
-    return ((n + kSimpleTX - 1) / kSimpleTX) * ((n + kSimpleTY - 1) / kSimpleTY) * ((n + zr - 1) / zr);
-}
-
-template <typename T>
-cudaError_t launch_step_simple(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, int zr,
-                               cudaStream_t st)
-{
-    const int n = M.n;
-    dim3 grid((n + kSimpleTX - 1) / kSimpleTX, (n + kSimpleTY - 1) / kSimpleTY, (n + zr - 1) / zr);
-    step_simple_kernel<T, kSimpleTX, kSimpleTY><<<grid, kSimpleTX * kSimpleTY, 0, st>>>(b, M, sc, partials, zr);
-    return cudaGetLastError();
-}
 
 // z runs per (x, y) column of the sums pass: about 4 x 152 x 256 threads'
 // worth of (column, run) items, runs of at least 4 planes
@@ -332,10 +196,6 @@ cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step_simple<float>(const Bufs<float>&, const Model&, DevScalars*, double*, int,
-                                               cudaStream_t);
-template cudaError_t launch_step_simple<double>(const Bufs<double>&, const Model&, DevScalars*, double*, int,
-                                                cudaStream_t);
 template cudaError_t launch_sums<float>(const Bufs<float>&, const Model&, DevScalars*, double*, cudaStream_t);
 template cudaError_t launch_sums<double>(const Bufs<double>&, const Model&, DevScalars*, double*, cudaStream_t);
 

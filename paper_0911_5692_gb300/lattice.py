@@ -27,7 +27,8 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_batch_evolve", "lat_batch_sync", "lat_batch_tune", "lat_batch_member", "lat_batch_info",
             "lat_batch_destroy", "lat_batch_check_barrier", "lat_slab_create", "lat_slab_sums", "lat_slab_step",
             "lat_slab_advance", "lat_energy_field", "lat_upload_state", "lat_get_hubble_length",
-            "lat_set_hubble_length")
+            "lat_set_hubble_length", "lat_download_state", "lat_get_background", "lat_set_background",
+            "lat_recenter")
 
 
 class LatParams(C.Structure):
@@ -40,7 +41,7 @@ class LatParams(C.Structure):
         ("A", C.c_double), ("B", C.c_double), ("r", C.c_double), ("s", C.c_double),
         ("kcut", C.c_double), ("fluct", C.c_double),
         ("seed", C.c_uint64),
-        ("stencil", C.c_int32), ("reserved", C.c_int32),
+        ("stencil", C.c_int32), ("split", C.c_int32),
     ]
 
 
@@ -82,6 +83,10 @@ def load_library(build_if_missing: bool = True):
             L.lat_energies.argtypes = [P, C.POINTER(LatEnergyReport)]
             L.lat_energy_field.argtypes = [P, P, P]
             L.lat_upload_state.argtypes = [P, C.POINTER(C.c_void_p), C.c_int]
+            L.lat_download_state.argtypes = [P, C.POINTER(C.c_void_p), C.c_int]
+            L.lat_get_background.argtypes = [P, dp]
+            L.lat_set_background.argtypes = [P, dp]
+            L.lat_recenter.argtypes = [P]
             L.lat_spectrum.argtypes = [P, C.c_int, C.c_int, dp, dp, i64p]
             L.lat_get_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
             L.lat_set_state.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
@@ -153,6 +158,7 @@ def make_params(d: dict) -> LatParams:
     p.kcut = float(d.get("kcut", 0.0)); p.fluct = float(d.get("fluct", 1.0))
     p.seed = int(d.get("seed", 0))
     p.stencil = int(d.get("stencil", 7))
+    p.split = int(d.get("split", 0))
     return p
 
 
@@ -262,41 +268,85 @@ class Lattice:
 
     # -- state
     def get_state_host(self, field: int, what: int) -> np.ndarray:
+        """One array on the host in the lattice dtype: what 0 = f, 1 = f' whole;
+        2, 3 as stored (for phi of a split lattice: the fluctuation about the
+        homogeneous mode)."""
         out = np.empty((self.n, self.n, self.n), dtype=self.np_dtype)
         _check(self._L.lat_get_state(self._h, field, what, out.ctypes.data_as(C.c_void_p), 0), "lat_get_state")
         return out
 
     def get_state(self):
-        """(f_phi, f_chi, pi_phi, pi_chi) as float64 numpy arrays [z][y][x]."""
+        """(f_phi, f_chi, pi_phi, pi_chi) whole, as float64 numpy arrays [z][y][x]
+        (rounded to the lattice precision)."""
         return tuple(self.get_state_host(i, w).astype(np.float64) for w in (0, 1) for i in (0, 1))
+
+    def get_state_stored(self):
+        """The four arrays as stored, float64 [z][y][x] (for a split lattice phi and
+        its momentum are the fluctuations about background())."""
+        return tuple(self.get_state_host(i, w).astype(np.float64) for w in (2, 3) for i in (0, 1))
+
+    def get_state_exact(self):
+        """(f_phi, f_chi, pi_phi, pi_chi) as the lattice holds them, in float64
+        without rounding: the stored arrays plus the homogeneous mode of a split
+        lattice."""
+        f0, f1, p0, p1 = self.get_state_stored()
+        P, Pi = self.background()
+        return f0 + P, f1, p0 + Pi, p1
 
     def set_state_host(self, field: int, what: int, arr: np.ndarray):
         a = np.ascontiguousarray(arr, dtype=self.np_dtype).reshape(self.n, self.n, self.n)
         _check(self._L.lat_set_state(self._h, field, what, a.ctypes.data_as(C.c_void_p), 0), "lat_set_state")
 
     def set_state(self, f0, f1, pi0, pi1, t=0.0, a=1.0, ad=0.0, step=0):
+        """Whole fields and momenta in (rounded to the lattice precision); on a
+        split lattice the homogeneous mode then moves to their means."""
         # scalars first: the step count selects which ping-pong set is current
         self.set_scalars(t, a, ad, step)
         for i, arr in enumerate((f0, f1)):
             self.set_state_host(i, 0, arr)
         for i, arr in enumerate((pi0, pi1)):
             self.set_state_host(i, 1, arr)
+        if self.params.get("split", 0):
+            self.recenter()
+
+    def background(self):
+        """(P, Pi): the homogeneous inflaton mode of split storage at the field
+        and momentum times (zero when phi is stored whole)."""
+        out = (C.c_double * 2)()
+        _check(self._L.lat_get_background(self._h, out), "lat_get_background")
+        return out[0], out[1]
+
+    def set_background(self, P: float, Pi: float):
+        v = (C.c_double * 2)(float(P), float(Pi))
+        _check(self._L.lat_set_background(self._h, v), "lat_set_background")
+
+    def recenter(self):
+        _check(self._L.lat_recenter(self._h), "lat_recenter")
 
     def upload_state(self, f0, f1, pi0, pi1):
-        """Queue the upload of the whole state (lat_upload_state) from four
-        contiguous tensors of N^3 lattice-dtype elements: CUDA tensors, or host
+        """Queue the upload of the whole state as stored (lat_upload_state) from
+        four contiguous tensors of N^3 lattice-dtype elements: CUDA tensors, or host
         tensors (page-locked for asynchronous copies). Returns without waiting for
         the copies; the sources must stay unchanged until the lattice's stream has
         passed them (e.g. sync())."""
+        ptrs = self._four(f0, f1, pi0, pi1, "upload_state")
+        _check(self._L.lat_upload_state(self._h, ptrs, 1 if f0.is_cuda else 0), "lat_upload_state")
+
+    def download_state(self, f0, f1, pi0, pi1):
+        """Copy the state as stored into four tensors (lat_download_state; the
+        counterpart of upload_state) and wait for the copies."""
+        ptrs = self._four(f0, f1, pi0, pi1, "download_state")
+        _check(self._L.lat_download_state(self._h, ptrs, 1 if f0.is_cuda else 0), "lat_download_state")
+
+    def _four(self, f0, f1, pi0, pi1, what):
         ts = (f0, f1, pi0, pi1)
         dev = all(t.is_cuda for t in ts)
         if not dev and any(t.is_cuda for t in ts):
-            raise ValueError("upload_state takes four CUDA tensors or four host tensors")
+            raise ValueError(f"{what} takes four CUDA tensors or four host tensors")
         for t in ts:
             if t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.n ** 3:
-                raise ValueError("upload_state arrays must be contiguous with N^3 lattice-dtype elements")
-        ptrs = (C.c_void_p * 4)(*[t.data_ptr() for t in ts])
-        _check(self._L.lat_upload_state(self._h, ptrs, 1 if dev else 0), "lat_upload_state")
+                raise ValueError(f"{what} arrays must be contiguous with N^3 lattice-dtype elements")
+        return (C.c_void_p * 4)(*[t.data_ptr() for t in ts])
 
     def set_state_device(self, field: int, what: int, tensor):
         t = tensor.contiguous()

@@ -17,6 +17,9 @@ Sec. III) and the lambda phi^4 lineage it compares against:
 * ``ensemble_64``     64 lambda phi^4 lattices, N cycling over 32, 48, 64, 96,
   g^2/lambda log-uniform in [50, 500].
 * ``lphi4_128_fp32``  the lambda phi^4 model at N = 128, FP32 (adjoint runs).
+
+``split=1`` stores the inflaton as an FP64 homogeneous mode plus FP32
+fluctuation arrays (lat_params.split); the FP32 evolution presets use it.
 """
 from __future__ import annotations
 
@@ -28,24 +31,27 @@ LAMBDA = 9e-14
 
 
 def lphi4(n: int, precision: int = 32, G: float = 200.0, seed: int = 0, expansion: int = 1,
-          L: float = 10.0, dt_over_dx: float = 1.0 / 20.0, fluct: float = 1.0) -> dict:
+          L: float = 10.0, dt_over_dx: float = 1.0 / 20.0, fluct: float = 1.0, split: int = 0) -> dict:
     dx = L / n
     return dict(n=n, precision=precision, model=0, expansion=expansion, L=L, dt=dx * dt_over_dx,
                 lam=LAMBDA, m=0.0, g2=G * LAMBDA, phi0=(0.342, 0.0), dphi0=(0.0, 0.0),
-                eight_pi_G=8.0 * math.pi, kcut=0.0, fluct=fluct, seed=seed)
+                eight_pi_G=8.0 * math.pi, kcut=0.0, fluct=fluct, seed=seed, split=split)
 
 
 def m2phi2(n: int, precision: int = 32, seed: int = 0, expansion: int = 1, L: float = 10.0,
-           dt: float = 2.0 ** -10, fluct: float = 1.0, g2: float = 2.5e-7, m: float = 1e-6) -> dict:
+           dt: float = 2.0 ** -10, fluct: float = 1.0, g2: float = 2.5e-7, m: float = 1e-6, split: int = 0) -> dict:
     return dict(n=n, precision=precision, model=1, expansion=expansion, L=L, dt=dt,
                 lam=0.0, m=m, g2=g2, phi0=(1.009343, 0.0), dphi0=(-0.7137 * m, 0.0),
-                eight_pi_G=1.0, kcut=0.0, fluct=fluct, seed=seed)
+                eight_pi_G=1.0, kcut=0.0, fluct=fluct, seed=seed, split=split)
 
 
+# FP32 evolution workloads store phi split (an FP64 homogeneous mode plus FP32
+# fluctuation arrays); the derivative workload stores it whole (lat_adjoint
+# does not take split lattices).
 WORKLOADS = {
     "lphi4_32_fp64": dict(params=lphi4(32, precision=64), steps=1000),
-    "m2phi2_256_fp32": dict(params=m2phi2(256, precision=32), steps=5000),
-    "lphi4_512_fp32": dict(params=lphi4(512, precision=32), steps=2000),
+    "m2phi2_256_fp32": dict(params=m2phi2(256, precision=32, split=1), steps=5000),
+    "lphi4_512_fp32": dict(params=lphi4(512, precision=32, split=1), steps=2000),
     "lphi4_128_fp32": dict(params=lphi4(128, precision=32), steps=2000),
 }
 

@@ -37,15 +37,16 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lattice.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lat_params), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lat_params), '
                    'offsetof(lat_params, seed), offsetof(lat_params, fluct), offsetof(lat_params, stencil), '
-                   'sizeof(lat_energy_report), '
+                   'offsetof(lat_params, split), sizeof(lat_energy_report), '
                    'offsetof(lat_energy_report, var));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [C.sizeof(lat.LatParams), lat.LatParams.seed.offset, lat.LatParams.fluct.offset,
-                    lat.LatParams.stencil.offset, C.sizeof(lat.LatEnergyReport), lat.LatEnergyReport.var.offset]
+                    lat.LatParams.stencil.offset, lat.LatParams.split.offset, C.sizeof(lat.LatEnergyReport),
+                    lat.LatEnergyReport.var.offset]
 
 
 def test_status_strings():
@@ -79,6 +80,7 @@ def _create_status(params):
     dict(A=1.0, B=1.0, r=1.0, s=0.0),   # violates s - 2r + 3 = 0
     dict(expansion=3),
     dict(stencil=9),          # 7 (or 0) and 27 points only
+    dict(split=2),            # phi stored whole (0) or split (1)
 ])
 def test_validation_rejects_bad_parameters(bad):
     p = dict(lphi4(16), **bad)
@@ -130,4 +132,8 @@ def test_null_arguments():
     assert L.lat_upload_state(None, None, 0) == 1
     assert L.lat_get_hubble_length(None, None) == 1
     assert L.lat_set_hubble_length(None, 1.0) == 1
+    assert L.lat_download_state(None, None, 0) == 1
+    assert L.lat_get_background(None, None) == 1
+    assert L.lat_set_background(None, None) == 1
+    assert L.lat_recenter(None) == 1
     L.lat_destroy(None)

@@ -230,8 +230,10 @@ def test_paths_without_27_point_form_refuse():
     n = 16
     p = _params("lphi4", n, 64)
     g = Lattice(p)
-    for variant in (1, 3):
-        with pytest.raises(LatticeError, match="UNSUPPORTED"):
+    with pytest.raises(LatticeError, match="UNSUPPORTED"):
+        g.set_kernel(4)       # the x-tiled ring is written for 7 points
+    for variant in (1, 3):    # no such kernels
+        with pytest.raises(LatticeError, match="EINVAL"):
             g.set_kernel(variant)
     g.set_kernel(2)
     assert g.kernel_info()["variant"] == 2
