@@ -289,24 +289,27 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8]);
  * pool, a fixed memory budget, or code that cannot take cudaMalloc's implicit
  * device-wide synchronisation).
  * f_phi, f_chi: device arrays of n^3 elements (float for precision 32, double
- * for 64), layout as in lat_get_state; model: LAT_MODEL_*; L: box side. Writes
- * to out_dev (device, 4 doubles, caller-owned) the averages <|grad f_phi|^2>,
- * <|grad f_chi|^2> (forward differences / dx^2), <f_phi^beta/beta> and
- * <f_phi^2 f_chi^2 / 2> in FP64 arithmetic: the averages lat_get_scalars
- * reports in out[4..7] for a handle holding these fields with the 7-point
- * stencil (equal to FP64 rounding for FP64 fields; a handle with FP32 fields
- * forms them in FP32 with compensated per-thread sums, within about 1e-7
+ * for 64), layout as in lat_get_state, holding the fields whole; model:
+ * LAT_MODEL_*; L: box side. Writes to out_dev (device, 4 doubles, caller-owned)
+ * the averages <|grad f_phi|^2>, <|grad f_chi|^2> (forward differences / dx^2),
+ * <f_phi^beta/beta> and <f_phi^2 f_chi^2 / 2> in FP64 arithmetic: the averages
+ * lat_get_scalars reports in out[4..7] for a handle holding these fields with the
+ * 7-point stencil (equal to FP64 rounding for FP64 fields; a handle with FP32
+ * fields forms them in FP32 with compensated per-thread sums, within about 1e-7
  * relative). The gradient average of the 27-point stencil is not served here.
  * Asynchronous on cuda_stream (a cudaStream_t; NULL = legacy default stream).
- * Scratch: one static device array per GPU (about 33 KB, held by every GPU that
- * loads the library until the process exits); it calls no cudaMalloc, cudaFree
- * or allocating library routine. The first call on a device looks the array up
- * with cudaGetSymbolAddress and clears it, synchronously; make that first call
- * before any stream capture. Every call shares the array, so calls that overlap
- * on the GPU (different streams or threads without ordering) race and give
- * wrong sums. Errors: LAT_EINVAL for null pointers or n not a multiple of 4 in
- * [4, ...], bad precision, model or L; LAT_EUNSUPPORTED for n > 1024 (the
- * largest lattice this scratch serves); LAT_ECUDA if the set-up or launch fails. */
+ * Scratch: one static device array per GPU (about 33 KB, the same for every n,
+ * held by every GPU that loads the library until the process exits); it calls no
+ * cudaMalloc, cudaFree or allocating library routine. The first call on a device
+ * looks the array up with cudaGetSymbolAddress and clears it, synchronously; make
+ * that first call before any stream capture. The address is kept for the life of
+ * the process, so do not use this entry point across a device reset
+ * (cudaDeviceReset). Every call shares the array, so calls that overlap on the
+ * GPU (different streams or threads without ordering) race: they may give wrong
+ * sums or leave out_dev unwritten. Errors: LAT_EINVAL for null pointers, n < 4,
+ * precision other than 32 or 64, an unknown model or L <= 0; LAT_EUNSUPPORTED for
+ * n > 1024 (the lattice sides the library serves, the range this entry point is
+ * tested over); LAT_ECUDA if the set-up or launch fails. */
 lat_status lat_field_sums_static(const void* f_phi, const void* f_chi, int n, int precision, int model, double L,
                                  double* out_dev, void* cuda_stream);
 

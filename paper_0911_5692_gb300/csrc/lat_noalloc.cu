@@ -93,7 +93,9 @@ std::mutex g_setup_mutex;
 unsigned char* g_scratch_addr[kMaxDevices];
 
 // Device address of the scratch array on the current device, looked up (and the
-// counter cleared) on the first call made on that device.
+// counter cleared) on the first call made on that device. The address is kept
+// for the life of the process: a device reset (cudaDeviceReset) would leave it
+// stale, so the entry point is not to be used across one.
 cudaError_t scratch_for_current_device(unsigned char** out)
 {
     int dev = 0;
@@ -125,8 +127,10 @@ extern "C" lat_status lat_field_sums_static(const void* f_phi, const void* f_chi
     if (precision != 32 && precision != 64) return LAT_EINVAL;
     if (model != LAT_MODEL_LPHI4 && model != LAT_MODEL_M2PHI2) return LAT_EINVAL;
     if (!(L > 0.0)) return LAT_EINVAL;
-    if (n < 4 || n % 4 != 0) return LAT_EINVAL;
-    if (n > 1024) return LAT_EUNSUPPORTED;       // beyond the largest lattice this entry point serves
+    if (n < 4) return LAT_EINVAL;
+    // the lattice sides the library serves (lat_params.n): the range this entry
+    // point is tested over; its scratch itself does not depend on n
+    if (n > 1024) return LAT_EUNSUPPORTED;
     unsigned char* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return LAT_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -122,7 +122,7 @@ struct Sums27 {
         for (int f = 0; f < 2; f++)
             v[f] = 14.0 * ((double)lo2(w14[f]) + (double)hi2(w14[f])) + 3.0 * ((double)lo2(w3[f]) + (double)hi2(w3[f]))
                    + ((double)lo2(w1[f]) + (double)hi2(w1[f]));
-        v[2] = ((double)lo2(vd) + (double)hi2(vd)) * (quartic ? 0.25 : 0.5);
+        v[2] = ((double)lo2(vd) + (double)hi2(vd)) * (double)site_vsum_factor<T>(quartic);
         v[3] = 0.5 * ((double)lo2(vi) + (double)hi2(vi));
     }
 };
@@ -409,17 +409,23 @@ __global__ void __launch_bounds__(MAXT, 1) step27_kernel(Bufs<T> B, Model M, Dev
     Sums27<T> A;
     A.zero();
 
-    // the nyt * nxt * n (tile, z plane) units in tile-major order (x tiles of a
-    // y tile adjacent), an equal share per block
-    const long long U = (long long)G.nyt * G.nxt * n;
-    long long u = (long long)blockIdx.x * U / gridDim.x;
-    const long long uend = ((long long)blockIdx.x + 1) * U / gridDim.x;
+    // The nxt x tiles of a y tile go to nxt consecutive blocks (a group) that
+    // take the same (y tile, z plane) units: the groups share the nyt * n units
+    // equally, and the blocks of a group march the same planes at the same
+    // time, so the 16-byte halo vectors each tile reads from its x neighbours lie
+    // in memory lines the neighbouring block is reading too, and come from L2
+    // instead of a second DRAM read of the whole line.
+    const int ngroups = gridDim.x / G.nxt;
+    const int grp = blockIdx.x / G.nxt, xt = blockIdx.x - grp * G.nxt;
+    const long long U = (long long)G.nyt * n;
+    long long u = (long long)grp * U / ngroups;
+    const long long uend = ((long long)grp + 1) * U / ngroups;
     for (bool first = true; u < uend; first = false) {
-        const int tile = (int)(u / n);
-        const int z0 = (int)(u - (long long)tile * n);
+        const int yt = (int)(u / n);
+        const int z0 = (int)(u - (long long)yt * n);
         const int nz = (int)min((long long)(n - z0), uend - u);
         u += nz;
-        march_segment27(L, tile % G.nxt, G.W, tile / G.nxt, z0, nz, S, A, first);
+        march_segment27(L, xt, G.W, yt, z0, nz, S, A, first);
     }
     double v[kSums];
     A.totals(L.K.quartic, v);
@@ -489,11 +495,13 @@ bool geom27(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     const long long tiles = (long long)nyt * nxt;
     const long long units = tiles * n;
     long long blocks = 0;
+    // whole groups of nxt blocks (the x tiles of a y tile, marching together)
     if (zr > 0) blocks = tiles * ((n + std::min(zr, n) - 1) / std::min(zr, n));
-    else blocks = std::min((long long)sms * occ, units);
+    else blocks = std::min((long long)sms * occ, units) / nxt * nxt;
+    const long long groups = blocks / nxt;
     cfg->ty = ty;
-    cfg->zr = (int)((units + blocks - 1) / blocks);
-    cfg->nzc = (int)((blocks + tiles - 1) / tiles);
+    cfg->zr = (int)(((long long)nyt * n + groups - 1) / groups);
+    cfg->nzc = (int)((groups + nyt - 1) / nyt);
     cfg->depth = depth;
     cfg->threads = threads;
     cfg->maxt = maxt;

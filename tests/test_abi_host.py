@@ -137,3 +137,31 @@ def test_null_arguments():
     assert L.lat_set_background(None, None) == 1
     assert L.lat_recenter(None) == 1
     L.lat_destroy(None)
+
+
+@pytest.mark.parametrize("case", ["null_phi", "null_chi", "null_out", "precision", "model", "L", "small"])
+def test_static_sums_argument_errors(case):
+    """lat_field_sums_static validates its arguments before any CUDA call: null
+    pointers, a precision other than 32 or 64, an unknown model, L <= 0 and
+    n < 4 give LAT_EINVAL."""
+    L = pkg.load_library()
+    buf = (C.c_double * 8)()
+    ptr = C.cast(buf, C.c_void_p)
+    args = dict(f_phi=ptr, f_chi=ptr, n=16, precision=32, model=0, L=10.0, out=ptr)
+    if case == "null_phi":
+        args["f_phi"] = None
+    elif case == "null_chi":
+        args["f_chi"] = None
+    elif case == "null_out":
+        args["out"] = None
+    elif case == "precision":
+        args["precision"] = 16
+    elif case == "model":
+        args["model"] = 7
+    elif case == "L":
+        args["L"] = 0.0
+    else:
+        args["n"] = 2
+    st = L.lat_field_sums_static(args["f_phi"], args["f_chi"], args["n"], args["precision"], args["model"],
+                                 args["L"], args["out"], None)
+    assert st == 1

@@ -3,11 +3,18 @@ torch.autograd binding) against the FP64 oracle's adjoint and against central
 finite differences of the GPU's own forward map.
 
 Tolerances: FP64 lattices agree with the oracle to 1e-10 normwise (the two
-sum the volume reductions in different orders); FP32 lattices to 2e-4 normwise
-(field arithmetic in FP32 over the whole reverse sweep, against an FP64
-reference); the central-difference check on 16^3 FP64 is the contract's
-rel <= 1e-5, asserted at 1e-7. Results do not depend on the checkpoint
-interval, bit for bit.
+sum the volume reductions in different orders). FP32 lattices (phi stored
+whole: the derivative does not take split lattices): every step of the forward
+recomputation and of the reverse sweep rounds each field value once or a few
+times to u = 2^-24 relative; the leapfrog's propagator neither grows nor damps
+these perturbations outside a resonance band, so after n steps they add up to
+about n times a few u. On top of that, phi ~ 1 held in FP32 is rounded to
+about 6e-8, which is 6e-5 of the 1e-3 fluctuations of the test states, and the
+gradient, which depends on those fluctuations, carries that relative error. The
+bound used is fp32_tol(n) = 6e-5 + 16 n u (1.1e-4 at 50 steps, 2.5e-4 at 200),
+normwise against an FP64 reference. The central-difference check
+on 16^3 FP64 is the contract's rel <= 1e-5, asserted at 1e-7. Results do not
+depend on the checkpoint interval, bit for bit.
 """
 import numpy as np
 import pytest
@@ -20,6 +27,12 @@ from paper_0911_5692_gb300.autograd import LatticeEvolve
 from paper_0911_5692_gb300.workloads import lphi4, m2phi2, random_state
 
 pytestmark = pytest.mark.gpu
+
+
+def fp32_tol(steps):
+    """Normwise bound of an FP32 gradient against an FP64 one after `steps`
+    steps (module docstring): 6e-5 + 16 n u, u = 2^-24."""
+    return 6e-5 + 16 * steps * 2.0 ** -24
 
 
 def _case(model, n, prec, expansion=1):
@@ -196,12 +209,12 @@ def test_adjoint_fp32_matches_oracle(model):
     g = _gpu(p, st, sc)
     J, df, dp, dg2 = g.adjoint(steps)
     Jo, dfo, dpo, dg2o = _oracle_grad(dict(p, precision=64), st, sc, steps)
-    assert abs(J - Jo) <= 1e-5 * abs(Jo)
-    assert abs(dg2 - dg2o) <= 2e-4 * abs(dg2o)
+    assert abs(J - Jo) <= fp32_tol(steps) * abs(Jo)
+    assert abs(dg2 - dg2o) <= fp32_tol(steps) * abs(dg2o), (dg2, dg2o)
     df, dp = df.cpu().numpy(), dp.cpu().numpy()
     for i in (0, 1):
-        assert normwise(df[i], dfo[i]) <= 2e-4, ("df", i, normwise(df[i], dfo[i]))
-        assert normwise(dp[i], dpo[i]) <= 2e-4, ("dp", i, normwise(dp[i], dpo[i]))
+        assert normwise(df[i], dfo[i]) <= fp32_tol(steps), ("df", i, normwise(df[i], dfo[i]))
+        assert normwise(dp[i], dpo[i]) <= fp32_tol(steps), ("dp", i, normwise(dp[i], dpo[i]))
 
 
 @pytest.mark.parametrize("model,n,steps", [("lphi4", 64, 12), ("m2phi2", 64, 12), ("lphi4", 128, 4)])
@@ -211,12 +224,12 @@ def test_adjoint_pair_kernel_fp32(model, n, steps):
     g = _gpu(p, st, sc)
     J, df, dp, dg2 = g.adjoint(steps)
     Jo, dfo, dpo, dg2o = _oracle_grad(dict(p, precision=64), st, sc, steps)
-    assert abs(J - Jo) <= 1e-5 * abs(Jo)
-    assert abs(dg2 - dg2o) <= 2e-4 * abs(dg2o)
+    assert abs(J - Jo) <= fp32_tol(steps) * abs(Jo)
+    assert abs(dg2 - dg2o) <= fp32_tol(steps) * abs(dg2o), (dg2, dg2o)
     df, dp = df.cpu().numpy(), dp.cpu().numpy()
     for i in (0, 1):
-        assert normwise(df[i], dfo[i]) <= 2e-4, ("df", i, normwise(df[i], dfo[i]))
-        assert normwise(dp[i], dpo[i]) <= 2e-4, ("dp", i, normwise(dp[i], dpo[i]))
+        assert normwise(df[i], dfo[i]) <= fp32_tol(steps), ("df", i, normwise(df[i], dfo[i]))
+        assert normwise(dp[i], dpo[i]) <= fp32_tol(steps), ("dp", i, normwise(dp[i], dpo[i]))
 
 
 def test_autograd_function():
@@ -316,12 +329,12 @@ def test_energy_fraction_fp32_matches_oracle(n, steps):
     g = _gpu(p, st, sc)
     J, df, dp, dg2 = g.adjoint(steps, observable=1)
     Jo, dfo, dpo, dg2o = _oracle_frac(dict(p, precision=64), st, sc, steps)
-    assert abs(J - Jo) <= 1e-5 * abs(Jo)
-    assert abs(dg2 - dg2o) <= 2e-4 * abs(dg2o)
+    assert abs(J - Jo) <= fp32_tol(steps) * abs(Jo)
+    assert abs(dg2 - dg2o) <= fp32_tol(steps) * abs(dg2o), (dg2, dg2o)
     df, dp = df.cpu().numpy(), dp.cpu().numpy()
     for i in (0, 1):
-        assert normwise(df[i], dfo[i]) <= 2e-4, ("df", i, normwise(df[i], dfo[i]))
-        assert normwise(dp[i], dpo[i]) <= 2e-4, ("dp", i, normwise(dp[i], dpo[i]))
+        assert normwise(df[i], dfo[i]) <= fp32_tol(steps), ("df", i, normwise(df[i], dfo[i]))
+        assert normwise(dp[i], dpo[i]) <= fp32_tol(steps), ("dp", i, normwise(dp[i], dpo[i]))
 
 
 def test_autograd_energy_fraction():
@@ -340,3 +353,30 @@ def test_autograd_energy_fraction():
         assert normwise(f.grad[i].cpu().numpy(), dfo[i]) <= 1e-10
         assert normwise(pi.grad[i].cpu().numpy(), dpo[i]) <= 1e-10
 
+
+
+@pytest.mark.parametrize("observable", [0, 1])
+def test_adjoint_fp32_against_fp64_c5_shape(observable):
+    """The derivative configuration's shape (lambda phi^4, 128^3, vacuum
+    initial conditions, J = <chi^2> or the energy fraction in chi) over 200
+    steps: the FP32 gradient against the FP64 gradient of the same start on the
+    GPU (the FP64 path is pinned to the oracle above), within fp32_tol(200) =
+    2.5e-4 normwise for dJ/df and dJ/dpi and relative for dJ/dg^2."""
+    n, steps = 128, 200
+    p = lphi4(n, precision=64)
+    g64 = Lattice(p)
+    g64.init_fields()
+    st = g64.get_state()
+    sc = g64.scalars()
+    g32 = Lattice(dict(p, precision=32))
+    g32.set_state(*st, t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
+    # both from the FP32-representable start
+    g64.set_state(*g32.get_state(), t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
+    J32, df32, dp32, dg32 = g32.adjoint(steps, observable=observable)
+    J64, df64, dp64, dg64 = g64.adjoint(steps, observable=observable)
+    tol = fp32_tol(steps)
+    errs = {"J": abs(J32 / J64 - 1), "dg2": abs(dg32 / dg64 - 1)}
+    for i in (0, 1):
+        errs[f"df{i}"] = normwise(df32[i].double().cpu().numpy(), df64[i].cpu().numpy())
+        errs[f"dp{i}"] = normwise(dp32[i].double().cpu().numpy(), dp64[i].cpu().numpy())
+    assert max(errs.values()) <= tol, errs

@@ -68,11 +68,22 @@ def test_one_step_parity(n, model, expansion, prec, variant):
     ta, tad = (1e-14, 1e-13) if prec == 64 else (1e-8, 1e-7)
     assert abs(gs["a"] - os_["a"]) <= ta * os_["a"]
     assert abs(gs["ad"] - os_["ad"]) <= tad * max(abs(os_["ad"]), 1.0)
-    # sums of the new fields: FP64 exact to rounding; FP32 gradient sums carry the
-    # FP32 rounding of f (~6e-8 on differences of ~1e-3)
-    stol = [1e-11, 1e-11, 1e-13, 1e-11] if prec == 64 else [3e-3, 3e-3, 1e-6, 1e-5]
+    # sums of the new fields. FP64: the oracle's, to rounding. FP32: the GPU sums
+    # the fields it writes, so they are compared with the oracle's FP64 sums of
+    # those same FP32 fields; what is left is the FP32 arithmetic of the sums
+    # (differences exact by Sterbenz, squares rounded to 6e-8, per-thread FP32
+    # accumulation over at most 2 x 64 terms before the FP64 block sums:
+    # a few 1e-7 in practice, 2e-6 at most for these lattices)
+    if prec == 64:
+        ref_s = os_["S"]
+        stol = [1e-11, 1e-11, 1e-13, 1e-11]
+    else:
+        own = Oracle(p)
+        own.set_state(*g.get_state(), t=gs["t"], a=gs["a"], ad=gs["ad"], step=gs["step"])
+        ref_s = own.scalars()["S"]
+        stol = [2e-6, 2e-6, 1e-6, 2e-6]
     for k in range(4):
-        ref = os_["S"][k]
+        ref = ref_s[k]
         assert abs(gs["S"][k] - ref) <= stol[k] * abs(ref) + 1e-300, (k, gs["S"][k], ref)
 
 

@@ -321,3 +321,46 @@ def test_background_calls_on_a_whole_lattice():
     assert e.value.status == 8   # LAT_ESTATE
     with pytest.raises(LatticeError):
         g.set_background(1.0, 0.0)
+
+
+def test_m2phi2_run_statistics_through_the_resonance():
+    """The m^2 phi^2 model with the couplings of the paper's run (m = 1e-6,
+    g^2 = 2.5e-7, dt = 2^-10, Sec. III) at 32^3 on the FP32 split path against the
+    FP64 oracle from the same start, every 1000 steps through the linear stage of
+    the resonance, in which var chi grows by more than nine orders of magnitude:
+    a, rho, var phi and var chi within 1e-3 relative and <phi> within 1e-3 of its
+    oscillation amplitude. The comparison ends at the first sample where the
+    inflaton's fluctuations have grown to var phi > 1e-3 of its oscillation
+    amplitude squared (backreaction; near step 68000 here): past that point the
+    dynamics are chaotic, and two FP64 runs that differ only in the order of
+    their sums (this library's FP64 path and the oracle) separate by a factor of
+    about 30 per 4000 steps, from 1e-13 to 1e-3 by the end of the growth of chi
+    (measured at this size), so no finite-precision run can be held to a fixed
+    tolerance beyond it."""
+    p = m2phi2(32, precision=32, split=1)
+    g = Lattice(p)
+    g.init_fields()
+    st = g.get_state_exact()
+    sc = g.scalars()
+    o = Oracle(dict(p, precision=64))
+    o.set_state(*st, t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
+    chunk = 1000
+    var1_start, amp, end = None, 0.0, None
+    for k in range(1, 131):
+        g.evolve(chunk)
+        o.step(chunk)
+        eg, eo = g.energies(), o.energies()
+        var1_start = var1_start if var1_start is not None else eo["var1"]
+        amp = max(amp, abs(eo["mean0"]))
+        where = f"step {k * chunk}"
+        assert abs(eg["a"] / eo["a"] - 1) <= 1e-3, where
+        assert abs(eg["rho"] / eo["rho"] - 1) <= 1e-3, where
+        assert abs(eg["mean0"] - eo["mean0"]) <= 1e-3 * amp, (where, eg["mean0"], eo["mean0"])
+        assert abs(eg["var0"] / eo["var0"] - 1) <= 1e-3, (where, eg["var0"], eo["var0"])
+        assert abs(eg["var1"] / eo["var1"] - 1) <= 1e-3, (where, eg["var1"], eo["var1"])
+        if eo["var0"] > 1e-3 * amp * amp:
+            end = k * chunk
+            growth = eo["var1"] / var1_start
+            break
+    assert end is not None, "no backreaction within 130000 steps"
+    assert growth > 1e9, growth   # the run went through the resonance
