@@ -88,18 +88,19 @@ def config_of(name, p, world):
 
 STEP_KERNEL_SOURCES = {
     7: ("lat_step_fast.cu", "lat_step_march.cu", "lat_march.cuh", "lat_common.cuh", "lat_pairs.cuh", "lat_async.cuh",
-        "lat_kernels.h"),
-    27: ("lat_step27.cu", "lat_march.cuh", "lat_common.cuh", "lat_pairs.cuh", "lat_async.cuh", "lat_kernels.h"),
+        "lat_kernels.h", "lat_site.cuh"),
+    27: ("lat_step27.cu", "lat_march.cuh", "lat_common.cuh", "lat_pairs.cuh", "lat_async.cuh", "lat_kernels.h",
+         "lat_site.cuh"),
 }
 
 
 def kernel_source_hash(stencil=7, variant=2):
     """Hash of the sources the fused step kernels of a stencil (and, for the
-    x-tiled variant 4, its own file) are built from: a recorded DRAM-traffic
-    figure is valid only for these exact sources."""
+    x-tiled variants 4 and 5, their own files) are built from: a recorded
+    DRAM-traffic figure is valid only for these exact sources."""
     d = os.path.join(ROOT, "paper_0911_5692_gb300", "csrc")
     h = hashlib.sha256()
-    files = STEP_KERNEL_SOURCES[stencil] + (("lat_step_xt.cu",) if variant == 4 else ())
+    files = STEP_KERNEL_SOURCES[stencil] + {4: ("lat_step_xt.cu",), 5: ("lat_step_xw.cu", "lat_site.cuh")}.get(variant, ())
     for f in files:
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())

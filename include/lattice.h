@@ -268,14 +268,18 @@ lat_status lat_save_checkpoint(lat_handle* h, void* dst, uint64_t bytes);
 lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
 
 /* Choose the step kernel (all compute the same step): variant 0 = automatic
- * (4 where a row is 128 or more 16-byte vectors: FP32 N >= 512, FP64 N >= 256;
- * else 2 where it fits, else 4), 2 = z-march through a shared-memory plane ring
- * over full x rows, filled by per-thread asynchronous copies, 4 = the same ring
- * over x tiles of at most 32 (or 16) 16-byte vectors with taller y tiles
- * (7-point only); ty = owned rows per tile, zr = planes per z-chunk, depth =
- * planes prefetched ahead, 0 = automatic. LAT_EINVAL for another variant;
- * LAT_EUNSUPPORTED if the variant cannot run this lattice (a 27-point lattice
- * runs on variant 2 only; ty, zr and depth apply to it as above). */
+ * (FP32 lattices with N = 256, 512 or 1024: 5; otherwise 4 where a row is 128 or
+ * more 16-byte vectors, FP32 N >= 512 or FP64 N >= 256, else 2 where it fits,
+ * else 4), 2 = z-march through a shared-memory plane ring over full x rows,
+ * filled by per-thread asynchronous copies, 4 = the same ring over x tiles of
+ * at most 32 (or 16) 16-byte vectors with taller y tiles, 5 = x tiles exactly
+ * 32 vectors wide (one warp per row) with N, ty and depth compiled in (FP32 N =
+ * 256, 512, 1024 with ty 16; FP64 N = 256, 512 with ty 16 and depth 1) and one
+ * warp that handles the tile's x neighbours (4 and 5: 7-point only);
+ * ty = owned rows per tile, zr = planes per z-chunk, depth = planes prefetched
+ * ahead, 0 = automatic. LAT_EINVAL for another variant; LAT_EUNSUPPORTED if the
+ * variant cannot run this lattice (a 27-point lattice runs on variant 2 only;
+ * ty, zr and depth apply to it as above). */
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth);
 
 /* Launch geometry of the current step kernel: out[0] = variant, out[1] = blocks

@@ -174,7 +174,7 @@ lat_status read_scalars(lat_handle* h, DevScalars* out)
 lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
 {
     const int n = h->p.n;
-    if (variant != 0 && variant != 2 && variant != 4) return LAT_EINVAL;
+    if (variant != 0 && variant != 2 && variant != 4 && variant != 5) return LAT_EINVAL;
     auto take = [&](const MarchConfig& cfg, int v) {
         h->mcfg = cfg;
         h->ty = cfg.ty;
@@ -185,7 +185,7 @@ lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int dept
     };
     auto fits = [&](const MarchConfig& cfg) { return (size_t)cfg.blocks * kSums <= h->partials_cap; };
     if (h->M.stencil == 27) {   // the 27-point Laplacian runs on its plane-ring kernel only
-        if (variant == 4) return LAT_EUNSUPPORTED;
+        if (variant == 4 || variant == 5) return LAT_EUNSUPPORTED;
         MarchConfig cfg;
         if (!march27_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr,
                             variant == 0 ? 0 : depth, &cfg) || !fits(cfg))
@@ -196,6 +196,18 @@ lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int dept
         MarchConfig cfg;
         if (!xt_config(n, (int)h->esize, ty, zr, depth, &cfg) || !fits(cfg)) return LAT_EUNSUPPORTED;
         return take(cfg, 4);
+    }
+    if (variant == 5) {   // x tiles one warp wide, compiled geometries (7-point)
+        MarchConfig cfg;
+        if (!xw_config(n, (int)h->esize, ty, zr, depth, &cfg) || !fits(cfg)) return LAT_EUNSUPPORTED;
+        return take(cfg, 5);
+    }
+    if (variant == 0 && h->esize == 4) {
+        // FP32: x tiles one warp wide with compiled geometry where an instance
+        // exists (N = 256, 512, 1024): 512^3 0.871 ms per step against 0.901 ms
+        // (variant 4); 256^3 0.124 against 0.128 ms (variant 2)
+        MarchConfig cfg;
+        if (xw_config(n, 4, 16, 0, 0, &cfg) && fits(cfg)) return take(cfg, 5);
     }
     if (variant == 0 && n / (16 / (int)h->esize) >= 128) {
         // rows of 128 16-byte vectors or more: full-row tiles leave room for at
@@ -340,7 +352,7 @@ lat_status lat_set_g2(lat_handle* h, double g2)
 
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth)
 {
-    if (!h || variant < 0 || variant > 4 || ty < 0 || zr < 0 || depth < 0) return LAT_EINVAL;
+    if (!h || variant < 0 || variant > 5 || ty < 0 || zr < 0 || depth < 0) return LAT_EINVAL;
     if (h->slab) return LAT_ESTATE;
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     return configure_kernel(h, variant, ty, zr, depth);

@@ -138,7 +138,7 @@ __device__ __noinline__ void member_scalars(const BatchLat<T>& BL, const double*
 // sc: two scalar slots per member ([2 l + slot]); slot 0 holds the scalars at
 // the start of the launch, slot (k & 1) those at the start of step k.
 // part: [2][nsegs][kSums]; cta: range table offsets per block.
-template <typename T, int MAXT>
+template <typename T, int MAXT, bool SPLIT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 3 : (MAXT <= 512 ? 2 : 1)) batch_kernel(const BatchLat<T>* __restrict__ lats,
                                                      const BatchSeg* __restrict__ segs, const int* __restrict__ cta,
                                                      int nsegs, DevScalars* sc, double* part, BatchCtl* ctl, int nsteps,
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 3 : (MAXT <= 512 ? 2 : 1))
                 L.zbase = 0;
                 MarchSums<T> A;
                 A.zero();
-                march_segment(L, g.yt, g.z0, g.nz, S, A, s == sb);
+                march_segment<T, SPLIT>(L, g.yt, g.z0, g.nz, S, A, s == sb);
                 T v[kSums];
                 A.totals(L.K.quartic, v);
                 block_reduce(v, red, bs);
@@ -238,13 +238,14 @@ __global__ void scalars_copy_kernel(DevScalars* const* hsc, DevScalars* sc, int 
     }
 }
 
+// the instance for a launch shape; `split`: some member stores phi split
 template <typename T>
-const void* batch_fn(int maxt)
+const void* batch_fn(int maxt, bool split)
 {
     switch (maxt) {
-    case 256: return (const void*)batch_kernel<T, 256>;
-    case 512: return (const void*)batch_kernel<T, 512>;
-    default: return (const void*)batch_kernel<T, 1024>;
+    case 256: return split ? (const void*)batch_kernel<T, 256, true> : (const void*)batch_kernel<T, 256, false>;
+    case 512: return split ? (const void*)batch_kernel<T, 512, true> : (const void*)batch_kernel<T, 512, false>;
+    default: return split ? (const void*)batch_kernel<T, 1024, true> : (const void*)batch_kernel<T, 1024, false>;
     }
 }
 
@@ -285,6 +286,7 @@ struct lat_batch {
     BatchCtl* dctl = nullptr;
     std::map<int64_t, cudaGraphExec_t> graphs;
     bool captured = false;
+    bool split = false;   // some member stores phi split
 };
 
 namespace {
@@ -331,7 +333,7 @@ bool shape_for(const lat_batch* b, int threads, BatchShape* out)
         smem = std::max(smem, ring_elems(n, best, 1) * b->esize);
     }
     s.smem = smem;
-    const void* fn = b->prec == 32 ? batch_fn<float>(s.maxt) : batch_fn<double>(s.maxt);
+    const void* fn = b->prec == 32 ? batch_fn<float>(s.maxt, b->split) : batch_fn<double>(s.maxt, b->split);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
     int occ = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
@@ -426,7 +428,7 @@ cudaError_t launch_batch(lat_batch* b, int64_t nsteps, unsigned int extra = 0,
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(b->dctl, 0, sizeof(BatchCtl), b->stream);
     if (e != cudaSuccess) return e;
-    const void* fn = batch_fn<T>(b->shape.maxt);
+    const void* fn = batch_fn<T>(b->shape.maxt, b->split);
     const BatchLat<T>* lats = (const BatchLat<T>*)b->dlats;
     int nsegs = b->nsegs, ns = (int)nsteps, nlat = nl;
     void* args[] = {(void*)&lats, (void*)&b->dsegs, (void*)&b->dcta, (void*)&nsegs, (void*)&b->dsc,
@@ -567,6 +569,7 @@ lat_status lat_batch_create(const lat_params* params, int count, void* cuda_stre
     b->prec = params[0].precision;
     b->esize = b->prec == 32 ? 4 : 8;
     b->stream = (cudaStream_t)cuda_stream;
+    for (int i = 0; i < count; i++) b->split = b->split || params[i].split != 0;
     lat_status st = LAT_OK;
     for (int i = 0; i < count && st == LAT_OK; i++) {
         lat_handle* h = nullptr;

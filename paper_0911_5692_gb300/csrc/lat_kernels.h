@@ -41,6 +41,7 @@ struct MarchConfig {
     int s27 = 0;   // 1: the 27-point Laplacian kernel (lat_step27.cu)
     int nxt = 1;   // 27-point and x-tiled kernels: x tiles per row
     int xt = 0;    // 1: the x-tiled 7-point kernel (lat_step_xt.cu)
+    int xw = 0;    // 1: the compile-time x-tiled kernel one warp wide (lat_step_xw.cu)
 };
 // kernel specialised for (element bytes, N, ty, depth), or null; *smem gets its
 // dynamic shared memory in bytes
@@ -60,6 +61,12 @@ cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, 
 bool xt_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
 template <typename T>
 cudaError_t launch_step_xt(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
+                           cudaStream_t st);
+// x tiles one warp wide with compile-time N, ty, depth and an edge warp for the
+// tile's x neighbours (whole periodic lattices; the compiled geometries only)
+bool xw_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
+template <typename T>
+cudaError_t launch_step_xw(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
                            cudaStream_t st);
 // the same ring with the 27-point Laplacian (whole periodic lattices)
 bool march27_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);

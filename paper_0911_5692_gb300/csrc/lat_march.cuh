@@ -96,8 +96,9 @@ struct MarchSums {
 // March planes [z0, z0 + nz) of y tile yt (rows yt*ty .. yt*ty+ty-1) through the
 // ring S: kick and drift of the owned sites, written to the other set, and the
 // sums of the new fields of those sites added to A. `first`: no earlier segment
-// of this block is still reading the ring.
-template <typename T>
+// of this block is still reading the ring. SPLIT: the lattice may store phi
+// split (lat_site.cuh); false compiles the forms for phi stored whole.
+template <typename T, bool SPLIT = true>
 __device__ void march_segment(const MarchLattice<T>& L, int yt, int z0, int nz, T* S, MarchSums<T>& A, bool first)
 {
     typedef typename PK<T>::P P;
@@ -232,7 +233,10 @@ __device__ void march_segment(const MarchLattice<T>& L, int yt, int z0, int nz, 
             }
             // potential part of the kick and the drift (lat_site.cuh)
 #pragma unroll
-            for (int v = 0; v < NP; v++) site_kick_drift<T>(L.K, cen[0][v], cen[1][v], pn[0][v], pn[1][v], g[0][v], g[1][v]);
+            for (int v = 0; v < NP; v++) {
+                if constexpr (SPLIT) site_kick_drift<T>(L.K, cen[0][v], cen[1][v], pn[0][v], pn[1][v], g[0][v], g[1][v]);
+                else site_kick_drift_whole<T>(L.K, cen[0][v], cen[1][v], pn[0][v], pn[1][v], g[0][v], g[1][v]);
+            }
             if (!ahead) {
                 if (own) {
                     const uint32_t gi = L.plane(z) * nn + rowg;
@@ -284,7 +288,10 @@ __device__ void march_segment(const MarchLattice<T>& L, int yt, int z0, int nz, 
                 else A.accg1 = acc;
             }
 #pragma unroll
-            for (int v = 0; v < NP; v++) site_vsum<T>(L.K, gq[0][v], gq[1][v], A.accvd, A.accvi);
+            for (int v = 0; v < NP; v++) {
+                if constexpr (SPLIT) site_vsum<T>(L.K, gq[0][v], gq[1][v], A.accvd, A.accvi);
+                else site_vsum_whole<T>(L.K, gq[0][v], gq[1][v], A.accvd, A.accvi);
+            }
             }
         }
     }

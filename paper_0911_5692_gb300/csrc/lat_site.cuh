@@ -68,6 +68,31 @@ __device__ __forceinline__ void site_kick_drift(const SiteCoefs<T>& C, typename 
     g1 = fma2(dt, pn1, a1);
 }
 
+// Scalar arithmetic without contraction, so that one site computed alone rounds
+// exactly as the same site in a packed pair (add.rn, mul.rn and fma.rn of the
+// f32x2 instructions act per element).
+__device__ __forceinline__ float s_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float s_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float s_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float s_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double s_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double s_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double s_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double s_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// site_kick_drift for one site, rounded as each element of the packed form.
+template <typename T>
+__device__ __forceinline__ void site_kick_drift1(const SiteCoefs<T>& C, T a0, T a1, T& pn0, T& pn1, T& g0, T& g1)
+{
+    const T u = s_add(C.bg, a0);
+    const T ue = s_mul(u, a1);
+    const T dom = C.quartic ? s_mul(a0, s_fma(u, s_add(u, C.bg), C.bg2)) : a0;
+    pn0 = s_fma(C.mdtcdom, dom, s_fma(C.mdtkap, s_mul(ue, a1), pn0));
+    pn1 = s_fma(C.mdtkap, s_mul(ue, u), pn1);
+    g0 = s_fma(C.dt, pn0, a0);
+    g1 = s_fma(C.dt, pn1, a1);
+}
+
 // Potential sums of one pair of new sites (d = field 0 as stored, e = chi) about
 // the new homogeneous mode P', u = P' + d: accd += u^beta - P'^beta (times 1/beta
 // later, site_vsum_factor), acci += u^2 e^2.
@@ -82,6 +107,37 @@ __device__ __forceinline__ void site_vsum(const SiteCoefs<T>& C, typename PK<T>:
     if (C.quartic) accd = fma2(mul2(d, s), fma2(u, u, mk2(C.bgn2, C.bgn2)), accd);
     else accd = fma2(d, s, accd);
     const P ue = mul2(u, e);
+    acci = fma2(ue, ue, acci);
+}
+
+// The same two helpers for a lattice that stores phi whole (P = P' = 0): the
+// arithmetic of the general forms with P = 0, instruction for instruction, but
+// without the mode's coefficients held in registers (kernels that are compiled
+// for both use these when no lattice they step stores phi split).
+template <typename T>
+__device__ __forceinline__ void site_kick_drift_whole(const SiteCoefs<T>& C, typename PK<T>::P a0, typename PK<T>::P a1,
+                                                      typename PK<T>::P& pn0, typename PK<T>::P& pn1,
+                                                      typename PK<T>::P& g0, typename PK<T>::P& g1)
+{
+    typedef typename PK<T>::P P;
+    const P mdtkap = mk2(C.mdtkap, C.mdtkap), mdtcdom = mk2(C.mdtcdom, C.mdtcdom);
+    const P ue = mul2(a0, a1);
+    const P dom = C.quartic ? mul2(a0, mul2(a0, a0)) : a0;
+    pn0 = fma2(mdtcdom, dom, fma2(mdtkap, mul2(ue, a1), pn0));
+    pn1 = fma2(mdtkap, mul2(ue, a0), pn1);
+    const P dt = mk2(C.dt, C.dt);
+    g0 = fma2(dt, pn0, a0);
+    g1 = fma2(dt, pn1, a1);
+}
+template <typename T>
+__device__ __forceinline__ void site_vsum_whole(const SiteCoefs<T>& C, typename PK<T>::P d, typename PK<T>::P e,
+                                                typename PK<T>::P& accd, typename PK<T>::P& acci)
+{
+    typedef typename PK<T>::P P;
+    const P sq = mul2(d, d);
+    if (C.quartic) accd = fma2(sq, sq, accd);
+    else accd = fma2(d, d, accd);
+    const P ue = mul2(d, e);
     acci = fma2(ue, ue, acci);
 }
 

@@ -26,7 +26,7 @@ struct MarchArgs {
     int periodic;   // 1: periodic z (a whole lattice); 0: z-slab with halo planes
 };
 
-template <typename T, int MAXT>
+template <typename T, int MAXT, bool SPLIT>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
     step_march_kernel(Bufs<T> B, Model M, DevScalars* sc, double* partials, MarchArgs G, double* sums_out)
 {
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
         const int z0 = (int)(u - (long long)yt * nzl);
         const int nz = (int)min((long long)(nzl - z0), uend - u);
         u += nz;
-        march_segment(L, yt, z0, nz, S, A, first);
+        march_segment<T, SPLIT>(L, yt, z0, nz, S, A, first);
     }
     T v[kSums];
     A.totals(L.K.quartic, v);
@@ -87,17 +87,31 @@ int maxt_for(int threads)
     return 0;
 }
 
+// the instance for a block size; `split`: the lattice stores phi split
 template <typename T>
-const void* march_fn(int maxt)
+const void* march_fn(int maxt, bool split)
 {
+#define LAT_MARCH_FN(MT) \
+    return split ? (const void*)step_march_kernel<T, MT, true> : (const void*)step_march_kernel<T, MT, false>
     switch (maxt) {
-    case 448: return (const void*)step_march_kernel<T, 448>;
-    case 512: return (const void*)step_march_kernel<T, 512>;
-    case 704: return (const void*)step_march_kernel<T, 704>;
-    case 768: return (const void*)step_march_kernel<T, 768>;
-    case 896: return (const void*)step_march_kernel<T, 896>;
-    default: return (const void*)step_march_kernel<T, 1024>;
+    case 448: LAT_MARCH_FN(448);
+    case 512: LAT_MARCH_FN(512);
+    case 704: LAT_MARCH_FN(704);
+    case 768: LAT_MARCH_FN(768);
+    case 896: LAT_MARCH_FN(896);
+    default: LAT_MARCH_FN(1024);
     }
+#undef LAT_MARCH_FN
+}
+
+// the dynamic shared memory opt-in for both instances of a block size
+bool march_smem_attr(int esize, int maxt, size_t smem)
+{
+    for (bool split : {false, true}) {
+        const void* fn = esize == 4 ? march_fn<float>(maxt, split) : march_fn<double>(maxt, split);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+    }
+    return true;
 }
 
 size_t march_smem(int n, int esize, int ty, int depth)
@@ -119,8 +133,10 @@ bool march_geom(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     const size_t smem = fast ? fast_smem : march_smem(n, esize, ty, depth);
     if (smem > 227 * 1024 - 2048) return false;   // the opt-in limit less the static arrays
     const int maxt = maxt_for(threads);
-    const void* fn = fast ? fast : esize == 4 ? march_fn<float>(maxt) : march_fn<double>(maxt);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+    const void* fn = fast ? fast : esize == 4 ? march_fn<float>(maxt, true) : march_fn<double>(maxt, true);
+    if (fast ? cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess
+             : !march_smem_attr(esize, maxt, smem))
+        return false;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
     // blocks: for a requested z length zr, nyt * ceil(n / zr) blocks (balanced
@@ -163,8 +179,8 @@ bool march_slab_config(int n, int elem_bytes, int nzl, MarchConfig* cfg)
         const size_t smem = march_smem(n, elem_bytes, ty, 1);
         if (smem > 227 * 1024 - 2048) continue;
         const int maxt = maxt_for(threads);
-        const void* fn = elem_bytes == 4 ? march_fn<float>(maxt) : march_fn<double>(maxt);
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) continue;
+        const void* fn = elem_bytes == 4 ? march_fn<float>(maxt, true) : march_fn<double>(maxt, true);
+        if (!march_smem_attr(elem_bytes, maxt, smem)) continue;
         int occ = 0, dev = 0, sms = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) continue;
         cudaGetDevice(&dev);
@@ -206,6 +222,10 @@ cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, 
         if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
         return launch_step_xt<T>(b, M, sc, partials, cfg, st);
     }
+    if (cfg.xw) {
+        if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
+        return launch_step_xw<T>(b, M, sc, partials, cfg, st);
+    }
     if (cfg.s27) {
         if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
         return launch_step27<T>(b, M, sc, partials, cfg, st);
@@ -213,14 +233,10 @@ cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, 
     if (cfg.fast && !sums_out && cfg.nzl == 0) return launch_step_fast<T>(b, M, sc, partials, cfg, st);
     MarchArgs G{cfg.ty, cfg.nzc, cfg.nyt, cfg.depth, cfg.nzl > 0 ? cfg.nzl : M.n, cfg.zbase, cfg.nzl > 0 ? 0 : 1};
     double* so = sums_out;
-    switch (cfg.maxt) {
-    case 448: step_march_kernel<T, 448><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
-    case 512: step_march_kernel<T, 512><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
-    case 704: step_march_kernel<T, 704><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
-    case 768: step_march_kernel<T, 768><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
-    case 896: step_march_kernel<T, 896><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
-    default: step_march_kernel<T, 1024><<<cfg.blocks, cfg.threads, cfg.smem, st>>>(b, M, sc, partials, G, so); break;
-    }
+    const void* fn = march_fn<T>(cfg.maxt, M.split != 0);
+    void* args[] = {(void*)&b, (void*)&M, (void*)&sc, (void*)&partials, (void*)&G, (void*)&so};
+    cudaError_t e = cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

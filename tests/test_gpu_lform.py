@@ -22,7 +22,7 @@ from paper_0911_5692_gb300.workloads import lphi4, m2phi2, random_state
 pytestmark = pytest.mark.gpu
 
 TOL = {32: 2e-6, 64: 1e-12}
-VARIANTS = [2, 4]
+VARIANTS = [2, 4, 5]
 
 
 def _params(model, n, prec, stencil=7):

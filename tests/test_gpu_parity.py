@@ -18,7 +18,7 @@ from paper_0911_5692_gb300.workloads import lphi4, m2phi2, random_state
 pytestmark = pytest.mark.gpu
 
 TOL = {32: 2e-6, 64: 1e-12}
-VARIANTS = [2, 4]
+VARIANTS = [2, 4, 5]
 
 
 def _params(model, n, prec, expansion):
@@ -442,21 +442,23 @@ def test_xtile_kernel_geometries(n, ty, prec):
     compare_states(g, o, steps * TOL[prec], f"x tiles N={n} ty={ty} fp{prec}")
 
 
-def test_xtile_kernel_full_size_512():
-    """Variant 4 on the 512^3 lambda phi^4 lattice (FP32): one step against the
-    oracle's full-lattice step."""
+@pytest.mark.parametrize("variant", [4, 5])
+def test_xtile_kernel_full_size_512(variant):
+    """The x-tiled kernels (variant 4; variant 5, one warp wide with an edge warp)
+    on the 512^3 lambda phi^4 lattice (FP32): one step against the oracle's
+    full-lattice step."""
     n = 512
     p = _params("lphi4", n, 32, 1)
     st = _state("lphi4", n, 32, seed=79)
     g = Lattice(p)
-    g.set_kernel(4)
+    g.set_kernel(variant)
     g.set_state(*st, t=0.0, a=1.02, ad=0.5)
     o = Oracle(p)
     o.set_state(*st, t=0.0, a=1.02, ad=0.5)
     del st
     g.evolve(1)
     o.step(1)
-    compare_states(g, o, TOL[32], "x tiles full size 512")
+    compare_states(g, o, TOL[32], f"x tiles full size 512 v{variant}")
 
 
 def test_fp64_full_size_default_kernel():
@@ -494,3 +496,35 @@ def test_fp64_full_size_512_two_steps():
     compare_states(g, o, 2 * TOL[64], "FP64 full size 512, two steps")
     assert abs(g.scalars()["a"] / o.scalars()["a"] - 1) < 1e-13
 
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("n,depth", [(256, 1), (256, 2), (512, 1)])
+def test_warp_tile_kernel(n, depth, prec):
+    """Variant 5 (x tiles one warp wide, compiled N, ty and depth, an edge warp
+    for the tile's x neighbours and its boundary column) on its compiled sides:
+    three steps against the oracle, and the sums of the new fields (whose x
+    differences at the tile edges come from the edge warp) against the oracle's
+    sums of the same fields."""
+    p = _params("lphi4", n, prec, 1)
+    st = _state("lphi4", n, prec, seed=n + depth)
+    g = Lattice(p)
+    try:
+        g.set_kernel(5, 16, 0, depth)
+    except LatticeError:
+        pytest.skip(f"no compiled instance for N={n} depth={depth} fp{prec}")
+    assert g.kernel_info()["variant"] == 5
+    g.set_state(*st, t=0.0, a=1.05, ad=0.5)
+    o = Oracle(p)
+    o.set_state(*st, t=0.0, a=1.05, ad=0.5)
+    del st
+    g.evolve(3)
+    o.step(3)
+    compare_states(g, o, 3 * TOL[prec], f"warp tiles N={n} depth={depth} fp{prec}")
+    gs = g.scalars()
+    own = Oracle(p)
+    own.set_state(*g.get_state(), t=gs["t"], a=gs["a"], ad=gs["ad"], step=gs["step"])
+    tol = [1e-11, 1e-11, 1e-13, 1e-11] if prec == 64 else [2e-6, 2e-6, 1e-6, 2e-6]
+    for k in range(4):
+        ref = own.scalars()["S"][k]
+        assert abs(gs["S"][k] - ref) <= tol[k] * abs(ref), (k, gs["S"][k], ref)

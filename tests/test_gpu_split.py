@@ -68,7 +68,7 @@ def _check_step(g, o, prec, what, steps=1):
 
 
 @pytest.mark.parametrize("prec", [32, 64])
-@pytest.mark.parametrize("kernel", ["v2", "v4", "27"])
+@pytest.mark.parametrize("kernel", ["v2", "v4", "v5", "27"])
 @pytest.mark.parametrize("model,expansion", [("lphi4", 1), ("m2phi2", 1), ("lphi4", 0)])
 @pytest.mark.parametrize("n", [16, 36, 64])
 def test_split_one_step_parity(n, model, expansion, kernel, prec):
@@ -80,9 +80,9 @@ def test_split_one_step_parity(n, model, expansion, kernel, prec):
     st = _state(model, n, prec, seed=n + prec)
     sc = (0.0, 1.2, 0.4, 0) if expansion else (0.0, 1.0, 0.0, 0)
     g, o = _pair(p, st, sc)
-    if kernel == "v4":
+    if kernel in ("v4", "v5"):
         try:
-            g.set_kernel(4)
+            g.set_kernel(int(kernel[1]))
         except LatticeError:
             pytest.skip("x-tiled kernel does not serve this lattice")
     P, Pi = g.background()
