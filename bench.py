@@ -235,7 +235,32 @@ def cpu_baseline(p, seconds, one_thread_seconds=6.0):
                            "sample": f"{steps1} steps of the same lattice on one thread ({el1:.1f} s)"}}
 
 
-def measure_adjoint(local, name="lphi4_128_fp32", n=None, steps=None):
+def state_error(x, ref, stride=1):
+    """FP32 against FP64: normwise max|x - ref| / max|ref| per array of (f_phi,
+    f_chi, pi_phi, pi_chi), and against the fluctuation part of the inflaton's
+    arrays (max|x - ref| / max|ref - <ref>|), on every stride-th site per axis."""
+    import numpy as np
+    names = ("f_phi", "f_chi", "pi_phi", "pi_chi")
+    err = {}
+    for k, (a, b) in enumerate(zip(x, ref)):
+        a, b = a[::stride, ::stride, ::stride], b[::stride, ::stride, ::stride]
+        diff = float(np.max(np.abs(a - b)))
+        err[names[k]] = diff / max(float(np.max(np.abs(b))), 1e-300)
+        if k in (0, 2):
+            err[names[k] + "_fluct"] = diff / max(float(np.max(np.abs(b - b.mean()))), 1e-300)
+    return err
+
+
+def fp64_twin(p, local):
+    """An FP64 lattice of the same parameters, phi stored whole, initialised from
+    the same seed by its own pipeline: the reference of the FP32 errors."""
+    from paper_0911_5692_gb300 import Lattice
+    g = Lattice(dict(p, precision=64, split=0), device=local)
+    g.init_fields()
+    return g
+
+
+def measure_adjoint(local, name="lphi4_128_fp32", n=None, steps=None, fp64=False):
     """Cost of the reverse-mode derivative on the 128^3 lambda phi^4 workload:
     J = <chi^2> after its 2000 steps and dJ/d(f, pi, g^2) by lat_adjoint
     (sqrt(n) checkpointing), against the plain forward evolution of the same
@@ -275,16 +300,39 @@ def measure_adjoint(local, name="lphi4_128_fp32", n=None, steps=None):
         res = {"workload": name, "n": p["n"], "steps": steps, "forward_s": tf, "adjoint_s": ta,
                "ratio_total": ta / tf, "ratio_backward": (ta - tf) / tf, "J": J, "dJ_dg2": dg2,
                "checkpoint_every": int(math.ceil(math.sqrt(steps))), "timing": "wall clock, second of two runs"}
+    if fp64:
+        # the same gradient from the same FP32-representable start with FP64 fields
+        g.load_checkpoint(blob)
+        J32, df32, dp32, dg32 = g.adjoint(steps)
+        g.load_checkpoint(blob)
+        st = g.get_state()
+        sc = g.scalars()
+        g.close()
+        h = Lattice(dict(p, precision=64), device=local)
+        h.set_state(*st, t=sc["t"], a=sc["a"], ad=sc["ad"], step=sc["step"])
+        J64, df64, dp64, dg64 = h.adjoint(steps)
+        import numpy as np
+        err = {"J_rel": abs(J32 / J64 - 1), "dJ_dg2_rel": abs(dg32 / dg64 - 1)}
+        for i, f in enumerate(("phi", "chi")):
+            for nm, a, b in (("dJ_df", df32, df64), ("dJ_dpi", dp32, dp64)):
+                a_, b_ = a[i].double().cpu().numpy(), b[i].cpu().numpy()
+                err[f"{nm}_{f}"] = float(np.max(np.abs(a_ - b_)) / max(float(np.max(np.abs(b_))), 1e-300))
+        res["fp64_error"] = dict(err, against="FP64 gradient on the GPU from the same start (the FP64 path is "
+                                               "pinned to the oracle's adjoint), normwise per array")
+        h.close()
     return res
 
 
 def measure_ensemble(local, steps=200):
     """The 64-member ensemble (N in 32, 48, 64, 96; g^2/lambda log-uniform in
-    [50, 500]; FP32) in one persistent launch per evolve call, after autotuning."""
+    [50, 500]; FP32, phi stored split) in one persistent launch per evolve call,
+    after autotuning; and the FP32 error against the same ensemble in FP64
+    (largest per-member normwise error) after the timed steps."""
     import torch
     from paper_0911_5692_gb300 import Ensemble
     from paper_0911_5692_gb300.workloads import ensemble_64
-    ens = Ensemble(ensemble_64(), device=local)
+    members = ensemble_64(split=1)
+    ens = Ensemble(members, device=local)
     ens.init_fields()
     ens.tune(20)
     ens.evolve(5)
@@ -300,10 +348,23 @@ def measure_ensemble(local, steps=200):
     su = info["sites"] / (ms / 1e3)
     peaks = measured_peaks()
     peak = float(peaks["hbm_gbs"]) if peaks and peaks.get("hbm_gbs") else FALLBACK_HBM_GBS
+    ref = Ensemble(ensemble_64(precision=64), device=local)
+    ref.init_fields()
+    ref.evolve(5 + steps)
+    ref.sync()
+    worst = {}
+    for i in range(len(members)):
+        err = state_error(ens.member(i).get_state_exact(), ref.member(i).get_state())
+        for k, v in err.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    ref.close()
     return {"workload": "ensemble_64", "members": info["members"], "sites": info["sites"], "steps": steps,
             "ms_per_step": ms, "value": su, "unit": UNIT, "hbm_frac": su * 32 / 1e9 / peak,
+            "storage": "phi split (FP64 homogeneous mode + FP32 fluctuations)",
             "launch": {"blocks": info["blocks"], "threads": info["threads"], "graph": bool(info["graph"]),
-                       "launches_per_evolve": info["launches"]}}
+                       "launches_per_evolve": info["launches"]},
+            "fp64_error": dict(worst, steps=steps + 5, against="the same 64 members in FP64 (phi whole), same "
+                                                                  "seeds; largest per-member normwise error")}
 
 
 def measure_stencil27(local, names=("m2phi2_256_fp32", "lphi4_512_fp32"), steps=100):
@@ -338,6 +399,12 @@ def measure_stencil27(local, names=("m2phi2_256_fp32", "lphi4_512_fp32"), steps=
         if name == "m2phi2_256_fp32":
             rec["paper_s_per_step"] = 0.022
             rec["vs_paper"] = 0.022 / (ms / 1e3)
+            ref = fp64_twin(p, local)
+            ref.evolve(10 + steps)
+            rec["fp64_error"] = dict(state_error(lat.get_state_exact(), ref.get_state(), stride=max(1, n // 32)),
+                                     steps=10 + steps, subset=f"every {max(1, n // 32)}th site per axis",
+                                     against="FP64 27-point lattice (phi whole), same seed")
+            ref.close()
         out.append(rec)
         lat.close()
     return out
@@ -461,6 +528,14 @@ def measure_lform(local, name, steps=320):
             best[e] = min(best[e], s.elapsed_time(t) / steps)
     a1, a2 = lats[1].scalars()["a"], lats[2].scalars()["a"]
     info = lats[2].kernel_info()
+    ref = fp64_twin(dict(base, expansion=2), local)
+    ref.evolve(64 + 2 * steps)
+    stride = max(1, n // 32)
+    err = dict(state_error(lats[2].get_state_exact(), ref.get_state(), stride=stride),
+               hubble_length_rel=abs(lats[2].hubble_length() / ref.hubble_length() - 1), steps=64 + 2 * steps,
+               subset=f"every {stride}th site per axis", against="FP64 lattice in the L = 1/H form (phi whole), "
+                                                               "same seed")
+    ref.close()
     for lat in lats.values():
         lat.close()
     pass_ms = best[2] - best[1]
@@ -469,7 +544,7 @@ def measure_lform(local, name, steps=320):
             "value": n ** 3 / (best[2] / 1e3), "unit": UNIT, "lform_pass_ms": pass_ms,
             "lform_pass_GBs": gbs, "lform_pass_hbm_frac": gbs / peak if gbs else None,
             "launches_per_step": info["launches_per_step"],
-            "a_rel_gap_after_run": a2 / a1 - 1.0}
+            "a_rel_gap_after_run": a2 / a1 - 1.0, "fp64_error": err}
 
 
 def measure_fp32_error(local, name, steps=200):
@@ -479,24 +554,16 @@ def measure_fp32_error(local, name, steps=200):
     same seed by their own pipelines, `steps` steps, normwise error on the strided
     subset of 32^3 sites, against the whole field and against its fluctuation
     part."""
-    import numpy as np
     from paper_0911_5692_gb300 import Lattice
     p = workload(name)
     n = p["n"]
-    g64 = Lattice(dict(p, precision=64, split=0), device=local)
-    g64.init_fields()
+    g64 = fp64_twin(p, local)
     g32 = Lattice(dict(p, precision=32), device=local)
     g32.init_fields()
     g32.evolve(steps)
     g64.evolve(steps)
     stride = max(1, n // 32)
-    names = ("f_phi", "f_chi", "pi_phi", "pi_chi")
-    err = {}
-    for k, (a, b) in enumerate(zip(g32.get_state_exact(), g64.get_state())):
-        a, b = a[::stride, ::stride, ::stride], b[::stride, ::stride, ::stride]
-        d = b - b.mean() if k in (0, 2) else b
-        err[names[k]] = float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
-        err[names[k] + "_fluct"] = float(np.max(np.abs(a - b)) / max(np.max(np.abs(d)), 1e-300))
+    err = state_error(g32.get_state_exact(), g64.get_state(), stride=stride)
     s32, s64 = g32.scalars(), g64.scalars()
     g32.close()
     g64.close()
@@ -681,7 +748,7 @@ def run_ours(args):
         line["step_256"] = measure_step(local, "m2phi2_256_fp32", steps=1000)
         line["fp32_vs_fp64"] = measure_fp32_error(local, args.workload)
         line["fp32_vs_fp64_256"] = measure_fp32_error(local, "m2phi2_256_fp32")
-        line["adjoint"] = measure_adjoint(local)
+        line["adjoint"] = measure_adjoint(local, fp64=True)
         line["adjoint_256"] = measure_adjoint(local, n=256, steps=400)
         line["ensemble"] = measure_ensemble(local)
         line["stencil27"] = measure_stencil27(local)

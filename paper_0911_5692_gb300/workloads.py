@@ -56,13 +56,13 @@ WORKLOADS = {
 }
 
 
-def ensemble_64(seed: int = 0, precision: int = 32) -> list[dict]:
+def ensemble_64(seed: int = 0, precision: int = 32, split: int = 0) -> list[dict]:
     """64 lattices: N cycles 32, 48, 64, 96; g^2/lambda = exp(U(ln 50, ln 500)) drawn
     from numpy's PCG64 seeded with ``seed``; lattice i uses init seed i; dt = dx_i/20."""
     rng = np.random.default_rng(seed)
     Gs = np.exp(rng.uniform(math.log(50.0), math.log(500.0), size=64))
     sizes = (32, 48, 64, 96)
-    return [lphi4(sizes[i % 4], precision=precision, G=float(Gs[i]), seed=i) for i in range(64)]
+    return [lphi4(sizes[i % 4], precision=precision, G=float(Gs[i]), seed=i, split=split) for i in range(64)]
 
 
 def random_state(n: int, seed: int, precision: int = 32, f_mean=(1.0, 0.0), f_amp=(1e-3, 1e-3),
