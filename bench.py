@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lphi4_512_fp32")
     ap.add_argument("--variant", type=int, default=0,
-                    help="step kernel: 0 auto, 2 plane ring over full rows, 4 plane ring over x tiles")
+                    help="step kernel: 0 autotuned, 2 plane ring over full rows, 4 plane ring over x tiles, "
+                         "5 x tiles one warp wide")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default kernel shape instead of autotuning it (lat_tune) before timing")
     ap.add_argument("--stencil", type=int, choices=[7, 27], default=7,
                     help="Laplacian: 7-point, or the paper's 27-point stencil (Sec. II.C)")
     ap.add_argument("--expansion", type=int, choices=[1, 2], default=1,
@@ -362,7 +365,9 @@ def measure_ensemble(local, steps=200):
             "ms_per_step": ms, "value": su, "unit": UNIT, "hbm_frac": su * 32 / 1e9 / peak,
             "storage": "phi split (FP64 homogeneous mode + FP32 fluctuations)",
             "launch": {"blocks": info["blocks"], "threads": info["threads"], "graph": bool(info["graph"]),
-                       "launches_per_evolve": info["launches"]},
+                       "launches_per_evolve": info["launches"],
+                       "ty_by_side": {str(p["n"]): t for p, t in zip(members, info["ty"])},
+                       "tuned_over": "block size x tile-height cap (lat_batch_tune)"},
             "fp64_error": dict(worst, steps=steps + 5, against="the same 64 members in FP64 (phi whole), same "
                                                                   "seeds; largest per-member normwise error")}
 
@@ -381,6 +386,7 @@ def measure_stencil27(local, names=("m2phi2_256_fp32", "lphi4_512_fp32"), steps=
         n = p["n"]
         lat = Lattice(p, device=local)
         lat.init_fields()
+        tuned = lat.tune(32)
         lat.evolve(10)
         lat.sync()
         s = torch.cuda.Event(enable_timing=True)
@@ -395,7 +401,8 @@ def measure_stencil27(local, names=("m2phi2_256_fp32", "lphi4_512_fp32"), steps=
         rec = {"workload": name, "stencil": 27, "steps": steps, "ms_per_step": ms, "value": su, "unit": UNIT,
                "hbm_frac": su * 32 / 1e9 / peak,
                "launch": {"blocks": info["blocks"], "threads": info["threads"], "ty": info["ty"],
-                          "smem": info["smem"]}}
+                          "depth": info["depth"], "smem": info["smem"],
+                          "tuned_over": tuned["candidates"]}}
         if name == "m2phi2_256_fp32":
             rec["paper_s_per_step"] = 0.022
             rec["vs_paper"] = 0.022 / (ms / 1e3)
@@ -464,8 +471,8 @@ def measure_diagnostics(local, name, every=512, steps=2048):
 
 
 def measure_step(local, name="m2phi2_256_fp32", steps=300):
-    """The fused 7-point step of another workload with the automatic kernel
-    choice (m^2 phi^2 at 256^3 FP32 is the configuration of the paper's own
+    """The fused 7-point step of another workload with the autotuned kernel
+    shape (m^2 phi^2 at 256^3 FP32 is the configuration of the paper's own
     timing). CUDA events over graph replays after warm-up; the state (537 MB at
     256^3) exceeds L2."""
     import torch
@@ -475,6 +482,7 @@ def measure_step(local, name="m2phi2_256_fp32", steps=300):
     esize = 4 if p["precision"] == 32 else 8
     lat = Lattice(p, device=local)
     lat.init_fields()
+    tuned = lat.tune(64)
     lat.evolve(32)
     lat.sync()
     s = torch.cuda.Event(enable_timing=True)
@@ -492,7 +500,7 @@ def measure_step(local, name="m2phi2_256_fp32", steps=300):
     return {"workload": name, "steps": steps, "ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": UNIT,
             "achieved_GBs": gbs, "hbm_frac": gbs / peak, "hbm_frac_of_nominal": gbs / NOMINAL_HBM_GBS,
             "kernel": {"variant": info["variant"], "blocks": info["blocks"], "threads": info["threads"],
-                       "ty": info["ty"], "depth": info["depth"]}}
+                       "ty": info["ty"], "depth": info["depth"], "tuned_over": tuned["candidates"]}}
 
 
 def measure_lform(local, name, steps=320):
@@ -634,10 +642,13 @@ def run_ours(args):
     n = p["n"]
     esize = 4 if p["precision"] == 32 else 8
     lat = Lattice(p, device=local)
+    tuned = None
+    lat.init_fields()
     if args.variant or args.ty or args.zr or args.depth:
         lat.set_kernel(args.variant, args.ty, args.zr, args.depth)
+    elif not args.no_tune:
+        tuned = lat.tune(64)     # untimed; the state is kept
     info = lat.kernel_info()
-    lat.init_fields()
     lat.evolve(args.warmup)
     lat.sync()
 
@@ -731,6 +742,10 @@ def run_ours(args):
                 "per_step": "upload of the stored state from pinned host memory, one step, download of the "
                             "evolved state and the scalars"},
         "gpu_launches": args.steps * info["launches_per_step"],
+        "tune": ({"chosen": {k: tuned[k] for k in ("variant", "ty", "zr", "depth", "blocks")},
+                  "candidates": tuned["candidates"], "best_ms": tuned["best_ms"], "slowest_ms": tuned["slowest_ms"],
+                  "by": "lat_tune: 64 steps per candidate shape on this lattice, CUDA events"}
+                 if tuned else None),
         "clocks": clocks.summary(),
         "context": {"paper_gtx260_256cubed_su_per_s": 7.6e8,
                     "paper_gtx260_128cubed_su_per_s": 6.2e8,

@@ -282,6 +282,20 @@ lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
  * ty, zr and depth apply to it as above). */
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth);
 
+/* Autotune the step kernel (the paper tunes its block size by hand, Sec. III):
+ * time `steps` steps (1 <= steps <= 100000, after a warm-up of 32 that also
+ * captures the graph) for every kernel shape that can run this lattice --
+ * variants 2, 4 and 5 over tile heights and prefetch depths (the 27-point
+ * stencil: variant 2 over tile heights and depths) -- on the lattice's own
+ * state, which is saved before and put back after every candidate and at the
+ * end; keep the fastest, and remember it for the process per (N, precision,
+ * stencil, split storage, expansion), so that handles created later with the
+ * same key start with it. out (host, 8 entries, may be NULL): the chosen
+ * variant, ty, zr, depth, the number of candidates timed, the best and the
+ * slowest time per step in ns, and the blocks per step. Synchronises. Returns
+ * a sticky device error if a candidate raised one (the previous kernel is kept). */
+lat_status lat_tune(lat_handle* h, int steps, int64_t out[8]);
+
 /* Launch geometry of the current step kernel: out[0] = variant, out[1] = blocks
  * per step, out[2] = threads per block, out[3] = dynamic shared memory bytes,
  * out[4] = kernels launched per step, out[5] = ty, out[6] = zr, out[7] = depth. */
@@ -430,11 +444,18 @@ lat_status lat_batch_evolve(lat_batch* b, int64_t n_steps);
  * member. */
 lat_status lat_batch_sync(lat_batch* b);
 
-/* Autotune the launch shape: time `steps` steps for each candidate block size
- * (tile heights follow from it) on the ensemble itself, keep the fastest and
- * cache it for this process per (sizes, precision). Member states are saved
- * before and restored after. Synchronises. */
+/* Autotune the launch shape: time `steps` steps for each candidate pair of
+ * block size (128 .. 1024) and tile-height cap (32, 16, 8, 4; each member takes
+ * the largest tile height up to the cap that divides its side and fits the
+ * block) on the ensemble itself, keep the fastest and cache it for this process
+ * per (sizes, precision); ensembles created later with the same sizes and
+ * precision start with it. Member states are saved before and restored after.
+ * Synchronises. */
 lat_status lat_batch_tune(lat_batch* b, int steps);
+
+/* The tile height (y rows per work unit) each member is stepped with:
+ * ty (host, one int32 per member, in creation order). */
+lat_status lat_batch_tile_heights(lat_batch* b, int32_t* ty);
 
 /* Self-test of the bounded grid barrier (failure detection without a fault):
  * launches the ensemble kernel so that its barrier waits for one block more

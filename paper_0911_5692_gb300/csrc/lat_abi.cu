@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "lat_internal.h"
@@ -227,6 +230,45 @@ lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int dept
     return LAT_EUNSUPPORTED;
 }
 
+// ---- the step-kernel autotuner: the fastest (variant, ty, zr, depth) measured on
+// a lattice, remembered for the process per (N, precision, stencil, split,
+// expansion) and taken by every handle created later with the same key
+struct TuneKey {
+    int n, prec, stencil, split, expansion;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(n, prec, stencil, split, expansion) < std::tie(o.n, o.prec, o.stencil, o.split, o.expansion);
+    }
+};
+struct TuneShape {
+    int variant, ty, zr, depth;
+};
+std::mutex g_tune_mx;
+std::map<TuneKey, TuneShape> g_tuned;
+
+TuneKey tune_key(const lat_handle* h)
+{
+    return TuneKey{h->p.n, h->prec, h->M.stencil, h->M.split, h->M.expansion};
+}
+
+// Candidate shapes for a lattice: every kernel that can run it, over tile
+// heights and prefetch depths (configure_kernel refuses the ones that do not fit).
+std::vector<TuneShape> tune_candidates(const lat_handle* h)
+{
+    std::vector<TuneShape> c;
+    if (h->M.stencil == 27) {
+        for (int ty : {16, 8, 4})
+            for (int d : {1, 2}) c.push_back({2, ty, 0, d});
+        return c;
+    }
+    for (int d : {1, 2}) c.push_back({5, 16, 0, d});
+    for (int ty : {32, 16, 8})
+        for (int d : {1, 2}) c.push_back({4, ty, 0, d});
+    for (int ty : {16, 8, 4, 2})
+        for (int d : {1, 2}) c.push_back({2, ty, 0, d});
+    return c;
+}
+
 lat_status create_common(const lat_params* params, void* stream, void* const bufs[8], lat_handle** out)
 {
     if (!out) return LAT_EINVAL;
@@ -271,6 +313,16 @@ lat_status create_common(const lat_params* params, void* stream, void* const buf
     }
     h->dirty = true;
     if (st == LAT_OK) st = configure_kernel(h, 0, 0, 0, 0);
+    if (st == LAT_OK) {   // a shape the autotuner chose for this key earlier in the process
+        TuneShape t{0, 0, 0, 0};
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mx);
+            auto it = g_tuned.find(tune_key(h));
+            if (it != g_tuned.end()) t = it->second;
+        }
+        if (t.variant && configure_kernel(h, t.variant, t.ty, t.zr, t.depth) != LAT_OK)
+            st = configure_kernel(h, 0, 0, 0, 0);
+    }
     if (st != LAT_OK) {
         lat_destroy(h);
         return st;
@@ -367,6 +419,88 @@ lat_status lat_kernel_info(lat_handle* h, int64_t out[8])
     out[5] = h->ty;
     out[6] = h->zr;
     out[7] = h->mcfg.depth;
+    return LAT_OK;
+}
+
+lat_status lat_tune(lat_handle* h, int steps, int64_t out[8])
+{
+    if (!h || steps < 1 || steps > 100000) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
+    LAT_TRY(ensure_prepared(h));
+    DevScalars s0;
+    LAT_TRY(read_scalars(h, &s0));
+    if (s0.status != LAT_OK) return (lat_status)s0.status;
+    const int par = (int)(s0.step & 1);
+    const size_t bytes = h->nsites * h->esize;
+    // the current state, saved and put back before every candidate and at the end
+    void* save = nullptr;
+    if (cudaMalloc(&save, 4 * bytes) != cudaSuccess) return LAT_ENOMEM;
+    lat_status st = LAT_OK;
+    for (int k = 0; k < 4 && st == LAT_OK; k++)
+        if (cudaMemcpyAsync((char*)save + k * bytes, h->buf[4 * par + k], bytes, cudaMemcpyDeviceToDevice, h->stream) !=
+            cudaSuccess)
+            st = LAT_ECUDA;
+    const bool was_dirty = h->dirty;
+    auto restore = [&]() {
+        for (int k = 0; k < 4; k++)
+            if (cudaMemcpyAsync(h->buf[4 * par + k], (char*)save + k * bytes, bytes, cudaMemcpyDeviceToDevice,
+                                h->stream) != cudaSuccess)
+                return LAT_ECUDA;
+        if (cudaMemcpyAsync(h->sc, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return LAT_ECUDA;
+        h->dirty = was_dirty;
+        return LAT_OK;
+    };
+    const int prev[4] = {h->variant, h->ty, h->zr, h->mcfg.depth};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == LAT_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = LAT_ECUDA;
+    TuneShape best{0, 0, 0, 0};
+    float best_ms = 0.0f, worst_ms = 0.0f;
+    int tried = 0;
+    for (const TuneShape& c : tune_candidates(h)) {
+        if (st != LAT_OK) break;
+        if (configure_kernel(h, c.variant, c.ty, c.zr, c.depth) != LAT_OK) continue;
+        // the geometry the kernel was configured with (an automatic zr, the depth taken)
+        const TuneShape got{h->variant, h->ty, 0, h->mcfg.depth};
+        if ((st = restore()) != LAT_OK) break;
+        // a warm-up that also captures the graph, then the timed steps
+        if ((st = lat_evolve(h, kGraphChunk)) != LAT_OK) break;
+        cudaEventRecord(e0, h->stream);
+        if ((st = lat_evolve(h, steps)) != LAT_OK) break;
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = LAT_ECUDA; break; }
+        DevScalars sn;
+        if ((st = read_scalars(h, &sn)) != LAT_OK) break;
+        if (sn.status != LAT_OK) { st = (lat_status)sn.status; break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)steps;
+        tried++;
+        if (!best.variant || ms < best_ms) { best = got; best_ms = ms; }
+        worst_ms = std::max(worst_ms, ms);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    lat_status rs = restore();
+    if (st == LAT_OK) st = rs;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
+    cudaFree(save);
+    if (st == LAT_OK && !best.variant) st = LAT_EUNSUPPORTED;
+    if (st != LAT_OK) {
+        configure_kernel(h, prev[0], prev[1], prev[2], prev[3]);
+        return st;
+    }
+    LAT_TRY(configure_kernel(h, best.variant, best.ty, 0, best.depth));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mx);
+        g_tuned[tune_key(h)] = TuneShape{best.variant, best.ty, 0, best.depth};
+    }
+    if (out) {
+        out[0] = h->variant; out[1] = h->ty; out[2] = h->zr; out[3] = h->mcfg.depth;
+        out[4] = tried;
+        out[5] = (int64_t)std::llround(best_ms * 1e6);   // nanoseconds per step
+        out[6] = (int64_t)std::llround(worst_ms * 1e6);
+        out[7] = h->mcfg.blocks;
+    }
     return LAT_OK;
 }
 

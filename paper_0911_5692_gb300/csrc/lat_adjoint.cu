@@ -931,11 +931,9 @@ lat_status vjp_impl(lat_handle* h, int64_t n, int64_t ckpt_every, T* fb_user, T*
     bool pair = false;
     if constexpr (sizeof(T) == 4)
         pair = M.n % (2 * kPX) == 0 &&
-               cudaFuncSetAttribute(adj_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(AdjPairSmem)) == cudaSuccess;
+               allow_dynamic_smem((const void*)adj_pair_kernel, sizeof(AdjPairSmem)) == cudaSuccess;
     const bool march = !pair && M.n % kMX == 0 &&
-                       cudaFuncSetAttribute(adj_march_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)adj_march_smem<T>()) == cudaSuccess;
+                       allow_dynamic_smem((const void*)adj_march_kernel<T>, adj_march_smem<T>()) == cudaSuccess;
     const int nzc =
         pair ? adj_zchunks(M.n, (M.n / (2 * kPX)) * (M.n / kPY),
                            resident_slots((const void*)adj_pair_kernel, kPX * kPY, sizeof(AdjPairSmem)))

@@ -18,9 +18,9 @@
 //
 // The launch is cooperative (the runtime refuses it unless every block is
 // resident, which the barrier needs) and is captured in a CUDA graph per step
-// count. The block size and the tile height of each member size come from a
-// small autotuner that times candidate shapes on the ensemble itself and caches
-// the choice per (sizes, precision) for the process.
+// count. The block size and the largest tile height a member may take come from
+// a small autotuner that times candidate shapes on the ensemble itself and
+// caches the choice per (sizes, precision) for the process.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -254,6 +254,7 @@ int maxt_of(int threads) { return threads <= 256 ? 256 : threads <= 512 ? 512 : 
 // Shape of one launch.
 struct BatchShape {
     int threads = 0;
+    int tycap = 32;       // largest tile height a member takes
     int maxt = 0;
     size_t smem = 0;
     int blocks = 0;
@@ -261,7 +262,7 @@ struct BatchShape {
 };
 
 std::mutex g_tune_mutex;
-std::map<std::string, int> g_tuned_threads;   // (sizes, precision) -> block size
+std::map<std::string, std::pair<int, int>> g_tuned;   // (sizes, precision) -> (block size, tile cap)
 
 } // namespace
 
@@ -309,12 +310,14 @@ std::string tune_key(const lat_batch* b)
     return k;
 }
 
-// Tile heights, ring size and resident blocks for a block size; false if some
-// member does not fit.
-bool shape_for(const lat_batch* b, int threads, BatchShape* out)
+// Tile heights (each member the largest of 32, 16, ... 1 that divides its side,
+// is at most tycap and fits the block), ring size and resident blocks for a
+// block size; false if some member does not fit.
+bool shape_for(const lat_batch* b, int threads, int tycap, BatchShape* out)
 {
     BatchShape s;
     s.threads = threads;
+    s.tycap = tycap;
     s.maxt = maxt_of(threads);
     const int vw = (int)(16 / b->esize);
     size_t smem = 0;
@@ -322,7 +325,7 @@ bool shape_for(const lat_batch* b, int threads, BatchShape* out)
         const int n = h->p.n;
         int best = 0;
         for (int ty : {32, 16, 8, 4, 2, 1}) {
-            if (ty > n || n % ty != 0) continue;
+            if (ty > n || ty > tycap || n % ty != 0) continue;
             if ((ty + 3) * (n / vw) > threads) continue;
             if (ring_elems(n, ty, 1) * b->esize > 200 * 1024) continue;
             best = ty;
@@ -334,7 +337,7 @@ bool shape_for(const lat_batch* b, int threads, BatchShape* out)
     }
     s.smem = smem;
     const void* fn = b->prec == 32 ? batch_fn<float>(s.maxt, b->split) : batch_fn<double>(s.maxt, b->split);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+    if (allow_dynamic_smem(fn, smem) != cudaSuccess) return false;
     int occ = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
     cudaGetDevice(&dev);
@@ -411,10 +414,10 @@ lat_status build_tables(lat_batch* b, const BatchShape& s)
     return LAT_OK;
 }
 
-lat_status configure(lat_batch* b, int threads)
+lat_status configure(lat_batch* b, int threads, int tycap)
 {
     BatchShape s;
-    if (!shape_for(b, threads, &s)) return LAT_EUNSUPPORTED;
+    if (!shape_for(b, threads, tycap, &s)) return LAT_EUNSUPPORTED;
     return b->prec == 32 ? build_tables<float>(b, s) : build_tables<double>(b, s);
 }
 
@@ -481,15 +484,23 @@ lat_status run_steps(lat_batch* b, int64_t nsteps)
     return LAT_OK;
 }
 
-// Time candidate block sizes on the ensemble itself (state saved and restored)
-// and keep the fastest.
+// Time candidate (block size, tile cap) pairs on the ensemble itself (state
+// saved and restored) and keep the fastest. Pairs that give every member the
+// same tile heights as a pair already listed, at the same block size, are one
+// candidate.
 lat_status autotune(lat_batch* b, int steps)
 {
     const std::string key = tune_key(b);
-    std::vector<int> cands;
+    std::vector<std::pair<int, int>> cands;
     for (int t : {128, 192, 256, 320, 384, 448, 512, 640, 768, 1024}) {
-        BatchShape s;
-        if (shape_for(b, t, &s)) cands.push_back(t);
+        std::vector<std::vector<int>> seen;
+        for (int cap : {32, 16, 8, 4}) {
+            BatchShape s;
+            if (!shape_for(b, t, cap, &s)) continue;
+            if (std::find(seen.begin(), seen.end(), s.ty) != seen.end()) continue;
+            seen.push_back(s.ty);
+            cands.push_back({t, cap});
+        }
     }
     if (cands.empty()) return LAT_EUNSUPPORTED;
     // save the current state of every member
@@ -510,12 +521,12 @@ lat_status autotune(lat_batch* b, int steps)
             st = LAT_ECUDA;
     }
     if (cudaStreamSynchronize(b->stream) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
-    int best_t = 0;
+    int best_t = 0, best_cap = 32;
     float best_ms = 0.0f;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == LAT_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = LAT_ECUDA;
     for (size_t c = 0; c < cands.size() && st == LAT_OK; c++) {
-        if (configure(b, cands[c]) != LAT_OK) continue;
+        if (configure(b, cands[c].first, cands[c].second) != LAT_OK) continue;
         if (run_steps(b, 2) != LAT_OK) continue;   // warm-up and graph
         cudaEventRecord(e0, b->stream);
         lat_status rs = run_steps(b, steps);
@@ -526,7 +537,7 @@ lat_status autotune(lat_batch* b, int steps)
         if (ctl.status != LAT_OK) { st = (lat_status)ctl.status; break; }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (!best_t || ms < best_ms) { best_t = cands[c]; best_ms = ms; }
+        if (!best_t || ms < best_ms) { best_t = cands[c].first; best_cap = cands[c].second; best_ms = ms; }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -545,9 +556,9 @@ lat_status autotune(lat_batch* b, int steps)
     if (!best_t) return LAT_EUNSUPPORTED;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tuned_threads[key] = best_t;
+        g_tuned[key] = {best_t, best_cap};
     }
-    return configure(b, best_t);
+    return configure(b, best_t, best_cap);
 }
 
 } // namespace
@@ -587,17 +598,17 @@ lat_status lat_batch_create(const lat_params* params, int count, void* cuda_stre
                          cudaMemset(b->dctl, 0, sizeof(BatchCtl)) != cudaSuccess))
         st = LAT_ECUDA;
     if (st == LAT_OK) {
-        int threads = 0;
+        std::pair<int, int> tuned{0, 32};
         {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
-            auto it = g_tuned_threads.find(tune_key(b));
-            if (it != g_tuned_threads.end()) threads = it->second;
+            auto it = g_tuned.find(tune_key(b));
+            if (it != g_tuned.end()) tuned = it->second;
         }
-        if (threads) st = configure(b, threads);
+        if (tuned.first) st = configure(b, tuned.first, tuned.second);
         else {
             st = LAT_EUNSUPPORTED;
             for (int t : {256, 512, 384, 640, 768, 1024, 128})
-                if ((st = configure(b, t)) == LAT_OK) break;
+                if ((st = configure(b, t, 32)) == LAT_OK) break;
         }
     }
     if (st != LAT_OK) {
@@ -650,6 +661,13 @@ lat_status lat_batch_check_barrier(lat_batch* b, int64_t timeout_ns)
     // the next launch starts from a cleared control word
     LAT_CUDA(cudaMemset(b->dctl, 0, sizeof(BatchCtl)));
     return (lat_status)ctl.status;
+}
+
+lat_status lat_batch_tile_heights(lat_batch* b, int32_t* ty)
+{
+    if (!b || !ty) return LAT_EINVAL;
+    for (int i = 0; i < b->count; i++) ty[i] = b->shape.ty[i];
+    return LAT_OK;
 }
 
 lat_status lat_batch_member(lat_batch* b, int i, lat_handle** out)

@@ -427,8 +427,7 @@ cudaError_t launch_spectrum_bins(const void* spec, int n, double L, int nbins, d
 {
     const size_t smem = (size_t)3 * nbins * sizeof(double);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(spectrum_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = allow_dynamic_smem((const void*)spectrum_bins_kernel, smem);
         if (e != cudaSuccess) return e;
     }
     spectrum_bins_kernel<<<spectrum_grid_blocks(n), 256, smem, st>>>((const cufftDoubleComplex*)spec, n, L, nbins,

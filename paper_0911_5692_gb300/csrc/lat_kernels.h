@@ -25,6 +25,12 @@ cudaError_t launch_sums(const Bufs<T>& b, const Model& M, DevScalars* sc, double
 
 // Plane-ring z-march fused steps (lat_step_march.cu, lat_step_fast.cu,
 // lat_step_xt.cu, lat_step27.cu).
+// Raise a kernel's dynamic shared memory opt-in to at least `bytes` on the
+// current device. The opt-in is process-wide per kernel function and is never
+// lowered here: lattices of different shapes share kernel functions, and a
+// lower limit set for one would refuse the launches of another.
+cudaError_t allow_dynamic_smem(const void* fn, size_t bytes);
+
 struct MarchConfig {
     int ty;        // owned rows per tile
     int zr;        // planes per z-chunk (the longest)

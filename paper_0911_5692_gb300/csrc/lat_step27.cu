@@ -485,7 +485,7 @@ bool geom27(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     if (smem > 227 * 1024 - 2048) return false;
     const int maxt = maxt27_for(threads);
     const void* fn = esize == 4 ? step27_fn<float>(maxt) : step27_fn<double>(maxt);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+    if (allow_dynamic_smem(fn, smem) != cudaSuccess) return false;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
     int dev = 0, sms = 0;

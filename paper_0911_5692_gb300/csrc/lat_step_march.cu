@@ -11,11 +11,30 @@
 // TMA boxes per block measured well below it (that variant is lat_step_tma.cu).
 // One persistent wave of blocks shares the (y tile, z plane) units evenly.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "lat_kernels.h"
 #include "lat_march.cuh"
 
 namespace lat {
+
+cudaError_t allow_dynamic_smem(const void* fn, size_t bytes)
+{
+    static std::mutex mx;
+    static std::map<std::pair<int, const void*>, size_t> granted;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mx);
+    size_t& g = granted[{dev, fn}];
+    if (bytes <= g) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g = bytes;
+    return e;
+}
+
 
 namespace {
 
@@ -109,7 +128,7 @@ bool march_smem_attr(int esize, int maxt, size_t smem)
 {
     for (bool split : {false, true}) {
         const void* fn = esize == 4 ? march_fn<float>(maxt, split) : march_fn<double>(maxt, split);
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+        if (allow_dynamic_smem(fn, smem) != cudaSuccess) return false;
     }
     return true;
 }
@@ -134,8 +153,7 @@ bool march_geom(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     if (smem > 227 * 1024 - 2048) return false;   // the opt-in limit less the static arrays
     const int maxt = maxt_for(threads);
     const void* fn = fast ? fast : esize == 4 ? march_fn<float>(maxt, true) : march_fn<double>(maxt, true);
-    if (fast ? cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess
-             : !march_smem_attr(esize, maxt, smem))
+    if (fast ? allow_dynamic_smem(fn, smem) != cudaSuccess : !march_smem_attr(esize, maxt, smem))
         return false;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;

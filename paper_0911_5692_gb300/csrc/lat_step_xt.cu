@@ -324,7 +324,7 @@ bool geom_xt(int n, int esize, int ty, int zr, int depth, MarchConfig* cfg)
     if (smem > 227 * 1024 - 2048) return false;
     const int maxt = maxt_xt_for(threads);
     const void* fn = esize == 4 ? step_xt_fn<float>(maxt) : step_xt_fn<double>(maxt);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+    if (allow_dynamic_smem(fn, smem) != cudaSuccess) return false;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
     int dev = 0, sms = 0;

@@ -419,7 +419,7 @@ bool xw_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cf
     if (!fn || smem > 227 * 1024 - 2048) return false;
     const int vw = 16 / elem_bytes, w = 32 * vw, nxt = n / w;
     const int threads = (tyv + 4) * 32;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+    if (allow_dynamic_smem(fn, smem) != cudaSuccess) return false;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
     int dev = 0, sms = 0;

@@ -28,7 +28,7 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_batch_destroy", "lat_batch_check_barrier", "lat_slab_create", "lat_slab_sums", "lat_slab_step",
             "lat_slab_advance", "lat_energy_field", "lat_upload_state", "lat_get_hubble_length",
             "lat_set_hubble_length", "lat_download_state", "lat_get_background", "lat_set_background",
-            "lat_recenter")
+            "lat_recenter", "lat_tune", "lat_batch_tile_heights")
 
 
 class LatParams(C.Structure):
@@ -97,6 +97,8 @@ def load_library(build_if_missing: bool = True):
             L.lat_sync.argtypes = [P]
             L.lat_set_kernel.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int]
             L.lat_kernel_info.argtypes = [P, i64p]
+            L.lat_tune.argtypes = [P, C.c_int, i64p]
+            L.lat_batch_tile_heights.argtypes = [P, C.POINTER(C.c_int32)]
             L.lat_checkpoint_bytes.argtypes = [P, C.POINTER(C.c_uint64)]
             L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
             L.lat_load_checkpoint.argtypes = [P, P, C.c_uint64]
@@ -259,6 +261,15 @@ class Lattice:
 
     def set_kernel(self, variant: int = 0, ty: int = 0, zr: int = 0, depth: int = 0):
         _check(self._L.lat_set_kernel(self._h, int(variant), int(ty), int(zr), int(depth)), "lat_set_kernel")
+
+    def tune(self, steps: int = 64) -> dict:
+        """Autotune the step kernel on this lattice (lat_tune); the state is kept.
+        Returns the chosen shape and the timings of the sweep."""
+        out = (C.c_int64 * 8)()
+        _check(self._L.lat_tune(self._h, int(steps), out), "lat_tune")
+        return {"variant": int(out[0]), "ty": int(out[1]), "zr": int(out[2]), "depth": int(out[3]),
+                "candidates": int(out[4]), "best_ms": out[5] * 1e-6, "slowest_ms": out[6] * 1e-6,
+                "blocks": int(out[7])}
 
     def kernel_info(self) -> dict:
         out = (C.c_int64 * 8)()
@@ -523,7 +534,11 @@ class Ensemble:
         out = (C.c_int64 * 8)()
         _check(self._L.lat_batch_info(self._h, out), "lat_batch_info")
         keys = ("blocks", "threads", "smem", "ranges", "graph", "sites", "members", "launches")
-        return dict(zip(keys, [int(v) for v in out]))
+        info = dict(zip(keys, [int(v) for v in out]))
+        ty = (C.c_int32 * len(self.params))()
+        _check(self._L.lat_batch_tile_heights(self._h, ty), "lat_batch_tile_heights")
+        info["ty"] = [int(v) for v in ty]
+        return info
 
     def member(self, i: int) -> Lattice:
         """Borrowed Lattice view of member i (state access, energies, spectra)."""

@@ -136,6 +136,8 @@ def test_null_arguments():
     assert L.lat_get_background(None, None) == 1
     assert L.lat_set_background(None, None) == 1
     assert L.lat_recenter(None) == 1
+    assert L.lat_tune(None, 10, None) == 1
+    assert L.lat_batch_tile_heights(None, None) == 1
     L.lat_destroy(None)
 
 

@@ -108,6 +108,32 @@ def test_tune_restores_state_and_keeps_results():
             assert normwise(a, b) <= 4 * TOL[32]
 
 
+def test_tuned_shape_is_taken_by_new_ensembles():
+    """lat_batch_tune sweeps block size x tile-height cap; every member's tile
+    height divides its side and stays within 32, and an ensemble created later
+    with the same sizes and precision starts with the tuned shape."""
+    ps, states = _members(32, sizes=(32, 64, 96))
+    ens = Ensemble(ps)
+    _load(ens, states)
+    ens.tune(3)
+    info = ens.info()
+    assert len(info["ty"]) == len(ps)
+    for p, ty in zip(ps, info["ty"]):
+        assert 1 <= ty <= 32 and p["n"] % ty == 0
+    again = Ensemble([dict(p, seed=p["seed"] + 100) for p in ps])
+    info2 = again.info()
+    assert (info2["threads"], info2["ty"]) == (info["threads"], info["ty"])
+    _load(again, states)
+    again.evolve(3)
+    again.sync()
+    for i, (p, st) in enumerate(zip(ps, states)):
+        o = Oracle(p)
+        o.set_state(*st, **SCAL)
+        o.step(3)
+        for a, b in zip(again.member(i).get_state(), o.get_state()):
+            assert normwise(a, b) <= 3 * TOL[32]
+
+
 def test_static_members():
     ps, states = _members(64, sizes=(32, 48), expansion=0)
     ens = Ensemble(ps)
