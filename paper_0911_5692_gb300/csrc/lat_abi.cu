@@ -187,9 +187,16 @@ lat_status configure_kernel(lat_handle* h, int variant, int ty, int zr, int dept
         return LAT_OK;
     };
     auto fits = [&](const MarchConfig& cfg) { return (size_t)cfg.blocks * kSums <= h->partials_cap; };
-    if (h->M.stencil == 27) {   // the 27-point Laplacian runs on its plane-ring kernel only
-        if (variant == 4 || variant == 5) return LAT_EUNSUPPORTED;
+    if (h->M.stencil == 27) {   // the 27-point Laplacian: its own kernels (variants 2 and 5)
+        if (variant == 4) return LAT_EUNSUPPORTED;
         MarchConfig cfg;
+        if (variant == 5 || variant == 0) {   // x tiles one warp wide where an instance is compiled
+            if (s27w_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr, variant == 0 ? 0 : depth,
+                            &cfg) &&
+                fits(cfg))
+                return take(cfg, 5);
+            if (variant == 5) return LAT_EUNSUPPORTED;
+        }
         if (!march27_config(n, (int)h->esize, variant == 0 ? 0 : ty, variant == 0 ? 0 : zr,
                             variant == 0 ? 0 : depth, &cfg) || !fits(cfg))
             return LAT_EUNSUPPORTED;
@@ -257,6 +264,7 @@ std::vector<TuneShape> tune_candidates(const lat_handle* h)
 {
     std::vector<TuneShape> c;
     if (h->M.stencil == 27) {
+        c.push_back({5, 16, 0, 1});
         for (int ty : {16, 8, 4})
             for (int d : {1, 2}) c.push_back({2, ty, 0, d});
         return c;

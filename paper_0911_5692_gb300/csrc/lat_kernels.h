@@ -79,6 +79,12 @@ bool march27_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfi
 template <typename T>
 cudaError_t launch_step27(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
                           cudaStream_t st);
+// the 27-point Laplacian over x tiles one warp wide with compile-time N, ty,
+// depth and an edge warp (whole periodic lattices; the compiled geometries only)
+bool s27w_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);
+template <typename T>
+cudaError_t launch_step27w(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
+                           cudaStream_t st);
 
 // Initial conditions (off the timed path).
 struct InitWork {

@@ -236,6 +236,10 @@ template <typename T>
 cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials,
                               const MarchConfig& cfg, cudaStream_t st, double* sums_out)
 {
+    if (cfg.s27) {
+        if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
+        return cfg.xw ? launch_step27w<T>(b, M, sc, partials, cfg, st) : launch_step27<T>(b, M, sc, partials, cfg, st);
+    }
     if (cfg.xt) {
         if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
         return launch_step_xt<T>(b, M, sc, partials, cfg, st);
@@ -243,10 +247,6 @@ cudaError_t launch_step_march(const Bufs<T>& b, const Model& M, DevScalars* sc, 
     if (cfg.xw) {
         if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
         return launch_step_xw<T>(b, M, sc, partials, cfg, st);
-    }
-    if (cfg.s27) {
-        if (sums_out || cfg.nzl) return cudaErrorInvalidValue;
-        return launch_step27<T>(b, M, sc, partials, cfg, st);
     }
     if (cfg.fast && !sums_out && cfg.nzl == 0) return launch_step_fast<T>(b, M, sc, partials, cfg, st);
     MarchArgs G{cfg.ty, cfg.nzc, cfg.nyt, cfg.depth, cfg.nzl > 0 ? cfg.nzl : M.n, cfg.zbase, cfg.nzl > 0 ? 0 : 1};

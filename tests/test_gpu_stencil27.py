@@ -232,6 +232,8 @@ def test_paths_without_27_point_form_refuse():
     g = Lattice(p)
     with pytest.raises(LatticeError, match="UNSUPPORTED"):
         g.set_kernel(4)       # the x-tiled ring is written for 7 points
+    with pytest.raises(LatticeError, match="UNSUPPORTED"):
+        g.set_kernel(5)       # warp-wide tiles: compiled sides only (256, 512)
     for variant in (1, 3):    # no such kernels
         with pytest.raises(LatticeError, match="EINVAL"):
             g.set_kernel(variant)
@@ -286,3 +288,83 @@ def test_nonfinite_is_sticky_27():
         g.evolve(3)
         g.sync()
     assert ei.value.status == 5
+
+
+def _own_sums_check(g, p, prec):
+    """The lattice's sums of its new fields against the oracle's sums of the
+    same fields (FP64 on the oracle side): per-thread FP32 accumulation of the
+    bond sums bounds the FP32 error at about 2e-6."""
+    gs = g.scalars()
+    own = Oracle(p)
+    own.set_state(*g.get_state(), t=gs["t"], a=gs["a"], ad=gs["ad"], step=gs["step"])
+    tol = [1e-9, 1e-9, 1e-13, 1e-11] if prec == 64 else [2e-6, 2e-6, 1e-6, 2e-6]
+    ref = own.scalars()["S"]
+    own.close()
+    for k in range(4):
+        assert abs(gs["S"][k] - ref[k]) <= tol[k] * abs(ref[k]), (k, gs["S"][k], ref[k])
+
+
+@pytest.mark.parametrize("zr", [0, 1, 7])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_warp_tiles_27(prec, zr):
+    """Variant 5 of the 27-point stencil: x tiles one warp wide with N = 256 and
+    ty = 16 compiled in, the Laplacian from per-plane aggregates carried along
+    z, an edge warp that computes each tile's boundary column, and the bond sums
+    counted at the left end of each bond. Two steps against the oracle with z
+    runs of every length (zr = 1: runs of one plane, each with its own prologue
+    and final bond pass; zr = 7: runs crossing y tiles), then the sums of the new
+    fields against the oracle's sums of the same fields."""
+    n = 256
+    p = _params("m2phi2", n, prec)
+    st = _state("m2phi2", n, prec, seed=40 + zr)
+    g = Lattice(p)
+    g.set_kernel(5, 16, zr, 1)
+    info = g.kernel_info()
+    assert (info["variant"], info["ty"], info["depth"]) == (5, 16, 1)
+    g.set_state(*st, t=0.0, a=1.05, ad=0.5)
+    o = Oracle(p)
+    o.set_state(*st, t=0.0, a=1.05, ad=0.5)
+    del st
+    g.evolve(2)
+    o.step(2)
+    compare_states(g, o, 2 * TOL[prec], f"27-point warp tiles zr={zr} fp{prec}")
+    _check_scalars(g, o, prec, 2)
+    o.close()
+    _own_sums_check(g, p, prec)
+
+
+def test_warp_tiles_27_fp64_512():
+    """Variant 5 of the 27-point stencil in FP64 at N = 512 (four x tiles per row):
+    one step against the oracle, and the sums of the new fields."""
+    n = 512
+    p = _params("lphi4", n, 64)
+    st = _state("lphi4", n, 64, seed=91)
+    g = Lattice(p)
+    g.set_kernel(5)
+    assert g.kernel_info()["variant"] == 5
+    g.set_state(*st, t=0.0, a=1.02, ad=0.5)
+    o = Oracle(p)
+    o.set_state(*st, t=0.0, a=1.02, ad=0.5)
+    del st
+    g.evolve(1)
+    o.step(1)
+    compare_states(g, o, TOL[64], "27-point warp tiles FP64 512")
+    o.close()
+    _own_sums_check(g, p, 64)
+
+
+def test_warp_tiles_27_match_plane_ring_kernel():
+    """The two 27-point kernels (variant 2: full-row plane ring; variant 5: warp-wide
+    tiles) from the same state: ten FP32 steps agree to FP32 rounding."""
+    n = 256
+    p = _params("lphi4", n, 32)
+    st = _state("lphi4", n, 32, seed=17)
+    a = Lattice(p)
+    a.set_kernel(5)
+    b = Lattice(p)
+    b.set_kernel(2)
+    for g in (a, b):
+        g.set_state(*st, t=0.0, a=1.0, ad=0.4)
+        g.evolve(10)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert normwise(x, y) <= 10 * 2e-6
