@@ -57,6 +57,23 @@ namespace lat {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+enum { kOwn, kAhead, kStage, kEdge };   // warp roles
+
+// v, or the shared-memory value at a where p holds: a predicated load, no branch
+__device__ __forceinline__ float ld_shared_if(bool p, const float* a, float v)
+{
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.shared.f32 %0, [%1];\n\t}"
+        : "+f"(v)
+        : "r"((uint32_t)__cvta_generic_to_shared(a)), "r"((int)p));
+    return v;
+}
+__device__ __forceinline__ double ld_shared_if(bool p, const double* a, double v)
+{
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.shared.f64 %0, [%1];\n\t}"
+        : "+d"(v)
+        : "r"((uint32_t)__cvta_generic_to_shared(a)), "r"((int)p));
+    return v;
+}
 
 template <int D>
 struct Ring27W {
@@ -116,10 +133,11 @@ struct S27 {
     static __device__ __forceinline__ bool edge_warp(const Ctx& C) { return C.rho == ROWS; }
 
     // plane z0 + zrel of the fields into ring slot `slot`
+    template <int ROLE>
     static __device__ __forceinline__ void fetch_f(Ctx& C, int zrel, int slot)
     {
         const uint32_t zoff = (uint32_t)wrapn(C.z0 + zrel, N) * NN;
-        if (!edge_warp(C)) {
+        if constexpr (ROLE != kEdge) {
             const uint32_t gi = zoff + C.rowg;
             T* d = C.S + slot * SLOTF + C.offF;
             cp_async16(d, C.f0 + gi);
@@ -137,11 +155,12 @@ struct S27 {
     }
     // momenta of plane z0 + zrel for the computed rows, and at x0 + W (edge warp,
     // lane r - 1 for row r)
+    template <int ROLE>
     static __device__ __forceinline__ void fetch_p(Ctx& C, int zrel, int slot)
     {
         const uint32_t zoff = (uint32_t)wrapn(C.z0 + zrel, N) * NN;
-        if (!edge_warp(C)) {
-            if (C.rho >= 1 && C.rho <= GR) {
+        if constexpr (ROLE != kEdge) {
+            if constexpr (ROLE != kStage) {
                 const uint32_t gi = zoff + C.rowg;
                 T* d = C.S + P0 + slot * SLOTP + C.offP;
                 cp_async16(d, C.p0 + gi);
@@ -156,13 +175,12 @@ struct S27 {
     }
 
     // x neighbours of this lane's vector: from the adjacent lanes, at the tile's
-    // ends the edge scalars (el at x0 - 1, er at x0 + W). Every lane calls this.
-    static __device__ __forceinline__ void xnb(const P (&v)[NP], T el, T er, int lane, T& l, T& r)
+    // ends the edge scalars (*el at x0 - 1, *er at x0 + W), read by those lanes
+    // only. Every lane calls this.
+    static __device__ __forceinline__ void xnb(const P (&v)[NP], const T* el, const T* er, int lane, T& l, T& r)
     {
-        const T sl = __shfl_up_sync(kFull, hi2(v[NP - 1]), 1);
-        const T sr = __shfl_down_sync(kFull, lo2(v[0]), 1);
-        l = lane == 0 ? el : sl;
-        r = lane == 31 ? er : sr;
+        l = ld_shared_if(lane == 0, el, __shfl_up_sync(kFull, hi2(v[NP - 1]), 1));
+        r = ld_shared_if(lane == 31, er, __shfl_down_sync(kFull, lo2(v[0]), 1));
     }
 
     // The aggregates of one field at this lane's sites of row rho: centres c,
@@ -178,9 +196,9 @@ struct S27 {
         PK<T>::ld(row + RS, p);
         const T* e = E + C.rho * 4;
         T cl, cr, ml, mr, pl, pr;
-        xnb(c, e[0], e[1], C.lane, cl, cr);
-        xnb(m, e[-4], e[-3], C.lane, ml, mr);
-        xnb(p, e[4], e[5], C.lane, pl, pr);
+        xnb(c, e, e + 1, C.lane, cl, cr);
+        xnb(m, e - 4, e - 3, C.lane, ml, mr);
+        xnb(p, e + 4, e + 5, C.lane, pl, pr);
         P v[NP];
         T cs[VW + 2], vs[VW + 2];
 #pragma unroll
@@ -252,11 +270,12 @@ struct S27 {
             PK<T>::ld(gu, u0);
             PK<T>::ld(gu + W, u1);
             const int eb = f * GR + C.rho - 1;
-            const T p0n = __shfl_down_sync(kFull, lo2(p0[0]), 1), p1n = __shfl_down_sync(kFull, lo2(p1[0]), 1);
-            const T u0n = __shfl_down_sync(kFull, lo2(u0[0]), 1), u1n = __shfl_down_sync(kFull, lo2(u1[0]), 1);
+            // right neighbours of element VW - 1; lane 31: the boundary column
             const bool last = C.lane == 31;
-            const T p0e = last ? EGp[eb] : p0n, p1e = last ? EGp[eb + 1] : p1n;
-            const T u0e = last ? EGu[eb] : u0n, u1e = last ? EGu[eb + 1] : u1n;
+            const T p0e = ld_shared_if(last, EGp + eb, __shfl_down_sync(kFull, lo2(p0[0]), 1));
+            const T p1e = ld_shared_if(last, EGp + eb + 1, __shfl_down_sync(kFull, lo2(p1[0]), 1));
+            const T u0e = ld_shared_if(last, EGu + eb, __shfl_down_sync(kFull, lo2(u0[0]), 1));
+            const T u1e = ld_shared_if(last, EGu + eb + 1, __shfl_down_sync(kFull, lo2(u1[0]), 1));
             // the rows shifted one site to the right
             P p0R[NP], p1R[NP], u0R[NP], u1R[NP];
 #pragma unroll
@@ -300,23 +319,40 @@ struct S27 {
 
     // the top of every plane: wait for plane k + 1 (and its momenta), the
     // barrier, then the prefetch of plane k + D + 1
-    template <int J>
+    template <int J, int ROLE>
     static __device__ __forceinline__ void plane_top(Ctx& C, int k)
     {
         cp_async_wait(D - 1);
         __syncthreads();
         if (k + D <= C.nz) {
-            fetch_f(C, k + D + 1, (J + D + 2) % RF);
-            fetch_p(C, k + D, (J + D) % RP);
+            fetch_f<ROLE>(C, k + D + 1, (J + D + 2) % RF);
+            fetch_p<ROLE>(C, k + D, (J + D) % RP);
         }
         cp_async_commit();
+    }
+    // the prologue of a run: planes z0 - 1 .. z0 + D of the fields, z0 .. z0 + D - 1
+    // of the momenta, one commit group per plane step
+    template <int ROLE>
+    static __device__ __forceinline__ void prologue(Ctx& C)
+    {
+        fetch_f<ROLE>(C, -1, 0);
+        fetch_f<ROLE>(C, 0, 1);
+        fetch_f<ROLE>(C, 1, 2);
+        fetch_p<ROLE>(C, 0, 0);
+        cp_async_commit();
+#pragma unroll
+        for (int j = 1; j < D; j++) {
+            fetch_f<ROLE>(C, j + 1, j + 2);
+            fetch_p<ROLE>(C, j, j);
+            cp_async_commit();
+        }
     }
 
     // Edge warp, plane k: the boundary column x0 + W of computed row r = lane + 1.
     template <int J>
     static __device__ __forceinline__ void plane_edge(Ctx& C, int k)
     {
-        plane_top<J>(C, k);
+        plane_top<J, kEdge>(C, k);
         const int r = C.lane + 1;
         if (r > GR) return;
         const T* Fm = C.S + (J % RF) * SLOTF;
@@ -359,12 +395,15 @@ struct S27 {
 
     // Row warps, plane k: kick and drift of the computed rows, and the bonds of
     // planes k - 2 and k - 1 (both written before the barrier) for the owned rows.
-    template <int J>
+    // ROLE (the same for the whole warp and the whole run): kOwn, kAhead (the
+    // look-ahead row, computed but not stored) or kStage (the halo rows, staged
+    // only).
+    template <int J, int ROLE>
     static __device__ __forceinline__ void plane_rows(Ctx& C, int k)
     {
-        plane_top<J>(C, k);
-        const bool comp = C.rho >= 1 && C.rho <= GR;
-        const bool own = C.rho >= 1 && C.rho <= TY;
+        plane_top<J, ROLE>(C, k);
+        constexpr bool comp = ROLE != kStage;
+        constexpr bool own = ROLE == kOwn;
         const T* Fm = C.S + (J % RF) * SLOTF;
         const T* Fc = C.S + ((J + 1) % RF) * SLOTF;
         const T* Fp = C.S + ((J + 2) % RF) * SLOTF;
@@ -428,14 +467,20 @@ struct S27 {
     }
 
     // planes k + J .. k + PERIOD - 1; false once the look-ahead plane is done
-    template <int J, bool EDGE>
+    template <int J, int ROLE>
     static __device__ __forceinline__ bool planes(Ctx& C, int k)
     {
-        if constexpr (EDGE) plane_edge<J>(C, k + J);
-        else plane_rows<J>(C, k + J);
+        if constexpr (ROLE == kEdge) plane_edge<J>(C, k + J);
+        else plane_rows<J, ROLE>(C, k + J);
         if (k + J + 1 > C.nz) return false;
-        if constexpr (J + 1 < PERIOD) return planes<J + 1, EDGE>(C, k);
+        if constexpr (J + 1 < PERIOD) return planes<J + 1, ROLE>(C, k);
         else return true;
+    }
+    template <int ROLE>
+    static __device__ __forceinline__ void run(Ctx& C)
+    {
+        prologue<ROLE>(C);
+        for (int k = 0; planes<0, ROLE>(C, k); k += PERIOD) {}
     }
 };
 
@@ -490,22 +535,11 @@ __global__ void __launch_bounds__(S27<T, N, TY, D>::THREADS, 1)
         // every thread is done with the previous segment's ring before the
         // prologue refills it
         if (!first) __syncthreads();
-        F::fetch_f(C, -1, 0);
-        F::fetch_f(C, 0, 1);
-        F::fetch_f(C, 1, 2);
-        F::fetch_p(C, 0, 0);
-        cp_async_commit();
-#pragma unroll
-        for (int j = 1; j < D; j++) {
-            F::fetch_f(C, j + 1, j + 2);
-            F::fetch_p(C, j, j);
-            cp_async_commit();
-        }
-        // the same barriers on both paths: one per plane, one after the run
-        if (F::edge_warp(C))
-            for (int k = 0; F::template planes<0, true>(C, k); k += F::PERIOD) {}
-        else
-            for (int k = 0; F::template planes<0, false>(C, k); k += F::PERIOD) {}
+        // the same barriers on every path: one per plane, one after the run
+        if (F::edge_warp(C)) F::template run<kEdge>(C);
+        else if (C.rho == 0 || C.rho == F::ROWS - 1) F::template run<kStage>(C);
+        else if (C.rho == F::GR) F::template run<kAhead>(C);
+        else F::template run<kOwn>(C);
         // the last bonds: planes nz - 1 and nz (the look-ahead plane)
         __syncthreads();
         if (!F::edge_warp(C) && C.rho >= 1 && C.rho <= TY) {
