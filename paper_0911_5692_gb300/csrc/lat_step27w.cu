@@ -59,22 +59,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 enum { kOwn, kAhead, kStage, kEdge };   // warp roles
 
-// v, or the shared-memory value at a where p holds: a predicated load, no branch
-__device__ __forceinline__ float ld_shared_if(bool p, const float* a, float v)
-{
-    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.shared.f32 %0, [%1];\n\t}"
-        : "+f"(v)
-        : "r"((uint32_t)__cvta_generic_to_shared(a)), "r"((int)p));
-    return v;
-}
-__device__ __forceinline__ double ld_shared_if(bool p, const double* a, double v)
-{
-    asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.shared.f64 %0, [%1];\n\t}"
-        : "+d"(v)
-        : "r"((uint32_t)__cvta_generic_to_shared(a)), "r"((int)p));
-    return v;
-}
-
 template <int D>
 struct Ring27W {
     static constexpr int RF = D == 1 ? 4 : 6;          // field plane slots (>= D + 3)

@@ -34,6 +34,8 @@ namespace lat {
 
 namespace {
 
+enum { kOwn, kAhead, kStage, kEdge };   // warp roles
+
 template <int D>
 struct RingXW {
     static constexpr int RF = D == 1 ? 4 : 6;          // field plane slots (>= D + 3)
@@ -85,10 +87,11 @@ struct XW {
 
     // plane z0 + zrel of the fields into slot `slot`: row warps their vectors,
     // the edge warp (lane r < ROWS for row r) the three edge scalars of each field
+    template <int ROLE>
     static __device__ __forceinline__ void fetch_f(Ctx& C, int zrel, int slot)
     {
         const uint32_t zoff = (uint32_t)wrapn(C.z0 + zrel, N) * NN;
-        if (!edge_warp(C)) {
+        if constexpr (ROLE != kEdge) {
             const uint32_t gi = zoff + C.rowg;
             T* d = C.S + slot * SLOTF + C.offF;
             cp_async16(d, C.f0 + gi);
@@ -106,11 +109,12 @@ struct XW {
     }
     // momenta of plane z0 + zrel: the computing rows' vectors, and the momenta at
     // x0 + W of the owned rows (edge warp, lane r - 1 for row r)
+    template <int ROLE>
     static __device__ __forceinline__ void fetch_p(Ctx& C, int zrel, int slot)
     {
         const uint32_t zoff = (uint32_t)wrapn(C.z0 + zrel, N) * NN;
-        if (!edge_warp(C)) {
-            if (C.rho >= 1 && C.rho <= TY + 1) {
+        if constexpr (ROLE != kEdge) {
+            if constexpr (ROLE != kStage) {
                 const uint32_t gi = zoff + C.rowg;
                 T* d = C.S + P0 + slot * SLOTP + C.offP;
                 cp_async16(d, C.p0 + gi);
@@ -124,20 +128,24 @@ struct XW {
         }
     }
 
-    template <int J>
+    // ROLE (the same for the whole warp and the whole run): kOwn (rows 1..TY),
+    // kAhead (the look-ahead row, computed but not stored), kStage (the halo
+    // rows, staged only) or kEdge (the edge warp)
+    template <int J, int ROLE>
     static __device__ __forceinline__ void plane(Ctx& C, int k)
     {
         const bool ahead = k == C.nz;
-        const bool edge = edge_warp(C);
-        const bool comp = !edge && C.rho >= 1 && C.rho <= TY + 1;
-        const bool own = !edge && C.rho >= 1 && C.rho <= TY;
+        constexpr bool edge = ROLE == kEdge;
+        constexpr bool comp = ROLE == kOwn || ROLE == kAhead;
+        constexpr bool own = ROLE == kOwn;
         cp_async_wait(D - 1);
         __syncthreads();
         if (k + D <= C.nz) {
-            fetch_f(C, k + D + 1, (J + D + 2) % RF);
-            fetch_p(C, k + D, (J + D) % RP);
+            fetch_f<ROLE>(C, k + D + 1, (J + D + 2) % RF);
+            fetch_p<ROLE>(C, k + D, (J + D) % RP);
         }
         cp_async_commit();
+        if constexpr (ROLE == kStage) return;
 
         const T* Fm = C.S + (J % RF) * SLOTF;
         const T* Fc = C.S + ((J + 1) % RF) * SLOTF;
@@ -152,7 +160,7 @@ struct XW {
         T* EGw = C.S + EG0 + (J & 1) * 2 * TY;
         const T* EGr = C.S + EG0 + ((J + 1) & 1) * 2 * TY;
 
-        if (edge) {
+        if constexpr (edge) {
             // the boundary column x0 + W of owned row r = lane + 1, rounded as the
             // neighbouring tile rounds its own first column
             const int r = C.lane + 1;
@@ -187,14 +195,13 @@ struct XW {
             PK<T>::ld(Ff, cen[f]);
             // the tile's edge values: one broadcast load for the whole warp and a
             // select, no branch on the lane
-            const T el = Ec[f * EF + C.rho * 4 + 0], er = Ec[f * EF + C.rho * 4 + 1];
-            const T sl = __shfl_up_sync(0xffffffffu, hi2(cen[f][NP - 1]), 1);
-            const T sr = __shfl_down_sync(0xffffffffu, lo2(cen[f][0]), 1);
-            lefts[f] = C.lane == 0 ? el : sl;
-            rights[f] = C.lane == 31 ? er : sr;
+            lefts[f] = ld_shared_if(C.lane == 0, Ec + f * EF + C.rho * 4 + 0,
+                                    __shfl_up_sync(0xffffffffu, hi2(cen[f][NP - 1]), 1));
+            rights[f] = ld_shared_if(C.lane == 31, Ec + f * EF + C.rho * 4 + 1,
+                                     __shfl_down_sync(0xffffffffu, lo2(cen[f][0]), 1));
         }
         P g[2][NP];
-        if (comp && !(ahead && C.rho == TY + 1)) {
+        if (comp && !(ahead && ROLE == kAhead)) {
             P pn[2][NP];
 #pragma unroll
             for (int f = 0; f < 2; f++) {
@@ -254,9 +261,8 @@ struct XW {
                 P yn[NP], xn[NP];
                 PK<T>::ld(Gf, gq[f]);
                 PK<T>::ld(Gf + W, yn);
-                const T xs = __shfl_down_sync(0xffffffffu, lo2(gq[f][0]), 1);
-                const T xe = EGr[f * TY + (C.rho - 1)];
-                const T xnext = C.lane == 31 ? xe : xs;
+                const T xnext = ld_shared_if(C.lane == 31, EGr + f * TY + (C.rho - 1),
+                                             __shfl_down_sync(0xffffffffu, lo2(gq[f][0]), 1));
                 if constexpr (NP == 2) {
                     T a, b, c, d;
                     un2(gq[f][0], a, b);
@@ -281,13 +287,32 @@ struct XW {
     }
 
     // planes k + J .. k + PERIOD - 1; false once the look-ahead plane is done
-    template <int J>
+    template <int J, int ROLE>
     static __device__ __forceinline__ bool planes(Ctx& C, int k)
     {
-        plane<J>(C, k + J);
+        plane<J, ROLE>(C, k + J);
         if (k + J + 1 > C.nz) return false;
-        if constexpr (J + 1 < PERIOD) return planes<J + 1>(C, k);
+        if constexpr (J + 1 < PERIOD) return planes<J + 1, ROLE>(C, k);
         else return true;
+    }
+    // one run of planes: the prologue (planes z0 - 1 .. z0 + D of the fields,
+    // z0 .. z0 + D - 1 of the momenta, one commit group per plane step), then the
+    // planes; every role passes the same barriers
+    template <int ROLE>
+    static __device__ __forceinline__ void run(Ctx& C)
+    {
+        fetch_f<ROLE>(C, -1, 0);
+        fetch_f<ROLE>(C, 0, 1);
+        fetch_f<ROLE>(C, 1, 2);
+        fetch_p<ROLE>(C, 0, 0);
+        cp_async_commit();
+#pragma unroll
+        for (int j = 1; j < D; j++) {
+            fetch_f<ROLE>(C, j + 1, j + 2);
+            fetch_p<ROLE>(C, j, j);
+            cp_async_commit();
+        }
+        for (int k = 0; planes<0, ROLE>(C, k); k += PERIOD) {}
     }
 };
 
@@ -345,18 +370,10 @@ __global__ void __launch_bounds__(XW<T, N, TY, D>::THREADS, 1)
         // the previous segment's last plane is read by every thread before the
         // prologue refills the ring
         if (!first) __syncthreads();
-        F::fetch_f(C, -1, 0);
-        F::fetch_f(C, 0, 1);
-        F::fetch_f(C, 1, 2);
-        F::fetch_p(C, 0, 0);
-        cp_async_commit();
-#pragma unroll
-        for (int j = 1; j < D; j++) {
-            F::fetch_f(C, j + 1, j + 2);
-            F::fetch_p(C, j, j);
-            cp_async_commit();
-        }
-        for (int k = 0; F::template planes<0>(C, k); k += F::PERIOD) {}
+        if (F::edge_warp(C)) F::template run<kEdge>(C);
+        else if (C.rho == 0 || C.rho == F::ROWS - 1) F::template run<kStage>(C);
+        else if (C.rho == TY + 1) F::template run<kAhead>(C);
+        else F::template run<kOwn>(C);
     }
 
     T v[kSums] = {lo2(C.accg0) + hi2(C.accg0), lo2(C.accg1) + hi2(C.accg1),
