@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--variant", type=int, default=0,
                     help="step kernel: 0 autotuned, 2 plane ring over full rows, 4 plane ring over x tiles, "
                          "5 x tiles one warp wide")
+    ap.add_argument("--slabs", type=int, default=0,
+                    help="z-slab mode: one lattice of the workload cut into z-slabs (phi stored whole); one rank: "
+                         "this many slabs on its GPU; under torchrun: one slab per rank (NCCL halos and sums, the "
+                         "interior stepped while the halos are in flight); strong scaling")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default kernel shape instead of autotuning it (lat_tune) before timing")
     ap.add_argument("--stencil", type=int, choices=[7, 27], default=7,
@@ -97,13 +101,17 @@ STEP_KERNEL_SOURCES = {
 }
 
 
+VARIANT_SOURCES = {(7, 4): ("lat_step_xt.cu",), (7, 5): ("lat_step_xw.cu", "lat_xw.cuh"),
+                   (27, 5): ("lat_step27w.cu",)}
+
+
 def kernel_source_hash(stencil=7, variant=2):
     """Hash of the sources the fused step kernels of a stencil (and, for the
     x-tiled variants 4 and 5, their own files) are built from: a recorded
     DRAM-traffic figure is valid only for these exact sources."""
     d = os.path.join(ROOT, "paper_0911_5692_gb300", "csrc")
     h = hashlib.sha256()
-    files = STEP_KERNEL_SOURCES[stencil] + {4: ("lat_step_xt.cu",), 5: ("lat_step_xw.cu", "lat_site.cuh")}.get(variant, ())
+    files = STEP_KERNEL_SOURCES[stencil] + VARIANT_SOURCES.get((stencil, variant), ())
     for f in files:
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
@@ -370,6 +378,76 @@ def measure_ensemble(local, steps=200):
                        "tuned_over": "block size x tile-height cap (lat_batch_tune)"},
             "fp64_error": dict(worst, steps=steps + 5, against="the same 64 members in FP64 (phi whole), same "
                                                                   "seeds; largest per-member normwise error")}
+
+
+def measure_slabs(local, parts=4, steps=200):
+    """One 512^3 FP32 lambda phi^4 lattice (phi stored whole) cut into `parts`
+    z-slabs on one GPU, all on one stream: halos by device copies, shares added
+    on the device, the scale-factor update per slab; two steps (one per
+    ping-pong parity) captured in a CUDA graph and replayed. Both schedules
+    (plain: exchange, then each slab whole; overlap: each slab's interior,
+    exchange, boundary pairs) against the same lattice stepped whole. On one GPU
+    nothing overlaps; the line measures what the slab form costs in extra
+    launches and copies."""
+    import numpy as np
+    import torch
+    from paper_0911_5692_gb300 import Lattice
+    from paper_0911_5692_gb300.slab import LocalComm, SlabEvolution, SlabGPU, slab_ranges
+    from paper_0911_5692_gb300.workloads import lphi4
+    p = lphi4(512, precision=32)
+    n = p["n"]
+    lat = Lattice(p, device=local)
+    lat.init_fields()
+    sc0 = lat.scalars()
+    arrs = [lat.get_state_device(f, w) for w in (0, 1) for f in (0, 1)]   # f0, f1, pi0, pi1
+
+    def timed(run, k):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record(stream)
+        for _ in range(k):
+            run()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return s.elapsed_time(e)
+
+    stream = lat.stream
+    lat.evolve(32)
+    whole_ms = timed(lambda: lat.evolve(steps), 1) / steps
+    out = {"workload": "lphi4_512_fp32 (phi whole)", "slabs": parts, "steps": steps, "whole_ms_per_step": whole_ms}
+    stream = torch.cuda.Stream(device=local)
+    slabs = [SlabGPU(p, z0, nzl, device=local, stream=stream) for z0, nzl in slab_ranges(n, parts)]
+    for overlap in (False, True):
+        for sl in slabs:
+            sl.load(*arrs, t=sc0["t"], a=sc0["a"], ad=sc0["ad"], step=sc0["step"])
+        ev = SlabEvolution(slabs, LocalComm(), overlap=overlap)
+        ev.prepare()
+        ev.step(2)                      # uncaptured: kernel configuration, shared-memory opt-ins
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            ev.step(2)
+        for sl in slabs:                # the capture ran nothing: the host step counts go back
+            sl.step_count -= 2
+
+        def replay():
+            with torch.cuda.stream(stream):     # the graph runs on the stream the events are recorded on
+                g.replay()
+            for sl in slabs:
+                sl.step_count += 2
+        replay()
+        ms = timed(replay, steps // 2) / (2 * (steps // 2))
+        for sl in slabs:
+            assert np.isfinite(sl.scalars()["S"]).all()
+        out["overlap" if overlap else "plain"] = {"ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": UNIT,
+                                                  "over_whole": ms / whole_ms,
+                                                  "launches_per_step": parts * (3 if overlap else 1)}
+        del g
+    for sl in slabs:
+        sl.close()
+    lat.close()
+    return out
 
 
 def measure_stencil27(local, names=("m2phi2_256_fp32", "lphi4_512_fp32"), steps=100):
@@ -769,8 +847,157 @@ def run_ours(args):
         line["stencil27"] = measure_stencil27(local)
         line["diagnostics"] = measure_diagnostics(local, args.workload)
         line["lform"] = measure_lform(local, args.workload)
+        line["slabs_1gpu"] = measure_slabs(local)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_slabs(args):
+    """bench.py --slabs: the workload's lattice (phi stored whole) cut into z-slabs.
+    One rank: args.slabs slabs on one GPU (halos by device copies, the plain
+    schedule, two steps per CUDA-graph replay). N ranks: one slab per rank, halos
+    by NCCL point-to-point messages, the interior of each slab stepped while
+    they are in flight, the four sums by all_reduce. value = the lattice's site
+    updates per second (the whole job)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_0911_5692_gb300 import Lattice
+    from paper_0911_5692_gb300.slab import DistComm, LocalComm, SlabEvolution, SlabGPU, slab_ranges
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = dict(workload(args.workload), split=0)
+    n = p["n"]
+    esize = 4 if p["precision"] == 32 else 8
+    parts = world if world > 1 else max(1, args.slabs)
+    ranges = slab_ranges(n, parts)
+    mine = [ranges[rank]] if world > 1 else ranges
+    # every rank builds the same initial state (same seed) and keeps its part
+    lat = Lattice(p, device=local)
+    lat.init_fields()
+    sc0 = lat.scalars()
+    arrs = [lat.get_state_device(f, w) for w in (0, 1) for f in (0, 1)]
+    lat.close()
+    stream = torch.cuda.Stream(device=local)
+    slabs = [SlabGPU(p, z0, nzl, device=local, stream=stream) for z0, nzl in mine]
+    for sl in slabs:
+        sl.load(*arrs, t=sc0["t"], a=sc0["a"], ad=sc0["ad"], step=sc0["step"])
+    del arrs
+    ev = SlabEvolution(slabs, DistComm() if world > 1 else LocalComm(), overlap=world > 1)
+    ev.prepare()
+    K = max(2, args.steps // 2 * 2)
+    if world == 1:
+        ev.step(2)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            ev.step(2)
+        for sl in slabs:
+            sl.step_count -= 2
+
+        def run(k):
+            for _ in range(k // 2):
+                with torch.cuda.stream(stream):
+                    g.replay()
+                for sl in slabs:
+                    sl.step_count += 2
+    else:
+        def run(k):
+            ev.step(k)
+    run(max(2, args.warmup // 2 * 2))
+    torch.cuda.synchronize()
+    gpu_id = torch.cuda.get_device_properties(local)
+    gpu_id = getattr(gpu_id, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else (gpu_id or local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    run(K)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks.stop()
+    t = torch.tensor([start.elapsed_time(end)], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item()) / K
+    for sl in slabs:
+        assert np.isfinite(sl.scalars()["S"]).all()
+    value = n ** 3 / (ms / 1e3)
+
+    # end to end: every step the owned planes of each slab go up from pinned host
+    # memory and come back after the step, with the scalars
+    E = max(2, args.e2e_steps)
+    host = []
+    for sl in slabs:
+        s = sl.current_set()
+        host.append([sl.buffers[4 * s + k][1:sl.nzl + 1].cpu().pin_memory() for k in range(4)])
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        for sl, hb in zip(slabs, host):
+            s = sl.current_set()
+            with torch.cuda.stream(stream):
+                for k in range(4):
+                    sl.buffers[4 * s + k][1:sl.nzl + 1].copy_(hb[k], non_blocking=True)
+        ev.step(1)
+        for sl, hb in zip(slabs, host):
+            s = sl.current_set()
+            with torch.cuda.stream(stream):
+                for k in range(4):
+                    hb[k].copy_(sl.buffers[4 * s + k][1:sl.nzl + 1], non_blocking=True)
+        stream.synchronize()
+        for sl in slabs:
+            sl.scalars()
+    te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = n ** 3 * E / float(te.item())
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    peak, peak_src = ((float(peaks["hbm_gbs"]), "measured") if peaks and peaks.get("hbm_gbs")
+                      else (FALLBACK_HBM_GBS, "fallback"))
+    per_gpu_bytes = 8 * esize * n ** 3 / world
+    achieved = per_gpu_bytes / (ms / 1e3) / 1e9
+    own_bytes = 4 * esize * sum(nzl for _, nzl in mine) * n * n
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32" if esize == 4 else "f64", "data": "synthetic",
+        "config": dict(config_of(args.workload, p, world), global_batch=1,
+                       parallelism=f"zslab{parts}" + (" on one GPU" if world == 1 else "")),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": per_gpu_bytes,
+                     "kernel": "fused slab step (variant 5 slab instance where compiled), all ranges of one step"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": own_bytes,
+                "d2h_bytes_per_step": own_bytes + 64 * len(slabs), "steps": E,
+                "per_step": "the owned planes of every slab up from pinned host memory, one step, back, and the scalars"},
+        "gpu_launches": K * len(slabs) * ((3 if ev.overlap else 1) + 1),
+        "clocks": clocks.summary(),
+        "slabs": {"count": parts, "schedule": "overlap" if ev.overlap else "plain",
+                  "planes": [nzl for _, nzl in ranges]},
+    }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -780,6 +1007,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.slabs:
+        run_slabs(args)
     else:
         run_ours(args)
 

@@ -410,6 +410,18 @@ lat_status lat_slab_sums(lat_handle* h, double* sums_dev);
  * fields into sums_dev (device, 4 doubles). Asynchronous. */
 lat_status lat_slab_step(lat_handle* h, double* sums_dev);
 
+/* The fused step on owned planes [zfirst, zfirst + zcount) only (0 <= zfirst,
+ * 1 <= zcount, zfirst + zcount <= nzl), with the shares of those planes'
+ * averages into sums_dev (device, 4 doubles); lat_slab_step is the range
+ * [0, nzl). The step of a range reads the current set's planes zfirst - 1 ..
+ * zfirst + zcount + 1 (owned z, stored z + 1) and the momenta of zfirst ..
+ * zfirst + zcount: planes 2 .. nzl - 3 touch no halo plane, so the caller can
+ * step them while the halo exchange is in flight and planes 0, 1, nzl - 2,
+ * nzl - 1 after it. Ranges of one step run one after another on the slab's
+ * stream (they share its block partials); the caller adds their shares.
+ * Asynchronous. */
+lat_status lat_slab_step_range(lat_handle* h, int zfirst, int zcount, double* sums_dev);
+
 /* The FP64 scale-factor update (eq. scale) from the total of all slabs'
  * shares (sums_dev: device, 4 doubles): advance = 1 after a step (a, a', t and
  * the step count advance), 0 to set the coefficients of the first step.

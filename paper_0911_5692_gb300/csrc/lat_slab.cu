@@ -16,6 +16,12 @@
 //      total, identical on every slab.
 // Before the first step, lat_slab_sums + lat_slab_advance(advance = 0) set the
 // coefficients from the starting fields.
+//
+// Step 2 may be taken in z ranges (lat_slab_step_range), each writing its own
+// shares: owned planes 2 .. nzl - 3 read no halo plane (their runs end on the
+// look-ahead plane nzl - 2, whose z neighbours are owned), so they can run while
+// the halos are still in flight; planes 0, 1 and nzl - 2, nzl - 1 follow once
+// the halos are in, and are the planes the neighbours need for the next step.
 #include <algorithm>
 
 #include "lat_internal.h"
@@ -135,15 +141,38 @@ lat_status lat_slab_sums(lat_handle* h, double* sums_dev)
     return cuda_status(cudaGetLastError());
 }
 
+lat_status lat_slab_step_range(lat_handle* h, int zfirst, int zcount, double* sums_dev)
+{
+    if (!h || !sums_dev) return LAT_EINVAL;
+    if (!h->slab) return LAT_ESTATE;
+    if (zfirst < 0 || zcount < 1 || zfirst + zcount > h->slab_nzl) return LAT_EINVAL;
+    // the range's stored planes start at 1 + zfirst; the kernels read one plane
+    // below it and two above, all within the slab's nzl + 3 stored planes
+    const int n = h->M.n;
+    MarchConfig cfg;
+    cudaError_t e;
+    if (slab_xw_config(n, (int)h->esize, zcount, &cfg) && (size_t)cfg.blocks * kSums <= h->partials_cap) {
+        e = h->prec == 32 ? launch_slab_xw<float>(bufs_of<float>(h), h->M, h->sc, h->partials, cfg, 1 + zfirst,
+                                                  sums_dev, h->stream)
+                          : launch_slab_xw<double>(bufs_of<double>(h), h->M, h->sc, h->partials, cfg, 1 + zfirst,
+                                                   sums_dev, h->stream);
+    } else {
+        if (!march_slab_config(n, (int)h->esize, zcount, &cfg) || (size_t)cfg.blocks * kSums > h->partials_cap)
+            return LAT_EUNSUPPORTED;
+        cfg.zbase = 1 + zfirst;
+        e = h->prec == 32 ? launch_step_march<float>(bufs_of<float>(h), h->M, h->sc, h->partials, cfg, h->stream,
+                                                     sums_dev)
+                          : launch_step_march<double>(bufs_of<double>(h), h->M, h->sc, h->partials, cfg, h->stream,
+                                                      sums_dev);
+    }
+    return cuda_status(e);
+}
+
 lat_status lat_slab_step(lat_handle* h, double* sums_dev)
 {
     if (!h || !sums_dev) return LAT_EINVAL;
     if (!h->slab) return LAT_ESTATE;
-    cudaError_t e = h->prec == 32 ? launch_step_march<float>(bufs_of<float>(h), h->M, h->sc, h->partials, h->mcfg,
-                                                             h->stream, sums_dev)
-                                  : launch_step_march<double>(bufs_of<double>(h), h->M, h->sc, h->partials, h->mcfg,
-                                                              h->stream, sums_dev);
-    return cuda_status(e);
+    return lat_slab_step_range(h, 0, h->slab_nzl, sums_dev);
 }
 
 lat_status lat_slab_advance(lat_handle* h, const double* sums_dev, int advance)

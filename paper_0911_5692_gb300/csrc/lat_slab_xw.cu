@@ -1,0 +1,85 @@
+// lat_slab_xw.cu -- the fused 7-point step over x tiles one warp wide (lat_xw.cuh)
+// for a range of a z-slab's owned planes: the compiled instances, their launch
+// configuration and launch.
+#include <algorithm>
+
+#include "lat_xw.cuh"
+
+namespace lat {
+
+namespace {
+
+template <typename T>
+const void* slab_xw_fn(int n, size_t* smem)
+{
+#define LAT_SLAB_XW_CASE(NN)                                                  \
+    if (n == NN) {                                                            \
+        *smem = xw::XW<T, NN, 16, 1, true>::SMEM;                             \
+        return (const void*)xw::step_xw_kernel<T, NN, 16, 1, true>;           \
+    }
+    if constexpr (sizeof(T) == 4) {
+        LAT_SLAB_XW_CASE(256) LAT_SLAB_XW_CASE(512)
+    } else {
+        LAT_SLAB_XW_CASE(256)
+    }
+#undef LAT_SLAB_XW_CASE
+    return nullptr;
+}
+
+} // namespace
+
+bool slab_xw_config(int n, int elem_bytes, int nz, MarchConfig* cfg)
+{
+    if (nz < 1) return false;
+    size_t smem = 0;
+    const void* fn = elem_bytes == 4 ? slab_xw_fn<float>(n, &smem) : slab_xw_fn<double>(n, &smem);
+    if (!fn || smem > 227 * 1024 - 2048) return false;
+    constexpr int ty = 16;
+    const int vw = 16 / elem_bytes, w = 32 * vw, nxt = n / w;
+    const int threads = (ty + 4) * 32;
+    if (allow_dynamic_smem(fn, smem) != cudaSuccess) return false;
+    int occ = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) return false;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return false;
+    const int nyt = n / ty;
+    const long long units = (long long)nyt * nz;
+    // whole groups of nxt blocks, at most one resident wave, at most one unit per group
+    const long long groups = std::max<long long>(1, std::min<long long>((long long)sms * occ / nxt, units));
+    cfg->ty = ty;
+    cfg->zr = (int)((units + groups - 1) / groups);
+    cfg->nzc = 0;
+    cfg->depth = 1;
+    cfg->threads = threads;
+    cfg->maxt = threads;
+    cfg->fast = 1;
+    cfg->smem = smem;
+    cfg->nyt = nyt;
+    cfg->blocks = (int)(groups * nxt);
+    cfg->nzl = nz;
+    cfg->zbase = 1;
+    cfg->s27 = 0;
+    cfg->xt = 0;
+    cfg->xw = 1;
+    cfg->nxt = nxt;
+    return true;
+}
+
+template <typename T>
+cudaError_t launch_slab_xw(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
+                           int zbase, double* sums_out, cudaStream_t st)
+{
+    size_t smem = 0;
+    const void* fn = slab_xw_fn<T>(M.n, &smem);
+    if (!fn || !sums_out) return cudaErrorInvalidValue;
+    xw::SlabRun R{cfg.nzl, zbase, sums_out};
+    void* args[] = {(void*)&b, (void*)&M, (void*)&sc, (void*)&partials, (void*)&R};
+    return cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+}
+
+template cudaError_t launch_slab_xw<float>(const Bufs<float>&, const Model&, DevScalars*, double*, const MarchConfig&,
+                                           int, double*, cudaStream_t);
+template cudaError_t launch_slab_xw<double>(const Bufs<double>&, const Model&, DevScalars*, double*,
+                                            const MarchConfig&, int, double*, cudaStream_t);
+
+} // namespace lat

@@ -28,7 +28,7 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_batch_destroy", "lat_batch_check_barrier", "lat_slab_create", "lat_slab_sums", "lat_slab_step",
             "lat_slab_advance", "lat_energy_field", "lat_upload_state", "lat_get_hubble_length",
             "lat_set_hubble_length", "lat_download_state", "lat_get_background", "lat_set_background",
-            "lat_recenter", "lat_tune", "lat_batch_tile_heights")
+            "lat_recenter", "lat_tune", "lat_batch_tile_heights", "lat_slab_step_range")
 
 
 class LatParams(C.Structure):
@@ -117,6 +117,7 @@ def load_library(build_if_missing: bool = True):
             L.lat_slab_create.argtypes = [C.POINTER(LatParams), C.c_int, C.c_int, P, C.POINTER(P), C.POINTER(P)]
             L.lat_slab_sums.argtypes = [P, P]
             L.lat_slab_step.argtypes = [P, P]
+            L.lat_slab_step_range.argtypes = [P, C.c_int, C.c_int, P]
             L.lat_slab_advance.argtypes = [P, P, C.c_int]
             L.lat_batch_destroy.argtypes = [P]
             L.lat_batch_destroy.restype = None

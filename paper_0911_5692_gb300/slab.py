@@ -7,11 +7,16 @@ slab. Per step (Sec. II.B, eq. evo with eq. scalar-evo and eq. scale):
 1. halo exchange of the current ping-pong set: every slab receives the f
    plane just below its range, the two f planes just above (the second for the
    look-ahead rim of the sums) and the pi plane just above;
-2. the fused step on the owned planes (CUDA, ``lat_slab_step``), which writes
-   the slab's share of the four volume averages of the new fields;
+2. the fused step on the owned planes (CUDA, ``lat_slab_step_range``), which
+   writes the slab's share of the four volume averages of the new fields;
 3. an allreduce adds the shares (four FP64 numbers);
 4. the FP64 scale-factor update from the total (``lat_slab_advance``),
    identical on every slab.
+
+With ``overlap`` (slabs of at least five planes) the exchange is posted first,
+the owned planes 2 .. nzl - 3 (which read no halo plane) are stepped while it is
+in flight, and planes 0, 1 and nzl - 2, nzl - 1 once it has completed; the
+three ranges write three shares, added on the device.
 
 This module is host-side orchestration only: the compute of each slab runs in
 the CUDA library. Halo planes move by torch.distributed point-to-point calls
@@ -94,6 +99,7 @@ class SlabGPU:
         n = self.n
         self.buffers = [torch.zeros((self.nzl + 3, n, n), dtype=self.dtype, device=self.device) for _ in range(8)]
         self.shares = torch.zeros(4, dtype=torch.float64, device=self.device)
+        self.range_shares = torch.zeros((3, 4), dtype=torch.float64, device=self.device)
         torch.cuda.synchronize(self.device)
         self._p = make_params(params)
         arr = (C.c_void_p * 8)(*[b.data_ptr() for b in self.buffers])
@@ -122,17 +128,23 @@ class SlabGPU:
         return self.buffers[4 * self.current_set() + a][p]
 
     def load(self, f0, f1, pi0, pi1, t=0.0, a=1.0, ad=0.0, step=0):
-        """Upload this slab's part (with its halos) of full-lattice arrays [z][y][x]."""
+        """Upload this slab's part (with its halos) of full-lattice arrays [z][y][x]
+        (host arrays, or device tensors of N^3 elements, gathered on the device)."""
         torch = self._torch
         self.step_count = int(step)
         v = (C.c_double * 4)(float(t), float(a), float(ad), float(step))
         _check(self._L.lat_set_scalars(self._h, v), "lat_set_scalars")
         idx = [(self.z0 - 1 + p) % self.n for p in range(self.nzl + 3)]
         s = self.current_set()
+        n = self.n
         with torch.cuda.stream(self.stream):
             for k, arr in enumerate((f0, f1, pi0, pi1)):
-                part = np.ascontiguousarray(np.asarray(arr)[idx])
-                self.buffers[4 * s + k].copy_(torch.from_numpy(part).to(self.dtype))
+                if isinstance(arr, torch.Tensor) and arr.is_cuda:
+                    sel = torch.tensor(idx, dtype=torch.long, device=arr.device)
+                    self.buffers[4 * s + k].copy_(arr.reshape(n, n, n).index_select(0, sel))
+                else:
+                    part = np.ascontiguousarray(np.asarray(arr)[idx])
+                    self.buffers[4 * s + k].copy_(torch.from_numpy(part).to(self.dtype))
         self.stream.synchronize()
 
     def owned(self):
@@ -154,6 +166,18 @@ class SlabGPU:
         _check(self._L.lat_slab_step(self._h, C.c_void_p(self.shares.data_ptr())), "lat_slab_step")
         return self.shares
 
+    def local_step_range(self, zfirst: int, zcount: int, slot: int):
+        """Step owned planes [zfirst, zfirst + zcount); their shares go to
+        range_shares[slot] (slots 0..2)."""
+        _check(self._L.lat_slab_step_range(self._h, int(zfirst), int(zcount),
+                                           C.c_void_p(self.range_shares[slot].data_ptr())), "lat_slab_step_range")
+
+    def range_total(self):
+        """The sum of the three range shares (on the slab's stream)."""
+        with self._torch.cuda.stream(self.stream):
+            self.shares.copy_(self.range_shares.sum(dim=0))
+        return self.shares
+
     def advance(self, total, advance: bool):
         _check(self._L.lat_slab_advance(self._h, C.c_void_p(total.data_ptr()), 1 if advance else 0),
                "lat_slab_advance")
@@ -168,6 +192,13 @@ class LocalComm:
     """All slabs of the lattice in this process: halos by device copies, the
     allreduce by adding the shares on the device."""
 
+    def post_exchange(self, slabs):
+        self.exchange(slabs)
+        return None
+
+    def finish_exchange(self, slabs, pending):
+        pass
+
     def exchange(self, slabs):
         import torch
         P = len(slabs)
@@ -175,10 +206,17 @@ class LocalComm:
             above, below = slabs[(i + 1) % P], slabs[(i - 1) % P]
             s.stream.wait_stream(above.stream)
             s.stream.wait_stream(below.stream)
+            dst, src = [], []
+            for msg in halo_plan():
+                nb = above if msg[0] == "down" else below
+                dst.append(s.plane(msg[2], recv_plane(msg, s.nzl)))
+                src.append(nb.plane(msg[2], send_plane(msg, nb.nzl)))
             with torch.cuda.stream(s.stream):
-                for msg in halo_plan():
-                    src = above if msg[0] == "down" else below
-                    s.plane(msg[2], recv_plane(msg, s.nzl)).copy_(src.plane(msg[2], send_plane(msg, src.nzl)))
+                if hasattr(torch, "_foreach_copy_"):    # the slab's eight planes in one multi-tensor copy
+                    torch._foreach_copy_(dst, src)
+                else:
+                    for d, q in zip(dst, src):
+                        d.copy_(q)
         # a slab's planes are read above before it may write them again
         for i, s in enumerate(slabs):
             s.stream.wait_stream(slabs[(i + 1) % P].stream)
@@ -214,13 +252,18 @@ class DistComm:
         return self.dist.get_global_rank(self.group, r) if self.group is not None else r
 
     def exchange(self, slabs):
+        self.finish_exchange(slabs, self.post_exchange(slabs))
+
+    def post_exchange(self, slabs):
+        """Post the halo messages of the current set (ordered after the work
+        queued so far on the slab's stream); returns the requests."""
         (s,) = slabs
         dist = self.dist
         with _stream_ctx(s):
             if self.world == 1:          # the whole lattice: halos are its own planes
                 for msg in halo_plan():
                     s.plane(msg[2], recv_plane(msg, s.nzl)).copy_(s.plane(msg[2], send_plane(msg, s.nzl)))
-                return
+                return []
             up, down = self._global((self.rank + 1) % self.world), self._global((self.rank - 1) % self.world)
             reqs = []
             for msg in halo_plan():      # receive 'down' messages from above, 'up' ones from below
@@ -229,6 +272,12 @@ class DistComm:
             for msg in halo_plan():      # send 'down' messages below, 'up' ones above
                 reqs.append(dist.isend(s.plane(msg[2], send_plane(msg, s.nzl)), dst=down if msg[0] == "down" else up,
                                        tag=msg[1], group=self.group))
+            return reqs
+
+    def finish_exchange(self, slabs, reqs):
+        """Wait for the posted messages (NCCL: the slab's stream waits; gloo:
+        the host waits)."""
+        with _stream_ctx(slabs[0]):
             for r in reqs:
                 r.wait()
 
@@ -249,13 +298,25 @@ def _stream_ctx(slab):
     return torch.cuda.stream(stream)
 
 
+def overlap_ranges(nzl: int):
+    """The three z ranges of one overlapped slab step as (zfirst, zcount):
+    the interior, which reads no halo plane, then the two boundary pairs; None
+    for slabs of fewer than five planes (stepped whole)."""
+    if nzl < 5:
+        return None
+    return [(2, nzl - 4), (0, 2), (nzl - 2, 2)]
+
+
 class SlabEvolution:
     """Steps the slabs of one lattice together: ``slabs`` are the slabs this
-    process holds (all of them with LocalComm, one with DistComm)."""
+    process holds (all of them with LocalComm, one with DistComm). With
+    ``overlap`` the interior of every slab is stepped while its halo exchange
+    is in flight (overlap_ranges)."""
 
-    def __init__(self, slabs, comm):
+    def __init__(self, slabs, comm, overlap: bool = True):
         self.slabs = list(slabs)
         self.comm = comm
+        self.overlap = bool(overlap) and all(overlap_ranges(s.nzl) for s in self.slabs)
 
     def prepare(self):
         """Coefficients of the first step from the current fields (after a load)."""
@@ -267,8 +328,19 @@ class SlabEvolution:
 
     def step(self, n_steps: int = 1):
         for _ in range(int(n_steps)):
-            self.comm.exchange(self.slabs)
-            shares = [s.local_step() for s in self.slabs]
+            if self.overlap:
+                pending = self.comm.post_exchange(self.slabs)
+                for s in self.slabs:
+                    zf, zc = overlap_ranges(s.nzl)[0]
+                    s.local_step_range(zf, zc, 0)
+                self.comm.finish_exchange(self.slabs, pending)
+                for s in self.slabs:
+                    for slot, (zf, zc) in enumerate(overlap_ranges(s.nzl)[1:], start=1):
+                        s.local_step_range(zf, zc, slot)
+                shares = [s.range_total() for s in self.slabs]
+            else:
+                self.comm.exchange(self.slabs)
+                shares = [s.local_step() for s in self.slabs]
             totals = self.comm.allreduce(self.slabs, shares)
             for s, t in zip(self.slabs, totals):
                 s.advance(t, True)
@@ -280,5 +352,5 @@ class SlabEvolution:
         return tuple(np.concatenate([p[k] for p in parts], axis=0) for k in range(4))
 
 
-__all__ = ["slab_ranges", "halo_plan", "send_plane", "recv_plane", "SlabGPU", "LocalComm", "DistComm", "SlabEvolution",
-           "LatticeError"]
+__all__ = ["slab_ranges", "halo_plan", "send_plane", "recv_plane", "overlap_ranges", "SlabGPU", "LocalComm", "DistComm",
+           "SlabEvolution", "LatticeError"]

@@ -13,7 +13,7 @@ import torch
 from gpu_helpers import normwise
 from oracle.oracle import Oracle
 from paper_0911_5692_gb300 import Lattice
-from paper_0911_5692_gb300.slab import DistComm, LocalComm, SlabEvolution, SlabGPU, slab_ranges
+from paper_0911_5692_gb300.slab import DistComm, LocalComm, SlabEvolution, SlabGPU, overlap_ranges, slab_ranges
 from paper_0911_5692_gb300.workloads import lphi4, m2phi2, random_state
 
 pytestmark = pytest.mark.gpu
@@ -63,12 +63,16 @@ def test_slabs_match_single_lattice_fp64(parts):
         assert abs(sc["a"] / o.scalars()["a"] - 1) <= 1e-13
 
 
-@pytest.mark.parametrize("model,n,parts", [("m2phi2", 64, 3), ("lphi4", 128, 4)])
-def test_slabs_fp32_match_oracle(model, n, parts):
+@pytest.mark.parametrize("overlap", [False, True])
+@pytest.mark.parametrize("model,n,parts", [("m2phi2", 64, 3), ("lphi4", 128, 4), ("lphi4", 256, 2), ("m2phi2", 256, 3)])
+def test_slabs_fp32_match_oracle(model, n, parts, overlap):
+    """N = 256 takes the compiled warp-tile slab instance, the others the generic
+    plane ring; overlap: interior planes first, then the boundary pairs."""
     steps = 4
     p, st = _case(model, n, 32)
     slabs = _slabs(p, st, parts)
-    ev = SlabEvolution(slabs, LocalComm())
+    ev = SlabEvolution(slabs, LocalComm(), overlap=overlap)
+    assert ev.overlap == overlap
     ev.prepare()
     ev.step(steps)
     got = ev.gather()
@@ -107,3 +111,57 @@ def test_slab_refuses_whole_lattice_calls():
     assert L.lat_evolve(s._h, 1) == 8          # LAT_ESTATE
     assert L.lat_init_fields(s._h) == 8
     assert L.lat_set_kernel(s._h, 1, 0, 0, 0) == 8
+
+
+def _poison_halos(s):
+    """NaN in every halo plane of the slab's current set (stored 0, nzl + 1, nzl + 2)."""
+    with torch.cuda.stream(s.stream):
+        for a in range(4):
+            for q in (0, s.nzl + 1, s.nzl + 2):
+                s.plane(a, q).fill_(float("nan"))
+
+
+@pytest.mark.parametrize("n,prec,parts", [(256, 32, 2), (48, 64, 3)])
+def test_interior_range_reads_no_halo(n, prec, parts):
+    """Before each step the halo planes of every slab are NaN while the interior
+    range (planes 2 .. nzl - 3) is stepped; the exchange then fills them and the
+    boundary pairs are stepped. Any halo read by the interior range would carry
+    a NaN into the fields or the sums (a sticky non-finite status). N = 256 FP32:
+    the warp-tile slab instance; N = 48 FP64: the generic plane ring."""
+    steps = 3
+    p, st = _case("lphi4", n, prec)
+    slabs = _slabs(p, st, parts)
+    comm = LocalComm()
+    ev = SlabEvolution(slabs, comm)
+    ev.prepare()
+    for _ in range(steps):
+        for s in slabs:
+            _poison_halos(s)
+            zf, zc = overlap_ranges(s.nzl)[0]
+            s.local_step_range(zf, zc, 0)
+        comm.exchange(slabs)
+        for s in slabs:
+            for slot, (zf, zc) in enumerate(overlap_ranges(s.nzl)[1:], start=1):
+                s.local_step_range(zf, zc, slot)
+        totals = comm.allreduce(slabs, [s.range_total() for s in slabs])
+        for s, t in zip(slabs, totals):
+            s.advance(t, True)
+    got = ev.gather()
+    for s in slabs:
+        assert np.isfinite(s.scalars()["S"]).all()
+    o = Oracle(p)
+    o.set_state(*st, **SCAL)
+    o.step(steps)
+    tol = steps * (2e-6 if prec == 32 else 1e-12)
+    for a, b in zip(got, o.get_state()):
+        assert normwise(a, b) <= tol
+
+
+def test_range_arguments_checked():
+    p, st = _case("lphi4", 32, 32)
+    (s,) = _slabs(p, st, 1)
+    L = s._L
+    out = C.c_void_p(s.range_shares.data_ptr())
+    for zf, zc in ((-1, 2), (0, 0), (31, 2), (0, 33)):
+        assert L.lat_slab_step_range(s._h, zf, zc, out) == 1     # LAT_EINVAL
+    assert L.lat_slab_step_range(s._h, 0, 32, None) == 1

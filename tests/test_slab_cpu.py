@@ -20,7 +20,7 @@ import torch.distributed as dist
 import torch.multiprocessing as mp
 
 from oracle.oracle import Oracle
-from paper_0911_5692_gb300.slab import (DistComm, SlabEvolution, halo_plan, recv_plane, send_plane,
+from paper_0911_5692_gb300.slab import (DistComm, SlabEvolution, halo_plan, overlap_ranges, recv_plane, send_plane,
                                         slab_ranges)
 from paper_0911_5692_gb300.workloads import lphi4, m2phi2, random_state
 
@@ -58,6 +58,7 @@ class NumpySlab:
         self.dx = params["L"] / self.n
         self.dt = params["dt"]
         self.buffers = [torch.zeros((nzl + 3, self.n, self.n), dtype=torch.float64) for _ in range(8)]
+        self.range_shares = torch.zeros((3, 4), dtype=torch.float64)
         self.step_count = 0
         self.orc = Oracle(params)
         d = self.orc.derived()
@@ -127,6 +128,36 @@ class NumpySlab:
         self.buffers[4 * o + 3][1:self.nzl + 1] = torch.from_numpy(q1[:-1].copy())
         return self._shares(g0[:-1], g1[:-1], g0[-1], g1[-1])
 
+    def local_step_range(self, zfirst, zcount, slot):
+        """Step owned planes [zfirst, zfirst + zcount) from a copy of the current
+        set in which every stored plane outside the range's window (stored
+        zfirst .. zfirst + zcount + 2) is NaN, so a read outside the window
+        shows in the result."""
+        s = self.current_set()
+        lo, hi = zfirst, zfirst + zcount + 3          # stored window [lo, hi)
+        win = []
+        for k in range(4):
+            a = self.buffers[4 * s + k].numpy().copy()
+            a[:lo] = np.nan
+            a[hi:] = np.nan
+            win.append(a)
+        f0, f1, p0, p1 = win
+        co, dt = self.co, self.dt
+        c0, c1 = f0[lo + 1:hi - 1], f1[lo + 1:hi - 1]            # planes zfirst .. zfirst + zcount
+        l0, l1 = _lap(f0[lo:hi], self.dx), _lap(f1[lo:hi], self.dx)
+        dv0 = co["cdom"] * c0 ** (self.beta - 1) + co["kappa"] * c0 * c1 * c1
+        dv1 = co["kappa"] * c0 * c0 * c1
+        q0 = p0[lo + 1:hi - 1] + dt * (co["cL"] * l0 + co["cF"] * c0 - dv0)
+        q1 = p1[lo + 1:hi - 1] + dt * (co["cL"] * l1 + co["cF"] * c1 - dv1)
+        g0, g1 = c0 + dt * q0, c1 + dt * q1
+        o = 1 - s
+        for k, v in enumerate((g0, g1, q0, q1)):
+            self.buffers[4 * o + k][lo + 1:hi - 2] = torch.from_numpy(v[:-1].copy())
+        self.range_shares[slot] = self._shares(g0[:-1], g1[:-1], g0[-1], g1[-1])
+
+    def range_total(self):
+        return self.range_shares.sum(dim=0)
+
     def advance(self, total, advance):
         S = total.numpy().tolist()
         sc = self.sc
@@ -147,7 +178,41 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, model, steps, out_dir):
+class SlowComm(DistComm):
+    """DistComm as a slow network: post_exchange fills the receiving halo planes
+    with NaN and receives into side buffers, which finish_exchange copies into
+    the halos after the messages have landed. A step that reads a halo between
+    the two calls reads NaN, whatever the timing of the messages."""
+
+    def post_exchange(self, slabs):
+        (s,) = slabs
+        if self.world == 1:
+            return super().post_exchange(slabs)
+        up, down = self._global((self.rank + 1) % self.world), self._global((self.rank - 1) % self.world)
+        reqs, side = [], []
+        for msg in halo_plan():
+            dst = s.plane(msg[2], recv_plane(msg, s.nzl))
+            buf = torch.empty_like(dst)
+            side.append((dst, buf))
+            reqs.append(self.dist.irecv(buf, src=up if msg[0] == "down" else down, tag=msg[1], group=self.group))
+        for msg in halo_plan():
+            reqs.append(self.dist.isend(s.plane(msg[2], send_plane(msg, s.nzl)), dst=down if msg[0] == "down" else up,
+                                        tag=msg[1], group=self.group))
+        for dst, _ in side:
+            dst.fill_(float("nan"))
+        return reqs, side
+
+    def finish_exchange(self, slabs, pending):
+        if self.world == 1:
+            return super().finish_exchange(slabs, pending)
+        reqs, side = pending
+        for r in reqs:
+            r.wait()
+        for dst, buf in side:
+            dst.copy_(buf)
+
+
+def _worker(rank, world, port, model, steps, out_dir, overlap=False):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -156,7 +221,8 @@ def _worker(rank, world, port, model, steps, out_dir):
         z0, nzl = slab_ranges(N, world)[rank]
         s = NumpySlab(p, z0, nzl)
         s.load(*st, **SCAL)
-        ev = SlabEvolution([s], DistComm())
+        ev = SlabEvolution([s], SlowComm() if overlap else DistComm(), overlap=overlap)
+        assert ev.overlap == (overlap and nzl >= 5)
         ev.prepare()
         ev.step(steps)
         parts = [None] * world
@@ -184,10 +250,27 @@ def test_slab_ranges():
         slab_ranges(8, 5)
 
 
-@pytest.mark.parametrize("world,model", [(1, "lphi4"), (2, "lphi4"), (3, "m2phi2"), (4, "lphi4")])
-def test_distributed_slabs_match_single_domain_oracle(tmp_path, world, model):
+def test_overlap_ranges():
+    assert overlap_ranges(4) is None
+    assert overlap_ranges(5) == [(2, 1), (0, 2), (3, 2)]
+    for nzl in range(5, 40):
+        covered = sorted(z for zf, zc in overlap_ranges(nzl) for z in range(zf, zf + zc))
+        assert covered == list(range(nzl))       # every owned plane exactly once
+        zf, zc = overlap_ranges(nzl)[0]
+        # the interior's window (stored zf .. zf + zc + 2) holds no halo plane
+        assert zf >= 1 and zf + zc + 2 <= nzl
+
+
+@pytest.mark.parametrize("world,model,overlap", [(1, "lphi4", False), (2, "lphi4", False), (3, "m2phi2", False),
+                                                 (4, "lphi4", False), (1, "lphi4", True), (2, "m2phi2", True),
+                                                 (3, "lphi4", True)])
+def test_distributed_slabs_match_single_domain_oracle(tmp_path, world, model, overlap):
+    """overlap: the exchange is posted, the interior stepped from a window that
+    holds no halo, the exchange finished, the boundary pairs stepped; the
+    receiving halos are NaN from the post until finish_exchange (SlowComm), so a
+    range stepped out of order would fail."""
     steps = 7
-    mp.start_processes(_worker, args=(world, _free_port(), model, steps, str(tmp_path)), nprocs=world,
+    mp.start_processes(_worker, args=(world, _free_port(), model, steps, str(tmp_path), overlap), nprocs=world,
                        start_method="spawn", join=True)
     parts = np.load(os.path.join(tmp_path, "result.npy"), allow_pickle=True)
     parts = sorted(parts, key=lambda r: r[0])
