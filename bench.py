@@ -125,9 +125,9 @@ def measured_peaks():
         return None
 
 
-def traffic_record(name, variant, stencil=7):
+def traffic_record(name, variant, stencil=7, depth=None):
     """DRAM bytes per launch of the step kernel from a committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+    was taken on the current kernel sources with the same shape; else None."""
     path = os.path.join(ROOT, "profiles", "step_traffic.json")
     try:
         recs = json.load(open(path))
@@ -136,7 +136,7 @@ def traffic_record(name, variant, stencil=7):
     hsh = kernel_source_hash(stencil, variant)
     for r in recs.get("records", []):
         if (r.get("kernel_hash") == hsh and r.get("workload") == name and r.get("variant") == variant
-                and r.get("stencil", 7) == stencil):
+                and r.get("stencil", 7) == stencil and r.get("depth") == depth):
             return r.get("dram_bytes_per_launch")
     return None
 
@@ -802,7 +802,7 @@ def run_ours(args):
         peak, peak_src = FALLBACK_HBM_GBS, "fallback"
     bytes_per_launch = 32 * n ** 3 if esize == 4 else 64 * n ** 3
     achieved = bytes_per_launch / (ms_per_step / 1e3) / 1e9
-    traffic = traffic_record(args.workload, info["variant"], args.stencil)
+    traffic = traffic_record(args.workload, info["variant"], args.stencil, info["depth"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

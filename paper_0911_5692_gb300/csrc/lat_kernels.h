@@ -80,8 +80,9 @@ template <typename T>
 cudaError_t launch_step27(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
                           cudaStream_t st);
 // the warp-wide x tiles (lat_xw.cuh) on a range of nz owned planes of a z-slab
-// (N = 256, 512 FP32 and 256 FP64 compiled): cfg->nzl = nz; the launch takes the
-// stored plane of the range's first plane and writes the range's shares
+// (N = 256, 512 FP32 with two planes in flight and 256 FP64 with one compiled):
+// cfg->nzl = nz; the launch takes the stored plane of the range's first plane
+// and writes the range's shares
 bool slab_xw_config(int n, int elem_bytes, int nz, MarchConfig* cfg);
 template <typename T>
 cudaError_t launch_slab_xw(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,

@@ -10,17 +10,19 @@ namespace lat {
 namespace {
 
 template <typename T>
-const void* slab_xw_fn(int n, size_t* smem)
+const void* slab_xw_fn(int n, size_t* smem, int* depth)
 {
-#define LAT_SLAB_XW_CASE(NN)                                                  \
+#define LAT_SLAB_XW_CASE(NN, DD)                                              \
     if (n == NN) {                                                            \
-        *smem = xw::XW<T, NN, 16, 1, true>::SMEM;                             \
-        return (const void*)xw::step_xw_kernel<T, NN, 16, 1, true>;           \
+        *depth = DD;                                                          \
+        *smem = xw::XW<T, NN, 16, DD, true>::SMEM;                            \
+        return (const void*)xw::step_xw_kernel<T, NN, 16, DD, true>;          \
     }
+    // two planes in flight for FP32 (as the whole-lattice default), one for FP64
     if constexpr (sizeof(T) == 4) {
-        LAT_SLAB_XW_CASE(256) LAT_SLAB_XW_CASE(512)
+        LAT_SLAB_XW_CASE(256, 2) LAT_SLAB_XW_CASE(512, 2)
     } else {
-        LAT_SLAB_XW_CASE(256)
+        LAT_SLAB_XW_CASE(256, 1)
     }
 #undef LAT_SLAB_XW_CASE
     return nullptr;
@@ -32,7 +34,8 @@ bool slab_xw_config(int n, int elem_bytes, int nz, MarchConfig* cfg)
 {
     if (nz < 1) return false;
     size_t smem = 0;
-    const void* fn = elem_bytes == 4 ? slab_xw_fn<float>(n, &smem) : slab_xw_fn<double>(n, &smem);
+    int d = 1;
+    const void* fn = elem_bytes == 4 ? slab_xw_fn<float>(n, &smem, &d) : slab_xw_fn<double>(n, &smem, &d);
     if (!fn || smem > 227 * 1024 - 2048) return false;
     constexpr int ty = 16;
     const int vw = 16 / elem_bytes, w = 32 * vw, nxt = n / w;
@@ -49,7 +52,7 @@ bool slab_xw_config(int n, int elem_bytes, int nz, MarchConfig* cfg)
     cfg->ty = ty;
     cfg->zr = (int)((units + groups - 1) / groups);
     cfg->nzc = 0;
-    cfg->depth = 1;
+    cfg->depth = d;
     cfg->threads = threads;
     cfg->maxt = threads;
     cfg->fast = 1;
@@ -70,8 +73,9 @@ cudaError_t launch_slab_xw(const Bufs<T>& b, const Model& M, DevScalars* sc, dou
                            int zbase, double* sums_out, cudaStream_t st)
 {
     size_t smem = 0;
-    const void* fn = slab_xw_fn<T>(M.n, &smem);
-    if (!fn || !sums_out) return cudaErrorInvalidValue;
+    int d = 1;
+    const void* fn = slab_xw_fn<T>(M.n, &smem, &d);
+    if (!fn || !sums_out || d != cfg.depth) return cudaErrorInvalidValue;
     xw::SlabRun R{cfg.nzl, zbase, sums_out};
     void* args[] = {(void*)&b, (void*)&M, (void*)&sc, (void*)&partials, (void*)&R};
     return cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);

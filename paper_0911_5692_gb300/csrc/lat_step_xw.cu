@@ -47,15 +47,15 @@ const void* xw_kernel(int esize, int n, int ty, int depth, size_t* smem)
 bool xw_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg)
 {
     const int tyv = ty > 0 ? ty : 16;
-    // the instance with the requested depth, else any compiled depth (1 first:
-    // one plane in flight measured faster than two, 0.871 against 0.972 ms at
-    // 512^3 FP32)
+    // the instance with the requested depth, else any compiled depth (2 first:
+    // two planes in flight measured 0.811-0.816 against 0.860 ms per step at
+    // 512^3 FP32, 0.117 against 0.124 ms at 256^3)
     int d = depth;
     size_t smem = 0;
     const void* fn = nullptr;
     if (d > 0) fn = xw_kernel(elem_bytes, n, tyv, d, &smem);
     else
-        for (int dd : {1, 2})
+        for (int dd : {2, 1})
             if ((fn = xw_kernel(elem_bytes, n, tyv, dd, &smem))) {
                 d = dd;
                 break;
