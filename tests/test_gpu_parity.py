@@ -499,7 +499,7 @@ def test_fp64_full_size_512_two_steps():
 
 
 @pytest.mark.parametrize("prec", [32, 64])
-@pytest.mark.parametrize("n,depth", [(256, 1), (256, 2), (512, 1)])
+@pytest.mark.parametrize("n,depth", [(256, 1), (256, 2), (512, 1), (512, 2)])
 def test_warp_tile_kernel(n, depth, prec):
     """Variant 5 (x tiles one warp wide, compiled N, ty and depth, an edge warp
     for the tile's x neighbours and its boundary column) on its compiled sides:
