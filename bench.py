@@ -82,7 +82,7 @@ def config_of(name, p, world):
     n = p["n"]
     esize = 4 if p["precision"] == 32 else 8
     state = 8 * n ** 3 * esize
-    return {"workload": name, "model": model_name(p), "stencil": int(p.get("stencil", 7)), "n": n, "sites": n ** 3,
+    return {"workload": name, "potential": model_name(p), "stencil": int(p.get("stencil", 7)), "n": n, "sites": n ** 3,
             "precision": p["precision"],
             "storage": "phi as an FP64 homogeneous mode + fluctuation arrays" if p.get("split") else "fields whole",
             "expansion": bool(p["expansion"]),

@@ -1,15 +1,17 @@
 // lat_step_march.cu -- the fused leapfrog step on a shared-memory plane ring,
 // for any lattice side and tile height (FP32 and FP64).
 //
-// Same step as lat_step_simple.cu (Sec. II.B, eq. evo with eq. scalar-evo:
-// 7-point Laplacian, potential derivative, kick and drift of both fields; the
-// sums of the new fields for eq. scale from a one-site look-ahead rim; the FP64
-// a(t) update in the last block), laid out for the GB300 memory system. The
-// z-march segment itself (ring, asynchronous copies, look-ahead rim) is in
-// lat_march.cuh. Per-thread asynchronous copies keep enough bytes moving per SM
-// to run near the HBM rate on this access pattern; a ring filled by a few large
-// TMA boxes per block measured well below it (that variant is lat_step_tma.cu).
-// One persistent wave of blocks shares the (y tile, z plane) units evenly.
+// The step (Sec. II.B, eq. evo with eq. scalar-evo: 7-point Laplacian,
+// potential derivative, kick and drift of both fields; the sums of the new
+// fields for eq. scale from a one-site look-ahead rim; the FP64 a(t) update in
+// the last block), laid out for the GB300 memory system. The z-march segment
+// itself (ring, asynchronous copies, look-ahead rim) is in lat_march.cuh.
+// Per-thread asynchronous copies keep enough bytes moving per SM to run near
+// the HBM rate on this access pattern; a ring filled by a few large TMA boxes
+// per block measured well below it and was not kept. One persistent wave of
+// blocks shares the (y tile, z plane) units evenly. This file also holds the
+// launch dispatch of every step kernel (launch_step_march) and the process-wide
+// shared-memory opt-in (allow_dynamic_smem).
 #include <algorithm>
 #include <map>
 #include <mutex>
