@@ -364,3 +364,30 @@ def test_m2phi2_run_statistics_through_the_resonance():
             break
     assert end is not None, "no backreaction within 130000 steps"
     assert growth > 1e9, growth   # the run went through the resonance
+
+
+@pytest.mark.parametrize("expansion", [1, 2])
+def test_benchmark_configuration_512(expansion):
+    """The benchmark's workload as it runs: the 512^3 lambda phi^4 lattice in FP32
+    with phi stored split, the default kernel (variant 5, two planes in flight)
+    and eq. scale (expansion 1) or the L = 1/H form with its pass (expansion 2):
+    one step against the oracle's full-lattice step, the inflaton's fluctuations
+    to the per-step bound relative to their own size, a, a' and the sums."""
+    from paper_0911_5692_gb300.workloads import WORKLOADS
+    p = dict(WORKLOADS["lphi4_512_fp32"]["params"], expansion=expansion)
+    assert p["split"] == 1 and p["n"] == 512 and p["precision"] == 32
+    st = _state("lphi4", 512, 32, seed=512 + expansion)
+    g, o = _pair(p, st, (0.0, 1.02, 0.5, 0))
+    del st
+    info = g.kernel_info()
+    assert (info["variant"], info["depth"]) == (5, 2)
+    g.evolve(1)
+    o.step(1)
+    _check_step(g, o, 32, f"benchmark configuration 512 expansion {expansion}")
+    gs, os_ = g.scalars(), o.scalars()
+    assert abs(gs["a"] - os_["a"]) <= 1e-8 * os_["a"]
+    assert abs(gs["ad"] - os_["ad"]) <= 1e-7 * max(abs(os_["ad"]), 1.0)
+    for k, tol in enumerate([1e-5, 1e-5, 1e-7, 1e-5]):
+        ref = os_["S"][k]
+        assert abs(gs["S"][k] - ref) <= tol * abs(ref) + 1e-300, (k, gs["S"][k], ref)
+    o.close()
