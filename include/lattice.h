@@ -282,7 +282,9 @@ lat_status lat_load_checkpoint(lat_handle* h, const void* src, uint64_t bytes);
  * ty, zr and depth apply to it as above). */
 lat_status lat_set_kernel(lat_handle* h, int variant, int ty, int zr, int depth);
 
-/* Autotune the step kernel (the paper tunes its block size by hand, Sec. III):
+/* Autotune the step kernel (the paper finds its block size by trial and error,
+ * Sec. II.C, keeping 256 computing threads after trying 64, 128 and 256,
+ * Sec. III):
  * time `steps` steps (1 <= steps <= 100000, after a warm-up of 32 that also
  * captures the graph) for every kernel shape that can run this lattice --
  * variants 2, 4 and 5 over tile heights and prefetch depths (the 27-point
