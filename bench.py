@@ -666,6 +666,52 @@ def measure_fp32_error(local, name, steps=200):
             "phi split" if p.get("split") else "fields whole", "normwise": err, "a_rel": abs(s32["a"] / s64["a"] - 1)}
 
 
+def measure_run_statistics(local, name="m2phi2_256_fp32", every=250):
+    """Statistics over the whole run of a workload (its own step count): the FP32
+    lattice as the workload stores it (phi split) against an FP64 lattice with
+    phi whole, both initialised from the same seed by their own pipelines, the
+    volume statistics of lat_energies compared every `every` steps: the largest
+    relative deviation of a, rho, <phi>, var phi and var chi over the run, <chi>
+    relative to the spread of chi, and the step at which var chi first left its
+    starting value by 1 % (the growth of the resonance)."""
+    import math as _m
+    from paper_0911_5692_gb300 import Lattice
+    from paper_0911_5692_gb300.workloads import WORKLOADS
+    p = workload(name)
+    steps = int(WORKLOADS[name]["steps"])
+    g64 = fp64_twin(p, local)
+    g32 = Lattice(dict(p, precision=32), device=local)
+    g32.init_fields()
+    keys = {"a": "a", "rho": "rho", "mean_phi": "mean0", "var_phi": "var0", "var_chi": "var1"}
+    worst = {k: 0.0 for k in keys}
+    worst["mean_chi_over_std_chi"] = 0.0
+    var_chi0 = None
+    grows_at = None
+    trace = []
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        g32.evolve(k)
+        g64.evolve(k)
+        done += k
+        e32, e64 = g32.energies(), g64.energies()
+        for key, ek in keys.items():
+            worst[key] = max(worst[key], abs(e32[ek] - e64[ek]) / max(abs(e64[ek]), 1e-300))
+        worst["mean_chi_over_std_chi"] = max(worst["mean_chi_over_std_chi"],
+                                             abs(e32["mean1"] - e64["mean1"]) / max(_m.sqrt(max(e64["var1"], 0.0)), 1e-300))
+        if var_chi0 is None:
+            var_chi0 = e64["var1"]
+        elif grows_at is None and abs(e64["var1"] / var_chi0 - 1.0) > 0.01:
+            grows_at = done
+        trace.append([done, e64["var1"], e64["a"]])
+    g32.close()
+    g64.close()
+    return {"workload": name, "steps": steps, "every": every, "max_rel_dev": worst, "bound": 1e-3,
+            "within_bound": all(v <= 1e-3 for v in worst.values()), "var_chi_leaves_start_at_step": grows_at,
+            "var_chi_and_a_fp64": trace[:: max(1, len(trace) // 10)],
+            "against": "FP64 lattice (phi whole) from the same seed, its own initialisation"}
+
+
 def run_reference(args):
     """The FP64 CPU oracle timed as the reference arm, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -857,6 +903,7 @@ def run_ours(args):
         line["diagnostics"] = measure_diagnostics(local, args.workload)
         line["lform"] = measure_lform(local, args.workload)
         line["slabs_1gpu"] = measure_slabs(local)
+        line["run_statistics_256"] = measure_run_statistics(local)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     print(json.dumps(line), flush=True)
