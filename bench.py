@@ -384,16 +384,18 @@ def measure_ensemble(local, steps=200):
             "launch": {"blocks": info["blocks"], "threads": info["threads"], "graph": bool(info["graph"]),
                        "launches_per_evolve": info["launches"],
                        "ty_by_side": {str(p["n"]): t for p, t in zip(members, info["ty"])},
-                       "tuned_over": "block size x tile-height cap (lat_batch_tune)"},
+                       "depth": info["depth"], "tile_cap": info["tile_cap"],
+                       "tuned_over": "block size x tile-height cap x prefetch depth (lat_batch_tune)"},
             "fp64_error": dict(worst, steps=steps + 5, against="the same 64 members in FP64 (phi whole), same "
                                                                   "seeds; largest per-member normwise error")}
 
 
 def measure_slabs(local, parts=4, steps=200):
     """One 512^3 FP32 lambda phi^4 lattice (phi stored whole) cut into `parts`
-    z-slabs on one GPU, all on one stream: halos by device copies, shares added
-    on the device, the scale-factor update per slab; two steps (one per
-    ping-pong parity) captured in a CUDA graph and replayed. Both schedules
+    z-slabs on one GPU, all on one stream: the halo planes of all slabs in one
+    copy launch, the shares added and every slab's scale factor advanced in one
+    launch; two steps (one per ping-pong parity) captured in a CUDA graph and
+    replayed. Both schedules
     (plain: exchange, then each slab whole; overlap: each slab's interior,
     exchange, boundary pairs) against the same lattice stepped whole. On one GPU
     nothing overlaps; the line measures what the slab form costs in extra
@@ -451,7 +453,7 @@ def measure_slabs(local, parts=4, steps=200):
             assert np.isfinite(sl.scalars()["S"]).all()
         out["overlap" if overlap else "plain"] = {"ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": UNIT,
                                                   "over_whole": ms / whole_ms,
-                                                  "launches_per_step": parts * (3 if overlap else 1)}
+                                                  "launches_per_step": parts * (3 if overlap else 1) + 2}
         del g
     for sl in slabs:
         sl.close()

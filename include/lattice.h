@@ -430,6 +430,27 @@ lat_status lat_slab_step_range(lat_handle* h, int zfirst, int zcount, double* su
  * Asynchronous. */
 lat_status lat_slab_advance(lat_handle* h, const double* sums_dev, int advance);
 
+/* Steps (3) and (4) above for slabs of one lattice held by one process (one
+ * GPU), in one launch on the stream of slabs[0]: the nshares share vectors
+ * (device pointers, 4 doubles each; a slab's whole-step share or its range
+ * shares) are added in the order given, and every slab's scalars advance
+ * with that total, as lat_slab_advance would. The caller orders the other
+ * slabs' streams against slabs[0]'s (the shares written before the call, the
+ * next step after it). 1 <= nslabs <= 64, 1 <= nshares <= 192. LAT_EINVAL for
+ * null pointers, counts out of range or slabs of different lattices (side,
+ * precision, model, expansion, dt or L differ), LAT_ESTATE for a handle that
+ * is not a slab. Asynchronous. */
+lat_status lat_slab_advance_local(lat_handle* const* slabs, int nslabs, const double* const* shares, int nshares,
+                                  int advance);
+
+/* Copy `count` device regions of `bytes` bytes each (src[i] to dst[i]; the
+ * regions must not overlap) in one launch per 64 regions on cuda_stream: the
+ * halo exchange of slabs that one process holds. Every pointer and `bytes`
+ * must be multiples of 16 bytes (a plane of an even-sided lattice is), else
+ * LAT_EINVAL; null arrays or pointers and count < 0 are LAT_EINVAL too.
+ * count = 0 or bytes = 0 copies nothing. Asynchronous. */
+lat_status lat_copy_regions(void* const* dst, const void* const* src, int count, uint64_t bytes, void* cuda_stream);
+
 /* ---- Ensembles: independent lattices of uneven size and coupling stepped
  * together by one persistent launch. The paper evolves one lattice at a time
  * (Sec. II.C); every member here follows the same step (Sec. II.B, eq. evo with
@@ -458,18 +479,29 @@ lat_status lat_batch_evolve(lat_batch* b, int64_t n_steps);
  * member. */
 lat_status lat_batch_sync(lat_batch* b);
 
-/* Autotune the launch shape: time `steps` steps for each candidate pair of
- * block size (128 .. 1024) and tile-height cap (32, 16, 8, 4; each member takes
- * the largest tile height up to the cap that divides its side and fits the
- * block) on the ensemble itself, keep the fastest and cache it for this process
- * per (sizes, precision); ensembles created later with the same sizes and
- * precision start with it. Member states are saved before and restored after.
- * Synchronises. */
+/* Autotune the launch shape: time `steps` steps for each candidate of block
+ * size (128 .. 1024), tile-height cap (32, 16, 8, 4; each member takes the
+ * largest tile height up to the cap that divides its side and fits the block)
+ * and prefetch depth (1 or 2 planes in flight ahead of the computed one) on the
+ * ensemble itself, keep the fastest and cache it for this process per (sizes,
+ * precision); ensembles created later with the same sizes and precision start
+ * with it. Member states are saved before and restored after. Synchronises. */
 lat_status lat_batch_tune(lat_batch* b, int steps);
 
 /* The tile height (y rows per work unit) each member is stepped with:
  * ty (host, one int32 per member, in creation order). */
 lat_status lat_batch_tile_heights(lat_batch* b, int32_t* ty);
+
+/* The launch shape in use: out (host) = threads per block, tile-height cap,
+ * prefetch depth, blocks. */
+lat_status lat_batch_shape(lat_batch* b, int64_t out[4]);
+
+/* Step with the given shape from now on: threads per block (32 .. 1024),
+ * tile-height cap (1 .. 32) and prefetch depth (1 or 2); the values are those
+ * lat_batch_tune sweeps. LAT_EINVAL out of those ranges, LAT_EUNSUPPORTED if
+ * some member's tile does not fit the block or the shared memory. Waits for the
+ * stream first; the member states are not touched. */
+lat_status lat_batch_set_shape(lat_batch* b, int threads, int tycap, int depth);
 
 /* Self-test of the bounded grid barrier (failure detection without a fault):
  * launches the ensemble kernel so that its barrier waits for one block more

@@ -255,6 +255,7 @@ int maxt_of(int threads) { return threads <= 256 ? 256 : threads <= 512 ? 512 : 
 struct BatchShape {
     int threads = 0;
     int tycap = 32;       // largest tile height a member takes
+    int depth = 1;        // planes in flight ahead of the one computed
     int maxt = 0;
     size_t smem = 0;
     int blocks = 0;
@@ -262,7 +263,10 @@ struct BatchShape {
 };
 
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tuned;   // (sizes, precision) -> (block size, tile cap)
+struct TunedShape {
+    int threads, tycap, depth;
+};
+std::map<std::string, TunedShape> g_tuned;   // (sizes, precision) -> the fastest shape timed
 
 } // namespace
 
@@ -311,13 +315,14 @@ std::string tune_key(const lat_batch* b)
 }
 
 // Tile heights (each member the largest of 32, 16, ... 1 that divides its side,
-// is at most tycap and fits the block), ring size and resident blocks for a
-// block size; false if some member does not fit.
-bool shape_for(const lat_batch* b, int threads, int tycap, BatchShape* out)
+// is at most tycap and fits the block), ring size for the prefetch depth and
+// resident blocks for a block size; false if some member does not fit.
+bool shape_for(const lat_batch* b, int threads, int tycap, int depth, BatchShape* out)
 {
     BatchShape s;
     s.threads = threads;
     s.tycap = tycap;
+    s.depth = depth;
     s.maxt = maxt_of(threads);
     const int vw = (int)(16 / b->esize);
     size_t smem = 0;
@@ -327,13 +332,13 @@ bool shape_for(const lat_batch* b, int threads, int tycap, BatchShape* out)
         for (int ty : {32, 16, 8, 4, 2, 1}) {
             if (ty > n || ty > tycap || n % ty != 0) continue;
             if ((ty + 3) * (n / vw) > threads) continue;
-            if (ring_elems(n, ty, 1) * b->esize > 200 * 1024) continue;
+            if (ring_elems(n, ty, depth) * b->esize > 200 * 1024) continue;
             best = ty;
             break;
         }
         if (!best) return false;
         s.ty.push_back(best);
-        smem = std::max(smem, ring_elems(n, best, 1) * b->esize);
+        smem = std::max(smem, ring_elems(n, best, depth) * b->esize);
     }
     s.smem = smem;
     const void* fn = b->prec == 32 ? batch_fn<float>(s.maxt, b->split) : batch_fn<double>(s.maxt, b->split);
@@ -369,7 +374,7 @@ lat_status build_tables(lat_batch* b, const BatchShape& s)
         lats[l].M = h->M;
         for (int i = 0; i < 8; i++) lats[l].buf[i] = (T*)h->buf[i];
         lats[l].ty = ty;
-        lats[l].depth = 1;
+        lats[l].depth = s.depth;
         lats[l].seg_begin = (int)segs.size();
         const long long per_plane = (long long)n * ty;
         for (int yt = 0; yt < n / ty; yt++) {
@@ -414,10 +419,10 @@ lat_status build_tables(lat_batch* b, const BatchShape& s)
     return LAT_OK;
 }
 
-lat_status configure(lat_batch* b, int threads, int tycap)
+lat_status configure(lat_batch* b, int threads, int tycap, int depth)
 {
     BatchShape s;
-    if (!shape_for(b, threads, tycap, &s)) return LAT_EUNSUPPORTED;
+    if (!shape_for(b, threads, tycap, depth, &s)) return LAT_EUNSUPPORTED;
     return b->prec == 32 ? build_tables<float>(b, s) : build_tables<double>(b, s);
 }
 
@@ -484,24 +489,25 @@ lat_status run_steps(lat_batch* b, int64_t nsteps)
     return LAT_OK;
 }
 
-// Time candidate (block size, tile cap) pairs on the ensemble itself (state
-// saved and restored) and keep the fastest. Pairs that give every member the
-// same tile heights as a pair already listed, at the same block size, are one
-// candidate.
+// Time candidate shapes (block size, tile cap, prefetch depth) on the ensemble
+// itself (state saved and restored) and keep the fastest. Caps that give every
+// member the same tile heights as one already listed, at the same block size
+// and depth, are one candidate.
 lat_status autotune(lat_batch* b, int steps)
 {
     const std::string key = tune_key(b);
-    std::vector<std::pair<int, int>> cands;
-    for (int t : {128, 192, 256, 320, 384, 448, 512, 640, 768, 1024}) {
-        std::vector<std::vector<int>> seen;
-        for (int cap : {32, 16, 8, 4}) {
-            BatchShape s;
-            if (!shape_for(b, t, cap, &s)) continue;
-            if (std::find(seen.begin(), seen.end(), s.ty) != seen.end()) continue;
-            seen.push_back(s.ty);
-            cands.push_back({t, cap});
+    std::vector<TunedShape> cands;
+    for (int depth : {1, 2})
+        for (int t : {128, 192, 256, 320, 384, 448, 512, 640, 768, 1024}) {
+            std::vector<std::vector<int>> seen;
+            for (int cap : {32, 16, 8, 4}) {
+                BatchShape s;
+                if (!shape_for(b, t, cap, depth, &s)) continue;
+                if (std::find(seen.begin(), seen.end(), s.ty) != seen.end()) continue;
+                seen.push_back(s.ty);
+                cands.push_back({t, cap, depth});
+            }
         }
-    }
     if (cands.empty()) return LAT_EUNSUPPORTED;
     // save the current state of every member
     const int nl = b->count;
@@ -521,12 +527,12 @@ lat_status autotune(lat_batch* b, int steps)
             st = LAT_ECUDA;
     }
     if (cudaStreamSynchronize(b->stream) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
-    int best_t = 0, best_cap = 32;
+    TunedShape best{0, 32, 1};
     float best_ms = 0.0f;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == LAT_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = LAT_ECUDA;
     for (size_t c = 0; c < cands.size() && st == LAT_OK; c++) {
-        if (configure(b, cands[c].first, cands[c].second) != LAT_OK) continue;
+        if (configure(b, cands[c].threads, cands[c].tycap, cands[c].depth) != LAT_OK) continue;
         if (run_steps(b, 2) != LAT_OK) continue;   // warm-up and graph
         cudaEventRecord(e0, b->stream);
         lat_status rs = run_steps(b, steps);
@@ -537,7 +543,10 @@ lat_status autotune(lat_batch* b, int steps)
         if (ctl.status != LAT_OK) { st = (lat_status)ctl.status; break; }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (!best_t || ms < best_ms) { best_t = cands[c].first; best_cap = cands[c].second; best_ms = ms; }
+        if (!best.threads || ms < best_ms) {
+            best = cands[c];
+            best_ms = ms;
+        }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -553,12 +562,12 @@ lat_status autotune(lat_batch* b, int steps)
     if (cudaStreamSynchronize(b->stream) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
     for (void* p : save) cudaFree(p);
     if (st != LAT_OK) return st;
-    if (!best_t) return LAT_EUNSUPPORTED;
+    if (!best.threads) return LAT_EUNSUPPORTED;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tuned[key] = {best_t, best_cap};
+        g_tuned[key] = best;
     }
-    return configure(b, best_t, best_cap);
+    return configure(b, best.threads, best.tycap, best.depth);
 }
 
 } // namespace
@@ -598,17 +607,17 @@ lat_status lat_batch_create(const lat_params* params, int count, void* cuda_stre
                          cudaMemset(b->dctl, 0, sizeof(BatchCtl)) != cudaSuccess))
         st = LAT_ECUDA;
     if (st == LAT_OK) {
-        std::pair<int, int> tuned{0, 32};
+        TunedShape tuned{0, 32, 1};
         {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
             auto it = g_tuned.find(tune_key(b));
             if (it != g_tuned.end()) tuned = it->second;
         }
-        if (tuned.first) st = configure(b, tuned.first, tuned.second);
+        if (tuned.threads) st = configure(b, tuned.threads, tuned.tycap, tuned.depth);
         else {
             st = LAT_EUNSUPPORTED;
             for (int t : {256, 512, 384, 640, 768, 1024, 128})
-                if ((st = configure(b, t, 32)) == LAT_OK) break;
+                if ((st = configure(b, t, 32, 1)) == LAT_OK) break;
         }
     }
     if (st != LAT_OK) {
@@ -667,6 +676,25 @@ lat_status lat_batch_tile_heights(lat_batch* b, int32_t* ty)
 {
     if (!b || !ty) return LAT_EINVAL;
     for (int i = 0; i < b->count; i++) ty[i] = b->shape.ty[i];
+    return LAT_OK;
+}
+
+lat_status lat_batch_set_shape(lat_batch* b, int threads, int tycap, int depth)
+{
+    if (!b || threads < 32 || threads > 1024 || tycap < 1 || tycap > 32 || depth < 1 || depth > 2) return LAT_EINVAL;
+    LAT_CUDA(cudaStreamSynchronize(b->stream));
+    BatchShape s;
+    if (!shape_for(b, threads, tycap, depth, &s)) return LAT_EUNSUPPORTED;
+    return configure(b, threads, tycap, depth);
+}
+
+lat_status lat_batch_shape(lat_batch* b, int64_t out[4])
+{
+    if (!b || !out) return LAT_EINVAL;
+    out[0] = b->shape.threads;
+    out[1] = b->shape.tycap;
+    out[2] = b->shape.depth;
+    out[3] = b->shape.blocks;
     return LAT_OK;
 }
 

@@ -23,6 +23,7 @@
 // the halos are still in flight; planes 0, 1 and nzl - 2, nzl - 1 follow once
 // the halos are in, and are the planes the neighbours need for the next step.
 #include <algorithm>
+#include <cstdint>
 
 #include "lat_internal.h"
 #include "lat_site.cuh"
@@ -80,6 +81,57 @@ __global__ void slab_advance_kernel(Model M, DevScalars* sc, const double* sums,
     advance_scalars(M, s, S, advance != 0);
     s.ticket = 0u;
     *sc = s;
+}
+
+// The scalars of every slab of a lattice held by this process after one step
+// (advance = 0: the coefficients of the first step), in one launch: each thread
+// adds the shares in the order given (so every slab sees the same total, bit
+// for bit, as after an allreduce in that order) and advances its own slab.
+constexpr int kMaxLocalSlabs = 64, kMaxLocalShares = 192;
+
+struct LocalAdvance {
+    DevScalars* sc[kMaxLocalSlabs];
+    const double* share[kMaxLocalShares];
+};
+
+__global__ void slab_advance_local_kernel(Model M, LocalAdvance A, int nslabs, int nshares, int advance)
+{
+    const int i = threadIdx.x;
+    if (i >= nslabs || blockIdx.x != 0) return;
+    double S[kSums] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < nshares; j++)
+        for (int k = 0; k < kSums; k++) S[k] += A.share[j][k];
+    DevScalars s = *A.sc[i];
+    if (s.status != LAT_OK) return;
+    advance_scalars(M, s, S, advance != 0);
+    s.ticket = 0u;
+    *A.sc[i] = s;
+}
+
+// Equal-sized device regions copied in one launch (the halo planes of the slabs
+// a process holds): blockIdx.y picks the region, the x blocks stride over its
+// 16-byte words, four in flight per thread.
+constexpr int kCopyChunk = 64;
+
+struct CopyList {
+    const uint4* src[kCopyChunk];
+    uint4* dst[kCopyChunk];
+};
+
+__global__ void __launch_bounds__(256) copy_regions_kernel(CopyList L, size_t words)
+{
+    const uint4* __restrict__ s = L.src[blockIdx.y];
+    uint4* __restrict__ d = L.dst[blockIdx.y];
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < words; i += 4 * stride) {
+        const uint4 a = s[i], b = s[i + stride], c = s[i + 2 * stride], e = s[i + 3 * stride];
+        d[i] = a;
+        d[i + stride] = b;
+        d[i + 2 * stride] = c;
+        d[i + 3 * stride] = e;
+    }
+    for (; i < words; i += stride) d[i] = s[i];
 }
 
 int slab_sum_blocks(int n)
@@ -181,6 +233,51 @@ lat_status lat_slab_advance(lat_handle* h, const double* sums_dev, int advance)
     if (!h->slab) return LAT_ESTATE;
     slab_advance_kernel<<<1, 32, 0, h->stream>>>(h->M, h->sc, sums_dev, advance);
     return cuda_status(cudaGetLastError());
+}
+
+lat_status lat_slab_advance_local(lat_handle* const* slabs, int nslabs, const double* const* shares, int nshares,
+                                  int advance)
+{
+    if (!slabs || !shares || nslabs < 1 || nslabs > kMaxLocalSlabs || nshares < 1 || nshares > kMaxLocalShares)
+        return LAT_EINVAL;
+    LocalAdvance A = {};
+    for (int i = 0; i < nslabs; i++) {
+        const lat_handle* h = slabs[i];
+        if (!h) return LAT_EINVAL;
+        if (!h->slab) return LAT_ESTATE;
+        if (h->p.n != slabs[0]->p.n || h->prec != slabs[0]->prec || h->p.model != slabs[0]->p.model ||
+            h->p.expansion != slabs[0]->p.expansion || h->p.dt != slabs[0]->p.dt || h->p.L != slabs[0]->p.L)
+            return LAT_EINVAL;   // not slabs of one lattice
+        A.sc[i] = h->sc;
+    }
+    for (int j = 0; j < nshares; j++) {
+        if (!shares[j]) return LAT_EINVAL;
+        A.share[j] = shares[j];
+    }
+    slab_advance_local_kernel<<<1, 64, 0, slabs[0]->stream>>>(slabs[0]->M, A, nslabs, nshares, advance);
+    return cuda_status(cudaGetLastError());
+}
+
+lat_status lat_copy_regions(void* const* dst, const void* const* src, int count, uint64_t bytes, void* cuda_stream)
+{
+    if (!dst || !src || count < 0) return LAT_EINVAL;
+    if (count == 0 || bytes == 0) return LAT_OK;
+    if (bytes % 16 != 0) return LAT_EINVAL;
+    for (int i = 0; i < count; i++)
+        if (!dst[i] || !src[i] || ((uintptr_t)dst[i] | (uintptr_t)src[i]) % 16 != 0) return LAT_EINVAL;
+    const size_t words = bytes / 16;
+    const unsigned int bx = (unsigned int)std::min<size_t>((words + 1023) / 1024, 128);
+    for (int c0 = 0; c0 < count; c0 += kCopyChunk) {
+        const int nc = std::min(kCopyChunk, count - c0);
+        CopyList L = {};
+        for (int i = 0; i < nc; i++) {
+            L.src[i] = (const uint4*)src[c0 + i];
+            L.dst[i] = (uint4*)dst[c0 + i];
+        }
+        copy_regions_kernel<<<dim3(bx, (unsigned int)nc), 256, 0, (cudaStream_t)cuda_stream>>>(L, words);
+        LAT_CUDA(cudaGetLastError());
+    }
+    return LAT_OK;
 }
 
 } // extern "C"

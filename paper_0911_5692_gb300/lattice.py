@@ -28,7 +28,8 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_batch_destroy", "lat_batch_check_barrier", "lat_slab_create", "lat_slab_sums", "lat_slab_step",
             "lat_slab_advance", "lat_energy_field", "lat_upload_state", "lat_get_hubble_length",
             "lat_set_hubble_length", "lat_download_state", "lat_get_background", "lat_set_background",
-            "lat_recenter", "lat_tune", "lat_batch_tile_heights", "lat_slab_step_range")
+            "lat_recenter", "lat_tune", "lat_batch_tile_heights", "lat_slab_step_range", "lat_batch_shape",
+            "lat_batch_set_shape", "lat_slab_advance_local", "lat_copy_regions")
 
 
 class LatParams(C.Structure):
@@ -99,6 +100,10 @@ def load_library(build_if_missing: bool = True):
             L.lat_kernel_info.argtypes = [P, i64p]
             L.lat_tune.argtypes = [P, C.c_int, i64p]
             L.lat_batch_tile_heights.argtypes = [P, C.POINTER(C.c_int32)]
+            L.lat_batch_shape.argtypes = [P, i64p]
+            L.lat_batch_set_shape.argtypes = [P, C.c_int, C.c_int, C.c_int]
+            L.lat_slab_advance_local.argtypes = [C.POINTER(P), C.c_int, C.POINTER(P), C.c_int, C.c_int]
+            L.lat_copy_regions.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int, C.c_uint64, P]
             L.lat_checkpoint_bytes.argtypes = [P, C.POINTER(C.c_uint64)]
             L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
             L.lat_load_checkpoint.argtypes = [P, P, C.c_uint64]
@@ -526,6 +531,11 @@ class Ensemble:
     def tune(self, steps: int = 10):
         _check(self._L.lat_batch_tune(self._h, int(steps)), "lat_batch_tune")
 
+    def set_shape(self, threads: int, tile_cap: int, depth: int = 1):
+        """Step with this launch shape (threads per block, tile-height cap,
+        prefetch depth) from now on."""
+        _check(self._L.lat_batch_set_shape(self._h, int(threads), int(tile_cap), int(depth)), "lat_batch_set_shape")
+
     def check_barrier(self, timeout_ns: int = 200_000_000) -> int:
         """Run the bounded-barrier self-test; returns the lat_status it ends with
         (LAT_ETIMEOUT = 6 when the timeout works)."""
@@ -539,6 +549,9 @@ class Ensemble:
         ty = (C.c_int32 * len(self.params))()
         _check(self._L.lat_batch_tile_heights(self._h, ty), "lat_batch_tile_heights")
         info["ty"] = [int(v) for v in ty]
+        shape = (C.c_int64 * 4)()
+        _check(self._L.lat_batch_shape(self._h, shape), "lat_batch_shape")
+        info["tile_cap"], info["depth"] = int(shape[1]), int(shape[2])
         return info
 
     def member(self, i: int) -> Lattice:

@@ -189,8 +189,11 @@ class SlabGPU:
 
 
 class LocalComm:
-    """All slabs of the lattice in this process: halos by device copies, the
-    allreduce by adding the shares on the device."""
+    """All slabs of the lattice in this process (SlabGPU on one GPU): halos by
+    device copies (lat_copy_regions: every plane of the exchange in one launch
+    when the slabs share a stream, else one launch per slab), the allreduce and
+    the scale-factor update of every slab in one launch
+    (lat_slab_advance_local)."""
 
     def post_exchange(self, slabs):
         self.exchange(slabs)
@@ -199,28 +202,56 @@ class LocalComm:
     def finish_exchange(self, slabs, pending):
         pass
 
+    @staticmethod
+    def _copy(dst, src, stream):
+        L = load_library()
+        if not dst:
+            return
+        nbytes = dst[0].numel() * dst[0].element_size()
+        d = (C.c_void_p * len(dst))(*[t.data_ptr() for t in dst])
+        q = (C.c_void_p * len(src))(*[t.data_ptr() for t in src])
+        _check(L.lat_copy_regions(d, q, len(dst), nbytes, C.c_void_p(stream.cuda_stream)), "lat_copy_regions")
+
     def exchange(self, slabs):
-        import torch
         P = len(slabs)
+        plans = []
         for i, s in enumerate(slabs):
             above, below = slabs[(i + 1) % P], slabs[(i - 1) % P]
-            s.stream.wait_stream(above.stream)
-            s.stream.wait_stream(below.stream)
             dst, src = [], []
             for msg in halo_plan():
                 nb = above if msg[0] == "down" else below
                 dst.append(s.plane(msg[2], recv_plane(msg, s.nzl)))
                 src.append(nb.plane(msg[2], send_plane(msg, nb.nzl)))
-            with torch.cuda.stream(s.stream):
-                if hasattr(torch, "_foreach_copy_"):    # the slab's eight planes in one multi-tensor copy
-                    torch._foreach_copy_(dst, src)
-                else:
-                    for d, q in zip(dst, src):
-                        d.copy_(q)
+            plans.append((dst, src))
+        if all(s.stream.cuda_stream == slabs[0].stream.cuda_stream for s in slabs):
+            self._copy([d for dst, _ in plans for d in dst], [q for _, src in plans for q in src], slabs[0].stream)
+            return
+        for i, (s, (dst, src)) in enumerate(zip(slabs, plans)):
+            s.stream.wait_stream(slabs[(i + 1) % P].stream)
+            s.stream.wait_stream(slabs[(i - 1) % P].stream)
+            self._copy(dst, src, s.stream)
         # a slab's planes are read above before it may write them again
         for i, s in enumerate(slabs):
             s.stream.wait_stream(slabs[(i + 1) % P].stream)
             s.stream.wait_stream(slabs[(i - 1) % P].stream)
+
+    def reduce_advance(self, slabs, shares, advance: bool):
+        """Add the shares (device tensors of four doubles, in the order given)
+        and advance the scalars of every slab with the total, in one launch on
+        the first slab's stream."""
+        L = load_library()
+        s0 = slabs[0]
+        for s in slabs[1:]:
+            s0.stream.wait_stream(s.stream)
+        hs = (C.c_void_p * len(slabs))(*[s._h.value for s in slabs])
+        ptrs = (C.c_void_p * len(shares))(*[t.data_ptr() for t in shares])
+        _check(L.lat_slab_advance_local(hs, len(slabs), ptrs, len(shares), 1 if advance else 0),
+               "lat_slab_advance_local")
+        for s in slabs[1:]:
+            s.stream.wait_stream(s0.stream)
+        if advance:
+            for s in slabs:
+                s.step_count += 1
 
     def allreduce(self, slabs, shares):
         import torch
@@ -318,15 +349,25 @@ class SlabEvolution:
         self.comm = comm
         self.overlap = bool(overlap) and all(overlap_ranges(s.nzl) for s in self.slabs)
 
+    def _advance(self, shares, advance: bool):
+        """Steps 3 and 4: the allreduce of the shares and the scale-factor
+        update, fused into one call where the communicator offers it (slabs of
+        one process)."""
+        fused = getattr(self.comm, "reduce_advance", None)
+        if fused is not None:
+            fused(self.slabs, shares, advance)
+            return
+        totals = self.comm.allreduce(self.slabs, shares)
+        for s, t in zip(self.slabs, totals):
+            s.advance(t, advance)
+
     def prepare(self):
         """Coefficients of the first step from the current fields (after a load)."""
         self.comm.exchange(self.slabs)
-        shares = [s.local_sums() for s in self.slabs]
-        totals = self.comm.allreduce(self.slabs, shares)
-        for s, t in zip(self.slabs, totals):
-            s.advance(t, False)
+        self._advance([s.local_sums() for s in self.slabs], False)
 
     def step(self, n_steps: int = 1):
+        fused = hasattr(self.comm, "reduce_advance")
         for _ in range(int(n_steps)):
             if self.overlap:
                 pending = self.comm.post_exchange(self.slabs)
@@ -337,13 +378,14 @@ class SlabEvolution:
                 for s in self.slabs:
                     for slot, (zf, zc) in enumerate(overlap_ranges(s.nzl)[1:], start=1):
                         s.local_step_range(zf, zc, slot)
-                shares = [s.range_total() for s in self.slabs]
+                if fused:    # the three range shares of every slab go to the fused sum as they are
+                    shares = [s.range_shares[k] for s in self.slabs for k in range(3)]
+                else:
+                    shares = [s.range_total() for s in self.slabs]
             else:
                 self.comm.exchange(self.slabs)
                 shares = [s.local_step() for s in self.slabs]
-            totals = self.comm.allreduce(self.slabs, shares)
-            for s, t in zip(self.slabs, totals):
-                s.advance(t, True)
+            self._advance(shares, True)
 
     def gather(self):
         """Full-lattice arrays (f0, f1, pi0, pi1) from the slabs of this process

@@ -138,7 +138,40 @@ def test_null_arguments():
     assert L.lat_recenter(None) == 1
     assert L.lat_tune(None, 10, None) == 1
     assert L.lat_batch_tile_heights(None, None) == 1
+    assert L.lat_batch_shape(None, None) == 1
+    assert L.lat_batch_set_shape(None, 256, 8, 1) == 1
+    assert L.lat_slab_advance_local(None, 1, None, 1, 1) == 1
+    assert L.lat_copy_regions(None, None, 1, 16, None) == 1
     L.lat_destroy(None)
+
+
+def test_copy_regions_argument_errors():
+    """lat_copy_regions checks its arguments before any CUDA call: a size or a
+    pointer that is not a multiple of 16 bytes, a null entry and a negative
+    count are LAT_EINVAL; nothing to copy is LAT_OK."""
+    L = pkg.load_library()
+    P = C.c_void_p
+    good = (P * 2)(4096, 8192)
+    odd = (P * 2)(4096, 8200)
+    null = (P * 2)(4096, None)
+    assert L.lat_copy_regions(good, good, 2, 24, None) == 1
+    assert L.lat_copy_regions(odd, good, 2, 32, None) == 1
+    assert L.lat_copy_regions(good, null, 2, 32, None) == 1
+    assert L.lat_copy_regions(good, good, -1, 32, None) == 1
+    assert L.lat_copy_regions(good, good, 0, 32, None) == 0
+    assert L.lat_copy_regions(good, good, 2, 0, None) == 0
+
+
+def test_slab_advance_local_argument_errors():
+    L = pkg.load_library()
+    P = C.c_void_p
+    hs = (P * 1)(None)
+    sh = (P * 1)(None)
+    assert L.lat_slab_advance_local(hs, 0, sh, 1, 1) == 1
+    assert L.lat_slab_advance_local(hs, 65, sh, 1, 1) == 1
+    assert L.lat_slab_advance_local(hs, 1, sh, 0, 1) == 1
+    assert L.lat_slab_advance_local(hs, 1, sh, 193, 1) == 1
+    assert L.lat_slab_advance_local(hs, 1, sh, 1, 1) == 1      # null handle
 
 
 @pytest.mark.parametrize("case", ["null_phi", "null_chi", "null_out", "precision", "model", "L", "small"])

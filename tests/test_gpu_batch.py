@@ -109,20 +109,21 @@ def test_tune_restores_state_and_keeps_results():
 
 
 def test_tuned_shape_is_taken_by_new_ensembles():
-    """lat_batch_tune sweeps block size x tile-height cap; every member's tile
-    height divides its side and stays within 32, and an ensemble created later
-    with the same sizes and precision starts with the tuned shape."""
+    """lat_batch_tune sweeps block size x tile-height cap x prefetch depth; every
+    member's tile height divides its side and stays within 32, and an ensemble
+    created later with the same sizes and precision starts with the tuned shape."""
     ps, states = _members(32, sizes=(32, 64, 96))
     ens = Ensemble(ps)
     _load(ens, states)
     ens.tune(3)
     info = ens.info()
     assert len(info["ty"]) == len(ps)
+    assert info["depth"] in (1, 2)
     for p, ty in zip(ps, info["ty"]):
         assert 1 <= ty <= 32 and p["n"] % ty == 0
     again = Ensemble([dict(p, seed=p["seed"] + 100) for p in ps])
     info2 = again.info()
-    assert (info2["threads"], info2["ty"]) == (info["threads"], info["ty"])
+    assert (info2["threads"], info2["ty"], info2["depth"]) == (info["threads"], info["ty"], info["depth"])
     _load(again, states)
     again.evolve(3)
     again.sync()
@@ -132,6 +133,50 @@ def test_tuned_shape_is_taken_by_new_ensembles():
         o.step(3)
         for a, b in zip(again.member(i).get_state(), o.get_state()):
             assert normwise(a, b) <= 3 * TOL[32]
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("threads,cap,depth", [(192, 4, 2), (256, 8, 2), (512, 32, 2), (384, 16, 1)])
+def test_launch_shapes_match_oracle(prec, threads, cap, depth):
+    """Every shape the tuner may pick steps the members as the oracle does: one
+    or two planes in flight, tile heights from 4 to 32 (many short ranges per
+    member at the small caps)."""
+    ps, states = _members(prec)
+    ens = Ensemble(ps)
+    _load(ens, states)
+    ens.set_shape(threads, cap, depth)
+    info = ens.info()
+    assert (info["threads"], info["tile_cap"], info["depth"]) == (threads, cap, depth)
+    steps = 5
+    ens.evolve(steps)
+    ens.sync()
+    for i, (p, st) in enumerate(zip(ps, states)):
+        o = Oracle(p)
+        o.set_state(*st, **SCAL)
+        o.step(steps)
+        for a, b in zip(ens.member(i).get_state(), o.get_state()):
+            assert normwise(a, b) <= steps * TOL[prec], (i, normwise(a, b))
+
+
+def test_set_shape_refusals():
+    """Out-of-range shapes are LAT_EINVAL; a block too small for a member's
+    tile is LAT_EUNSUPPORTED; the ensemble keeps its shape and still steps."""
+    from paper_0911_5692_gb300.lattice import LatticeError
+    ps, states = _members(32, sizes=(32, 96))
+    ens = Ensemble(ps)
+    _load(ens, states)
+    before = ens.info()
+    for args in ((256, 8, 3), (256, 0, 1), (16, 8, 1), (2048, 8, 1)):
+        with pytest.raises(LatticeError) as e:
+            ens.set_shape(*args)
+        assert e.value.status == 1
+    with pytest.raises(LatticeError) as e:
+        ens.set_shape(64, 32, 1)          # a side-96 tile needs (ty + 3) rows of 24 threads: none fits 64
+    assert e.value.status == 7
+    after = ens.info()
+    assert (after["threads"], after["ty"], after["depth"]) == (before["threads"], before["ty"], before["depth"])
+    ens.evolve(2)
+    ens.sync()
 
 
 def test_static_members():

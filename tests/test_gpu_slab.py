@@ -165,3 +165,72 @@ def test_range_arguments_checked():
     for zf, zc in ((-1, 2), (0, 0), (31, 2), (0, 33)):
         assert L.lat_slab_step_range(s._h, zf, zc, out) == 1     # LAT_EINVAL
     assert L.lat_slab_step_range(s._h, 0, 32, None) == 1
+
+
+def test_copy_regions_bit_exact():
+    """lat_copy_regions moves every region whole (70 regions: two launches of
+    at most 64), leaves the bytes around them alone and copies nothing for
+    count 0."""
+    from paper_0911_5692_gb300.lattice import load_library
+    L = load_library()
+    g = torch.Generator(device="cuda").manual_seed(3)
+    words = 4 * 1031                      # 16.5 KB regions, not a multiple of the block stride
+    src = torch.randint(-2**31, 2**31 - 1, (70, words + 8), dtype=torch.int32, device="cuda", generator=g)
+    dst = torch.zeros_like(src)
+    stream = torch.cuda.current_stream()
+    d = (C.c_void_p * 70)(*[dst[i].data_ptr() for i in range(70)])
+    q = (C.c_void_p * 70)(*[src[i].data_ptr() for i in range(70)])
+    assert L.lat_copy_regions(d, q, 70, words * 4, C.c_void_p(stream.cuda_stream)) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(dst[:, :words], src[:, :words])
+    assert not dst[:, words:].any()
+    assert L.lat_copy_regions(d, q, 0, words * 4, C.c_void_p(stream.cuda_stream)) == 0
+
+
+@pytest.mark.parametrize("parts", [2, 4])
+def test_fused_advance_matches_allreduce(parts):
+    """lat_slab_advance_local (shares added in the order given, every slab
+    advanced in one launch) gives the scalars of an allreduce followed by
+    lat_slab_advance on each slab, to the rounding of the sum's order."""
+    n = 64
+    p, st = _case("m2phi2", n, 64)
+    a = _slabs(p, st, parts)
+    b = _slabs(p, st, parts)
+    comm = LocalComm()
+    for slabs in (a, b):
+        comm.exchange(slabs)
+    shares_a = [s.local_sums() for s in a]
+    comm.reduce_advance(a, shares_a, False)
+    totals = comm.allreduce(b, [s.local_sums() for s in b])
+    for s, t in zip(b, totals):
+        s.advance(t, False)
+    for slabs in (a, b):
+        comm.exchange(slabs)
+    comm.reduce_advance(a, [s.local_step() for s in a], True)
+    totals = comm.allreduce(b, [s.local_step() for s in b])
+    for s, t in zip(b, totals):
+        s.advance(t, True)
+    for x, y in zip(a, b):
+        sx, sy = x.scalars(), y.scalars()
+        assert sx["step"] == sy["step"] == 1 and x.step_count == y.step_count == 1
+        for k in ("t", "a", "ad"):
+            assert abs(sx[k] - sy[k]) <= 1e-14 * max(1.0, abs(sy[k])), k
+        for u, v in zip(sx["S"], sy["S"]):
+            assert abs(u - v) <= 1e-14 * max(1.0, abs(v))
+    sa = [x.scalars() for x in a]
+    assert all(s == sa[0] for s in sa[1:])      # one total: every slab holds the same scalars
+
+
+def test_fused_advance_refusals():
+    from paper_0911_5692_gb300.lattice import load_library
+    L = load_library()
+    p, st = _case("lphi4", 32, 32)
+    s32 = _slabs(p, st, 2)
+    q, st2 = _case("lphi4", 48, 32)
+    (s48,) = _slabs(q, st2, 1)
+    sh = (C.c_void_p * 1)(s32[0].shares.data_ptr())
+    mixed = (C.c_void_p * 2)(s32[0]._h.value, s48._h.value)
+    assert L.lat_slab_advance_local(mixed, 2, sh, 1, 1) == 1        # slabs of different lattices
+    g = Lattice(p)
+    whole = (C.c_void_p * 1)(g._h.value)
+    assert L.lat_slab_advance_local(whole, 1, sh, 1, 1) == 8        # not a slab: LAT_ESTATE
