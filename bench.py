@@ -1051,7 +1051,9 @@ def run_slabs(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": own_bytes,
                 "d2h_bytes_per_step": own_bytes + 64 * len(slabs), "steps": E,
                 "per_step": "the owned planes of every slab up from pinned host memory, one step, back, and the scalars"},
-        "gpu_launches": K * len(slabs) * ((3 if ev.overlap else 1) + 1),
+        # per step: the slab step ranges; one rank holding every slab adds one halo
+        # copy and one fused sum + scale-factor update, a rank of many one update
+        "gpu_launches": K * (len(slabs) * (3 if ev.overlap else 1) + (2 if world == 1 else 1)),
         "clocks": clocks.summary(),
         "slabs": {"count": parts, "schedule": "overlap" if ev.overlap else "plain",
                   "planes": [nzl for _, nzl in ranges]},
