@@ -815,11 +815,14 @@ def run_ours(args):
     value = world * n ** 3 * args.steps / sec
     ms_per_step = ms_max / args.steps
 
-    # end to end through the C ABI with host buffers: every step uploads the
-    # stored state (4 arrays) from pinned host memory (lat_upload_state), advances
-    # one step (the sums of the uploaded fields, then the fused step), and copies
-    # the evolved state back into the same host arrays (lat_download_state) and
-    # the scalars (t, a, a', step, sums; lat_get_scalars).
+    # end to end through the C ABI with host buffers (lat_evolve_host): every step
+    # uploads the stored state (4 arrays) from pinned host memory, advances one
+    # step (the sums of the uploaded fields, then the fused step) and copies the
+    # evolved state back into the same host arrays, with the scalars of every
+    # step; the copies run in z-chunks, one stream per direction, so a step's
+    # download and the next step's upload share the link. The same steps call by
+    # call (lat_upload_state, lat_evolve, lat_download_state, lat_get_scalars:
+    # one direction at a time) are timed after it.
     E = max(1, args.e2e_steps)
     host = []
     for w in (2, 3):
@@ -830,21 +833,34 @@ def run_ours(args):
             host.append(hbuf)
     lib, h = lat._L, lat._h
     out8 = (C.c_double * 8)()
+    rows = (C.c_double * (8 * E))()
     bufs = (C.c_void_p * 4)(*[hbuf.data_ptr() for hbuf in host])   # f0, f1, pi0, pi1 as stored
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(E):
-        assert lib.lat_upload_state(h, bufs, 0) == 0
-        assert lib.lat_evolve(h, 1) == 0
-        assert lib.lat_download_state(h, bufs, 0) == 0
-        assert lib.lat_get_scalars(h, out8) == 0
-    e2e_sec = time.perf_counter() - t0
-    te = torch.tensor([e2e_sec], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * n ** 3 * E / float(te.item())
+
+    def e2e_leg(run):
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        run()
+        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=f"cuda:{local}")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        return world * n ** 3 * E / float(te.item())
+
+    def call_by_call():
+        for _ in range(E):
+            assert lib.lat_upload_state(h, bufs, 0) == 0
+            assert lib.lat_evolve(h, 1) == 0
+            assert lib.lat_download_state(h, bufs, 0) == 0
+            assert lib.lat_get_scalars(h, out8) == 0
+
+    def host_resident():
+        st = lib.lat_evolve_host(h, bufs, E, 0, rows)
+        if st != 0:
+            raise RuntimeError(f"lat_evolve_host: status {st}")
+
+    e2e_value = e2e_leg(host_resident)
+    e2e_serial = e2e_leg(call_by_call)
     del host
 
     if rank != 0:
@@ -875,7 +891,11 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n ** 3 * esize,
                 "d2h_bytes_per_step": 4 * n ** 3 * esize + 8 * 8, "steps": E,
                 "per_step": "upload of the stored state from pinned host memory, one step, download of the "
-                            "evolved state and the scalars"},
+                            "evolved state and the scalars",
+                "call": "lat_evolve_host (copies in 16 z-chunks, one stream per direction: a step's download "
+                        "overlaps the next step's upload)",
+                "call_by_call": {"value": e2e_serial, "unit": UNIT,
+                                 "calls": "lat_upload_state, lat_evolve(1), lat_download_state, lat_get_scalars"}},
         "gpu_launches": args.steps * info["launches_per_step"],
         "tune": ({"chosen": {k: tuned[k] for k in ("variant", "ty", "zr", "depth", "blocks")},
                   "candidates": tuned["candidates"], "best_ms": tuned["best_ms"], "slowest_ms": tuned["slowest_ms"],

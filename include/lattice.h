@@ -196,6 +196,23 @@ lat_status lat_upload_state(lat_handle* h, const void* const src[4], int src_is_
  * pointer. */
 lat_status lat_download_state(lat_handle* h, void* const dst[4], int dst_is_device);
 
+/* Evolve a state held in host memory: n_steps times, upload host[0..3] (the
+ * four stored arrays, as lat_upload_state takes them), take one step (the sums
+ * of the uploaded fields, then the fused step of Sec. II.B) and download the
+ * evolved arrays back into host[0..3] (as lat_download_state gives them). The
+ * copies run in `chunks` z-ranges of planes (0: 16; at most 64 and N) on two
+ * streams of the call's own, one per direction: chunk c of a step's upload
+ * waits only for chunk c of the previous step's download (the same host
+ * bytes), so a step's download and the next step's upload share the host link
+ * in both directions. host[k] must be page-locked (LAT_EINVAL otherwise:
+ * cudaHostAlloc or cudaHostRegister memory) and must not be touched until the
+ * call returns. scalars_out (host, may be NULL): n_steps rows of the eight
+ * values of lat_get_scalars after each step. Queued after the work already on
+ * the handle's stream; waits for everything it queued before returning the
+ * first error, or a sticky device error. LAT_EINVAL for null pointers, n_steps
+ * < 0 or chunks out of range; LAT_ESTATE on a slab. */
+lat_status lat_evolve_host(lat_handle* h, void* const host[4], int64_t n_steps, int chunks, double* scalars_out);
+
 /* The homogeneous inflaton mode of split storage (lat_params.split = 1), in
  * program units: out[0] = its value P at the field time t + dt/2, out[1] = its
  * momentum at t. Zero on a lattice that stores phi whole. Synchronises. */

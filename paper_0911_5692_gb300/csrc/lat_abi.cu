@@ -690,6 +690,105 @@ lat_status lat_download_state(lat_handle* h, void* const dst[4], int dst_is_devi
     return LAT_OK;
 }
 
+lat_status lat_evolve_host(lat_handle* h, void* const host[4], int64_t n_steps, int chunks, double* scalars_out)
+{
+    if (!h || !host || n_steps < 0) return LAT_EINVAL;
+    if (h->slab) return LAT_ESTATE;
+    for (int k = 0; k < 4; k++) {
+        if (!host[k]) return LAT_EINVAL;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, host[k]) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return LAT_EINVAL;   // not page-locked: the copies could not run asynchronously
+        }
+    }
+    if (chunks == 0) chunks = 16;
+    if (chunks < 1 || chunks > 64) return LAT_EINVAL;
+    const int n = h->p.n;
+    chunks = std::min(chunks, n);
+    if (n_steps == 0) return LAT_OK;
+    DevScalars s0;
+    LAT_TRY(read_scalars(h, &s0));
+    if (s0.status != LAT_OK) return (lat_status)s0.status;
+    int par = (int)(s0.step & 1);
+    const size_t plane = (size_t)n * n * h->esize;
+
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t up_done = nullptr, comp_done = nullptr, down_ev[64] = {};
+    DevScalars* dlog = nullptr;
+    lat_status st = LAT_OK;
+    auto ok = [&](cudaError_t e) {
+        if (e != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
+        return st == LAT_OK;
+    };
+    ok(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking)) &&
+        ok(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking)) &&
+        ok(cudaEventCreateWithFlags(&up_done, cudaEventDisableTiming)) &&
+        ok(cudaEventCreateWithFlags(&comp_done, cudaEventDisableTiming));
+    for (int c = 0; c < chunks && st == LAT_OK; c++) ok(cudaEventCreateWithFlags(&down_ev[c], cudaEventDisableTiming));
+    if (st == LAT_OK && scalars_out && cudaMalloc((void**)&dlog, sizeof(DevScalars) * (size_t)n_steps) != cudaSuccess)
+        st = LAT_ENOMEM;
+    // the upload of the first step follows the work already queued on the handle
+    if (st == LAT_OK) ok(cudaEventRecord(comp_done, h->stream)) && ok(cudaStreamWaitEvent(up, comp_done, 0));
+    for (int64_t k = 0; k < n_steps && st == LAT_OK; k++) {
+        // up: chunk c of the four arrays into the current set, once the previous
+        // step's download of the same chunk (the same host bytes) has landed
+        for (int c = 0; c < chunks && st == LAT_OK; c++) {
+            const size_t z0 = (size_t)c * n / chunks, z1 = (size_t)(c + 1) * n / chunks;
+            if (k > 0) ok(cudaStreamWaitEvent(up, down_ev[c], 0));
+            for (int a = 0; a < 4 && st == LAT_OK; a++)
+                ok(cudaMemcpyAsync((char*)h->buf[4 * par + a] + z0 * plane, (const char*)host[a] + z0 * plane,
+                                   (z1 - z0) * plane, cudaMemcpyHostToDevice, up));
+        }
+        if (st != LAT_OK) break;
+        ok(cudaEventRecord(up_done, up)) && ok(cudaStreamWaitEvent(h->stream, up_done, 0));
+        if (st != LAT_OK) break;
+        // the step: the sums of the uploaded fields, then the fused step
+        h->dirty = true;
+        if ((st = ensure_prepared(h)) != LAT_OK || (st = launch_one_step(h)) != LAT_OK) break;
+        if (dlog) ok(cudaMemcpyAsync(dlog + k, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, h->stream));
+        ok(cudaEventRecord(comp_done, h->stream)) && ok(cudaStreamWaitEvent(down, comp_done, 0));
+        // down: the evolved set, chunk by chunk
+        for (int c = 0; c < chunks && st == LAT_OK; c++) {
+            const size_t z0 = (size_t)c * n / chunks, z1 = (size_t)(c + 1) * n / chunks;
+            for (int a = 0; a < 4 && st == LAT_OK; a++)
+                ok(cudaMemcpyAsync((char*)host[a] + z0 * plane, (const char*)h->buf[4 * (1 - par) + a] + z0 * plane,
+                                   (z1 - z0) * plane, cudaMemcpyDeviceToHost, down));
+            ok(cudaEventRecord(down_ev[c], down));
+        }
+        par ^= 1;
+    }
+    // the handle's stream continues after the last download (its next work may
+    // overwrite the set being read)
+    if (down) {
+        if (cudaStreamSynchronize(down) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
+    }
+    if (up && cudaStreamSynchronize(up) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
+    if (st == LAT_OK && dlog) {
+        std::vector<DevScalars> log((size_t)n_steps);
+        if (cudaMemcpy(log.data(), dlog, sizeof(DevScalars) * (size_t)n_steps, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = LAT_ECUDA;
+        for (int64_t k = 0; k < n_steps && st == LAT_OK; k++) {
+            const DevScalars& q = log[(size_t)k];
+            double* o = scalars_out + 8 * k;
+            o[0] = q.t; o[1] = q.a; o[2] = q.ad; o[3] = (double)q.step;
+            for (int j = 0; j < 4; j++) o[4 + j] = q.S[j];
+        }
+    }
+    cudaFree(dlog);
+    for (int c = 0; c < chunks; c++)
+        if (down_ev[c]) cudaEventDestroy(down_ev[c]);
+    if (up_done) cudaEventDestroy(up_done);
+    if (comp_done) cudaEventDestroy(comp_done);
+    if (up) cudaStreamDestroy(up);
+    if (down) cudaStreamDestroy(down);
+    if (st != LAT_OK) return st;
+    DevScalars s1;
+    LAT_TRY(read_scalars(h, &s1));
+    return (lat_status)s1.status;
+}
+
 lat_status lat_get_background(lat_handle* h, double out[2])
 {
     if (!h || !out) return LAT_EINVAL;

@@ -29,7 +29,8 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_slab_advance", "lat_energy_field", "lat_upload_state", "lat_get_hubble_length",
             "lat_set_hubble_length", "lat_download_state", "lat_get_background", "lat_set_background",
             "lat_recenter", "lat_tune", "lat_batch_tile_heights", "lat_slab_step_range", "lat_batch_shape",
-            "lat_batch_set_shape", "lat_slab_advance_local", "lat_copy_regions")
+            "lat_batch_set_shape", "lat_slab_advance_local", "lat_copy_regions",
+            "lat_evolve_host")
 
 
 class LatParams(C.Structure):
@@ -104,6 +105,7 @@ def load_library(build_if_missing: bool = True):
             L.lat_batch_set_shape.argtypes = [P, C.c_int, C.c_int, C.c_int]
             L.lat_slab_advance_local.argtypes = [C.POINTER(P), C.c_int, C.POINTER(P), C.c_int, C.c_int]
             L.lat_copy_regions.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int, C.c_uint64, P]
+            L.lat_evolve_host.argtypes = [P, C.POINTER(P), C.c_int64, C.c_int, dp]
             L.lat_checkpoint_bytes.argtypes = [P, C.POINTER(C.c_uint64)]
             L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
             L.lat_load_checkpoint.argtypes = [P, P, C.c_uint64]
@@ -354,6 +356,22 @@ class Lattice:
         counterpart of upload_state) and wait for the copies."""
         ptrs = self._four(f0, f1, pi0, pi1, "download_state")
         _check(self._L.lat_download_state(self._h, ptrs, 1 if f0.is_cuda else 0), "lat_download_state")
+
+    def evolve_host(self, f0, f1, pi0, pi1, n_steps: int, chunks: int = 0):
+        """Evolve a state held in four page-locked host tensors (the stored
+        arrays) by n_steps, the state crossing the host link every step
+        (lat_evolve_host: upload, step, download, the copies in z-chunks on one
+        stream per direction). The tensors hold the evolved state on return.
+        Returns the scalars after each step as a float64 array [n_steps, 8]
+        (t, a, a', step, four sums)."""
+        import numpy as np
+        if any(t.is_cuda for t in (f0, f1, pi0, pi1)):
+            raise ValueError("evolve_host takes four host tensors")
+        ptrs = self._four(f0, f1, pi0, pi1, "evolve_host")
+        out = np.zeros((max(0, int(n_steps)), 8), dtype=np.float64)
+        _check(self._L.lat_evolve_host(self._h, ptrs, int(n_steps), int(chunks),
+                                       out.ctypes.data_as(C.POINTER(C.c_double))), "lat_evolve_host")
+        return out
 
     def _four(self, f0, f1, pi0, pi1, what):
         ts = (f0, f1, pi0, pi1)
