@@ -383,6 +383,13 @@ void lat_destroy(lat_handle* h)
     if (h->sc) cudaFree(h->sc);
     if (h->partials) cudaFree(h->partials);
     if (h->means) cudaFree(h->means);
+    for (cudaEvent_t e : h->host_down_ev)
+        if (e) cudaEventDestroy(e);
+    if (h->host_up_done) cudaEventDestroy(h->host_up_done);
+    if (h->host_comp_done) cudaEventDestroy(h->host_comp_done);
+    if (h->host_up) cudaStreamDestroy(h->host_up);
+    if (h->host_down) cudaStreamDestroy(h->host_down);
+    if (h->host_log) cudaFree(h->host_log);
     delete h;
 }
 
@@ -713,21 +720,30 @@ lat_status lat_evolve_host(lat_handle* h, void* const host[4], int64_t n_steps, 
     int par = (int)(s0.step & 1);
     const size_t plane = (size_t)n * n * h->esize;
 
-    cudaStream_t up = nullptr, down = nullptr;
-    cudaEvent_t up_done = nullptr, comp_done = nullptr, down_ev[64] = {};
-    DevScalars* dlog = nullptr;
     lat_status st = LAT_OK;
     auto ok = [&](cudaError_t e) {
         if (e != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
         return st == LAT_OK;
     };
-    ok(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking)) &&
-        ok(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking)) &&
-        ok(cudaEventCreateWithFlags(&up_done, cudaEventDisableTiming)) &&
-        ok(cudaEventCreateWithFlags(&comp_done, cudaEventDisableTiming));
-    for (int c = 0; c < chunks && st == LAT_OK; c++) ok(cudaEventCreateWithFlags(&down_ev[c], cudaEventDisableTiming));
-    if (st == LAT_OK && scalars_out && cudaMalloc((void**)&dlog, sizeof(DevScalars) * (size_t)n_steps) != cudaSuccess)
-        st = LAT_ENOMEM;
+    // streams, events and the scalar log live with the handle (lat_destroy)
+    if (!h->host_up) ok(cudaStreamCreateWithFlags(&h->host_up, cudaStreamNonBlocking));
+    if (!h->host_down && st == LAT_OK) ok(cudaStreamCreateWithFlags(&h->host_down, cudaStreamNonBlocking));
+    if (!h->host_up_done && st == LAT_OK) ok(cudaEventCreateWithFlags(&h->host_up_done, cudaEventDisableTiming));
+    if (!h->host_comp_done && st == LAT_OK) ok(cudaEventCreateWithFlags(&h->host_comp_done, cudaEventDisableTiming));
+    for (int c = 0; c < chunks && st == LAT_OK; c++)
+        if (!h->host_down_ev[c]) ok(cudaEventCreateWithFlags(&h->host_down_ev[c], cudaEventDisableTiming));
+    if (st != LAT_OK) return st;
+    if (scalars_out && h->host_log_cap < (size_t)n_steps) {
+        if (h->host_log) cudaFree(h->host_log);
+        h->host_log = nullptr;
+        h->host_log_cap = 0;
+        if (cudaMalloc((void**)&h->host_log, sizeof(DevScalars) * (size_t)n_steps) != cudaSuccess) return LAT_ENOMEM;
+        h->host_log_cap = (size_t)n_steps;
+    }
+    cudaStream_t up = h->host_up, down = h->host_down;
+    cudaEvent_t up_done = h->host_up_done, comp_done = h->host_comp_done;
+    cudaEvent_t* down_ev = h->host_down_ev;
+    DevScalars* dlog = scalars_out ? h->host_log : nullptr;
     // the upload of the first step follows the work already queued on the handle
     if (st == LAT_OK) ok(cudaEventRecord(comp_done, h->stream)) && ok(cudaStreamWaitEvent(up, comp_done, 0));
     for (int64_t k = 0; k < n_steps && st == LAT_OK; k++) {
@@ -760,10 +776,8 @@ lat_status lat_evolve_host(lat_handle* h, void* const host[4], int64_t n_steps, 
     }
     // the handle's stream continues after the last download (its next work may
     // overwrite the set being read)
-    if (down) {
-        if (cudaStreamSynchronize(down) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
-    }
-    if (up && cudaStreamSynchronize(up) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
+    if (cudaStreamSynchronize(down) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
+    if (cudaStreamSynchronize(up) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess && st == LAT_OK) st = LAT_ECUDA;
     if (st == LAT_OK && dlog) {
         std::vector<DevScalars> log((size_t)n_steps);
@@ -776,13 +790,6 @@ lat_status lat_evolve_host(lat_handle* h, void* const host[4], int64_t n_steps, 
             for (int j = 0; j < 4; j++) o[4 + j] = q.S[j];
         }
     }
-    cudaFree(dlog);
-    for (int c = 0; c < chunks; c++)
-        if (down_ev[c]) cudaEventDestroy(down_ev[c]);
-    if (up_done) cudaEventDestroy(up_done);
-    if (comp_done) cudaEventDestroy(comp_done);
-    if (up) cudaStreamDestroy(up);
-    if (down) cudaStreamDestroy(down);
     if (st != LAT_OK) return st;
     DevScalars s1;
     LAT_TRY(read_scalars(h, &s1));

@@ -25,6 +25,12 @@ struct lat_handle {
     int graph_steps;
     bool slab;           // a z-slab of a larger lattice (lat_slab_create)
     int slab_z0, slab_nzl;
+    // lat_evolve_host: one copy stream per direction, its events and the
+    // device log of the scalars after each step (created on first use)
+    cudaStream_t host_up, host_down;
+    cudaEvent_t host_up_done, host_comp_done, host_down_ev[64];
+    lat::DevScalars* host_log;
+    size_t host_log_cap;   // entries
 };
 
 #define LAT_TRY(expr)                          \
