@@ -55,6 +55,11 @@ struct PK<float> {
     {
         *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(v[0].v, v[1].v);
     }
+    // a global store not read again soon: evict first from the caches
+    static __device__ __forceinline__ void st_stream(void* p, const P (&v)[2])
+    {
+        __stcs(reinterpret_cast<ulonglong2*>(p), make_ulonglong2(v[0].v, v[1].v));
+    }
 };
 template <>
 struct PK<double> {
@@ -68,6 +73,10 @@ struct PK<double> {
     static __device__ __forceinline__ void st(void* p, const P (&v)[1])
     {
         *reinterpret_cast<double2*>(p) = make_double2(v[0].x, v[0].y);
+    }
+    static __device__ __forceinline__ void st_stream(void* p, const P (&v)[1])
+    {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(v[0].x, v[0].y));
     }
 };
 

@@ -77,7 +77,10 @@ bool xw_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cf
     else blocks = std::min((long long)sms * occ, units) / nxt * nxt;
     const long long groups = blocks / nxt;
     cfg->ty = tyv;
-    cfg->zr = (int)(((long long)nyt * n + groups - 1) / groups);
+    // planes of the first group's first run (the z chunk of one tile when the
+    // groups march the tiles in step, lat_layout.cuh)
+    const Layout L0 = tile_layout(nyt, (int)groups, 0, n);
+    cfg->zr = std::min(L0.uend - L0.ubeg, L0.zspan);
     cfg->nzc = (int)((groups + nyt - 1) / nyt);
     cfg->depth = d;
     cfg->threads = threads;

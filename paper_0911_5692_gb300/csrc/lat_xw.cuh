@@ -32,6 +32,7 @@
 #include <algorithm>
 
 #include "lat_async.cuh"
+#include "lat_layout.cuh"
 #include "lat_kernels.h"
 #include "lat_pairs.cuh"
 #include "lat_site.cuh"
@@ -262,10 +263,11 @@ struct XW {
             if (!ahead) {
                 if (own) {
                     const uint32_t gi = zplane(C, k) * NN + C.rowg;
-                    PK<T>::st(C.op0 + gi, pn[0]);
-                    PK<T>::st(C.op1 + gi, pn[1]);
-                    PK<T>::st(C.of0 + gi, g[0]);
-                    PK<T>::st(C.of1 + gi, g[1]);
+                    // the new state is read again only by the next step
+                    PK<T>::st_stream(C.op0 + gi, pn[0]);
+                    PK<T>::st_stream(C.op1 + gi, pn[1]);
+                    PK<T>::st_stream(C.of0 + gi, g[0]);
+                    PK<T>::st_stream(C.of1 + gi, g[1]);
                 }
                 PK<T>::st(Gw + C.offP, g[0]);
                 PK<T>::st(Gw + FIELDP + C.offP, g[1]);
@@ -368,23 +370,23 @@ __global__ void __launch_bounds__(XW<T, N, TY, D, SLAB>::THREADS, 1)
     C.accg0 = C.accg1 = C.accvd = C.accvi = mk2(T(0), T(0));
 
     // groups of NXT blocks: the x tiles of one y tile, marching the same
-    // (y tile, z plane) units (an equal share of the (N / TY) * N units per group)
+    // (y tile, z plane) units
     const int ngroups = gridDim.x / NXT;
     const int grp = blockIdx.x / NXT, xt = blockIdx.x - grp * NXT;
+    const Layout Lw = tile_layout(N / TY, ngroups, grp, SLAB ? R.nz : N);
     const int x0 = xt * W;
     // edge columns (periodic in x)
     C.exl = (uint32_t)(x0 == 0 ? N - 1 : x0 - 1);
     C.exr = (uint32_t)(x0 + W == N ? 0 : x0 + W);
     C.exr1 = (uint32_t)(x0 + W + 1 >= N ? x0 + W + 1 - N : x0 + W + 1);
     C.zb = R.zb;
-    const long long U = (long long)(N / TY) * (SLAB ? R.nz : N);
-    long long u = (long long)grp * U / ngroups;
-    const long long uend = ((long long)grp + 1) * U / ngroups;
-    for (bool first = true; u < uend; first = false) {
-        const int zn = SLAB ? R.nz : N;   // planes per y tile
-        const int yt = (int)(u / zn);
-        C.z0 = (int)(u - (long long)yt * zn);
-        C.nz = (int)min((long long)(zn - C.z0), uend - u);
+    int u = Lw.ubeg;
+    for (bool first = true; u < Lw.uend; first = false) {
+        const int zt = Lw.zspan;   // planes per y tile in this group's unit space
+        const int yt = u / zt;
+        const int zrel = u - yt * zt;
+        C.z0 = Lw.zoff + zrel;
+        C.nz = min(zt - zrel, Lw.uend - u);
         u += C.nz;
         const int rrow = F::edge_warp(C) ? C.lane : C.rho;   // the row this thread stages
         C.rowg = (uint32_t)wrapn(yt * TY - 1 + (F::edge_warp(C) ? 0 : C.rho), N) * N + x0 + C.lane * VW;
