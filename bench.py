@@ -101,7 +101,7 @@ STEP_KERNEL_SOURCES = {
 }
 
 
-VARIANT_SOURCES = {(7, 4): ("lat_step_xt.cu",), (7, 5): ("lat_step_xw.cu", "lat_xw.cuh"),
+VARIANT_SOURCES = {(7, 4): ("lat_step_xt.cu",), (7, 5): ("lat_step_xw.cu", "lat_xw.cuh", "lat_layout.cuh"),
                    (27, 5): ("lat_step27w.cu",)}
 
 

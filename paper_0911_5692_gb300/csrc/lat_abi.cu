@@ -23,6 +23,25 @@ constexpr int kGraphChunk = 32;
 
 lat_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LAT_OK : LAT_ECUDA; }
 
+// The eight arrays of a state are read and written at the same site index in
+// the same instant. Where their starts are equal modulo 2 KB (arrays of a
+// power-of-two size allocated one after another are), those accesses meet in
+// the same memory partitions: the 512^3 FP32 step measured 0.79 ms with such
+// starts and 0.73 ms with starts that differ modulo 2 KB. Array k starts at
+// k * (its size rounded up to 2 KB + 128 bytes): offsets k * 128 mod 2048, all
+// eight distinct, 128-byte aligned. Of the staggers measured over several
+// placements of the allocation in physical memory, 128 bytes had the best
+// worst case at 512^3 (0.728-0.732 ms) and at 256^3 (0.108-0.109 ms); 256
+// and 1280 bytes were 3-6 % slower at 256^3.
+constexpr uint64_t kArrayAlign = 2048, kArrayStagger = 128;
+
+void buffer_layout(size_t array_bytes, uint64_t offsets[8], uint64_t* total)
+{
+    const uint64_t stride = (array_bytes + kArrayAlign - 1) / kArrayAlign * kArrayAlign + kArrayStagger;
+    for (int k = 0; k < 8; k++) offsets[k] = (uint64_t)k * stride;
+    *total = 7 * stride + array_bytes;
+}
+
 // Sec. II.B: rescaling for a dominant term cpl/beta phi^beta and the program-unit
 // potential V_pr = (A^2/B^2) a^(2r-2s) V(f / (A a^r)), which for
 // V = cpl/beta phi^beta + g2/2 phi^2 chi^2 is
@@ -295,16 +314,21 @@ lat_status create_common(const lat_params* params, void* stream, void* const buf
     h->stream = (cudaStream_t)stream;
     h->owns = bufs == nullptr;
     lat_status st = LAT_OK;
-    for (int i = 0; i < 8 && st == LAT_OK; i++) {
-        if (bufs) {
+    if (bufs) {
+        for (int i = 0; i < 8 && st == LAT_OK; i++) {
             h->buf[i] = bufs[i];
             if (!bufs[i] || ((uintptr_t)bufs[i] & 15u)) st = LAT_EINVAL;
-        } else if (cudaMalloc(&h->buf[i], h->nsites * h->esize) != cudaSuccess) {
-            h->buf[i] = nullptr;
+        }
+    } else {   // one allocation, the arrays at staggered offsets (buffer_layout)
+        uint64_t off[8], total = 0;
+        buffer_layout(h->nsites * h->esize, off, &total);
+        if (cudaMalloc(&h->arena, total) != cudaSuccess) {
+            h->arena = nullptr;
             st = LAT_ENOMEM;
-        } else if (cudaMemsetAsync(h->buf[i], 0, h->nsites * h->esize, h->stream) != cudaSuccess) {
+        } else if (cudaMemsetAsync(h->arena, 0, total, h->stream) != cudaSuccess) {
             st = LAT_ECUDA;
         }
+        for (int i = 0; i < 8 && st == LAT_OK; i++) h->buf[i] = (char*)h->arena + off[i];
     }
     h->partials_cap = partials_needed(params->n);
     if (st == LAT_OK && cudaMalloc((void**)&h->sc, sizeof(DevScalars)) != cudaSuccess) st = LAT_ENOMEM;
@@ -377,9 +401,7 @@ void lat_destroy(lat_handle* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     drop_graph(h);
-    if (h->owns)
-        for (int i = 0; i < 8; i++)
-            if (h->buf[i]) cudaFree(h->buf[i]);
+    if (h->owns && h->arena) cudaFree(h->arena);
     if (h->sc) cudaFree(h->sc);
     if (h->partials) cudaFree(h->partials);
     if (h->means) cudaFree(h->means);
@@ -694,6 +716,13 @@ lat_status lat_download_state(lat_handle* h, void* const dst[4], int dst_is_devi
         LAT_CUDA(cudaMemcpyAsync(dst[k], h->buf[4 * par + k], h->nsites * h->esize,
                                  dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     LAT_CUDA(cudaStreamSynchronize(h->stream));
+    return LAT_OK;
+}
+
+lat_status lat_buffer_layout(uint64_t array_bytes, uint64_t offsets[8], uint64_t* total_bytes)
+{
+    if (!offsets || !total_bytes || array_bytes == 0 || array_bytes > (1ull << 40)) return LAT_EINVAL;
+    buffer_layout((size_t)array_bytes, offsets, total_bytes);
     return LAT_OK;
 }
 

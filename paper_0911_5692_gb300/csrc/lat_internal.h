@@ -13,6 +13,7 @@ struct lat_handle {
     cudaStream_t stream;
     void* buf[8];        // f0, f1, p0, p1 of set 0, then of set 1
     bool owns;
+    void* arena;         // the one allocation the eight arrays are cut from (owned buffers)
     lat::DevScalars* sc;      // device
     double* partials;    // device, per-block sums
     size_t partials_cap; // doubles
@@ -45,6 +46,9 @@ struct lat_handle {
     } while (0)
 
 namespace lat {
+
+// Byte offsets of the eight state arrays in one allocation, and its size.
+void buffer_layout(size_t array_bytes, uint64_t offsets[8], uint64_t* total);
 
 template <typename T>
 Bufs<T> bufs_of(const lat_handle* h)

@@ -30,7 +30,7 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_set_hubble_length", "lat_download_state", "lat_get_background", "lat_set_background",
             "lat_recenter", "lat_tune", "lat_batch_tile_heights", "lat_slab_step_range", "lat_batch_shape",
             "lat_batch_set_shape", "lat_slab_advance_local", "lat_copy_regions",
-            "lat_evolve_host")
+            "lat_evolve_host", "lat_buffer_layout")
 
 
 class LatParams(C.Structure):
@@ -106,6 +106,7 @@ def load_library(build_if_missing: bool = True):
             L.lat_slab_advance_local.argtypes = [C.POINTER(P), C.c_int, C.POINTER(P), C.c_int, C.c_int]
             L.lat_copy_regions.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int, C.c_uint64, P]
             L.lat_evolve_host.argtypes = [P, C.POINTER(P), C.c_int64, C.c_int, dp]
+            L.lat_buffer_layout.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
             L.lat_checkpoint_bytes.argtypes = [P, C.POINTER(C.c_uint64)]
             L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
             L.lat_load_checkpoint.argtypes = [P, P, C.c_uint64]
@@ -172,6 +173,20 @@ def make_params(d: dict) -> LatParams:
     return p
 
 
+def staggered_buffers(lib, elems: int, dtype, device):
+    """Eight zeroed arrays of `elems` elements cut from one torch allocation at
+    the offsets lat_buffer_layout gives (starts distinct modulo 2 KB, so that
+    same-index accesses to the eight arrays spread over the memory partitions).
+    The views keep the allocation alive."""
+    import torch
+    esize = torch.empty((), dtype=dtype).element_size()
+    off = (C.c_uint64 * 8)()
+    total = C.c_uint64()
+    _check(lib.lat_buffer_layout(elems * esize, off, C.byref(total)), "lat_buffer_layout")
+    arena = torch.zeros((total.value + esize - 1) // esize, dtype=dtype, device=device)
+    return [arena[o // esize:o // esize + elems] for o in off]
+
+
 def _check(st: int, what: str):
     if st != LAT_OK:
         raise LatticeError(st, what)
@@ -206,8 +221,7 @@ class Lattice:
         sptr = C.c_void_p(self.stream.cuda_stream)
         self.buffers = None
         if torch_buffers:
-            n3 = self.n ** 3
-            self.buffers = [torch.zeros(n3, dtype=self.dtype, device=self.device) for _ in range(8)]
+            self.buffers = staggered_buffers(self._L, self.n ** 3, self.dtype, self.device)
             torch.cuda.synchronize(self.device)
             arr = (C.c_void_p * 8)(*[b.data_ptr() for b in self.buffers])
             _check(self._L.lat_create_with_buffers(C.byref(self._p), sptr, arr, C.byref(h)), "lat_create_with_buffers")

@@ -34,7 +34,7 @@ import ctypes as C
 
 import numpy as np
 
-from .lattice import LatticeError, _check, load_library, make_params
+from .lattice import LatticeError, _check, load_library, make_params, staggered_buffers
 
 # array index within a ping-pong set: f_phi, f_chi, pi_phi, pi_chi
 F0, F1, P0, P1 = 0, 1, 2, 3
@@ -97,7 +97,8 @@ class SlabGPU:
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         n = self.n
-        self.buffers = [torch.zeros((self.nzl + 3, n, n), dtype=self.dtype, device=self.device) for _ in range(8)]
+        self.buffers = [b.view(self.nzl + 3, n, n)
+                        for b in staggered_buffers(self._L, (self.nzl + 3) * n * n, self.dtype, self.device)]
         self.shares = torch.zeros(4, dtype=torch.float64, device=self.device)
         self.range_shares = torch.zeros((3, 4), dtype=torch.float64, device=self.device)
         torch.cuda.synchronize(self.device)

@@ -201,3 +201,28 @@ def test_static_sums_argument_errors(case):
     st = L.lat_field_sums_static(args["f_phi"], args["f_chi"], args["n"], args["precision"], args["model"],
                                  args["L"], args["out"], None)
     assert st == 1
+
+
+@pytest.mark.parametrize("array_bytes", [64 * 4, 36 ** 3 * 8, 256 ** 3 * 4, 512 ** 3 * 4, 1024 ** 3 * 4, 130 * 130 * 515 * 8])
+def test_buffer_layout(array_bytes):
+    """lat_buffer_layout (host only): eight non-overlapping arrays in one
+    allocation, 128-byte aligned, with starts that differ modulo 2 KB."""
+    L = pkg.load_library()
+    off = (C.c_uint64 * 8)()
+    total = C.c_uint64()
+    assert L.lat_buffer_layout(array_bytes, off, C.byref(total)) == 0
+    o = list(off)
+    assert o[0] == 0 and all(x % 128 == 0 for x in o)
+    assert all(o[k + 1] - o[k] >= array_bytes for k in range(7))
+    assert total.value >= o[7] + array_bytes
+    assert len({x % 2048 for x in o}) == 8
+
+
+def test_buffer_layout_argument_errors():
+    L = pkg.load_library()
+    off = (C.c_uint64 * 8)()
+    total = C.c_uint64()
+    assert L.lat_buffer_layout(0, off, C.byref(total)) == 1
+    assert L.lat_buffer_layout((1 << 40) + 1, off, C.byref(total)) == 1
+    assert L.lat_buffer_layout(4096, None, C.byref(total)) == 1
+    assert L.lat_buffer_layout(4096, off, None) == 1
