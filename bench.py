@@ -393,9 +393,9 @@ def measure_ensemble(local, steps=200):
 def measure_slabs(local, parts=4, steps=200):
     """One 512^3 FP32 lambda phi^4 lattice (phi stored whole) cut into `parts`
     z-slabs on one GPU, all on one stream: the halo planes of all slabs in one
-    copy launch, the shares added and every slab's scale factor advanced in one
-    launch; two steps (one per ping-pong parity) captured in a CUDA graph and
-    replayed. Both schedules
+    copy launch, the owned planes of all slabs in one step launch, the shares
+    added and every slab's scale factor advanced in one launch; two steps (one
+    per ping-pong parity) captured in a CUDA graph and replayed. Both schedules
     (plain: exchange, then each slab whole; overlap: each slab's interior,
     exchange, boundary pairs) against the same lattice stepped whole. On one GPU
     nothing overlaps; the line measures what the slab form costs in extra
@@ -453,7 +453,7 @@ def measure_slabs(local, parts=4, steps=200):
             assert np.isfinite(sl.scalars()["S"]).all()
         out["overlap" if overlap else "plain"] = {"ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": UNIT,
                                                   "over_whole": ms / whole_ms,
-                                                  "launches_per_step": parts * (3 if overlap else 1) + 2}
+                                                  "launches_per_step": (2 if overlap else 1) + 2}
         del g
     for sl in slabs:
         sl.close()
@@ -1071,9 +1071,10 @@ def run_slabs(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": own_bytes,
                 "d2h_bytes_per_step": own_bytes + 64 * len(slabs), "steps": E,
                 "per_step": "the owned planes of every slab up from pinned host memory, one step, back, and the scalars"},
-        # per step: the slab step ranges; one rank holding every slab adds one halo
-        # copy and one fused sum + scale-factor update, a rank of many one update
-        "gpu_launches": K * (len(slabs) * (3 if ev.overlap else 1) + (2 if world == 1 else 1)),
+        # per step: one rank holding every slab: one halo copy, one launch over all
+        # its slabs' planes, one fused sum + scale-factor update; a rank of many:
+        # its slab's three ranges and the scale-factor update
+        "gpu_launches": K * (3 if world == 1 else 4),
         "clocks": clocks.summary(),
         "slabs": {"count": parts, "schedule": "overlap" if ev.overlap else "plain",
                   "planes": [nzl for _, nzl in ranges]},

@@ -459,6 +459,22 @@ lat_status lat_slab_step_range(lat_handle* h, int zfirst, int zcount, double* su
  * Asynchronous. */
 lat_status lat_slab_advance(lat_handle* h, const double* sums_dev, int advance);
 
+/* Step (2) for slabs of one lattice held by one process (one GPU), in one
+ * launch on the stream of slabs[0]: `ranges` holds nranges triples (slab
+ * index into slabs[], first owned plane, plane count) of owned-plane ranges,
+ * each under the conditions of lat_slab_step_range (the halos it reads are in
+ * place), and sums_dev (device, 4 doubles) receives the sum of their shares.
+ * The slabs' scalar blocks must agree (they do when every step ends with
+ * lat_slab_advance_local); the coefficients are read from slabs[0]'s. The
+ * caller orders the other slabs' streams against slabs[0]'s. 1 <= nslabs <= 8,
+ * 1 <= nranges <= 16. LAT_EINVAL for null pointers, counts out of range, a
+ * range outside its slab or slabs of different lattices; LAT_ESTATE for a
+ * handle that is not a slab; LAT_EUNSUPPORTED for lattice sides without a
+ * compiled warp-tile slab kernel (N = 256 or 512 in FP32, 256 in FP64), where
+ * each range is stepped by lat_slab_step_range instead. Asynchronous. */
+lat_status lat_slab_step_ranges(lat_handle* const* slabs, int nslabs, const int32_t* ranges, int nranges,
+                                double* sums_dev);
+
 /* Steps (3) and (4) above for slabs of one lattice held by one process (one
  * GPU), in one launch on the stream of slabs[0]: the nshares share vectors
  * (device pointers, 4 doubles each; a slab's whole-step share or its range

@@ -79,14 +79,32 @@ bool march27_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfi
 template <typename T>
 cudaError_t launch_step27(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
                           cudaStream_t st);
-// the warp-wide x tiles (lat_xw.cuh) on a range of nz owned planes of a z-slab
+namespace xw {
+
+// What one launch of a SLAB instance steps: z ranges of one or several
+// z-slabs of one lattice held by this process, each slab with its own eight
+// arrays (f_phi, f_chi, pi_phi, pi_chi of set 0, then of set 1). Range r is
+// rn[r] planes stored from plane rzb[r] of slab rslab[r]'s arrays; the ranges
+// are laid end to end in z (range r from plane rz[r], nz planes in all) for
+// the block layout, and a run never crosses from one range into the next. The
+// sum of the ranges' shares of the volume averages goes to sums_out.
+constexpr int kMaxSlabRanges = 16, kMaxLocalSlabs = 8;
+struct SlabRun {
+    int nranges, nz;
+    double* sums_out;
+    int rz[kMaxSlabRanges], rn[kMaxSlabRanges], rzb[kMaxSlabRanges], rslab[kMaxSlabRanges];
+    void* buf[kMaxLocalSlabs][8];
+};
+
+} // namespace xw
+
+// the warp-wide x tiles (lat_xw.cuh) on z ranges of the owned planes of z-slabs
 // (N = 256, 512 FP32 with two planes in flight and 256 FP64 with one compiled):
-// cfg->nzl = nz; the launch takes the stored plane of the range's first plane
-// and writes the range's shares
+// nz = the ranges' planes in all; the launch writes the ranges' summed shares
 bool slab_xw_config(int n, int elem_bytes, int nz, MarchConfig* cfg);
 template <typename T>
-cudaError_t launch_slab_xw(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
-                           int zbase, double* sums_out, cudaStream_t st);
+cudaError_t launch_slab_xw(const xw::SlabRun& R, const Model& M, DevScalars* sc, double* partials,
+                           const MarchConfig& cfg, cudaStream_t st);
 // the 27-point Laplacian over x tiles one warp wide with compile-time N, ty,
 // depth and an edge warp (whole periodic lattices; the compiled geometries only)
 bool s27w_config(int n, int elem_bytes, int ty, int zr, int depth, MarchConfig* cfg);

@@ -204,10 +204,17 @@ lat_status lat_slab_step_range(lat_handle* h, int zfirst, int zcount, double* su
     MarchConfig cfg;
     cudaError_t e;
     if (slab_xw_config(n, (int)h->esize, zcount, &cfg) && (size_t)cfg.blocks * kSums <= h->partials_cap) {
-        e = h->prec == 32 ? launch_slab_xw<float>(bufs_of<float>(h), h->M, h->sc, h->partials, cfg, 1 + zfirst,
-                                                  sums_dev, h->stream)
-                          : launch_slab_xw<double>(bufs_of<double>(h), h->M, h->sc, h->partials, cfg, 1 + zfirst,
-                                                   sums_dev, h->stream);
+        xw::SlabRun R = {};
+        R.nranges = 1;
+        R.nz = zcount;
+        R.sums_out = sums_dev;
+        R.rz[0] = 0;
+        R.rn[0] = zcount;
+        R.rzb[0] = 1 + zfirst;
+        R.rslab[0] = 0;
+        for (int i = 0; i < 8; i++) R.buf[0][i] = h->buf[i];
+        e = h->prec == 32 ? launch_slab_xw<float>(R, h->M, h->sc, h->partials, cfg, h->stream)
+                          : launch_slab_xw<double>(R, h->M, h->sc, h->partials, cfg, h->stream);
     } else {
         if (!march_slab_config(n, (int)h->esize, zcount, &cfg) || (size_t)cfg.blocks * kSums > h->partials_cap)
             return LAT_EUNSUPPORTED;
@@ -217,6 +224,45 @@ lat_status lat_slab_step_range(lat_handle* h, int zfirst, int zcount, double* su
                           : launch_step_march<double>(bufs_of<double>(h), h->M, h->sc, h->partials, cfg, h->stream,
                                                       sums_dev);
     }
+    return cuda_status(e);
+}
+
+lat_status lat_slab_step_ranges(lat_handle* const* slabs, int nslabs, const int32_t* ranges, int nranges,
+                                double* sums_dev)
+{
+    if (!slabs || !ranges || !sums_dev || nslabs < 1 || nslabs > xw::kMaxLocalSlabs || nranges < 1 ||
+        nranges > xw::kMaxSlabRanges)
+        return LAT_EINVAL;
+    lat_handle* h0 = slabs[0];
+    for (int i = 0; i < nslabs; i++) {
+        const lat_handle* h = slabs[i];
+        if (!h) return LAT_EINVAL;
+        if (!h->slab) return LAT_ESTATE;
+        if (h->p.n != h0->p.n || h->prec != h0->prec || h->p.model != h0->p.model ||
+            h->p.expansion != h0->p.expansion || h->p.dt != h0->p.dt || h->p.L != h0->p.L)
+            return LAT_EINVAL;   // not slabs of one lattice
+    }
+    xw::SlabRun R = {};
+    R.nranges = nranges;
+    R.sums_out = sums_dev;
+    int total = 0;
+    for (int r = 0; r < nranges; r++) {
+        const int s = ranges[3 * r], zfirst = ranges[3 * r + 1], zcount = ranges[3 * r + 2];
+        if (s < 0 || s >= nslabs || zfirst < 0 || zcount < 1 || zfirst + zcount > slabs[s]->slab_nzl) return LAT_EINVAL;
+        R.rz[r] = total;
+        R.rn[r] = zcount;
+        R.rzb[r] = 1 + zfirst;
+        R.rslab[r] = s;
+        total += zcount;
+    }
+    R.nz = total;
+    for (int s = 0; s < nslabs; s++)
+        for (int i = 0; i < 8; i++) R.buf[s][i] = slabs[s]->buf[i];
+    MarchConfig cfg;
+    if (!slab_xw_config(h0->M.n, (int)h0->esize, total, &cfg) || (size_t)cfg.blocks * kSums > h0->partials_cap)
+        return LAT_EUNSUPPORTED;
+    const cudaError_t e = h0->prec == 32 ? launch_slab_xw<float>(R, h0->M, h0->sc, h0->partials, cfg, h0->stream)
+                                         : launch_slab_xw<double>(R, h0->M, h0->sc, h0->partials, cfg, h0->stream);
     return cuda_status(e);
 }
 

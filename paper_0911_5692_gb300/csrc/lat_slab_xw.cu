@@ -69,21 +69,22 @@ bool slab_xw_config(int n, int elem_bytes, int nz, MarchConfig* cfg)
 }
 
 template <typename T>
-cudaError_t launch_slab_xw(const Bufs<T>& b, const Model& M, DevScalars* sc, double* partials, const MarchConfig& cfg,
-                           int zbase, double* sums_out, cudaStream_t st)
+cudaError_t launch_slab_xw(const xw::SlabRun& R, const Model& M, DevScalars* sc, double* partials,
+                           const MarchConfig& cfg, cudaStream_t st)
 {
     size_t smem = 0;
     int d = 1;
     const void* fn = slab_xw_fn<T>(M.n, &smem, &d);
-    if (!fn || !sums_out || d != cfg.depth) return cudaErrorInvalidValue;
-    xw::SlabRun R{cfg.nzl, zbase, sums_out};
-    void* args[] = {(void*)&b, (void*)&M, (void*)&sc, (void*)&partials, (void*)&R};
+    if (!fn || !R.sums_out || d != cfg.depth || R.nranges < 1 || R.nranges > xw::kMaxSlabRanges)
+        return cudaErrorInvalidValue;
+    const Bufs<T> unused{};
+    void* args[] = {(void*)&unused, (void*)&M, (void*)&sc, (void*)&partials, (void*)&R};
     return cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
 }
 
-template cudaError_t launch_slab_xw<float>(const Bufs<float>&, const Model&, DevScalars*, double*, const MarchConfig&,
-                                           int, double*, cudaStream_t);
-template cudaError_t launch_slab_xw<double>(const Bufs<double>&, const Model&, DevScalars*, double*,
-                                            const MarchConfig&, int, double*, cudaStream_t);
+template cudaError_t launch_slab_xw<float>(const xw::SlabRun&, const Model&, DevScalars*, double*, const MarchConfig&,
+                                           cudaStream_t);
+template cudaError_t launch_slab_xw<double>(const xw::SlabRun&, const Model&, DevScalars*, double*,
+                                            const MarchConfig&, cudaStream_t);
 
 } // namespace lat

@@ -43,13 +43,6 @@ namespace xw {
 
 enum { kOwn, kAhead, kStage, kEdge };   // warp roles
 
-// The owned z range of a slab (SLAB instances): nz planes, the first at stored
-// plane zb; the shares of the averages go to sums_out.
-struct SlabRun {
-    int nz, zb;
-    double* sums_out;
-};
-
 template <int D>
 struct RingXW {
     static constexpr int RF = D == 1 ? 4 : 6;          // field plane slots (>= D + 3)
@@ -356,14 +349,16 @@ __global__ void __launch_bounds__(XW<T, N, TY, D, SLAB>::THREADS, 1)
     C.offF = (uint32_t)C.rho * W + C.lane * VW;
     C.offP = (uint32_t)(C.rho >= 1 && C.rho <= TY + 1 ? C.rho - 1 : 0) * W + C.lane * VW;
     const bool par = (sc->step & 1) != 0;
-    C.f0 = par ? B.f[1][0] : B.f[0][0];
-    C.f1 = par ? B.f[1][1] : B.f[0][1];
-    C.p0 = par ? B.p[1][0] : B.p[0][0];
-    C.p1 = par ? B.p[1][1] : B.p[0][1];
-    C.of0 = par ? B.f[0][0] : B.f[1][0];
-    C.of1 = par ? B.f[0][1] : B.f[1][1];
-    C.op0 = par ? B.p[0][0] : B.p[1][0];
-    C.op1 = par ? B.p[0][1] : B.p[1][1];
+    if constexpr (!SLAB) {
+        C.f0 = par ? B.f[1][0] : B.f[0][0];
+        C.f1 = par ? B.f[1][1] : B.f[0][1];
+        C.p0 = par ? B.p[1][0] : B.p[0][0];
+        C.p1 = par ? B.p[1][1] : B.p[0][1];
+        C.of0 = par ? B.f[0][0] : B.f[1][0];
+        C.of1 = par ? B.f[0][1] : B.f[1][1];
+        C.op0 = par ? B.p[0][0] : B.p[1][0];
+        C.op1 = par ? B.p[0][1] : B.p[1][1];
+    }
     C.K = site_coefs<T>(sc, M.beta);
     C.dtcl2 = mk2(C.K.dtcl, C.K.dtcl);
     C.dtcf2 = mk2(C.K.dtcf, C.K.dtcf);
@@ -379,7 +374,7 @@ __global__ void __launch_bounds__(XW<T, N, TY, D, SLAB>::THREADS, 1)
     C.exl = (uint32_t)(x0 == 0 ? N - 1 : x0 - 1);
     C.exr = (uint32_t)(x0 + W == N ? 0 : x0 + W);
     C.exr1 = (uint32_t)(x0 + W + 1 >= N ? x0 + W + 1 - N : x0 + W + 1);
-    C.zb = R.zb;
+    C.zb = 0;
     int u = Lw.ubeg;
     for (bool first = true; u < Lw.uend; first = false) {
         const int zt = Lw.zspan;   // planes per y tile in this group's unit space
@@ -387,6 +382,24 @@ __global__ void __launch_bounds__(XW<T, N, TY, D, SLAB>::THREADS, 1)
         const int zrel = u - yt * zt;
         C.z0 = Lw.zoff + zrel;
         C.nz = min(zt - zrel, Lw.uend - u);
+        if constexpr (SLAB) {
+            // the range holding plane z0 of the end-to-end z space: the run stays
+            // within it, on its slab's arrays, from its stored planes
+            int r = 0;
+            while (r + 1 < R.nranges && C.z0 >= R.rz[r + 1]) r++;
+            C.z0 -= R.rz[r];
+            C.nz = min(C.nz, R.rn[r] - C.z0);
+            C.zb = R.rzb[r];
+            void* const* bs = R.buf[R.rslab[r]];
+            C.f0 = (const T*)bs[par ? 4 : 0];
+            C.f1 = (const T*)bs[par ? 5 : 1];
+            C.p0 = (const T*)bs[par ? 6 : 2];
+            C.p1 = (const T*)bs[par ? 7 : 3];
+            C.of0 = (T*)bs[par ? 0 : 4];
+            C.of1 = (T*)bs[par ? 1 : 5];
+            C.op0 = (T*)bs[par ? 2 : 6];
+            C.op1 = (T*)bs[par ? 3 : 7];
+        }
         u += C.nz;
         const int rrow = F::edge_warp(C) ? C.lane : C.rho;   // the row this thread stages
         C.rowg = (uint32_t)wrapn(yt * TY - 1 + (F::edge_warp(C) ? 0 : C.rho), N) * N + x0 + C.lane * VW;

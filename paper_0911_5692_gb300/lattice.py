@@ -30,7 +30,7 @@ EXPORTED = ("lat_create", "lat_create_with_buffers", "lat_init_fields", "lat_evo
             "lat_set_hubble_length", "lat_download_state", "lat_get_background", "lat_set_background",
             "lat_recenter", "lat_tune", "lat_batch_tile_heights", "lat_slab_step_range", "lat_batch_shape",
             "lat_batch_set_shape", "lat_slab_advance_local", "lat_copy_regions",
-            "lat_evolve_host", "lat_buffer_layout")
+            "lat_evolve_host", "lat_buffer_layout", "lat_slab_step_ranges")
 
 
 class LatParams(C.Structure):
@@ -107,6 +107,7 @@ def load_library(build_if_missing: bool = True):
             L.lat_copy_regions.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int, C.c_uint64, P]
             L.lat_evolve_host.argtypes = [P, C.POINTER(P), C.c_int64, C.c_int, dp]
             L.lat_buffer_layout.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+            L.lat_slab_step_ranges.argtypes = [C.POINTER(P), C.c_int, C.POINTER(C.c_int32), C.c_int, P]
             L.lat_checkpoint_bytes.argtypes = [P, C.POINTER(C.c_uint64)]
             L.lat_save_checkpoint.argtypes = [P, P, C.c_uint64]
             L.lat_load_checkpoint.argtypes = [P, P, C.c_uint64]

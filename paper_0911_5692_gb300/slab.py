@@ -236,6 +236,43 @@ class LocalComm:
             s.stream.wait_stream(slabs[(i + 1) % P].stream)
             s.stream.wait_stream(slabs[(i - 1) % P].stream)
 
+    def step_ranges(self, slabs, ranges, slot: int = 0):
+        """Step owned-plane ranges (slab index, first plane, planes) of the slabs
+        in one launch (lat_slab_step_ranges) on the first slab's stream; returns
+        the device tensors holding the ranges' shares (one tensor; for lattice
+        sides without a compiled warp-tile slab kernel, one per range, stepped
+        by lat_slab_step_range). `slot` (0 or 1) keeps the shares of two calls
+        of one step apart."""
+        import torch
+        L = load_library()
+        s0 = slabs[0]
+        buf = getattr(self, "_shares", None)
+        if buf is None or buf.device != s0.shares.device:
+            buf = self._shares = torch.zeros((2, 1 + 16, 4), dtype=torch.float64, device=s0.shares.device)
+        for s in slabs[1:]:
+            s0.stream.wait_stream(s.stream)
+        hs = (C.c_void_p * len(slabs))(*[s._h.value for s in slabs])
+        flat = [int(v) for r in ranges for v in r]
+        arr = (C.c_int32 * len(flat))(*flat)
+        st = L.lat_slab_step_ranges(hs, len(slabs), arr, len(ranges), C.c_void_p(buf[slot, 0].data_ptr()))
+        if st == 7:                      # LAT_EUNSUPPORTED: one launch per range
+            if len(ranges) > 16:
+                raise ValueError("at most 16 ranges")
+            out = []
+            for j, (i, zf, zc) in enumerate(ranges):
+                sl = slabs[i]
+                sl.stream.wait_stream(s0.stream)
+                _check(L.lat_slab_step_range(sl._h, int(zf), int(zc), C.c_void_p(buf[slot, 1 + j].data_ptr())),
+                       "lat_slab_step_range")
+                s0.stream.wait_stream(sl.stream)
+                out.append(buf[slot, 1 + j])
+        else:
+            _check(st, "lat_slab_step_ranges")
+            out = [buf[slot, 0]]
+        for s in slabs[1:]:
+            s.stream.wait_stream(s0.stream)
+        return out
+
     def reduce_advance(self, slabs, shares, advance: bool):
         """Add the shares (device tensors of four doubles, in the order given)
         and advance the scalars of every slab with the total, in one launch on
@@ -369,23 +406,34 @@ class SlabEvolution:
 
     def step(self, n_steps: int = 1):
         fused = hasattr(self.comm, "reduce_advance")
+        together = getattr(self.comm, "step_ranges", None)   # every slab of the process in one launch
         for _ in range(int(n_steps)):
             if self.overlap:
                 pending = self.comm.post_exchange(self.slabs)
-                for s in self.slabs:
-                    zf, zc = overlap_ranges(s.nzl)[0]
-                    s.local_step_range(zf, zc, 0)
-                self.comm.finish_exchange(self.slabs, pending)
-                for s in self.slabs:
-                    for slot, (zf, zc) in enumerate(overlap_ranges(s.nzl)[1:], start=1):
-                        s.local_step_range(zf, zc, slot)
-                if fused:    # the three range shares of every slab go to the fused sum as they are
-                    shares = [s.range_shares[k] for s in self.slabs for k in range(3)]
+                if together is not None:
+                    shares = together(self.slabs, [(i, *overlap_ranges(s.nzl)[0]) for i, s in enumerate(self.slabs)], 0)
                 else:
-                    shares = [s.range_total() for s in self.slabs]
+                    for s in self.slabs:
+                        zf, zc = overlap_ranges(s.nzl)[0]
+                        s.local_step_range(zf, zc, 0)
+                self.comm.finish_exchange(self.slabs, pending)
+                if together is not None:
+                    shares = shares + together(self.slabs, [(i, zf, zc) for i, s in enumerate(self.slabs)
+                                                            for zf, zc in overlap_ranges(s.nzl)[1:]], 1)
+                else:
+                    for s in self.slabs:
+                        for slot, (zf, zc) in enumerate(overlap_ranges(s.nzl)[1:], start=1):
+                            s.local_step_range(zf, zc, slot)
+                    if fused:    # the three range shares of every slab go to the fused sum as they are
+                        shares = [s.range_shares[k] for s in self.slabs for k in range(3)]
+                    else:
+                        shares = [s.range_total() for s in self.slabs]
             else:
                 self.comm.exchange(self.slabs)
-                shares = [s.local_step() for s in self.slabs]
+                if together is not None:
+                    shares = together(self.slabs, [(i, 0, s.nzl) for i, s in enumerate(self.slabs)], 0)
+                else:
+                    shares = [s.local_step() for s in self.slabs]
             self._advance(shares, True)
 
     def gather(self):

@@ -143,6 +143,7 @@ def test_null_arguments():
     assert L.lat_slab_advance_local(None, 1, None, 1, 1) == 1
     assert L.lat_copy_regions(None, None, 1, 16, None) == 1
     assert L.lat_evolve_host(None, None, 1, 0, None) == 1
+    assert L.lat_slab_step_ranges(None, 1, None, 1, None) == 1
     L.lat_destroy(None)
 
 

@@ -234,3 +234,69 @@ def test_fused_advance_refusals():
     g = Lattice(p)
     whole = (C.c_void_p * 1)(g._h.value)
     assert L.lat_slab_advance_local(whole, 1, sh, 1, 1) == 8        # not a slab: LAT_ESTATE
+
+
+def _ranges_arg(ranges):
+    flat = [int(v) for r in ranges for v in r]
+    return (C.c_int32 * max(1, len(flat)))(*flat)
+
+
+@pytest.mark.parametrize("n,prec,parts", [(256, 32, 4), (512, 32, 3), (256, 64, 2)])
+def test_step_ranges_one_launch_matches_per_slab(n, prec, parts):
+    """lat_slab_step_ranges over every slab's owned planes (and over the
+    interior and boundary ranges of the overlapped schedule) writes the fields
+    the per-slab launches write, bit for bit, and shares that add to theirs."""
+    from paper_0911_5692_gb300.lattice import load_library
+    L = load_library()
+    p, st = _case("lphi4", n, prec)
+    a = _slabs(p, st, parts)
+    b = _slabs(p, st, parts)
+    comm = LocalComm()
+    for slabs in (a, b):
+        SlabEvolution(slabs, comm).prepare()
+    comm.exchange(a)
+    comm.exchange(b)
+    # a: one launch; b: one launch per slab
+    got = comm.step_ranges(a, [(i, 0, s.nzl) for i, s in enumerate(a)], 0)
+    assert len(got) == 1
+    ref = [s.local_step() for s in b]          # queued on each slab's own stream
+    torch.cuda.synchronize()
+    total = sum(r.clone() for r in ref)
+    assert torch.allclose(got[0], total, rtol=1e-12 if prec == 64 else 1e-5, atol=0)
+    for x, y in zip(a, b):
+        for k in range(8):
+            assert torch.equal(x.buffers[k][1:x.nzl + 1], y.buffers[k][1:y.nzl + 1])
+    # the overlapped schedule's two launches step the same planes
+    c = _slabs(p, st, parts)
+    SlabEvolution(c, comm).prepare()
+    comm.exchange(c)
+    comm.step_ranges(c, [(i, *overlap_ranges(s.nzl)[0]) for i, s in enumerate(c)], 0)
+    comm.step_ranges(c, [(i, zf, zc) for i, s in enumerate(c) for zf, zc in overlap_ranges(s.nzl)[1:]], 1)
+    torch.cuda.synchronize()
+    for x, y in zip(c, b):
+        for k in range(8):
+            assert torch.equal(x.buffers[k][1:x.nzl + 1], y.buffers[k][1:y.nzl + 1])
+
+
+def test_step_ranges_refusals():
+    from paper_0911_5692_gb300.lattice import load_library
+    L = load_library()
+    p, st = _case("lphi4", 256, 32)
+    slabs = _slabs(p, st, 2)
+    hs = (C.c_void_p * 2)(slabs[0]._h.value, slabs[1]._h.value)
+    out = C.c_void_p(slabs[0].shares.data_ptr())
+    nzl = slabs[0].nzl
+    for ranges, nr in (([(2, 0, 4)], 1), ([(0, -1, 4)], 1), ([(0, 0, nzl + 1)], 1), ([(0, 0, 0)], 1), ([(0, 0, 4)], 0),
+                       ([(0, 0, 4)] * 17, 17)):
+        assert L.lat_slab_step_ranges(hs, 2, _ranges_arg(ranges), nr, out) == 1
+    assert L.lat_slab_step_ranges(hs, 9, _ranges_arg([(0, 0, 4)]), 1, out) == 1
+    q, st2 = _case("lphi4", 128, 32)
+    (other,) = _slabs(q, st2, 1)
+    mixed = (C.c_void_p * 2)(slabs[0]._h.value, other._h.value)
+    assert L.lat_slab_step_ranges(mixed, 2, _ranges_arg([(0, 0, 4)]), 1, out) == 1
+    g = Lattice(p)
+    whole = (C.c_void_p * 1)(g._h.value)
+    assert L.lat_slab_step_ranges(whole, 1, _ranges_arg([(0, 0, 4)]), 1, out) == 8
+    (small,) = _slabs(*_case("lphi4", 64, 32), 1)   # no compiled warp-tile slab kernel for N = 64
+    one = (C.c_void_p * 1)(small._h.value)
+    assert L.lat_slab_step_ranges(one, 1, _ranges_arg([(0, 0, 8)]), 1, C.c_void_p(small.shares.data_ptr())) == 7
