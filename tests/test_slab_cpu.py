@@ -287,3 +287,85 @@ def test_distributed_slabs_match_single_domain_oracle(tmp_path, world, model, ov
         assert abs(sc["a"] - o.scalars()["a"]) <= 1e-14 * abs(o.scalars()["a"])
         for k in range(4):
             assert abs(sc["S"][k] - o.scalars()["S"][k]) <= 1e-12 * abs(o.scalars()["S"][k])
+
+
+class NumpyLocalComm:
+    """The one-process communicator's interface (slabs held together, as
+    LocalComm offers it for slabs on one GPU) over NumpySlab: halos by copies,
+    every slab's ranges stepped by one call (step_ranges, one summed share) and
+    one call that adds the shares and advances every slab (reduce_advance).
+    post_exchange leaves the receiving halos NaN until finish_exchange, so a
+    range stepped before the exchange has landed and reading a halo fails."""
+
+    def _plan(self, slabs):
+        P = len(slabs)
+        out = []
+        for i, s in enumerate(slabs):
+            above, below = slabs[(i + 1) % P], slabs[(i - 1) % P]
+            for msg in halo_plan():
+                nb = above if msg[0] == "down" else below
+                out.append((s.plane(msg[2], recv_plane(msg, s.nzl)), nb.plane(msg[2], send_plane(msg, nb.nzl)).clone()))
+        return out
+
+    def exchange(self, slabs):
+        for dst, src in self._plan(slabs):
+            dst.copy_(src)
+
+    def post_exchange(self, slabs):
+        plan = self._plan(slabs)
+        for dst, _ in plan:
+            dst.fill_(float("nan"))
+        return plan
+
+    def finish_exchange(self, slabs, pending):
+        for dst, src in pending:
+            dst.copy_(src)
+
+    def allreduce(self, slabs, shares):
+        total = sum(shares)
+        return [total] * len(slabs)
+
+    def step_ranges(self, slabs, ranges, slot=0):
+        used = {}
+        total = torch.zeros(4, dtype=torch.float64)
+        for i, zf, zc in ranges:
+            j = used.get(i, 0)
+            used[i] = j + 1
+            slabs[i].local_step_range(zf, zc, j)
+            total += slabs[i].range_shares[j]
+        return [total]
+
+    def reduce_advance(self, slabs, shares, advance):
+        total = sum(shares)
+        for s in slabs:
+            s.advance(total, advance)
+
+
+@pytest.mark.parametrize("parts,model,overlap", [(1, "lphi4", False), (3, "m2phi2", False), (4, "lphi4", False),
+                                                 (2, "lphi4", True), (3, "m2phi2", True)])
+def test_slabs_of_one_process_stepped_together(parts, model, overlap):
+    """SlabEvolution with a communicator that steps every slab's ranges in one
+    call and advances every slab in one call (the path slabs on one GPU take):
+    the plain schedule (all owned planes at once) and the overlapped one (the
+    interiors while the halos are NaN, then the boundary pairs) against the
+    single-domain oracle."""
+    steps = 6
+    p, st = _case(model)
+    slabs = []
+    for z0, nzl in slab_ranges(N, parts):
+        s = NumpySlab(p, z0, nzl)
+        s.load(*st, **SCAL)
+        slabs.append(s)
+    ev = SlabEvolution(slabs, NumpyLocalComm(), overlap=overlap)
+    assert ev.overlap == (overlap and min(s.nzl for s in slabs) >= 5)
+    ev.prepare()
+    ev.step(steps)
+    got = [np.concatenate([s.owned()[k] for s in slabs], axis=0) for k in range(4)]
+    o = Oracle(p)
+    o.set_state(*st, **SCAL)
+    o.step(steps)
+    for a, b in zip(got, o.get_state()):
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    for s in slabs:
+        assert s.sc["step"] == steps and s.step_count == steps
+        assert abs(s.sc["a"] - o.scalars()["a"]) <= 1e-14 * abs(o.scalars()["a"])
