@@ -22,6 +22,10 @@
 // look-ahead plane nzl - 2, whose z neighbours are owned), so they can run while
 // the halos are still in flight; planes 0, 1 and nzl - 2, nzl - 1 follow once
 // the halos are in, and are the planes the neighbours need for the next step.
+// Slabs of one lattice held by one process (one GPU) can take step 2 in one
+// launch over ranges of all of them (lat_slab_step_ranges), copy their halos in
+// one launch (lat_copy_regions) and take steps 3 and 4 in one launch
+// (lat_slab_advance_local).
 #include <algorithm>
 #include <cstdint>
 

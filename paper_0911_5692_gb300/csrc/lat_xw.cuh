@@ -22,11 +22,16 @@
 // The NXT = N / W x tiles of a y tile are taken by NXT consecutive blocks that
 // march the same (y tile, z plane) units at the same time, so the scalars one
 // tile reads from its neighbours' columns lie in memory lines the neighbouring
-// blocks are reading too (L2 hits).
+// blocks are reading too (L2 hits); and neighbouring y tiles are marched at the
+// same planes at the same time (lat_layout.cuh), so that a tile's halo rows,
+// its neighbours' owned rows, are L2 hits too. The new state is written with
+// streaming stores: only the next step reads it.
 //
-// SLAB instances step a range of a z-slab's owned planes (stored planes with
-// their halos, no wrap in z) and write the range's shares of the volume
-// averages instead of advancing the scalars (lat_slab.cu).
+// SLAB instances step z ranges of the owned planes of one or several z-slabs
+// (stored planes with their halos, no wrap in z; each slab with its own
+// arrays), laid end to end in z for the block layout, and write the ranges'
+// summed shares of the volume averages instead of advancing the scalars
+// (lat_slab.cu).
 #pragma once
 
 #include <algorithm>
