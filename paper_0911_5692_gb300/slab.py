@@ -189,6 +189,25 @@ class SlabGPU:
         self.stream.synchronize()
 
 
+def plan_range_launches(ranges, max_slabs: int = 8, max_ranges: int = 16):
+    """Cut (slab index, first plane, planes) ranges into launches of at most
+    `max_slabs` slabs and `max_ranges` ranges each (the limits of
+    lat_slab_step_ranges): a list of (slab indices of the launch, its ranges
+    with slab indices local to the launch), covering every range once, in order
+    within each launch."""
+    launches, cur_slabs, cur_ranges = [], [], []
+    for i, zf, zc in ranges:
+        if i not in cur_slabs and len(cur_slabs) == max_slabs or len(cur_ranges) == max_ranges:
+            launches.append((cur_slabs, cur_ranges))
+            cur_slabs, cur_ranges = [], []
+        if i not in cur_slabs:
+            cur_slabs.append(i)
+        cur_ranges.append((cur_slabs.index(i), zf, zc))
+    if cur_ranges:
+        launches.append((cur_slabs, cur_ranges))
+    return launches
+
+
 class LocalComm:
     """All slabs of the lattice in this process (SlabGPU on one GPU): halos by
     device copies (lat_copy_regions: every plane of the exchange in one launch
@@ -238,37 +257,40 @@ class LocalComm:
 
     def step_ranges(self, slabs, ranges, slot: int = 0):
         """Step owned-plane ranges (slab index, first plane, planes) of the slabs
-        in one launch (lat_slab_step_ranges) on the first slab's stream; returns
-        the device tensors holding the ranges' shares (one tensor; for lattice
-        sides without a compiled warp-tile slab kernel, one per range, stepped
-        by lat_slab_step_range). `slot` (0 or 1) keeps the shares of two calls
-        of one step apart."""
+        on the first slab's stream, in as few launches of lat_slab_step_ranges
+        as its limits allow (plan_range_launches: 8 slabs, 16 ranges a launch);
+        returns the device tensors holding the shares, one per launch (for
+        lattice sides without a compiled warp-tile slab kernel one per range,
+        stepped by lat_slab_step_range). `slot` (0 or 1) keeps the shares of two
+        calls of one step apart."""
         import torch
         L = load_library()
         s0 = slabs[0]
+        launches = plan_range_launches(ranges)
+        need = max(len(launches), len(ranges))
         buf = getattr(self, "_shares", None)
-        if buf is None or buf.device != s0.shares.device:
-            buf = self._shares = torch.zeros((2, 1 + 16, 4), dtype=torch.float64, device=s0.shares.device)
+        if buf is None or buf.device != s0.shares.device or buf.shape[1] < need:
+            buf = self._shares = torch.zeros((2, need, 4), dtype=torch.float64, device=s0.shares.device)
         for s in slabs[1:]:
             s0.stream.wait_stream(s.stream)
-        hs = (C.c_void_p * len(slabs))(*[s._h.value for s in slabs])
-        flat = [int(v) for r in ranges for v in r]
-        arr = (C.c_int32 * len(flat))(*flat)
-        st = L.lat_slab_step_ranges(hs, len(slabs), arr, len(ranges), C.c_void_p(buf[slot, 0].data_ptr()))
-        if st == 7:                      # LAT_EUNSUPPORTED: one launch per range
-            if len(ranges) > 16:
-                raise ValueError("at most 16 ranges")
-            out = []
-            for j, (i, zf, zc) in enumerate(ranges):
-                sl = slabs[i]
-                sl.stream.wait_stream(s0.stream)
-                _check(L.lat_slab_step_range(sl._h, int(zf), int(zc), C.c_void_p(buf[slot, 1 + j].data_ptr())),
-                       "lat_slab_step_range")
-                s0.stream.wait_stream(sl.stream)
-                out.append(buf[slot, 1 + j])
-        else:
+        out = []
+        for j, (ids, local) in enumerate(launches):
+            hs = (C.c_void_p * len(ids))(*[slabs[i]._h.value for i in ids])
+            flat = [int(v) for r in local for v in r]
+            arr = (C.c_int32 * len(flat))(*flat)
+            st = L.lat_slab_step_ranges(hs, len(ids), arr, len(local), C.c_void_p(buf[slot, j].data_ptr()))
+            if st == 7:                  # LAT_EUNSUPPORTED: one launch per range
+                out = []
+                for q, (i, zf, zc) in enumerate(ranges):
+                    sl = slabs[i]
+                    sl.stream.wait_stream(s0.stream)
+                    _check(L.lat_slab_step_range(sl._h, int(zf), int(zc), C.c_void_p(buf[slot, q].data_ptr())),
+                           "lat_slab_step_range")
+                    s0.stream.wait_stream(sl.stream)
+                    out.append(buf[slot, q])
+                break
             _check(st, "lat_slab_step_ranges")
-            out = [buf[slot, 0]]
+            out.append(buf[slot, j])
         for s in slabs[1:]:
             s.stream.wait_stream(s0.stream)
         return out
@@ -443,5 +465,5 @@ class SlabEvolution:
         return tuple(np.concatenate([p[k] for p in parts], axis=0) for k in range(4))
 
 
-__all__ = ["slab_ranges", "halo_plan", "send_plane", "recv_plane", "overlap_ranges", "SlabGPU", "LocalComm", "DistComm",
-           "SlabEvolution", "LatticeError"]
+__all__ = ["slab_ranges", "halo_plan", "send_plane", "recv_plane", "overlap_ranges", "plan_range_launches", "SlabGPU",
+           "LocalComm", "DistComm", "SlabEvolution", "LatticeError"]

@@ -64,10 +64,13 @@ def test_slabs_match_single_lattice_fp64(parts):
 
 
 @pytest.mark.parametrize("overlap", [False, True])
-@pytest.mark.parametrize("model,n,parts", [("m2phi2", 64, 3), ("lphi4", 128, 4), ("lphi4", 256, 2), ("m2phi2", 256, 3)])
+@pytest.mark.parametrize("model,n,parts", [("m2phi2", 64, 3), ("lphi4", 128, 4), ("lphi4", 256, 2), ("m2phi2", 256, 3),
+                                          ("lphi4", 256, 10)])
 def test_slabs_fp32_match_oracle(model, n, parts, overlap):
     """N = 256 takes the compiled warp-tile slab instance, the others the generic
-    plane ring; overlap: interior planes first, then the boundary pairs."""
+    plane ring; overlap: interior planes first, then the boundary pairs. Ten
+    slabs need more than one launch per schedule step (at most 8 slabs and 16
+    ranges a launch)."""
     steps = 4
     p, st = _case(model, n, 32)
     slabs = _slabs(p, st, parts)

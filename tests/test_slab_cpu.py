@@ -369,3 +369,27 @@ def test_slabs_of_one_process_stepped_together(parts, model, overlap):
     for s in slabs:
         assert s.sc["step"] == steps and s.step_count == steps
         assert abs(s.sc["a"] - o.scalars()["a"]) <= 1e-14 * abs(o.scalars()["a"])
+
+
+def test_plan_range_launches():
+    """Ranges of many slabs cut into launches within lat_slab_step_ranges'
+    limits (8 slabs, 16 ranges): every range once, in order, each launch's
+    local slab indices mapping back to the slabs of its ranges."""
+    from paper_0911_5692_gb300.slab import plan_range_launches
+    cases = [
+        [(i, 0, 10) for i in range(4)],                                  # one launch
+        [(i, 0, 10) for i in range(20)],                                 # 20 slabs: 8 + 8 + 4
+        [(i, zf, 2) for i in range(12) for zf in (0, 8)],                # two ranges per slab
+        [(i % 3, 2 * i, 1) for i in range(40)],                          # 3 slabs, 40 ranges
+    ]
+    for ranges in cases:
+        launches = plan_range_launches(ranges)
+        back = []
+        for ids, local in launches:
+            assert 1 <= len(ids) <= 8 and 1 <= len(local) <= 16
+            assert len(set(ids)) == len(ids)
+            assert {r[0] for r in local} == set(range(len(ids)))
+            back += [(ids[k], zf, zc) for k, zf, zc in local]
+        assert back == ranges
+    assert len(plan_range_launches([(i, 0, 10) for i in range(20)])) == 3
+    assert plan_range_launches([]) == []
