@@ -196,7 +196,9 @@ lat_status lat_upload_state(lat_handle* h, const void* const src[4], int src_is_
  * pointer. */
 lat_status lat_download_state(lat_handle* h, void* const dst[4], int dst_is_device);
 
-/* Where to put the eight state arrays (f_phi, f_chi, pi_phi, pi_chi of set 0,
+/* No counterpart in the paper: where the state that the step of Sec. II.B
+ * reads and writes lies in memory. Where to put the eight state arrays
+ * (f_phi, f_chi, pi_phi, pi_chi of set 0,
  * then of set 1; array_bytes each) in one allocation of *total_bytes bytes:
  * offsets[k] (host, bytes from its start, multiples of 128; the allocation
  * itself 16-byte aligned at least). The library lays out the buffers it
@@ -459,7 +461,9 @@ lat_status lat_slab_step_range(lat_handle* h, int zfirst, int zcount, double* su
  * Asynchronous. */
 lat_status lat_slab_advance(lat_handle* h, const double* sums_dev, int advance);
 
-/* Step (2) for slabs of one lattice held by one process (one GPU), in one
+/* Step (2) -- the fused step of Sec. II.B, eq. evo with eq. scalar-evo, and the
+ * sums of the new fields for eq. scale -- for slabs of one lattice held by one
+ * process (one GPU), in one
  * launch on the stream of slabs[0]: `ranges` holds nranges triples (slab
  * index into slabs[], first owned plane, plane count) of owned-plane ranges,
  * each under the conditions of lat_slab_step_range (the halos it reads are in
@@ -475,7 +479,8 @@ lat_status lat_slab_advance(lat_handle* h, const double* sums_dev, int advance);
 lat_status lat_slab_step_ranges(lat_handle* const* slabs, int nslabs, const int32_t* ranges, int nranges,
                                 double* sums_dev);
 
-/* Steps (3) and (4) above for slabs of one lattice held by one process (one
+/* Steps (3) and (4) above (the volume averages of Sec. II.B and the
+ * scale-factor update of eq. scale) for slabs of one lattice held by one process (one
  * GPU), in one launch on the stream of slabs[0]: the nshares share vectors
  * (device pointers, 4 doubles each; a slab's whole-step share or its range
  * shares) are added in the order given, and every slab's scalars advance
@@ -488,7 +493,9 @@ lat_status lat_slab_step_ranges(lat_handle* const* slabs, int nslabs, const int3
 lat_status lat_slab_advance_local(lat_handle* const* slabs, int nslabs, const double* const* shares, int nshares,
                                   int advance);
 
-/* Copy `count` device regions of `bytes` bytes each (src[i] to dst[i]; the
+/* No counterpart in the paper, whose program runs one lattice on one GPU
+ * (Sec. II.C; several GPUs are its future work, Sec. IV). Copy `count` device
+ * regions of `bytes` bytes each (src[i] to dst[i]; the
  * regions must not overlap) in one launch per 64 regions on cuda_stream: the
  * halo exchange of slabs that one process holds. Every pointer and `bytes`
  * must be multiples of 16 bytes (a plane of an even-sided lattice is), else
@@ -537,11 +544,13 @@ lat_status lat_batch_tune(lat_batch* b, int steps);
  * ty (host, one int32 per member, in creation order). */
 lat_status lat_batch_tile_heights(lat_batch* b, int32_t* ty);
 
-/* The launch shape in use: out (host) = threads per block, tile-height cap,
- * prefetch depth, blocks. */
+/* The launch shape in use (the block shape the paper picks by trial, Sec. II.C
+ * and Sec. III, here chosen by lat_batch_tune): out (host) = threads per
+ * block, tile-height cap, prefetch depth, blocks. */
 lat_status lat_batch_shape(lat_batch* b, int64_t out[4]);
 
-/* Step with the given shape from now on: threads per block (32 .. 1024),
+/* Step with the given shape from now on (the paper fixes its block shape by
+ * hand, Sec. II.C): threads per block (32 .. 1024),
  * tile-height cap (1 .. 32) and prefetch depth (1 or 2); the values are those
  * lat_batch_tune sweeps. LAT_EINVAL out of those ranges, LAT_EUNSUPPORTED if
  * some member's tile does not fit the block or the shared memory. Waits for the
